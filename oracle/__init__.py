@@ -1,0 +1,291 @@
+"""FP64 CPU oracle of the electrostatic PIC cycle (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
+this package.  It wraps the plain C reference in `pic_oracle.c` with ctypes and
+composes the cycle in the order of the paper's worked example (Sec. 3.1,
+Listing 1): load -> field update -> initial half push, then per step: velocity
+push (gather + Boris) -> position update with periodic wrap -> field update.
+It shares no code with the CUDA path.
+
+Parity status per function (details in the repository's design notes):
+  locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris, move,
+  sort_key, counting_sort, kinetic, field_energy, momentum: pinned by the
+  tests under tests/test_oracle_*.py.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build())
+        _declare(_lib)
+    return _lib
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int)
+
+
+def _declare(L):
+    i, i64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.orc_locate.argtypes = [i, _I32, _D, i64, _D, _I64, _D]
+    L.orc_deposit.argtypes = [i, _I32, _D, i64, _D, d, _D]
+    L.orc_gather.argtypes = [i, _I32, _D, i64, _D, _D, _D]
+    L.orc_neg_laplacian.argtypes = [i, _I32, _D, _D, _D]
+    L.orc_poisson_pcg.argtypes = [i, _I32, _D, _D, _D, d, i, _I32, _D]
+    L.orc_poisson_pcg.restype = i
+    L.orc_efield.argtypes = [i, _I32, _D, _D, _D]
+    L.orc_boris.argtypes = [i, i, i64, _D, _D, _D, _D, d, d]
+    L.orc_move.argtypes = [i, _I32, _D, i, i64, _D, _D, d]
+    L.orc_sort_key.argtypes = [i, _I32, _I32, i64, _I64, _I64]
+    L.orc_counting_sort.argtypes = [i64, _I64, i64, _I64]
+    L.orc_counting_sort.restype = i
+    L.orc_kinetic.argtypes = [i, i64, _D, d]
+    L.orc_kinetic.restype = d
+    L.orc_field_energy.argtypes = [i, _I32, _D, _D]
+    L.orc_field_energy.restype = d
+    L.orc_momentum.argtypes = [i, i64, _D, d, _D]
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _i64p(a: np.ndarray):
+    assert a.dtype == np.int64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_I64)
+
+
+def _n3(n: Sequence[int]):
+    t = list(n) + [1] * (3 - len(n))
+    return (ctypes.c_int * 3)(*t[:3])
+
+
+def _dx3(dx: Sequence[float]):
+    t = list(dx) + [1.0] * (3 - len(dx))
+    return (ctypes.c_double * 3)(*t[:3])
+
+
+def _cells(ndim, n):
+    return int(np.prod(list(n)[:ndim]))
+
+
+# ---- thin functional wrappers -------------------------------------------------------------
+
+def locate(ndim, n, dx, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    npart = x.shape[0]
+    cell = np.empty(npart, np.int64)
+    off = np.empty((npart, ndim), np.float64)
+    lib().orc_locate(ndim, _n3(n), _dx3(dx), npart, _dp(x), _i64p(cell), _dp(off))
+    return cell, off
+
+
+def deposit(ndim, n, dx, x, qw):
+    """Electron charge density on the nodes (Sec. 2.2 B_Scatter)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    rho = np.empty(_cells(ndim, n), np.float64)
+    lib().orc_deposit(ndim, _n3(n), _dx3(dx), x.shape[0], _dp(x), float(qw), _dp(rho))
+    return rho
+
+
+def gather(ndim, n, dx, x, E):
+    """Grid field at the particles (Sec. 2.2 C_Gather)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    Ep = np.empty((x.shape[0], ndim), np.float64)
+    lib().orc_gather(ndim, _n3(n), _dx3(dx), x.shape[0], _dp(x), _dp(E), _dp(Ep))
+    return Ep
+
+
+def neg_laplacian(ndim, n, dx, u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    lib().orc_neg_laplacian(ndim, _n3(n), _dx3(dx), _dp(u), _dp(out))
+    return out
+
+
+def poisson(ndim, n, dx, rho, rtol=1e-12, maxit=200000):
+    """-lap(phi) = rho - mean(rho), zero-mean phi (Sec. 2.2 D_Poisson)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    phi = np.empty_like(rho)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = lib().orc_poisson_pcg(ndim, _n3(n), _dx3(dx), _dp(rho), _dp(phi), rtol, maxit,
+                               ctypes.byref(it), ctypes.byref(rel))
+    if st != 0:
+        raise RuntimeError(f"oracle PCG did not converge: {it.value} iterations, "
+                           f"relative residual {rel.value:.3e}")
+    return phi, it.value, rel.value
+
+
+def efield(ndim, n, dx, phi):
+    """E = -grad(phi), centred differences (module D06, Sec. 3.1)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    E = np.empty(ndim * phi.size, np.float64)
+    lib().orc_efield(ndim, _n3(n), _dx3(dx), _dp(phi), _dp(E))
+    return E
+
+
+def boris(ndim, v, Ep, E0, B0, qm, h):
+    """In-place Boris velocity advance by step h (Sec. 2.2 A_Pusher)."""
+    assert v.dtype == np.float64 and v.flags.c_contiguous
+    npart, nv = v.shape
+    Epp = _dp(np.ascontiguousarray(Ep, dtype=np.float64)) if Ep is not None else None
+    e0 = (ctypes.c_double * 3)(*(list(E0) + [0.0] * 3)[:3])
+    b0 = (ctypes.c_double * 3)(*(list(B0) + [0.0] * 3)[:3])
+    keep = Ep  # noqa: F841  (keep the array alive during the call)
+    lib().orc_boris(ndim, nv, npart, _dp(v), Epp, e0, b0, float(qm), float(h))
+    return v
+
+
+def move(ndim, n, dx, x, v, dt):
+    """In-place x += v dt with periodic wrap (application code, Sec. 3.1)."""
+    assert x.dtype == np.float64 and x.flags.c_contiguous
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    lib().orc_move(ndim, _n3(n), _dx3(dx), v.shape[1], x.shape[0], _dp(x), _dp(v), float(dt))
+    return x
+
+
+def sort_key(ndim, n, brick, cell):
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    key = np.empty_like(cell)
+    b = (ctypes.c_int * 3)(*(list(brick) + [1, 1, 1])[:3])
+    lib().orc_sort_key(ndim, _n3(n), b, cell.size, _i64p(cell), _i64p(key))
+    return key
+
+
+def num_keys(ndim, n, brick):
+    nk = 1
+    for a in range(ndim):
+        nb = -(-n[a] // brick[a])
+        nk *= nb * brick[a]
+    return nk
+
+
+def counting_sort(key, nkeys):
+    key = np.ascontiguousarray(key, dtype=np.int64)
+    perm = np.empty_like(key)
+    if lib().orc_counting_sort(key.size, _i64p(key), int(nkeys), _i64p(perm)) != 0:
+        raise ValueError("sort key out of range")
+    return perm
+
+
+def kinetic(v, mw):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return lib().orc_kinetic(v.shape[1], v.shape[0], _dp(v), float(mw))
+
+
+def field_energy(ndim, n, dx, E):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    return lib().orc_field_energy(ndim, _n3(n), _dx3(dx), _dp(E))
+
+
+def momentum(v, mw):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros(3, np.float64)
+    lib().orc_momentum(v.shape[1], v.shape[0], _dp(v), float(mw), _dp(out))
+    return out[: v.shape[1]]
+
+
+# ---- the cycle ----------------------------------------------------------------------------
+
+class Simulation:
+    """The electrostatic PIC cycle of Listing 1 (Sec. 3.1) in FP64.
+
+    `rho_background=None` neutralises the loaded electrons exactly:
+    rho_ion = -q w N_p / V.
+    """
+
+    def __init__(self, ndim, n, dx, dt, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0),
+                 E0=(0, 0, 0), rho_background: Optional[float] = None, rtol=1e-12,
+                 maxit=200000):
+        self.ndim = ndim
+        self.n = tuple(list(n)[:3]) + (1,) * (3 - len(n))
+        self.dx = tuple(list(dx)[:3]) + (1.0,) * (3 - len(dx))
+        self.dt, self.q, self.m, self.w = float(dt), float(q), float(m), float(weight)
+        self.B0 = tuple(B0) + (0.0,) * (3 - len(B0))
+        self.E0 = tuple(E0) + (0.0,) * (3 - len(E0))
+        self.rho_background = rho_background
+        self.rtol, self.maxit = rtol, maxit
+        self.cells = _cells(ndim, self.n)
+        self.dV = float(np.prod(self.dx[:ndim]))
+        self.V = self.dV * self.cells
+        self.t = 0.0
+        self.step_count = 0
+        self.cg_iters = 0
+        self.ke = 0.0
+
+    # field update: B01 -> D02 -> D05/D06
+    def update_field(self):
+        npart = self.x.shape[0]
+        self.rho_e = deposit(self.ndim, self.n, self.dx, self.x, self.q * self.w)
+        bg = (-self.q * self.w * npart / self.V if self.rho_background is None
+              else float(self.rho_background))
+        self.rho = self.rho_e + bg
+        self.phi, self.cg_iters, self.cg_res = poisson(self.ndim, self.n, self.dx, self.rho,
+                                                       self.rtol, self.maxit)
+        self.E = efield(self.ndim, self.n, self.dx, self.phi)
+
+    def load(self, x, v, half_push=True):
+        self.x = np.array(x, dtype=np.float64, order="C")
+        self.v = np.array(v, dtype=np.float64, order="C")
+        self.update_field()
+        if half_push:
+            Ep = gather(self.ndim, self.n, self.dx, self.x, self.E)
+            v0 = self.v.copy()
+            boris(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, -0.5 * self.dt)
+            self.ke = kinetic(v0, self.m * self.w)
+        return self
+
+    def push(self):
+        """Gather (C01) + Boris (A01) by one full step; returns the
+        time-centred kinetic energy (mean of the two half-step energies)."""
+        Ep = gather(self.ndim, self.n, self.dx, self.x, self.E)
+        ke_old = kinetic(self.v, self.m * self.w)
+        boris(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, self.dt)
+        self.ke = 0.5 * (ke_old + kinetic(self.v, self.m * self.w))
+        return self.ke
+
+    def move(self):
+        move(self.ndim, self.n, self.dx, self.x, self.v, self.dt)
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            self.push()
+            self.move()
+            self.update_field()
+            self.t += self.dt
+            self.step_count += 1
+        return self
+
+    def field_energy(self):
+        return field_energy(self.ndim, self.n, self.dx, self.E)
+
+    def momentum(self):
+        return momentum(self.v, self.m * self.w)
+
+    def cells_offsets(self):
+        return locate(self.ndim, self.n, self.dx, self.x)
+
+    def sort(self, brick):
+        cell, _ = self.cells_offsets()
+        key = sort_key(self.ndim, self.n, brick, cell)
+        perm = counting_sort(key, num_keys(self.ndim, self.n, brick))
+        self.x = np.ascontiguousarray(self.x[perm])
+        self.v = np.ascontiguousarray(self.v[perm])
+        return perm

@@ -1,0 +1,366 @@
+/*
+ * pic_oracle.c -- plain, slow, FP64 CPU reference of the electrostatic
+ * particle-in-cell cycle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg are the only callers.  It shares no code,
+ * header, table or constant with the CUDA path and must never be used as a
+ * fallback for it.
+ *
+ * What it follows (AlgoPlasma paper):
+ *   Sec. 2.2  module roles: B_Scatter deposits charge on the grid, C_Gather
+ *             interpolates the grid field to particles, D_Poisson solves the
+ *             Poisson equation and evaluates E, A_Pusher advances velocities
+ *             with the Boris scheme.
+ *   Sec. 3.1  the worked example's cycle (Listing 1): load, update the field
+ *             (deposit -> Poisson -> potential -> E), initial half push of the
+ *             velocities, then per step: full velocity push (gather + Boris),
+ *             position update with periodic boundaries, field update.
+ * Where the paper is silent, the readings are: node-centred periodic grid,
+ * linear (cloud-in-cell) weights shared by deposit and gather, second-order
+ * (2d+1)-point Laplacian, centred-difference E, Jacobi-preconditioned CG,
+ * backward half push with step -dt/2, x == L wraps to 0.
+ *
+ * Units are Debye units with eps0 = 1: the field equation is
+ *   -lap(phi) = rho,   E = -grad(phi).
+ *
+ * Layout: grid arrays are flat with axis 0 fastest,
+ *   node(j0, j1, j2) = j0 + n0 * (j1 + n1 * j2);
+ * vector fields are stored component-major (E[a * cells + node]).
+ * Particle positions x are row-major (np x ndim), velocities (np x nv).
+ * Every loop is a plain sequential loop; nothing is blocked or reordered.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int64_t cells_of(int ndim, const int *n)
+{
+    int64_t c = 1;
+    for (int a = 0; a < ndim; ++a) c *= n[a];
+    return c;
+}
+
+static int64_t node_index(const int *n, const int *j)
+{
+    return (int64_t)j[0] + (int64_t)n[0] * ((int64_t)j[1] + (int64_t)n[1] * (int64_t)j[2]);
+}
+
+/* Cell and in-cell offset of one position: c = floor(x / dx), f = x / dx - c.
+ * A position that rounds onto x / dx == n (x at L) belongs to node 0. */
+static void locate_one(int ndim, const int *n, const double *dx, const double *x,
+                       int *c, double *f)
+{
+    for (int a = 0; a < 3; ++a) { c[a] = 0; f[a] = 0.0; }
+    for (int a = 0; a < ndim; ++a) {
+        double u = x[a] / dx[a];
+        double fl = floor(u);
+        int ca = (int)fl;
+        double fa = u - fl;
+        if (ca >= n[a] || ca < 0) { ca = 0; fa = 0.0; }  /* x rounding onto L is x = 0 */
+        c[a] = ca;
+        f[a] = fa;
+    }
+}
+
+/* Linear cell index and offsets of every particle. */
+void orc_locate(int ndim, const int *n, const double *dx, int64_t np, const double *x,
+                int64_t *cell, double *off)
+{
+    for (int64_t p = 0; p < np; ++p) {
+        int c[3];
+        double f[3];
+        locate_one(ndim, n, dx, x + p * ndim, c, f);
+        cell[p] = node_index(n, c);
+        for (int a = 0; a < ndim; ++a) off[p * ndim + a] = f[a];
+    }
+}
+
+/* Cloud-in-cell weight of corner s (bit a of s selects the upper node on
+ * axis a): product over axes of (1 - f_a) or f_a. */
+static double cic_weight(int ndim, const double *f, int s)
+{
+    double w = 1.0;
+    for (int a = 0; a < ndim; ++a) w *= ((s >> a) & 1) ? f[a] : (1.0 - f[a]);
+    return w;
+}
+
+static int64_t corner_node(int ndim, const int *n, const int *c, int s)
+{
+    int j[3] = {0, 0, 0};
+    for (int a = 0; a < ndim; ++a) {
+        j[a] = c[a] + ((s >> a) & 1);
+        if (j[a] == n[a]) j[a] = 0;
+    }
+    return node_index(n, j);
+}
+
+/* B_Scatter (Sec. 2.2; module B01 in Sec. 3.1): electron charge density on
+ * the nodes, rho_e[j] = (q w / dV) * sum_p W_j(x_p), with W the CIC weights.
+ * rho is overwritten. */
+void orc_deposit(int ndim, const int *n, const double *dx, int64_t np, const double *x,
+                 double qw, double *rho)
+{
+    int64_t cells = cells_of(ndim, n);
+    double dV = 1.0;
+    for (int a = 0; a < ndim; ++a) dV *= dx[a];
+    double scale = qw / dV;
+    memset(rho, 0, (size_t)cells * sizeof(double));
+    for (int64_t p = 0; p < np; ++p) {
+        int c[3];
+        double f[3];
+        locate_one(ndim, n, dx, x + p * ndim, c, f);
+        for (int s = 0; s < (1 << ndim); ++s)
+            rho[corner_node(ndim, n, c, s)] += scale * cic_weight(ndim, f, s);
+    }
+}
+
+/* C_Gather (Sec. 2.2; module C01 in Sec. 3.1): field at each particle,
+ * Ep[p][a] = sum_j W_j(x_p) E_a[j], with the same weights as the deposit. */
+void orc_gather(int ndim, const int *n, const double *dx, int64_t np, const double *x,
+                const double *E, double *Ep)
+{
+    int64_t cells = cells_of(ndim, n);
+    for (int64_t p = 0; p < np; ++p) {
+        int c[3];
+        double f[3];
+        locate_one(ndim, n, dx, x + p * ndim, c, f);
+        for (int a = 0; a < ndim; ++a) Ep[p * ndim + a] = 0.0;
+        for (int s = 0; s < (1 << ndim); ++s) {
+            int64_t j = corner_node(ndim, n, c, s);
+            double w = cic_weight(ndim, f, s);
+            for (int a = 0; a < ndim; ++a) Ep[p * ndim + a] += w * E[a * cells + j];
+        }
+    }
+}
+
+/* out = -lap_h(u), the (2d+1)-point periodic Laplacian with sign flipped so
+ * that the operator is positive semi-definite. */
+void orc_neg_laplacian(int ndim, const int *n, const double *dx, const double *u, double *out)
+{
+    int n3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) n3[a] = n[a];
+    for (int j2 = 0; j2 < n3[2]; ++j2)
+        for (int j1 = 0; j1 < n3[1]; ++j1)
+            for (int j0 = 0; j0 < n3[0]; ++j0) {
+                int j[3] = {j0, j1, j2};
+                int64_t id = node_index(n3, j);
+                double acc = 0.0;
+                for (int a = 0; a < ndim; ++a) {
+                    int jp[3] = {j0, j1, j2}, jm[3] = {j0, j1, j2};
+                    jp[a] = (j[a] + 1) % n3[a];
+                    jm[a] = (j[a] - 1 + n3[a]) % n3[a];
+                    acc += (2.0 * u[id] - u[node_index(n3, jp)] - u[node_index(n3, jm)]) /
+                           (dx[a] * dx[a]);
+                }
+                out[id] = acc;
+            }
+}
+
+static double dot(int64_t m, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* D_Poisson (Sec. 2.2; module D02 in Sec. 3.1): solve -lap_h(phi) = rho on the
+ * periodic grid.  The singular periodic problem is made consistent by
+ * removing the mean of rho, and phi is returned with zero mean.  Jacobi-
+ * preconditioned conjugate gradients from phi = 0, stopping when
+ * ||r||_2 <= rtol ||b||_2 or after maxit iterations.  Returns 0 on
+ * convergence, 1 otherwise; iterations and final relative residual through
+ * the pointers. */
+int orc_poisson_pcg(int ndim, const int *n, const double *dx, const double *rho, double *phi,
+                    double rtol, int maxit, int *iters, double *relres)
+{
+    int64_t m = cells_of(ndim, n);
+    double *b = malloc((size_t)m * sizeof(double));
+    double *r = malloc((size_t)m * sizeof(double));
+    double *z = malloc((size_t)m * sizeof(double));
+    double *p = malloc((size_t)m * sizeof(double));
+    double *q = malloc((size_t)m * sizeof(double));
+    double mean = 0.0;
+    for (int64_t i = 0; i < m; ++i) mean += rho[i];
+    mean /= (double)m;
+    for (int64_t i = 0; i < m; ++i) b[i] = rho[i] - mean;
+
+    double diag = 0.0;  /* Jacobi preconditioner: the operator's (constant) diagonal */
+    for (int a = 0; a < ndim; ++a) diag += 2.0 / (dx[a] * dx[a]);
+
+    for (int64_t i = 0; i < m; ++i) { phi[i] = 0.0; r[i] = b[i]; }
+    double bnorm = sqrt(dot(m, b, b));
+    int k = 0, status = 0;
+    double rel = 0.0;
+    if (bnorm > 0.0) {
+        for (int64_t i = 0; i < m; ++i) { z[i] = r[i] / diag; p[i] = z[i]; }
+        double rz = dot(m, r, z);
+        rel = 1.0;
+        status = 1;
+        while (k < maxit) {
+            orc_neg_laplacian(ndim, n, dx, p, q);
+            double alpha = rz / dot(m, p, q);
+            for (int64_t i = 0; i < m; ++i) { phi[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+            ++k;
+            rel = sqrt(dot(m, r, r)) / bnorm;
+            if (rel <= rtol) { status = 0; break; }
+            for (int64_t i = 0; i < m; ++i) z[i] = r[i] / diag;
+            double rz_new = dot(m, r, z);
+            double beta = rz_new / rz;
+            rz = rz_new;
+            for (int64_t i = 0; i < m; ++i) p[i] = z[i] + beta * p[i];
+        }
+        double pm = 0.0;
+        for (int64_t i = 0; i < m; ++i) pm += phi[i];
+        pm /= (double)m;
+        for (int64_t i = 0; i < m; ++i) phi[i] -= pm;
+    }
+    if (iters) *iters = k;
+    if (relres) *relres = rel;
+    free(b); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* D06 (Sec. 3.1): E = -grad(phi) by periodic centred differences,
+ * E_a[j] = -(phi[j + e_a] - phi[j - e_a]) / (2 dx_a). */
+void orc_efield(int ndim, const int *n, const double *dx, const double *phi, double *E)
+{
+    int n3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) n3[a] = n[a];
+    int64_t cells = cells_of(ndim, n);
+    for (int j2 = 0; j2 < n3[2]; ++j2)
+        for (int j1 = 0; j1 < n3[1]; ++j1)
+            for (int j0 = 0; j0 < n3[0]; ++j0) {
+                int j[3] = {j0, j1, j2};
+                int64_t id = node_index(n3, j);
+                for (int a = 0; a < ndim; ++a) {
+                    int jp[3] = {j0, j1, j2}, jm[3] = {j0, j1, j2};
+                    jp[a] = (j[a] + 1) % n3[a];
+                    jm[a] = (j[a] - 1 + n3[a]) % n3[a];
+                    E[a * cells + id] = -(phi[node_index(n3, jp)] - phi[node_index(n3, jm)]) /
+                                        (2.0 * dx[a]);
+                }
+            }
+}
+
+/* A_Pusher, Boris scheme (Sec. 2.2; module A01 in Sec. 3.1), one velocity
+ * advance by the step h for every particle:
+ *   v- = v + (q/m) E h/2
+ *   t  = (q/m) B h/2,  v' = v- + v- x t,  s = 2 t / (1 + |t|^2),  v+ = v- + v' x s
+ *   v  = v+ + (q/m) E h/2
+ * E is the gathered grid field (ndim components per particle) plus the
+ * uniform external E0; B is the uniform B0.  Velocity components beyond nv
+ * enter as zero and are not stored back.  With B = 0 this is the leapfrog
+ * kick v += (q/m) E h. */
+void orc_boris(int ndim, int nv, int64_t np, double *v, const double *Ep, const double *E0,
+               const double *B0, double qm, double h)
+{
+    double t[3], tt = 0.0;
+    for (int a = 0; a < 3; ++a) { t[a] = qm * B0[a] * 0.5 * h; tt += t[a] * t[a]; }
+    double s[3];
+    for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + tt);
+    for (int64_t p = 0; p < np; ++p) {
+        double E[3], u[3];
+        for (int a = 0; a < 3; ++a) {
+            E[a] = E0[a] + (a < ndim && Ep ? Ep[p * ndim + a] : 0.0);
+            u[a] = a < nv ? v[p * nv + a] : 0.0;
+        }
+        double vm[3], vp[3], w[3];
+        for (int a = 0; a < 3; ++a) vm[a] = u[a] + qm * E[a] * 0.5 * h;
+        w[0] = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
+        w[1] = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
+        w[2] = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
+        vp[0] = vm[0] + (w[1] * s[2] - w[2] * s[1]);
+        vp[1] = vm[1] + (w[2] * s[0] - w[0] * s[2]);
+        vp[2] = vm[2] + (w[0] * s[1] - w[1] * s[0]);
+        for (int a = 0; a < nv && a < 3; ++a) v[p * nv + a] = vp[a] + qm * E[a] * 0.5 * h;
+    }
+}
+
+/* Position update with periodic boundaries (application code in Sec. 3.1):
+ * x_a += v_a dt on the ndim spatial axes, then x_a -= L_a floor(x_a / L_a);
+ * a result that rounds to L_a is set to 0. */
+void orc_move(int ndim, const int *n, const double *dx, int nv, int64_t np, double *x,
+              const double *v, double dt)
+{
+    for (int64_t p = 0; p < np; ++p)
+        for (int a = 0; a < ndim; ++a) {
+            double L = n[a] * dx[a];
+            double xa = x[p * ndim + a] + v[p * nv + a] * dt;
+            xa -= L * floor(xa / L);
+            if (xa >= L || xa < 0.0) xa = 0.0;
+            x[p * ndim + a] = xa;
+        }
+}
+
+/* Brick-major sort key of a cell: the grid is tiled by bricks of
+ * b0 x b1 x b2 cells (the last brick on an axis may be partial); the key is
+ *   brick_id * (b0 b1 b2) + local_id,
+ *   brick_id = B0 + nb0 * (B1 + nb1 * B2),  B_a = c_a / b_a, nb_a = ceil(n_a / b_a),
+ *   local_id = l0 + b0 * (l1 + b1 * l2),    l_a = c_a mod b_a.
+ * The ordering of particles by this key is the per-cell sort. */
+void orc_sort_key(int ndim, const int *n, const int *brick, int64_t np, const int64_t *cell,
+                  int64_t *key)
+{
+    int n3[3] = {1, 1, 1}, b3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) { n3[a] = n[a]; b3[a] = brick[a]; }
+    int64_t nb[3];
+    for (int a = 0; a < 3; ++a) nb[a] = (n3[a] + b3[a] - 1) / b3[a];
+    int64_t bcells = (int64_t)b3[0] * b3[1] * b3[2];
+    for (int64_t p = 0; p < np; ++p) {
+        int64_t c = cell[p];
+        int64_t ca[3];
+        ca[0] = c % n3[0];
+        ca[1] = (c / n3[0]) % n3[1];
+        ca[2] = c / ((int64_t)n3[0] * n3[1]);
+        int64_t bid = ca[0] / b3[0] + nb[0] * (ca[1] / b3[1] + nb[1] * (ca[2] / b3[2]));
+        int64_t lid = ca[0] % b3[0] + b3[0] * (ca[1] % b3[1] + (int64_t)b3[1] * (ca[2] % b3[2]));
+        key[p] = bid * bcells + lid;
+    }
+}
+
+/* Stable counting sort: perm[r] = index of the particle of rank r when
+ * particles are ordered by key, ties kept in input order.  Keys lie in
+ * [0, nkeys).  Returns 0, or 1 if a key is out of range. */
+int orc_counting_sort(int64_t np, const int64_t *key, int64_t nkeys, int64_t *perm)
+{
+    int64_t *start = calloc((size_t)nkeys + 1, sizeof(int64_t));
+    for (int64_t p = 0; p < np; ++p) {
+        if (key[p] < 0 || key[p] >= nkeys) { free(start); return 1; }
+        start[key[p] + 1] += 1;
+    }
+    for (int64_t k = 0; k < nkeys; ++k) start[k + 1] += start[k];
+    for (int64_t p = 0; p < np; ++p) perm[start[key[p]]++] = p;
+    free(start);
+    return 0;
+}
+
+/* Diagnostics (Sec. 3.2, the energy balance): kinetic energy
+ * (1/2) m w sum_p |v_p|^2 over nv components. */
+double orc_kinetic(int nv, int64_t np, const double *v, double mw)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < np * nv; ++i) s += v[i] * v[i];
+    return 0.5 * mw * s;
+}
+
+/* Field energy (1/2) dV sum_j |E_j|^2. */
+double orc_field_energy(int ndim, const int *n, const double *dx, const double *E)
+{
+    int64_t cells = cells_of(ndim, n);
+    double dV = 1.0;
+    for (int a = 0; a < ndim; ++a) dV *= dx[a];
+    double s = 0.0;
+    for (int64_t i = 0; i < cells * ndim; ++i) s += E[i] * E[i];
+    return 0.5 * dV * s;
+}
+
+/* Total momentum m w sum_p v_p, per component (nv of them). */
+void orc_momentum(int nv, int64_t np, const double *v, double mw, double *out)
+{
+    for (int a = 0; a < nv; ++a) out[a] = 0.0;
+    for (int64_t p = 0; p < np; ++p)
+        for (int a = 0; a < nv; ++a) out[a] += v[p * nv + a];
+    for (int a = 0; a < nv; ++a) out[a] *= mw;
+}
