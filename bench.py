@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the electrostatic PIC hot path on one B300 (or N replicas).
+
+Metric: particle-steps per second of gather + Boris push + move + CIC deposit
+(the fused particle pass plus the int64 -> rho conversion), with the per-cell
+sort at its cadence, on the 2D two-stream workload: 512 x 512 nodes, dx = 1,
+64 electrons per cell (16,777,216), beams at +-3 v_te with v_te = 1, dt = 0.1,
+sort every 20 steps.  One step of the timed loop = one pass of those stages
+over every particle; particle state (335 MB) is larger than L2, so no L2
+flush is needed between steps.  The field solve (CG + E) is run and timed
+separately, and it is inside the end-to-end number.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the single-instance
+path does not shard): value = all ranks' particle-steps / max rank time.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on this host's cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle-steps/s (gather+push+deposit)"
+UNIT = "particle-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6400.0, "fallback"
+
+
+def _workload(args):
+    if args.workload == "two_stream_2d":
+        return workloads.two_stream_2d(n=(args.n, args.n), ppc=args.ppc, seed=2)
+    if args.workload == "magnetized_3d":
+        return workloads.magnetized_3d(n=(args.n,) * 3, ppc=args.ppc)
+    if args.workload == "precision_3d":
+        return workloads.precision_3d(n=(args.n,) * 3, ppc=args.ppc)
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def _bytes_per_particle(ndim, nv):
+    # cell (int32) + ndim FP32 offsets + nv FP32 velocities, read and written once
+    return 2 * (4 + 4 * ndim + 4 * nv)
+
+
+def _grid_bytes_per_node(ndim):
+    # E read (ndim FP32) + the int64 accumulator written once
+    return 4 * ndim + 8
+
+
+class Clocks:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(w, sample_np, steps, warmup):
+    """The oracle's gather + push + move + deposit on `sample_np` particles of the
+    workload (full grid), `warmup` untimed then `steps` timed steps; returns
+    (particle-steps/s, seconds)."""
+    import oracle
+
+    sim = oracle.Simulation(w.ndim, w.n, w.dx, w.dt, q=w.q, m=w.m, weight=w.weight, B0=w.B0,
+                            E0=w.E0, rtol=1e-8)
+    sim.load(w.x[:sample_np], w.v[:sample_np])
+    for _ in range(warmup):
+        sim.push()
+        sim.move()
+        oracle.deposit(w.ndim, w.n, w.dx, sim.x, w.q * w.weight)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.push()
+        sim.move()
+        oracle.deposit(w.ndim, w.n, w.dx, sim.x, w.q * w.weight)
+    dt = time.perf_counter() - t0
+    return sample_np * steps / dt, dt
+
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args)
+    sample = min(w.np_, args.ref_sample)
+    val, secs = run_oracle_sample(w, sample, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config(args, w),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of {w.np_} particles on the full grid, "
+                                   f"{args.steps} steps of gather+push+move+deposit"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, w):
+    return {"workload": f"{w.name} {w.n[0]}x{w.n[1]}" + (f"x{w.n[2]}" if w.ndim == 3 else "")
+            + f", {args.ppc} ppc, {w.np_} electrons, dt={w.dt}, sort every {w.sort_every}",
+            "grid": list(w.n[: w.ndim]), "particles": w.np_, "ppc": args.ppc,
+            "sort_every": w.sort_every, "parallelism": f"replicas x{args.gpus}",
+            "l2": "particle state larger than L2 (no flush)"}
+
+
+def bench_ours(args):
+    import torch
+
+    import paper_2608_15249_b300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = _workload(args)
+    stream = torch.cuda.current_stream()
+    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol)
+    g.load(w.x, w.v)
+    sort_every = w.sort_every
+
+    def hot_step(k):
+        g.push_deposit()
+        if sort_every and k % sort_every == 0:
+            g.sort()
+
+    for k in range(1, args.warmup + 1):
+        hot_step(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g.set_timing(True)
+    launches0 = pk.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for k in range(args.warmup + 1, args.warmup + args.steps + 1):
+            hot_step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = pk.kernel_launches() - launches0
+    stages = g.get_timing()
+    g.set_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_ps = w.np_ * args.steps * world
+    value = total_ps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused particle pass)
+    peak, peak_kind = _peaks()
+    pd_ms, pd_n = stages["push_deposit"]
+    avg_ms = pd_ms / max(pd_n, 1)
+    alg_bytes = (w.np_ * _bytes_per_particle(w.ndim, w.nv)
+                 + w.cells * _grid_bytes_per_node(w.ndim))
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    breakdown = {k: (v[0] / max(v[1], 1)) for k, v in stages.items() if v[1]}
+
+    # field solve timed separately, then the end-to-end job through host buffers
+    g.set_timing(True)
+    g.solve_field()
+    fs = g.get_timing()["field"]
+    g.set_timing(False)
+    e2e = run_e2e(args, w, pk, torch, stream) if not args.no_e2e else None
+    g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = min(w.np_, args.cpu_sample)
+        val, secs = run_oracle_sample(w, sample, args.cpu_steps, 0)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sample} of {w.np_} particles on the full grid, {args.cpu_steps} "
+                         f"steps of gather+push+move+deposit ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(args, w),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_particle_pass (gather+Boris+move+deposit)",
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                         "peak_kind": peak_kind},
+            "stage_ms_per_call": breakdown,
+            "field_solve_ms": fs[0] / max(fs[1], 1),
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, w, pk, torch, stream):
+    """Load from pinned host memory, run the full cycle (with field solves) for
+    e2e_steps steps reading the diagnostics back every step, then read rho."""
+    import ctypes
+
+    xs = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
+    vs = torch.from_numpy(np.ascontiguousarray(w.v)).pin_memory()
+    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol)
+    steps = args.e2e_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.load_ptr(w.np_, xs.data_ptr(), vs.data_ptr())
+    for _ in range(steps):
+        g.step(1)
+        g.get_diag()
+    rho = g.get_rho()
+    t1 = time.perf_counter()
+    g.close()
+    h2d = w.x.nbytes + w.v.nbytes
+    d2h = ctypes.sizeof(pk.ap_pic_diag) + 4  # diagnostics (+ error word) each step
+    return {"value": w.np_ * steps / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h + rho.nbytes / steps,
+            "steps": steps, "seconds": t1 - t0,
+            "what": "load from pinned host + full cycle (push, deposit, sort, CG, E) per step "
+                    "+ diagnostics read each step + final rho read"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="two_stream_2d")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--ppc", type=int, default=64)
+    ap.add_argument("--cg-rtol", type=float, default=1e-6)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 22)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--ref-sample", type=int, default=1 << 16)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * ap_pic.h -- C ABI of the B300 electrostatic particle-in-cell hot path.
+ *
+ * The library advances one (or a batch of) periodic electrostatic PIC
+ * instance(s) on one CUDA device.  The cycle is the one of the AlgoPlasma
+ * paper's worked example (Sec. 3.1, Listing 1):
+ *
+ *   load:  initialise particles (I01) -> update the field -> initial half push
+ *   step:  push velocities (C01 gather + A01 Boris) -> move + periodic wrap
+ *          -> update the field (B01 deposit -> D02 Poisson -> D05/D06 E)
+ *
+ * Physics conventions (Debye units, eps0 = 1):
+ *   - node-centred periodic grid: node j_a sits at x = j_a dx_a, L_a = n_a dx_a;
+ *     flat node index j0 + n0 (j1 + n1 j2) (axis 0 fastest);
+ *   - linear (cloud-in-cell) weights for both deposit and gather;
+ *   - -lap_h(phi) = rho - mean(rho) with the (2 ndim + 1)-point Laplacian,
+ *     phi of zero mean, E = -grad_h(phi) by centred differences;
+ *   - Boris velocity advance (Sec. 2.2, A_Pusher); with B0 = 0 it is the
+ *     leapfrog kick;  the initial half push is a Boris step of -dt/2.
+ *
+ * Storage (precision AP_PIC_FP32_CELLOFF): each particle is an int32 linear
+ * cell index plus FP32 in-cell offsets in [0, 1) per axis and FP32
+ * velocities; charge is accumulated as int64 fixed point (2^S per particle,
+ * exactly), so the deposit is run-to-run deterministic and conserves the
+ * total charge bit for bit.  AP_PIC_FP64_PLAIN keeps FP64 positions and
+ * velocities instead (comparison form).
+ *
+ * Conventions for every call:
+ *   - Return value: AP_PIC_OK or a negative ap_pic_status; no call aborts or
+ *     exits.  ap_pic_last_error() gives a one-line reason.
+ *   - Asynchrony: compute calls are enqueued on the handle's stream and return
+ *     without waiting; calls that copy into host buffers (ap_pic_get_*)
+ *     synchronise the stream first.
+ *   - Device-detected errors (non-finite particle state, a CG solve that did
+ *     not converge) are latched on the device and reported by the next
+ *     synchronising call; once latched they stay until ap_pic_destroy.
+ *   - Ownership: the caller owns every host buffer it passes; the library owns
+ *     all device memory, obtained through the optional allocator (NULL:
+ *     cudaMalloc / cudaFree).
+ *   - Threading: a handle may be used by one host thread at a time.
+ */
+#ifndef AP_PIC_H
+#define AP_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AP_PIC_OK = 0,
+    AP_PIC_ERR_ARG = -1,           /* invalid argument or configuration        */
+    AP_PIC_ERR_UNSUPPORTED = -2,   /* valid but not implemented (e.g. bc)      */
+    AP_PIC_ERR_NOMEM = -3,         /* device allocation failed                 */
+    AP_PIC_ERR_CUDA = -4,          /* a CUDA runtime call failed               */
+    AP_PIC_ERR_NOT_CONVERGED = -5, /* field solve hit cg_maxit                 */
+    AP_PIC_ERR_BOUNDS = -6,        /* non-finite or out-of-range particle      */
+    AP_PIC_ERR_STATE = -7          /* call out of order (e.g. step before load) */
+} ap_pic_status;
+
+enum { AP_PIC_BC_PERIODIC = 0 };
+
+enum {
+    AP_PIC_FP32_CELLOFF = 0,  /* int32 cell + FP32 offsets/velocities (default)   */
+    AP_PIC_FP64_PLAIN = 1     /* FP64 positions/velocities, no sort, no tiling     */
+};
+
+/* ap_pic_load flags */
+enum { AP_PIC_LOAD_NO_HALFPUSH = 1u };
+
+typedef struct {
+    int ndim;              /* 1, 2 or 3 spatial dimensions                        */
+    int n[3];              /* nodes (= cells) per axis; unused axes ignored        */
+    double dx[3];          /* node spacing per axis (> 0)                          */
+    double dt;             /* time step                                            */
+    double q, m;           /* species charge and mass (electrons: -1, 1)           */
+    double weight;         /* physical particles per macro-particle (> 0)          */
+    double rho_background; /* uniform immobile charge density; NaN: neutralise the
+                              loaded particles exactly (-q w np / V)              */
+    double E0[3], B0[3];   /* uniform external fields; B0 enters the Boris turn    */
+    int bc;                /* AP_PIC_BC_PERIODIC only                              */
+    int precision;         /* AP_PIC_FP32_CELLOFF or AP_PIC_FP64_PLAIN             */
+    int nv;                /* stored velocity components, ndim <= nv <= 3; nv must
+                              be 3 when B0 != 0                                    */
+    int sort_every;        /* ap_pic_step sorts by cell every this many steps (0:
+                              never); ignored by AP_PIC_FP64_PLAIN                 */
+    int fx_bits;           /* fixed-point fraction bits S of the charge
+                              accumulator (0: 40); capped at 62 - bitlen(np) so the
+                              int64 sum can never overflow                         */
+    double cg_rtol;        /* field-solve relative residual target (0: 1e-7)      */
+    int cg_maxit;          /* field-solve iteration cap (0: 20000)                 */
+    int brick[3];          /* sort brick in cells per axis (0: library default)    */
+    int diag_every;        /* diagnostics every this many steps (0: every step)    */
+} ap_pic_config;
+
+typedef struct {
+    /* Returns device memory of `bytes` bytes (>= 256-byte aligned) or NULL. */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *ctx);
+    void *ctx;
+} ap_pic_allocator;
+
+typedef struct {
+    int64_t step;           /* steps taken since load                            */
+    double t;               /* simulated time = step * dt                        */
+    int64_t np;             /* particles                                         */
+    int fx_bits;            /* S in use                                          */
+    int64_t charge_fx_sum;  /* sum of the int64 accumulator; np * 2^S when exact  */
+    double total_charge;    /* q w (charge_fx_sum / 2^S)                          */
+    double kinetic;         /* (1/2) m w sum |v|^2, time-centred at the last push
+                               (mean of the two half-step energies)               */
+    double field_energy;    /* (1/2) dV sum_j |E_j|^2 of the current field        */
+    double momentum[3];     /* m w sum v after the last push                      */
+    int cg_iters;           /* iterations of the last field solve                 */
+    double cg_relres;       /* its final relative residual                        */
+    int error_flags;        /* latched device error bits (AP_PIC_EFLAG_*)         */
+} ap_pic_diag;
+
+enum {
+    AP_PIC_EFLAG_NONFINITE = 1,     /* a particle's offset or velocity was not finite */
+    AP_PIC_EFLAG_CG = 2,            /* a field solve stopped at cg_maxit              */
+    AP_PIC_EFLAG_OVERFLOW = 4       /* a particle count exceeded the fixed-point range */
+};
+
+typedef struct ap_pic ap_pic;
+
+/* Fills *cfg with defaults (1D, 64 nodes, dx = 1, dt = 0.1, electrons, w = 1,
+ * neutralising background, periodic, FP32 cell+offset, nv = 1, sort every 20). */
+void ap_pic_config_default(ap_pic_config *cfg);
+
+/* Creates an instance on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL: the legacy default stream).  `alloc` may be NULL.
+ * The grid arrays are allocated here; particle arrays at ap_pic_load. */
+ap_pic_status ap_pic_create(const ap_pic_config *cfg, const ap_pic_allocator *alloc,
+                            void *cuda_stream, ap_pic **out);
+
+/* The instance's configuration after validation, with every default resolved
+ * (fx_bits is the value in use once particles are loaded). */
+ap_pic_status ap_pic_get_config(const ap_pic *h, ap_pic_config *out);
+
+/* Frees every device allocation and the handle (NULL is accepted). */
+ap_pic_status ap_pic_destroy(ap_pic *h);
+
+/* I01 + field update + initial half push (Sec. 3.1, Listing 1).
+ * x: host FP64, np x ndim row-major, each coordinate in [0, L_a) (a value equal
+ * to L_a is taken as 0; anything else outside is AP_PIC_ERR_BOUNDS).
+ * v: host FP64, np x nv row-major.  The call copies x and v to the device,
+ * converts them to the instance's storage, sorts by cell (FP32 form),
+ * deposits, solves for E and, unless AP_PIC_LOAD_NO_HALFPUSH, moves v back
+ * half a step (Boris with -dt/2).  Synchronises the stream. */
+ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, const double *v,
+                          unsigned flags);
+
+/* Loads an exact FP32 state (checkpoint restore): cell[np] linear cell
+ * indices, off (np x ndim, row-major, each in [0, 1)), v (np x nv).  Host
+ * buffers.  Then deposits and solves as ap_pic_load (no half push unless
+ * flags lacks AP_PIC_LOAD_NO_HALFPUSH).  FP32_CELLOFF only. */
+ap_pic_status ap_pic_load_state(ap_pic *h, int64_t np, const int32_t *cell, const float *off,
+                                const float *v, unsigned flags);
+
+/* C01 + A01 + position update (Sec. 3.1): gathers E at each particle, advances
+ * v by a Boris step of dt and x by v dt with periodic wrap.  Does not deposit. */
+ap_pic_status ap_pic_gather_push(ap_pic *h);
+
+/* B01 (Sec. 2.2, Sec. 3.1): deposits the charge of the current positions into
+ * the int64 fixed-point accumulator and converts it to rho (FP64, with the
+ * background). */
+ap_pic_status ap_pic_deposit(ap_pic *h);
+
+/* The fused hot path: ap_pic_gather_push followed by ap_pic_deposit in one
+ * pass over the particles (identical results, bit for bit). */
+ap_pic_status ap_pic_push_deposit(ap_pic *h);
+
+/* D02 + D05/D06 (Sec. 2.2, Sec. 3.1): solves -lap_h(phi) = rho - mean(rho) by
+ * Jacobi-preconditioned CG (FP32 vectors, FP64 dot products, warm start from
+ * the previous phi) and sets E = -grad_h(phi).  Synchronises the stream once
+ * per block of iterations to test convergence. */
+ap_pic_status ap_pic_solve_field(ap_pic *h);
+
+/* Per-cell sort: stable reorder of the particle arrays by the brick-major
+ * cell key (ties keep their order).  FP32_CELLOFF only; a no-op for FP64_PLAIN. */
+ap_pic_status ap_pic_sort(ap_pic *h);
+
+/* nsteps full cycles: push+deposit (fused), sort when due, field solve,
+ * diagnostics when due. */
+ap_pic_status ap_pic_step(ap_pic *h, int nsteps);
+
+/* Host copies (each synchronises the stream).
+ * rho: cells doubles (total charge density incl. background).
+ * E:   ndim x cells doubles, component-major.
+ * phi: cells doubles. */
+ap_pic_status ap_pic_get_rho(ap_pic *h, double *rho);
+ap_pic_status ap_pic_get_E(ap_pic *h, double *E);
+ap_pic_status ap_pic_get_phi(ap_pic *h, double *phi);
+/* The raw int64 fixed-point accumulator of the last deposit (cells entries). */
+ap_pic_status ap_pic_get_rho_fx(ap_pic *h, int64_t *acc);
+
+/* Particle state in storage order; any pointer may be NULL.
+ * cell: np int32; off: np x ndim float; v: np x nv float;
+ * x: np x ndim double, reconstructed as (cell_a + off_a) dx_a (FP64_PLAIN:
+ * the stored position; cell/off/v then come from it). */
+ap_pic_status ap_pic_get_particles(ap_pic *h, int32_t *cell, float *off, float *v, double *x);
+/* FP64 velocities of the FP64_PLAIN form (np x nv). */
+ap_pic_status ap_pic_get_velocities_f64(ap_pic *h, double *v);
+
+/* Permutation applied by the most recent sort: perm[r] = storage position,
+ * before that sort, of the particle now at position r (np int64). */
+ap_pic_status ap_pic_get_perm(ap_pic *h, int64_t *perm);
+
+ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out);
+
+/* Stage timing with CUDA events recorded on the handle's stream.
+ * ap_pic_set_timing(h, 1) starts recording an event pair around every stage
+ * launched afterwards (and clears the totals); ap_pic_get_timing synchronises
+ * and returns, per stage, the summed milliseconds and the number of timed
+ * occurrences.  Arrays have AP_PIC_NSTAGES entries. */
+enum {
+    AP_PIC_STAGE_PUSH_DEPOSIT = 0, /* the particle pass (gather, push, move, deposit) */
+    AP_PIC_STAGE_RHO = 1,          /* fixed point -> rho conversion                  */
+    AP_PIC_STAGE_SORT = 2,         /* keys, radix passes, record gather              */
+    AP_PIC_STAGE_FIELD = 3,        /* CG iterations and E                            */
+    AP_PIC_STAGE_DIAG = 4,         /* diagnostics reduction                          */
+    AP_PIC_NSTAGES = 8
+};
+ap_pic_status ap_pic_set_timing(ap_pic *h, int enable);
+ap_pic_status ap_pic_get_timing(ap_pic *h, double *ms, int64_t *count);
+
+/* Kernels this library has launched in the process so far (all handles). */
+int64_t ap_pic_kernel_launches(void);
+
+/* Number of particles loaded (0 before ap_pic_load). */
+int64_t ap_pic_num_particles(const ap_pic *h);
+
+/* Last error message of the handle ("" if none); valid until the next call. */
+const char *ap_pic_last_error(const ap_pic *h);
+
+/* Library version string. */
+const char *ap_pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AP_PIC_H */

@@ -1,0 +1,877 @@
+// ap_pic.cu -- host side of the C ABI declared in include/ap_pic.h: instance
+// state, device memory, and the order of the cycle of the paper's worked
+// example (Sec. 3.1, Listing 1).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "ap_pic.h"
+#include "pic_internal.cuh"
+
+using namespace apk;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void apk::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int DEFAULT_FX_BITS = 40;
+constexpr double DEFAULT_CG_RTOL = 1e-7;
+constexpr int DEFAULT_CG_MAXIT = 20000;
+constexpr int64_t LOAD_CHUNK = int64_t(1) << 23;  // particles per host->device load chunk
+
+int bitlen(uint64_t x)
+{
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace
+
+struct ap_pic {
+    ap_pic_config cfg;
+    ap_pic_allocator alloc;
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<std::pair<void *, size_t>> owned;
+
+    int ndim = 1, nv = 1;
+    int64_t cells = 0;
+    int64_t np = 0;
+    int fx_bits = DEFAULT_FX_BITS;
+    int brick[3] = {1, 1, 1};
+    int key_bits = 0;
+    double dV = 1.0, V = 1.0;
+    int64_t step = 0;
+    bool loaded = false;
+
+    // particles (FP32 cell + offset form)
+    ParticlesF32 p{};
+    ParticlesF32 p_alt{};
+    SortScratch sort{};
+    int perm_slot = -1;
+
+    // grid
+    FieldBufs f{};
+    DiagPartials dpart{};
+    double *d_diag = nullptr;      // [8]
+    long long *d_accsum = nullptr; // [1]
+    int *d_err = nullptr;
+
+    // pinned host mirrors
+    int *h_done = nullptr;
+    double *h_diag = nullptr;
+    long long *h_accsum = nullptr;
+    int *h_err = nullptr;
+    int *h_iters = nullptr;
+
+    int last_cg_iters = 0;
+    double last_cg_relres = 0.0;
+    bool diag_valid = false;
+
+    // stage timing: event pairs recorded on the stream, summed on request
+    bool timing = false;
+    struct Mark {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    double stage_ms[AP_PIC_NSTAGES] = {0};
+    int64_t stage_n[AP_PIC_NSTAGES] = {0};
+};
+
+// Records the start of a timed stage; returns the index of its mark (-1 when off).
+static int stage_begin(ap_pic *h, int stage)
+{
+    if (!h->timing) return -1;
+    ap_pic::Mark m{stage, nullptr, nullptr};
+    if (cudaEventCreate(&m.a) != cudaSuccess || cudaEventCreate(&m.b) != cudaSuccess) return -1;
+    cudaEventRecord(m.a, h->stream);
+    h->marks.push_back(m);
+    return (int)h->marks.size() - 1;
+}
+
+static void stage_end(ap_pic *h, int mark)
+{
+    if (mark < 0) return;
+    cudaEventRecord(h->marks[(size_t)mark].b, h->stream);
+}
+
+static void drain_marks(ap_pic *h)
+{
+    if (h->marks.empty()) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &m : h->marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            h->stage_ms[m.stage] += ms;
+            h->stage_n[m.stage] += 1;
+        }
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    h->marks.clear();
+}
+
+// ---- small helpers ---------------------------------------------------------------------------
+
+static ap_pic_status fail(ap_pic *h, ap_pic_status st, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+#define CU(h, call)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((h), AP_PIC_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                   \
+    } while (0)
+
+#define TRY(expr)                                                                              \
+    do {                                                                                       \
+        ap_pic_status s_ = (expr);                                                             \
+        if (s_ != AP_PIC_OK) return s_;                                                        \
+    } while (0)
+
+static void *dev_alloc(ap_pic *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    void *ptr = nullptr;
+    if (h->has_alloc) {
+        ptr = h->alloc.alloc(bytes, h->alloc.ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) h->owned.push_back({ptr, bytes});
+    return ptr;
+}
+
+static void dev_free(ap_pic *h, void *ptr)
+{
+    if (!ptr) return;
+    for (size_t i = 0; i < h->owned.size(); ++i) {
+        if (h->owned[i].first == ptr) {
+            const size_t bytes = h->owned[i].second;
+            if (h->has_alloc) h->alloc.free(ptr, bytes, h->alloc.ctx);
+            else cudaFree(ptr);
+            h->owned.erase(h->owned.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+template <typename T>
+static ap_pic_status alloc_n(ap_pic *h, T **out, size_t count)
+{
+    *out = static_cast<T *>(dev_alloc(h, count * sizeof(T)));
+    if (!*out)
+        return fail(h, AP_PIC_ERR_NOMEM, "device allocation of %zu bytes failed",
+                    count * sizeof(T));
+    return AP_PIC_OK;
+}
+
+static GridParams grid_params(const ap_pic *h, double step_h)
+{
+    GridParams g{};
+    const ap_pic_config &c = h->cfg;
+    g.ndim = h->ndim;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < h->ndim ? c.n[a] : 1;
+        g.dtdx[a] = a < h->ndim ? (float)(c.dt / c.dx[a]) : 0.0f;
+        g.E0[a] = (float)c.E0[a];
+    }
+    const double qm = c.q / c.m;
+    g.qmh2 = (float)(qm * step_h * 0.5);
+    double t[3], tt = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        t[a] = qm * c.B0[a] * step_h * 0.5;
+        tt += t[a] * t[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        g.t[a] = (float)t[a];
+        g.s[a] = (float)(2.0 * t[a] / (1.0 + tt));
+    }
+    g.magnetised = (c.B0[0] != 0.0 || c.B0[1] != 0.0 || c.B0[2] != 0.0) ? 1 : 0;
+    g.fx_bits = h->fx_bits;
+    return g;
+}
+
+// Reads the latched device error word (synchronises the stream).
+static ap_pic_status sync_check(ap_pic *h)
+{
+    CU(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    const int e = *h->h_err;
+    if (e & EF_NONFINITE)
+        return fail(h, AP_PIC_ERR_BOUNDS,
+                    "a particle position or velocity was not finite or outside the box");
+    if (e & EF_OVERFLOW) return fail(h, AP_PIC_ERR_BOUNDS, "fixed-point charge overflow");
+    if (e & EF_CG)
+        return fail(h, AP_PIC_ERR_NOT_CONVERGED, "field solve stopped at cg_maxit = %d",
+                    h->cfg.cg_maxit);
+    return AP_PIC_OK;
+}
+
+// ---- configuration ---------------------------------------------------------------------------
+
+extern "C" void ap_pic_config_default(ap_pic_config *c)
+{
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->ndim = 1;
+    c->n[0] = 64;
+    c->n[1] = c->n[2] = 1;
+    c->dx[0] = c->dx[1] = c->dx[2] = 1.0;
+    c->dt = 0.1;
+    c->q = -1.0;
+    c->m = 1.0;
+    c->weight = 1.0;
+    c->rho_background = NAN;
+    c->bc = AP_PIC_BC_PERIODIC;
+    c->precision = AP_PIC_FP32_CELLOFF;
+    c->nv = 1;
+    c->sort_every = 20;
+    c->fx_bits = DEFAULT_FX_BITS;
+    c->cg_rtol = DEFAULT_CG_RTOL;
+    c->cg_maxit = DEFAULT_CG_MAXIT;
+}
+
+static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
+{
+    if (c->ndim < 1 || c->ndim > 3) return fail(h, AP_PIC_ERR_ARG, "ndim must be 1, 2 or 3");
+    int64_t cells = 1;
+    for (int a = 0; a < c->ndim; ++a) {
+        if (c->n[a] < 2) return fail(h, AP_PIC_ERR_ARG, "n[%d] must be >= 2", a);
+        if (!(c->dx[a] > 0.0) || !isfinite(c->dx[a]))
+            return fail(h, AP_PIC_ERR_ARG, "dx[%d] must be positive and finite", a);
+        cells *= c->n[a];
+    }
+    if (cells > (int64_t(1) << 30))
+        return fail(h, AP_PIC_ERR_ARG, "grid of %lld nodes exceeds 2^30", (long long)cells);
+    for (int a = c->ndim; a < 3; ++a) {
+        c->n[a] = 1;
+        if (!(c->dx[a] > 0.0)) c->dx[a] = 1.0;
+    }
+    if (!(c->dt > 0.0) || !isfinite(c->dt)) return fail(h, AP_PIC_ERR_ARG, "dt must be > 0");
+    if (!(c->m > 0.0) || !isfinite(c->q)) return fail(h, AP_PIC_ERR_ARG, "need m > 0, finite q");
+    if (!(c->weight > 0.0)) return fail(h, AP_PIC_ERR_ARG, "weight must be > 0");
+    if (c->bc != AP_PIC_BC_PERIODIC)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "only periodic boundaries are implemented");
+    if (c->precision != AP_PIC_FP32_CELLOFF && c->precision != AP_PIC_FP64_PLAIN)
+        return fail(h, AP_PIC_ERR_ARG, "unknown precision %d", c->precision);
+    if (c->precision == AP_PIC_FP64_PLAIN)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "FP64 plain form not built in this library");
+    if (c->nv < c->ndim || c->nv > 3) return fail(h, AP_PIC_ERR_ARG, "need ndim <= nv <= 3");
+    const bool mag = c->B0[0] != 0.0 || c->B0[1] != 0.0 || c->B0[2] != 0.0;
+    if (mag && c->nv != 3) return fail(h, AP_PIC_ERR_ARG, "B0 != 0 needs nv = 3");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(c->E0[a]) || !isfinite(c->B0[a]))
+            return fail(h, AP_PIC_ERR_ARG, "E0 and B0 must be finite");
+    if (c->sort_every < 0) return fail(h, AP_PIC_ERR_ARG, "sort_every must be >= 0");
+    if (c->fx_bits == 0) c->fx_bits = DEFAULT_FX_BITS;
+    if (c->fx_bits < 8 || c->fx_bits > 52) return fail(h, AP_PIC_ERR_ARG, "fx_bits in [8, 52]");
+    if (c->cg_rtol == 0.0) c->cg_rtol = DEFAULT_CG_RTOL;
+    if (!(c->cg_rtol > 0.0)) return fail(h, AP_PIC_ERR_ARG, "cg_rtol must be > 0");
+    if (c->cg_maxit == 0) c->cg_maxit = DEFAULT_CG_MAXIT;
+    if (c->cg_maxit < 1) return fail(h, AP_PIC_ERR_ARG, "cg_maxit must be >= 1");
+    if (c->diag_every < 0) return fail(h, AP_PIC_ERR_ARG, "diag_every must be >= 0");
+    if (c->diag_every == 0) c->diag_every = 1;
+    // default sort brick: 64 cells in 1D, 8 x 8 in 2D, 8 x 8 x 8 in 3D (capped by n)
+    for (int a = 0; a < 3; ++a) {
+        if (a >= c->ndim) {
+            c->brick[a] = 1;
+            continue;
+        }
+        if (c->brick[a] == 0) c->brick[a] = c->ndim == 1 ? 64 : 8;
+        if (c->brick[a] < 1) return fail(h, AP_PIC_ERR_ARG, "brick[%d] must be >= 1", a);
+        if (c->brick[a] > c->n[a]) c->brick[a] = c->n[a];
+    }
+    return AP_PIC_OK;
+}
+
+// ---- create / destroy ------------------------------------------------------------------------
+
+static ap_pic_status create_grid(ap_pic *h)
+{
+    FieldBufs &f = h->f;
+    f.ndim = h->ndim;
+    f.cells = h->cells;
+    for (int a = 0; a < 3; ++a) {
+        f.n[a] = h->cfg.n[a];
+        f.dx[a] = h->cfg.dx[a];
+    }
+    f.Estride = h->ndim == 3 ? 4 : h->ndim;
+    f.nblocks = field_blocks(h->cells);
+    const size_t c = (size_t)h->cells;
+    TRY(alloc_n(h, &f.acc, c));
+    TRY(alloc_n(h, &f.rho, c));
+    TRY(alloc_n(h, &f.b, c));
+    TRY(alloc_n(h, &f.phi, c));
+    TRY(alloc_n(h, &f.r, c));
+    TRY(alloc_n(h, &f.p, c));
+    TRY(alloc_n(h, &f.q, c));
+    TRY(alloc_n(h, &f.E, c * f.Estride));
+    for (int k = 0; k < 3; ++k) TRY(alloc_n(h, &f.part[k], (size_t)f.nblocks));
+    TRY(alloc_n(h, &f.scal, 8));
+    TRY(alloc_n(h, &f.done, 1));
+    TRY(alloc_n(h, &f.iters, 1));
+    TRY(alloc_n(h, &f.isum_part, (size_t)f.nblocks));
+    TRY(alloc_n(h, &f.fe_part, (size_t)f.nblocks));
+    TRY(alloc_n(h, &h->d_diag, 8));
+    TRY(alloc_n(h, &h->d_accsum, 1));
+    TRY(alloc_n(h, &h->d_err, 1));
+    CU(h, cudaMemsetAsync(f.acc, 0, c * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.phi, 0, c * 4, h->stream));
+    CU(h, cudaMemsetAsync(f.E, 0, c * f.Estride * 4, h->stream));
+    CU(h, cudaMemsetAsync(f.isum_part, 0, (size_t)f.nblocks * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.fe_part, 0, (size_t)f.nblocks * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.scal, 0, 64, h->stream));
+    CU(h, cudaMemsetAsync(f.iters, 0, 4, h->stream));
+    CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
+    CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
+    CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+    CU(h, cudaMallocHost(&h->h_done, 64));
+    CU(h, cudaMallocHost(&h->h_diag, 64));
+    CU(h, cudaMallocHost(&h->h_accsum, 64));
+    CU(h, cudaMallocHost(&h->h_err, 64));
+    CU(h, cudaMallocHost(&h->h_iters, 64));
+    return AP_PIC_OK;
+}
+
+static void free_particles(ap_pic *h)
+{
+    dev_free(h, h->p.cell);
+    dev_free(h, h->p.off);
+    dev_free(h, h->p.v);
+    dev_free(h, h->p_alt.cell);
+    dev_free(h, h->p_alt.off);
+    dev_free(h, h->p_alt.v);
+    for (int k = 0; k < 2; ++k) {
+        dev_free(h, h->sort.keys[k]);
+        dev_free(h, h->sort.idx[k]);
+    }
+    dev_free(h, h->sort.hist);
+    dev_free(h, h->sort.scan_tmp);
+    dev_free(h, h->dpart.blocks);
+    h->p = ParticlesF32{};
+    h->p_alt = ParticlesF32{};
+    h->sort = SortScratch{};
+    h->dpart = DiagPartials{};
+    h->np = 0;
+    h->perm_slot = -1;
+}
+
+extern "C" ap_pic_status ap_pic_create(const ap_pic_config *cfg, const ap_pic_allocator *alloc,
+                                       void *cuda_stream, ap_pic **out)
+{
+    if (!cfg || !out) return AP_PIC_ERR_ARG;
+    *out = nullptr;
+    ap_pic *h = new ap_pic();
+    h->cfg = *cfg;
+    ap_pic_status st = validate(h, &h->cfg);
+    if (st != AP_PIC_OK) {
+        // the handle carries the message; hand it back so ap_pic_last_error works
+        *out = h;
+        return st;
+    }
+    if (alloc && alloc->alloc && alloc->free) {
+        h->alloc = *alloc;
+        h->has_alloc = true;
+    }
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ndim = h->cfg.ndim;
+    h->nv = h->cfg.nv;
+    h->cells = 1;
+    h->dV = 1.0;
+    for (int a = 0; a < h->ndim; ++a) {
+        h->cells *= h->cfg.n[a];
+        h->dV *= h->cfg.dx[a];
+    }
+    h->V = h->dV * (double)h->cells;
+    for (int a = 0; a < 3; ++a) h->brick[a] = h->cfg.brick[a];
+    int64_t nkeys = 1;
+    for (int a = 0; a < h->ndim; ++a)
+        nkeys *= (int64_t)((h->cfg.n[a] + h->brick[a] - 1) / h->brick[a]) * h->brick[a];
+    h->key_bits = bitlen((uint64_t)(nkeys - 1));
+    if (nkeys > (int64_t(1) << 32)) {
+        *out = h;
+        return fail(h, AP_PIC_ERR_ARG, "sort key range exceeds 32 bits");
+    }
+    st = create_grid(h);
+    *out = h;
+    return st;
+}
+
+extern "C" ap_pic_status ap_pic_get_config(const ap_pic *h, ap_pic_config *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    *out = h->cfg;
+    out->fx_bits = h->fx_bits;
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_destroy(ap_pic *h)
+{
+    if (!h) return AP_PIC_OK;
+    drain_marks(h);
+    if (!h->owned.empty()) cudaStreamSynchronize(h->stream);
+    while (!h->owned.empty()) dev_free(h, h->owned.back().first);
+    if (h->h_done) cudaFreeHost(h->h_done);
+    if (h->h_diag) cudaFreeHost(h->h_diag);
+    if (h->h_accsum) cudaFreeHost(h->h_accsum);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_iters) cudaFreeHost(h->h_iters);
+    delete h;
+    return AP_PIC_OK;
+}
+
+// ---- particle storage ------------------------------------------------------------------------
+
+static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
+{
+    free_particles(h);
+    h->np = np;
+    const size_t n = (size_t)(np > 0 ? np : 1);
+    ParticlesF32 *ps[2] = {&h->p, &h->p_alt};
+    for (ParticlesF32 *q : ps) {
+        TRY(alloc_n(h, &q->cell, n));
+        TRY(alloc_n(h, &q->off, n * h->ndim));
+        TRY(alloc_n(h, &q->v, n * h->nv));
+        q->np = np;
+        q->nv = h->nv;
+    }
+    for (int k = 0; k < 2; ++k) {
+        TRY(alloc_n(h, &h->sort.keys[k], n));
+        TRY(alloc_n(h, &h->sort.idx[k], n));
+    }
+    const size_t hl = sort_hist_len(np > 0 ? np : 1);
+    TRY(alloc_n(h, &h->sort.hist, hl));
+    h->sort.scan_tmp_len = sort_scan_tmp_len(hl);
+    TRY(alloc_n(h, &h->sort.scan_tmp, h->sort.scan_tmp_len));
+    h->sort.capacity = np;
+    h->dpart.nblocks = particle_pass_blocks(np > 0 ? np : 1);
+    TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
+    CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
+    // fixed-point scale: S <= 62 - bitlen(np) keeps |sum| < 2^62 whatever the clustering
+    const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
+    h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
+    return AP_PIC_OK;
+}
+
+// ---- the cycle's stages ----------------------------------------------------------------------
+
+static double bg_density(const ap_pic *h)
+{
+    const double c = h->cfg.rho_background;
+    return isnan(c) ? -h->cfg.q * h->cfg.weight * (double)h->np / h->V : c;
+}
+
+// rho from the accumulator: rho_e = q w / dV * acc / 2^S;  b = rho_e - mean(rho_e)
+// (mean exact: every particle deposits 2^S, so mean(rho_e) = q w np / V).
+static ap_pic_status convert_rho(ap_pic *h)
+{
+    const double scale = h->cfg.q * h->cfg.weight / h->dV * ldexp(1.0, -h->fx_bits);
+    const double mean_e = h->cfg.q * h->cfg.weight * (double)h->np / h->V;
+    const int mk = stage_begin(h, AP_PIC_STAGE_RHO);
+    CU(h, launch_rho_convert(h->f, scale, bg_density(h), mean_e, false, h->stream));
+    stage_end(h, mk);
+    return AP_PIC_OK;
+}
+
+static ap_pic_status deposit_only(ap_pic *h)
+{
+    CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
+    const GridParams g = grid_params(h, h->cfg.dt);
+    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, false, false, true, DiagPartials{},
+                               h->d_err, h->stream));
+    return convert_rho(h);
+}
+
+static ap_pic_status solve_field(ap_pic *h)
+{
+    FieldBufs &f = h->f;
+    const double rtol = h->cfg.cg_rtol;
+    const int maxit = h->cfg.cg_maxit;
+    const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
+    CU(h, launch_cg_init(f, rtol, h->stream));
+    int it = 0, chunk = 8;
+    while (true) {
+        CU(h, cudaMemcpyAsync(h->h_done, f.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        if (*h->h_done || it >= maxit) break;
+        CU(h, launch_cg_iters(f, it, chunk, maxit, rtol, h->stream));
+        it += chunk;
+        if (chunk < 64) chunk *= 2;
+    }
+    CU(h, launch_cg_finish(f, rtol, h->d_err, h->stream));
+    CU(h, launch_efield(f, h->stream));
+    stage_end(h, mk);
+    CU(h, cudaMemcpyAsync(h->h_iters, f.iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    double rel = 0.0;
+    CU(h, cudaMemcpyAsync(h->h_diag + 7, f.scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    rel = h->h_diag[7];
+    h->last_cg_iters = *h->h_iters;
+    h->last_cg_relres = rel;
+    if (rel > rtol)
+        return fail(h, AP_PIC_ERR_NOT_CONVERGED,
+                    "field solve stopped at %d iterations, relative residual %.3e > %.3e",
+                    h->last_cg_iters, rel, rtol);
+    return AP_PIC_OK;
+}
+
+static ap_pic_status sort_particles(ap_pic *h)
+{
+    if (h->np == 0) return AP_PIC_OK;
+    const GridParams g = grid_params(h, h->cfg.dt);
+    int slot = 0;
+    const int mk = stage_begin(h, AP_PIC_STAGE_SORT);
+    CU(h, launch_sort_perm(g, h->brick, h->key_bits, h->p.cell, h->np, h->sort, &slot, h->stream));
+    CU(h, launch_apply_perm(h->sort.idx[slot], h->p, h->p_alt, h->ndim, h->stream));
+    stage_end(h, mk);
+    ParticlesF32 t = h->p;
+    h->p = h->p_alt;
+    h->p_alt = t;
+    h->perm_slot = slot;
+    return AP_PIC_OK;
+}
+
+static ap_pic_status finalize_diag(ap_pic *h, bool have_particles)
+{
+    const int mk = stage_begin(h, AP_PIC_STAGE_DIAG);
+    CU(h, launch_diag_finalize(h->dpart, have_particles, h->f, h->d_diag, h->d_accsum, h->stream));
+    stage_end(h, mk);
+    h->diag_valid = true;
+    return AP_PIC_OK;
+}
+
+// Field update after particles moved: deposit -> rho -> Poisson -> E (D06).
+static ap_pic_status field_update(ap_pic *h)
+{
+    TRY(deposit_only(h));
+    return solve_field(h);
+}
+
+static ap_pic_status half_push(ap_pic *h)
+{
+    const GridParams g = grid_params(h, -0.5 * h->cfg.dt);
+    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, false, false, DiagPartials{},
+                               h->d_err, h->stream));
+    return AP_PIC_OK;
+}
+
+static ap_pic_status after_load(ap_pic *h, unsigned flags)
+{
+    TRY(sync_check(h));
+    TRY(sort_particles(h));
+    TRY(field_update(h));
+    TRY(finalize_diag(h, false));
+    if (!(flags & AP_PIC_LOAD_NO_HALFPUSH)) TRY(half_push(h));
+    h->step = 0;
+    h->loaded = true;
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, const double *v,
+                                     unsigned flags)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    if (np < 0 || np >= (int64_t(1) << 31)) return fail(h, AP_PIC_ERR_ARG, "np out of range");
+    if (np > 0 && (!x || !v)) return fail(h, AP_PIC_ERR_ARG, "x and v are required");
+    TRY(alloc_particles(h, np));
+    const int64_t chunk = np < LOAD_CHUNK ? (np > 0 ? np : 1) : LOAD_CHUNK;
+    double *dx_buf = nullptr, *dv_buf = nullptr;
+    TRY(alloc_n(h, &dx_buf, (size_t)chunk * h->ndim));
+    TRY(alloc_n(h, &dv_buf, (size_t)chunk * h->nv));
+    const GridParams g = grid_params(h, h->cfg.dt);
+    for (int64_t first = 0; first < np; first += chunk) {
+        const int64_t cnt = np - first < chunk ? np - first : chunk;
+        CU(h, cudaMemcpyAsync(dx_buf, x + first * h->ndim, (size_t)cnt * h->ndim * 8,
+                              cudaMemcpyHostToDevice, h->stream));
+        CU(h, cudaMemcpyAsync(dv_buf, v + first * h->nv, (size_t)cnt * h->nv * 8,
+                              cudaMemcpyHostToDevice, h->stream));
+        CU(h, launch_load_convert(g, h->cfg.dx, dx_buf, dv_buf, h->p, first, cnt, h->d_err,
+                                  h->stream));
+    }
+    CU(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, dx_buf);
+    dev_free(h, dv_buf);
+    CU(h, cudaMemsetAsync(h->f.phi, 0, (size_t)h->cells * 4, h->stream));
+    return after_load(h, flags);
+}
+
+extern "C" ap_pic_status ap_pic_load_state(ap_pic *h, int64_t np, const int32_t *cell,
+                                           const float *off, const float *v, unsigned flags)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    if (np < 0 || np >= (int64_t(1) << 31)) return fail(h, AP_PIC_ERR_ARG, "np out of range");
+    if (np > 0 && (!cell || !off || !v)) return fail(h, AP_PIC_ERR_ARG, "cell, off, v required");
+    TRY(alloc_particles(h, np));
+    if (np > 0) {
+        // the alternate buffers double as staging for the row-major host layout
+        CU(h, cudaMemcpyAsync(h->p_alt.cell, cell, (size_t)np * 4, cudaMemcpyHostToDevice,
+                              h->stream));
+        CU(h, cudaMemcpyAsync(h->p_alt.off, off, (size_t)np * h->ndim * 4, cudaMemcpyHostToDevice,
+                              h->stream));
+        CU(h, cudaMemcpyAsync(h->p_alt.v, v, (size_t)np * h->nv * 4, cudaMemcpyHostToDevice,
+                              h->stream));
+        const GridParams g = grid_params(h, h->cfg.dt);
+        CU(h, launch_load_state(g, h->p_alt.cell, h->p_alt.off, h->p_alt.v, h->p, h->d_err,
+                                h->stream));
+    }
+    CU(h, cudaMemsetAsync(h->f.phi, 0, (size_t)h->cells * 4, h->stream));
+    return after_load(h, flags);
+}
+
+static ap_pic_status need_loaded(ap_pic *h)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    if (!h->loaded) return fail(h, AP_PIC_ERR_STATE, "no particles loaded");
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_gather_push(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    const GridParams g = grid_params(h, h->cfg.dt);
+    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, true, false, h->dpart, h->d_err,
+                               h->stream));
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_deposit(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    return deposit_only(h);
+}
+
+static ap_pic_status push_deposit(ap_pic *h, bool diag)
+{
+    CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
+    const GridParams g = grid_params(h, h->cfg.dt);
+    const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
+    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, true, true,
+                               diag ? h->dpart : DiagPartials{}, h->d_err, h->stream));
+    stage_end(h, mk);
+    return convert_rho(h);
+}
+
+extern "C" ap_pic_status ap_pic_push_deposit(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    return push_deposit(h, true);
+}
+
+extern "C" ap_pic_status ap_pic_solve_field(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    return solve_field(h);
+}
+
+extern "C" ap_pic_status ap_pic_sort(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    return sort_particles(h);
+}
+
+extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
+{
+    TRY(need_loaded(h));
+    if (nsteps < 0) return fail(h, AP_PIC_ERR_ARG, "nsteps must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        const int64_t k = h->step + 1;
+        const bool diag = (k % h->cfg.diag_every) == 0;
+        TRY(push_deposit(h, diag));
+        if (h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0) TRY(sort_particles(h));
+        TRY(solve_field(h));
+        if (diag) TRY(finalize_diag(h, true));
+        h->step = k;
+    }
+    return AP_PIC_OK;
+}
+
+// ---- read-back -------------------------------------------------------------------------------
+
+extern "C" ap_pic_status ap_pic_get_rho(ap_pic *h, double *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    CU(h, cudaMemcpyAsync(out, h->f.rho, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_rho_fx(ap_pic *h, int64_t *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    CU(h, cudaMemcpyAsync(out, h->f.acc, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_E(ap_pic *h, double *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    double *tmp = nullptr;
+    TRY(alloc_n(h, &tmp, (size_t)h->cells * h->ndim));
+    CU(h, launch_e_to_f64(h->f, tmp, h->stream));
+    CU(h, cudaMemcpyAsync(out, tmp, (size_t)h->cells * h->ndim * 8, cudaMemcpyDeviceToHost,
+                          h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, tmp);
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_phi(ap_pic *h, double *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    double *tmp = nullptr;
+    TRY(alloc_n(h, &tmp, (size_t)h->cells));
+    CU(h, launch_phi_to_f64(h->f, tmp, h->stream));
+    CU(h, cudaMemcpyAsync(out, tmp, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, tmp);
+    // phi is defined up to a constant; report the zero-mean representative
+    double mean = 0.0;
+    for (int64_t i = 0; i < h->cells; ++i) mean += out[i];
+    mean /= (double)h->cells;
+    for (int64_t i = 0; i < h->cells; ++i) out[i] -= mean;
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_particles(ap_pic *h, int32_t *cell, float *off, float *v,
+                                              double *x)
+{
+    TRY(need_loaded(h));
+    const int64_t np = h->np;
+    if (np == 0) return AP_PIC_OK;
+    if (cell)
+        CU(h, cudaMemcpyAsync(cell, h->p.cell, (size_t)np * 4, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<float> tmp;
+    if (off) {
+        tmp.resize((size_t)np * h->ndim);
+        CU(h, cudaMemcpyAsync(tmp.data(), h->p.off, tmp.size() * 4, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        for (int64_t i = 0; i < np; ++i)
+            for (int a = 0; a < h->ndim; ++a) off[i * h->ndim + a] = tmp[(size_t)a * np + i];
+    }
+    if (v) {
+        tmp.resize((size_t)np * h->nv);
+        CU(h, cudaMemcpyAsync(tmp.data(), h->p.v, tmp.size() * 4, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        for (int64_t i = 0; i < np; ++i)
+            for (int a = 0; a < h->nv; ++a) v[i * h->nv + a] = tmp[(size_t)a * np + i];
+    }
+    if (x) {
+        double *dxp = nullptr;
+        TRY(alloc_n(h, &dxp, (size_t)np * h->ndim));
+        const GridParams g = grid_params(h, h->cfg.dt);
+        CU(h, launch_positions_f64(g, h->cfg.dx, h->p, dxp, h->stream));
+        CU(h, cudaMemcpyAsync(x, dxp, (size_t)np * h->ndim * 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        dev_free(h, dxp);
+    }
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_velocities_f64(ap_pic *h, double *v)
+{
+    if (!h || !v) return AP_PIC_ERR_ARG;
+    return fail(h, AP_PIC_ERR_UNSUPPORTED, "only the FP64 plain form stores FP64 velocities");
+}
+
+extern "C" ap_pic_status ap_pic_get_perm(ap_pic *h, int64_t *perm)
+{
+    TRY(need_loaded(h));
+    if (!perm) return fail(h, AP_PIC_ERR_ARG, "perm is NULL");
+    if (h->perm_slot < 0) return fail(h, AP_PIC_ERR_STATE, "no sort has run");
+    std::vector<uint32_t> tmp((size_t)h->np);
+    if (h->np)
+        CU(h, cudaMemcpyAsync(tmp.data(), h->sort.idx[h->perm_slot], (size_t)h->np * 4,
+                              cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < h->np; ++i) perm[i] = tmp[(size_t)i];
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    memset(out, 0, sizeof *out);
+    CU(h, cudaMemcpyAsync(h->h_diag, h->d_diag, 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CU(h, cudaMemcpyAsync(h->h_accsum, h->d_accsum, sizeof(long long), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CU(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    const double mw = h->cfg.m * h->cfg.weight;
+    out->step = h->step;
+    out->t = (double)h->step * h->cfg.dt;
+    out->np = h->np;
+    out->fx_bits = h->fx_bits;
+    out->charge_fx_sum = *h->h_accsum;
+    out->total_charge = h->cfg.q * h->cfg.weight * ldexp((double)*h->h_accsum, -h->fx_bits);
+    out->kinetic = 0.5 * mw * h->h_diag[0];
+    for (int a = 0; a < 3; ++a) out->momentum[a] = mw * h->h_diag[1 + a];
+    out->field_energy = 0.5 * h->dV * h->h_diag[4];
+    out->cg_iters = h->last_cg_iters;
+    out->cg_relres = h->last_cg_relres;
+    out->error_flags = *h->h_err;
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_set_timing(ap_pic *h, int enable)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    drain_marks(h);
+    for (int k = 0; k < AP_PIC_NSTAGES; ++k) {
+        h->stage_ms[k] = 0.0;
+        h->stage_n[k] = 0;
+    }
+    h->timing = enable != 0;
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_get_timing(ap_pic *h, double *ms, int64_t *count)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    drain_marks(h);
+    for (int k = 0; k < AP_PIC_NSTAGES; ++k) {
+        if (ms) ms[k] = h->stage_ms[k];
+        if (count) count[k] = h->stage_n[k];
+    }
+    return AP_PIC_OK;
+}
+
+extern "C" int64_t ap_pic_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int64_t ap_pic_num_particles(const ap_pic *h) { return h ? h->np : 0; }
+
+extern "C" const char *ap_pic_last_error(const ap_pic *h) { return h ? h->err.c_str() : ""; }
+
+extern "C" const char *ap_pic_version(void) { return "ap_pic 0.1 (sm_103a)"; }

@@ -1,0 +1,411 @@
+// pic_field.cu -- grid side of the electrostatic PIC cycle: conversion of the
+// int64 fixed-point charge to rho, the periodic Poisson solve
+// -lap_h(phi) = rho - mean(rho) by Jacobi-preconditioned conjugate gradients
+// (D_Poisson, Sec. 2.2; module D02 in Sec. 3.1), E = -grad_h(phi) by centred
+// differences (D06), and the diagnostics reductions.
+//
+// Precision: CG vectors are FP32; every dot product is accumulated in FP64
+// and reduced deterministically (fixed per-block order, then every block that
+// needs the total re-reduces the block partials in the same fixed order, so
+// all blocks see bit-identical scalars without an extra launch).
+// The Jacobi preconditioner of the constant-coefficient Laplacian is the
+// constant diagonal 2 sum_a 1/dx_a^2.
+#include <math.h>
+
+#include "pic_internal.cuh"
+
+namespace apk {
+
+constexpr int FT = 256;  // threads per block of the grid kernels
+
+// Device scalar slots.
+enum : int { SC_BNORM = 0, SC_RZ0 = 1, SC_RZ1 = 2, SC_RELRES = 3, SC_NSCAL = 8 };
+
+int field_blocks(int64_t cells)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    int64_t need = (cells + FT - 1) / FT;
+    int64_t cap = (int64_t)sms * 4;
+    int64_t b = need < cap ? need : cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Sum over the block in a fixed order; result valid in every thread.
+__device__ double block_sum(double x)
+{
+    __shared__ double red[FT / 32];
+    __shared__ double total;
+    x = warp_sum(x);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int j = 0; j < FT / 32; ++j) t += red[j];
+        total = t;
+    }
+    __syncthreads();
+    const double r = total;
+    __syncthreads();
+    return r;
+}
+
+__device__ long long block_sum_ll(long long x)
+{
+    __shared__ long long red[FT / 32];
+    __shared__ long long total;
+    x = warp_sum_ll(x);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int j = 0; j < FT / 32; ++j) t += red[j];
+        total = t;
+    }
+    __syncthreads();
+    const long long r = total;
+    __syncthreads();
+    return r;
+}
+
+// Sum of `n` block partials in a fixed order (identical in every block).
+__device__ double reduce_partials(const double *__restrict__ part, int n)
+{
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += FT) s += part[j];
+    return block_sum(s);
+}
+
+// Node coordinates from a flat index (axis 0 fastest).
+__device__ __forceinline__ void node_coords(int64_t id, const FieldBufs &f, int *j)
+{
+    j[0] = (int)(id % f.n[0]);
+    const int64_t r = id / f.n[0];
+    j[1] = f.ndim >= 2 ? (int)(r % f.n[1]) : 0;
+    j[2] = f.ndim >= 3 ? (int)(r / f.n[1]) : 0;
+}
+
+// (-lap_h u)[id] on the periodic grid.
+__device__ __forceinline__ float neg_lap(const float *__restrict__ u, int64_t id, const int *j,
+                                         const FieldBufs &f, const float *idx2)
+{
+    const float c = u[id];
+    float acc = 0.0f;
+    int64_t stride = 1;
+    for (int a = 0; a < f.ndim; ++a) {
+        const int na = f.n[a];
+        const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
+        const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
+        acc += (2.0f * c - u[up] - u[dn]) * idx2[a];
+        stride *= na;
+    }
+    return acc;
+}
+
+// ---- charge conversion ----------------------------------------------------------------------
+
+__global__ void __launch_bounds__(FT)
+    k_rho_convert(FieldBufs f, double scale, double bg, double mean_e)
+{
+    long long isum = 0;
+    for (int64_t j = (int64_t)blockIdx.x * FT + threadIdx.x; j < f.cells;
+         j += (int64_t)gridDim.x * FT) {
+        const long long a = (long long)f.acc[j];
+        isum += a;
+        const double re = scale * (double)a;
+        f.rho[j] = re + bg;
+        f.b[j] = (float)(re - mean_e);
+    }
+    const long long t = block_sum_ll(isum);
+    if (threadIdx.x == 0) f.isum_part[blockIdx.x] = t;
+}
+
+cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mean_e, bool,
+                               cudaStream_t st)
+{
+    k_rho_convert<<<f.nblocks, FT, 0, st>>>(f, scale, bg, mean_e);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- CG -------------------------------------------------------------------------------------
+
+struct Lap {
+    float idx2[3];  // 1 / dx_a^2
+    float inv_diag; // 1 / (2 sum_a 1/dx_a^2)
+};
+
+static Lap make_lap(const FieldBufs &f)
+{
+    Lap L;
+    double d = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        L.idx2[a] = a < f.ndim ? (float)(1.0 / (f.dx[a] * f.dx[a])) : 0.0f;
+        if (a < f.ndim) d += 2.0 / (f.dx[a] * f.dx[a]);
+    }
+    L.inv_diag = (float)(1.0 / d);
+    return L;
+}
+
+// r = b - A phi;  p = M^-1 r;  partials of r.r and b.b.
+__global__ void __launch_bounds__(FT) k_cg_init(FieldBufs f, Lap L)
+{
+    double rr = 0.0, bb = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT) {
+        int j[3];
+        node_coords(id, f, j);
+        const float bi = f.b[id];
+        const float ri = bi - neg_lap(f.phi, id, j, f, L.idx2);
+        f.r[id] = ri;
+        f.p[id] = ri * L.inv_diag;
+        rr += (double)ri * ri;
+        bb += (double)bi * bi;
+    }
+    rr = block_sum(rr);
+    bb = block_sum(bb);
+    if (threadIdx.x == 0) {
+        f.part[0][blockIdx.x] = rr;
+        f.part[2][blockIdx.x] = bb;
+    }
+}
+
+__global__ void __launch_bounds__(FT) k_cg_init_fin(FieldBufs f, Lap L, double rtol)
+{
+    const double rr = reduce_partials(f.part[0], f.nblocks);
+    const double bb = reduce_partials(f.part[2], f.nblocks);
+    if (threadIdx.x == 0) {
+        const double bn = sqrt(bb);
+        f.scal[SC_BNORM] = bn;
+        f.scal[SC_RZ0] = rr * (double)L.inv_diag;
+        const double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+        f.scal[SC_RELRES] = rel;
+        *f.iters = 0;
+        *f.done = (bn == 0.0 || rel <= rtol) ? 1 : 0;
+    }
+}
+
+// q = A p;  partial p.q -> part[0].
+__global__ void __launch_bounds__(FT) k_cg_matvec(FieldBufs f, Lap L)
+{
+    if (*f.done) return;
+    double pq = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT) {
+        int j[3];
+        node_coords(id, f, j);
+        const float qi = neg_lap(f.p, id, j, f, L.idx2);
+        f.q[id] = qi;
+        pq += (double)f.p[id] * qi;
+    }
+    pq = block_sum(pq);
+    if (threadIdx.x == 0) f.part[0][blockIdx.x] = pq;
+}
+
+// alpha = rz / p.q;  phi += alpha p;  r -= alpha q;  partial r.r -> part[1].
+__global__ void __launch_bounds__(FT) k_cg_update(FieldBufs f, int it)
+{
+    if (*f.done) return;
+    const double pq = reduce_partials(f.part[0], f.nblocks);
+    const double rz = f.scal[SC_RZ0 + (it & 1)];
+    const float alpha = (float)(rz / pq);
+    double rr = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT) {
+        f.phi[id] += alpha * f.p[id];
+        const float ri = f.r[id] - alpha * f.q[id];
+        f.r[id] = ri;
+        rr += (double)ri * ri;
+    }
+    rr = block_sum(rr);
+    if (threadIdx.x == 0) f.part[1][blockIdx.x] = rr;
+}
+
+// beta = rz_new / rz;  p = M^-1 r + beta p;  convergence test.
+__global__ void __launch_bounds__(FT) k_cg_dir(FieldBufs f, Lap L, int it, int maxit, double rtol)
+{
+    if (*f.done) return;
+    const double rr = reduce_partials(f.part[1], f.nblocks);
+    const double rz_new = rr * (double)L.inv_diag;
+    const double rz = f.scal[SC_RZ0 + (it & 1)];
+    const double rel = sqrt(rr) / f.scal[SC_BNORM];
+    const bool stop = rel <= rtol || it + 1 >= maxit;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        f.scal[SC_RZ0 + ((it + 1) & 1)] = rz_new;
+        f.scal[SC_RELRES] = rel;
+        *f.iters = it + 1;
+        if (stop) *f.done = 1;
+    }
+    if (stop) return;
+    const float beta = (float)(rz_new / rz);
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT)
+        f.p[id] = f.r[id] * L.inv_diag + beta * f.p[id];
+}
+
+__global__ void k_cg_finish(FieldBufs f, double rtol, int *err)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (f.scal[SC_RELRES] > rtol) atomicOr(err, EF_CG);
+    }
+}
+
+cudaError_t launch_cg_init(FieldBufs &f, double rtol, cudaStream_t st)
+{
+    const Lap L = make_lap(f);
+    k_cg_init<<<f.nblocks, FT, 0, st>>>(f, L);
+    note_launch();
+    k_cg_init_fin<<<1, FT, 0, st>>>(f, L, rtol);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_iters(FieldBufs &f, int first, int count, int maxit, double rtol,
+                            cudaStream_t st)
+{
+    const Lap L = make_lap(f);
+    for (int it = first; it < first + count && it < maxit; ++it) {
+        k_cg_matvec<<<f.nblocks, FT, 0, st>>>(f, L);
+        note_launch();
+        k_cg_update<<<f.nblocks, FT, 0, st>>>(f, it);
+        note_launch();
+        k_cg_dir<<<f.nblocks, FT, 0, st>>>(f, L, it, maxit, rtol);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err, cudaStream_t st)
+{
+    k_cg_finish<<<1, 32, 0, st>>>(f, rtol, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- E = -grad phi ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(FT) k_efield(FieldBufs f, float h0, float h1, float h2)
+{
+    const float h[3] = {h0, h1, h2};  // 1 / (2 dx_a)
+    double fe = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT) {
+        int j[3];
+        node_coords(id, f, j);
+        float e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int64_t stride = 1;
+        for (int a = 0; a < f.ndim; ++a) {
+            const int na = f.n[a];
+            const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
+            const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
+            e[a] = -(f.phi[up] - f.phi[dn]) * h[a];
+            fe += (double)e[a] * e[a];
+            stride *= na;
+        }
+        if (f.Estride == 1) {
+            f.E[id] = e[0];
+        } else if (f.Estride == 2) {
+            reinterpret_cast<float2 *>(f.E)[id] = make_float2(e[0], e[1]);
+        } else {
+            reinterpret_cast<float4 *>(f.E)[id] = make_float4(e[0], e[1], e[2], 0.0f);
+        }
+    }
+    fe = block_sum(fe);
+    if (threadIdx.x == 0) f.fe_part[blockIdx.x] = fe;
+}
+
+cudaError_t launch_efield(FieldBufs &f, cudaStream_t st)
+{
+    float h[3] = {0.0f, 0.0f, 0.0f};
+    for (int a = 0; a < f.ndim; ++a) h[a] = (float)(0.5 / f.dx[a]);
+    k_efield<<<f.nblocks, FT, 0, st>>>(f, h[0], h[1], h[2]);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- diagnostics -----------------------------------------------------------------------------
+
+// out: [0] sum (|v_old|^2 + |v_new|^2)/2, [1..3] sum v, [4] sum |E|^2, [5] relres,
+// [6] iterations (as double);  acc_sum_out: sum of the accumulator.
+__global__ void __launch_bounds__(FT)
+    k_diag_finalize(const double *__restrict__ pblocks, int npb, FieldBufs f, double *out,
+                    long long *acc_sum_out)
+{
+    for (int k = 0; k < 4; ++k) {
+        double s = 0.0;
+        if (pblocks)
+            for (int j = threadIdx.x; j < npb; j += FT) s += pblocks[j * 4 + k];
+        s = block_sum(s);
+        if (threadIdx.x == 0 && pblocks) out[k] = s;
+    }
+    const double fe = reduce_partials(f.fe_part, f.nblocks);
+    long long is = 0;
+    for (int j = threadIdx.x; j < f.nblocks; j += FT) is += f.isum_part[j];
+    is = block_sum_ll(is);
+    if (threadIdx.x == 0) {
+        out[4] = fe;
+        out[5] = f.scal[SC_RELRES];
+        out[6] = (double)*f.iters;
+        *acc_sum_out = is;
+    }
+}
+
+cudaError_t launch_diag_finalize(const DiagPartials &pd, bool have_particles, FieldBufs &f,
+                                 double *out, long long *acc_sum_out, cudaStream_t st)
+{
+    k_diag_finalize<<<1, FT, 0, st>>>(have_particles ? pd.blocks : nullptr, pd.nblocks, f, out,
+                                      acc_sum_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- read-back helpers -----------------------------------------------------------------------
+
+__global__ void k_e_to_f64(FieldBufs f, double *__restrict__ out)
+{
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < f.ndim; ++a) out[a * f.cells + id] = f.E[id * f.Estride + a];
+}
+
+cudaError_t launch_e_to_f64(FieldBufs &f, double *out, cudaStream_t st)
+{
+    k_e_to_f64<<<f.nblocks, FT, 0, st>>>(f, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_phi_to_f64(FieldBufs f, double *__restrict__ out)
+{
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * blockDim.x)
+        out[id] = f.phi[id];
+}
+
+cudaError_t launch_phi_to_f64(FieldBufs &f, double *out, cudaStream_t st)
+{
+    k_phi_to_f64<<<f.nblocks, FT, 0, st>>>(f, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace apk

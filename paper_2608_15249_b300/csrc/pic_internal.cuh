@@ -1,0 +1,189 @@
+// pic_internal.cuh -- shared declarations of the CUDA translation units of the
+// electrostatic PIC library (device-side parameter blocks, launcher
+// prototypes).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ap_pic.h"
+
+namespace apk {
+
+// Counts kernel launches (process-wide); every launcher calls it once per kernel.
+void note_launch(int n = 1);
+
+// Everything a particle kernel needs about the grid and the push, by value.
+struct GridParams {
+    int ndim;
+    int n[3];          // nodes per axis (unused axes 1)
+    float dtdx[3];     // dt / dx_a in FP32 (position update in cell units)
+    float qmh2;        // (q/m) h / 2 for the step h of this launch
+    float E0[3];       // uniform external field
+    float t[3];        // Boris t = (q/m) B0 h / 2
+    float s[3];        // Boris s = 2 t / (1 + |t|^2)
+    int fx_bits;       // S
+    int magnetised;    // B0 != 0
+};
+
+// Error bits latched in the device word (same values as AP_PIC_EFLAG_*).
+enum : int { EF_NONFINITE = 1, EF_CG = 2, EF_OVERFLOW = 4 };
+
+// ---- particle kernels (pic_particles.cu) --------------------------------------------------
+struct ParticlesF32 {
+    int32_t *cell;     // [np]
+    float *off;        // [ndim][np]
+    float *v;          // [nv][np]
+    int64_t np;
+    int nv;
+};
+
+struct DiagPartials {
+    double *blocks;    // [nblocks][4]: kinetic, momentum x, y, z
+    int nblocks;
+};
+
+// Converts host-layout FP64 positions/velocities (row-major, one chunk) into
+// cell + FP32 offset + FP32 velocity storage at [first, first + count).
+cudaError_t launch_load_convert(const GridParams &g, const double *dx, const double *x,
+                                const double *v, ParticlesF32 p, int64_t first, int64_t count,
+                                int *err_flags, cudaStream_t st);
+
+// Copies an exact FP32 state (row-major host layout already on the device).
+cudaError_t launch_load_state(const GridParams &g, const int32_t *cell, const float *off,
+                              const float *v, ParticlesF32 p, int *err_flags, cudaStream_t st);
+
+// One pass over the particles: optional gather+Boris push (step h encoded in g),
+// optional move, optional deposit into acc, optional diagnostics partials.
+cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const float *E,
+                                 unsigned long long *acc, bool push, bool move, bool deposit,
+                                 DiagPartials diag, int *err_flags, cudaStream_t st);
+
+// Number of blocks the particle pass uses for np particles (fixed, so the
+// diagnostics reduction order is deterministic).
+int particle_pass_blocks(int64_t np);
+
+// Reconstruct positions (FP64) from cell + offset for host read-back.
+cudaError_t launch_positions_f64(const GridParams &g, const double *dx, ParticlesF32 p,
+                                 double *x, cudaStream_t st);
+
+// ---- FP64 plain form (pic_plain.cu) --------------------------------------------------------
+struct ParticlesF64 {
+    double *x;         // [ndim][np]
+    double *v;         // [nv][np]
+    int64_t np;
+    int nv;
+};
+
+struct GridParamsF64 {
+    int ndim;
+    int n[3];
+    double dx[3];
+    double inv_dx[3];
+    double L[3];
+    double dt;
+    double qmh2;
+    double E0[3], t[3], s[3];
+    int fx_bits;
+    int magnetised;
+};
+
+cudaError_t launch_plain_load(const GridParamsF64 &g, const double *x, const double *v,
+                              ParticlesF64 p, int64_t first, int64_t count, int *err_flags,
+                              cudaStream_t st);
+cudaError_t launch_plain_pass(const GridParamsF64 &g, ParticlesF64 p, const double *E,
+                              unsigned long long *acc, bool push, bool move, bool deposit,
+                              DiagPartials diag, int *err_flags, cudaStream_t st);
+
+// ---- sort (pic_sort.cu) ---------------------------------------------------------------------
+struct SortScratch {
+    uint32_t *keys[2];
+    uint32_t *idx[2];
+    uint32_t *hist;        // 256 * ntiles
+    uint32_t *scan_tmp;    // scan partials
+    size_t scan_tmp_len;
+    int64_t capacity;      // particles
+};
+
+size_t sort_hist_len(int64_t np);
+size_t sort_scan_tmp_len(size_t n);
+
+// Computes keys, sorts (stable LSD radix, 8-bit digits) and leaves the final
+// permutation in s.idx[*perm_slot]; returns which slot through perm_slot.
+cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bits,
+                             const int32_t *cell, int64_t np, SortScratch &s, int *perm_slot,
+                             cudaStream_t st);
+// dst[r] = src[perm[r]] for the SoA particle record.
+cudaError_t launch_apply_perm(const uint32_t *perm, ParticlesF32 src, ParticlesF32 dst,
+                              int ndim, cudaStream_t st);
+cudaError_t launch_exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp,
+                                      cudaStream_t st);
+
+// ---- field (pic_field.cu) -------------------------------------------------------------------
+struct FieldBufs {
+    int ndim;
+    int n[3];
+    int64_t cells;
+    double dx[3];
+    unsigned long long *acc;   // int64 fixed point
+    double *rho;               // total charge density (FP64)
+    float *b;                  // rho - mean(rho), FP32
+    float *phi, *r, *p, *q;    // CG vectors
+    float *E;                  // interleaved, stride Estride floats per node
+    int Estride;
+    double *part[3];           // reduction partials (ping-pong + spare), nblocks each
+    int nblocks;
+    double *scal;              // device scalars, see pic_field.cu
+    int *done;                 // CG done flag
+    int *iters;                // CG iteration count
+    long long *isum_part;      // int64 partials for the accumulator sum
+    double *fe_part;           // field-energy partials
+};
+
+int field_blocks(int64_t cells);
+
+// rho = scale * acc + bg;  b = scale * acc - mean_e;  partial sums of acc.
+cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mean_e,
+                               bool zero_acc, cudaStream_t st);
+// CG set-up from the current phi (warm start); returns nothing to the host.
+cudaError_t launch_cg_init(FieldBufs &f, double rtol, cudaStream_t st);
+// `count` CG iterations starting at iteration `first` (device early-exit once
+// converged or at maxit).
+cudaError_t launch_cg_iters(FieldBufs &f, int first, int count, int maxit, double rtol,
+                            cudaStream_t st);
+cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err_flags, cudaStream_t st);
+cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
+// Finalise diagnostics: reduce particle partials, accumulator sum, field energy
+// into out[0..7] = {kinetic, px, py, pz, field_energy, acc_sum (as bits), -, -}.
+cudaError_t launch_diag_finalize(const DiagPartials &pd, bool have_particles, FieldBufs &f,
+                                 double *out, long long *acc_sum_out, cudaStream_t st);
+cudaError_t launch_e_to_f64(FieldBufs &f, double *out, cudaStream_t st);
+cudaError_t launch_phi_to_f64(FieldBufs &f, double *out, cudaStream_t st);
+
+// ---- FP64 plain field path (pic_plain.cu) ---------------------------------------------------
+struct FieldBufsF64 {
+    int ndim;
+    int n[3];
+    int64_t cells;
+    double dx[3];
+    unsigned long long *acc;
+    double *rho, *b, *phi, *r, *p, *q, *E;   // E component-major [ndim][cells]
+    double *part[3];
+    int nblocks;
+    double *scal;
+    int *done, *iters;
+    long long *isum_part;
+    double *fe_part;
+};
+cudaError_t launch_plain_rho_convert(FieldBufsF64 &f, double scale, double bg, double mean_e,
+                                     cudaStream_t st);
+cudaError_t launch_plain_cg_init(FieldBufsF64 &f, double rtol, cudaStream_t st);
+cudaError_t launch_plain_cg_iters(FieldBufsF64 &f, int first, int count, int maxit, double rtol,
+                                  cudaStream_t st);
+cudaError_t launch_plain_cg_finish(FieldBufsF64 &f, double rtol, int *err_flags, cudaStream_t st);
+cudaError_t launch_plain_efield(FieldBufsF64 &f, cudaStream_t st);
+cudaError_t launch_plain_diag_finalize(const DiagPartials &pd, bool have_particles,
+                                       FieldBufsF64 &f, double *out, long long *acc_sum_out,
+                                       cudaStream_t st);
+
+}  // namespace apk

@@ -1,0 +1,309 @@
+// pic_sort.cu -- stable per-cell sort of the particles (a layout step: the
+// paper does not name one; it keeps gather and deposit accesses local).
+//
+// Key: brick-major cell index.  The grid is tiled by bricks of b0 x b1 x b2
+// cells (the last brick on an axis may be partial):
+//   key = brick_id * (b0 b1 b2) + local_id,
+//   brick_id = c0/b0 + nb0 (c1/b1 + nb1 c2/b2),   nb_a = ceil(n_a / b_a),
+//   local_id = c0%b0 + b0 (c1%b1 + b1 c2%b2).
+// Sort: least-significant-digit radix sort over (key, index) pairs with 8-bit
+// digits.  Each pass is stable (per-tile digit histograms, a device-wide
+// exclusive scan in digit-major order, and a scatter whose in-tile ranks keep
+// input order), so the result is the unique stable permutation.  The
+// particle record is then gathered through the permutation.
+#include "pic_internal.cuh"
+
+namespace apk {
+
+constexpr int ST_THREADS = 256;
+constexpr int ST_WARPS = ST_THREADS / 32;
+constexpr int ST_ITEMS = 16;
+constexpr int ST_TILE = ST_THREADS * ST_ITEMS;  // 4096 items per tile
+constexpr int RADIX = 256;
+constexpr int NO_DIGIT = RADIX;                 // marks an item past the end
+
+static int64_t tiles_of(int64_t np) { return (np + ST_TILE - 1) / ST_TILE; }
+
+size_t sort_hist_len(int64_t np) { return (size_t)RADIX * (size_t)tiles_of(np); }
+
+// ---- keys ----------------------------------------------------------------------------------
+
+__global__ void k_keys(int ndim, int n0, int n1, int b0, int b1, int b2, int nb0, int nb1,
+                       const int32_t *__restrict__ cell, int64_t np, uint32_t *__restrict__ keys)
+{
+    const uint32_t bcells = (uint32_t)b0 * b1 * b2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cell[i];
+        int c0, c1 = 0, c2 = 0;
+        if (ndim == 1) {
+            c0 = c;
+        } else if (ndim == 2) {
+            c1 = c / n0;
+            c0 = c - c1 * n0;
+        } else {
+            const int c12 = c / n0;
+            c0 = c - c12 * n0;
+            c2 = c12 / n1;
+            c1 = c12 - c2 * n1;
+        }
+        const uint32_t bid = (uint32_t)(c0 / b0) + (uint32_t)nb0 * ((uint32_t)(c1 / b1) +
+                                                                   (uint32_t)nb1 * (c2 / b2));
+        const uint32_t lid = (uint32_t)(c0 % b0) + (uint32_t)b0 * ((uint32_t)(c1 % b1) +
+                                                                  (uint32_t)b1 * (c2 % b2));
+        keys[i] = bid * bcells + lid;
+    }
+}
+
+// ---- per-tile digit histogram ----------------------------------------------------------------
+
+__global__ void __launch_bounds__(ST_THREADS)
+    k_hist(const uint32_t *__restrict__ keys, int64_t np, int shift, uint32_t *__restrict__ hist,
+           int64_t ntiles)
+{
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * ST_TILE;
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int k = 0; k < ST_ITEMS; ++k) {
+        const int64_t i = base + (int64_t)k * ST_THREADS + threadIdx.x;
+        const int d = i < np ? (int)((keys[i] >> shift) & (RADIX - 1)) : NO_DIGIT;
+        const unsigned m = __match_any_sync(0xffffffffu, d);
+        if (d != NO_DIGIT && lane == __ffs(m) - 1) atomicAdd(&h[d], (uint32_t)__popc(m));
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// ---- stable scatter --------------------------------------------------------------------------
+
+// Warp w of a tile owns the contiguous items [w*512, (w+1)*512) of the tile and
+// walks them in 16 rounds of 32, so (warp, round, lane) order is input order.
+__global__ void __launch_bounds__(ST_THREADS)
+    k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
+              int shift, const uint32_t *__restrict__ offs, int64_t ntiles,
+              uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
+{
+    __shared__ uint32_t wcount[ST_WARPS][RADIX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < ST_WARPS * RADIX; j += ST_THREADS) (&wcount[0][0])[j] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * ST_TILE + (int64_t)w * (ST_ITEMS * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t key[ST_ITEMS], rank[ST_ITEMS];
+    int dig[ST_ITEMS];
+#pragma unroll
+    for (int r = 0; r < ST_ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = i < np ? keys_in[i] : 0u;
+        const int d = i < np ? (int)((key[r] >> shift) & (RADIX - 1)) : NO_DIGIT;
+        dig[r] = d;
+        const unsigned m = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (d != NO_DIGIT) before = wcount[w][d];
+        rank[r] = before + (uint32_t)__popc(m & lt);
+        __syncwarp();
+        if (d != NO_DIGIT && (m & lt) == 0) wcount[w][d] = before + (uint32_t)__popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // ST_THREADS == RADIX
+        uint32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
+        for (int ww = 0; ww < ST_WARPS; ++ww) {
+            const uint32_t t = wcount[ww][d];
+            wcount[ww][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ST_ITEMS; ++r) {
+        if (dig[r] == NO_DIGIT) continue;
+        const int64_t i = base + r * 32 + lane;
+        const uint32_t pos = wcount[w][dig[r]] + rank[r];
+        if (keys_out) keys_out[pos] = key[r];
+        idx_out[pos] = idx_in ? idx_in[i] : (uint32_t)i;
+    }
+}
+
+// ---- device-wide exclusive scan of u32 (three phases, recursive on the partials) ------------
+
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 16;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+size_t sort_scan_tmp_len(size_t n)
+{
+    size_t total = 0;
+    while (n > (size_t)SC_TILE) {
+        n = (n + SC_TILE - 1) / SC_TILE;
+        total += n;
+    }
+    return total + 1;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of one tile held 16 consecutive items per thread; returns the
+// tile total in *total (all threads).
+__device__ void block_excl_scan(uint32_t (&v)[SC_ITEMS], uint32_t *total)
+{
+    __shared__ uint32_t wsum[SC_THREADS / 32];
+    uint32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        const uint32_t t = v[k];
+        v[k] = run;
+        run += t;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_scan(run);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, tot = 0;
+    for (int j = 0; j < SC_THREADS / 32; ++j) {
+        if (j < w) wbase += wsum[j];
+        tot += wsum[j];
+    }
+    const uint32_t excl = wbase + incl - run;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) v[k] += excl;
+    *total = tot;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SC_THREADS)
+    k_scan_reduce(const uint32_t *__restrict__ in, size_t n, uint32_t *__restrict__ sums)
+{
+    const size_t base = (size_t)blockIdx.x * SC_TILE + (size_t)threadIdx.x * SC_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    __shared__ uint32_t red[SC_THREADS / 32];
+    s = warp_incl_scan(s);
+    if ((threadIdx.x & 31) == 31) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int j = 0; j < SC_THREADS / 32; ++j) t += red[j];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(SC_THREADS)
+    k_scan_down(const uint32_t *__restrict__ in, size_t n, const uint32_t *__restrict__ block_off,
+                uint32_t *__restrict__ out)
+{
+    const size_t base = (size_t)blockIdx.x * SC_TILE + (size_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    uint32_t total;
+    block_excl_scan(v, &total);
+    const uint32_t off = block_off ? block_off[blockIdx.x] : 0u;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k)
+        if (base + k < n) out[base + k] = v[k] + off;
+}
+
+cudaError_t launch_exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp,
+                                      cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb == 1) {
+        k_scan_down<<<1, SC_THREADS, 0, st>>>(in, n, nullptr, out);
+        note_launch();
+        return cudaGetLastError();
+    }
+    uint32_t *sums = tmp;
+    uint32_t *rest = tmp + nb;
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, sums);
+    note_launch();
+    cudaError_t e = launch_exclusive_scan_u32(sums, sums, nb, rest, st);
+    if (e != cudaSuccess) return e;
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, n, sums, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bits,
+                             const int32_t *cell, int64_t np, SortScratch &s, int *perm_slot,
+                             cudaStream_t st)
+{
+    if (np <= 0) {
+        *perm_slot = 0;
+        return cudaSuccess;
+    }
+    const int b0 = brick[0], b1 = g.ndim >= 2 ? brick[1] : 1, b2 = g.ndim >= 3 ? brick[2] : 1;
+    const int nb0 = (g.n[0] + b0 - 1) / b0;
+    const int nb1 = g.ndim >= 2 ? (g.n[1] + b1 - 1) / b1 : 1;
+    int64_t kb = (np + 255) / 256;
+    if (kb > 65535) kb = 65535;
+    k_keys<<<(int)kb, 256, 0, st>>>(g.ndim, g.n[0], g.n[1], b0, b1, b2, nb0, nb1, cell, np,
+                                     s.keys[0]);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = tiles_of(np);
+    const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_hist<<<(unsigned)ntiles, ST_THREADS, 0, st>>>(s.keys[cur], np, shift, s.hist, ntiles);
+        note_launch();
+        e = launch_exclusive_scan_u32(s.hist, s.hist, (size_t)RADIX * ntiles, s.scan_tmp, st);
+        if (e != cudaSuccess) return e;
+        const bool last = pass == passes - 1;
+        k_scatter<<<(unsigned)ntiles, ST_THREADS, 0, st>>>(
+            s.keys[cur], pass == 0 ? nullptr : s.idx[cur], np, shift, s.hist, ntiles,
+            last ? nullptr : s.keys[cur ^ 1], s.idx[cur ^ 1]);
+        note_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    *perm_slot = cur;
+    return cudaSuccess;
+}
+
+// ---- gather the record through the permutation ----------------------------------------------
+
+__global__ void k_apply_perm(const uint32_t *__restrict__ perm, ParticlesF32 src, ParticlesF32 dst,
+                             int ndim)
+{
+    const int64_t np = src.np;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < np;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = perm[r];
+        dst.cell[r] = src.cell[j];
+        for (int a = 0; a < ndim; ++a) dst.off[a * np + r] = src.off[a * np + j];
+        for (int a = 0; a < src.nv; ++a) dst.v[a * np + r] = src.v[a * np + j];
+    }
+}
+
+cudaError_t launch_apply_perm(const uint32_t *perm, ParticlesF32 src, ParticlesF32 dst, int ndim,
+                              cudaStream_t st)
+{
+    if (src.np <= 0) return cudaSuccess;
+    int64_t nb = (src.np + 255) / 256;
+    if (nb > 65535) nb = 65535;
+    k_apply_perm<<<(int)nb, 256, 0, st>>>(perm, src, dst, ndim);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace apk

@@ -16,5 +16,6 @@ from .plasma import (  # noqa: F401
     precision_3d,
     batch_instances,
     maxwellian_box,
+    fp32_exact,
     by_name,
 )

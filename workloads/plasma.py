@@ -277,6 +277,25 @@ def batch_instances(count=1024, seed=5, n_range=(32, 1024), np_range=(1_000, 200
     return out
 
 
+def fp32_exact(w: Workload) -> Workload:
+    """Round a load so that an FP32 cell + offset store and an FP64 store hold the same
+    state: each offset x / dx - floor(x / dx) and each velocity is rounded to the
+    nearest FP32 value (offsets that would round up to 1 are clamped below 1).  Exact
+    only when every dx is a power of two, which is asserted."""
+    for a in range(w.ndim):
+        m, _ = math.frexp(w.dx[a])
+        assert m == 0.5, "fp32_exact needs power-of-two dx"
+    x = w.x.copy()
+    for a in range(w.ndim):
+        u = x[:, a] / w.dx[a]
+        c = np.floor(u)
+        f = (u - c).astype(np.float32)
+        f = np.minimum(f, np.float32(np.nextafter(np.float32(1), np.float32(0))))
+        x[:, a] = (c + f.astype(np.float64)) * w.dx[a]
+    v = w.v.astype(np.float32).astype(np.float64)
+    return dataclasses.replace(w, x=x, v=v)
+
+
 def by_name(name: str, **kw) -> Workload:
     table = {
         "langmuir_1d": langmuir_1d,
