@@ -58,14 +58,16 @@ def _workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
-def _bytes_per_particle(ndim, nv):
+def _bytes_per_particle(ndim, nv, f64=False):
+    if f64:  # FP64 plain form: ndim FP64 positions + nv FP64 velocities, read and written
+        return 2 * (8 * ndim + 8 * nv)
     # cell (int32) + ndim FP32 offsets + nv FP32 velocities, read and written once
     return 2 * (4 + 4 * ndim + 4 * nv)
 
 
-def _grid_bytes_per_node(ndim):
-    # E read (ndim FP32) + the int64 accumulator written once
-    return 4 * ndim + 8
+def _grid_bytes_per_node(ndim, f64=False):
+    # E read (ndim FP32, or FP64) + the int64 accumulator written once
+    return (8 if f64 else 4) * ndim + 8
 
 
 class Clocks:
@@ -169,6 +171,7 @@ def _config(args, w):
             + f", {args.ppc} ppc, {w.np_} electrons, dt={w.dt}, sort every {w.sort_every}",
             "grid": list(w.n[: w.ndim]), "particles": w.np_, "ppc": args.ppc,
             "sort_every": w.sort_every, "parallelism": f"replicas x{args.gpus}",
+            "storage": "FP64 plain" if args.precision == "f64" else "int32 cell + FP32 offset",
             "l2": "particle state larger than L2 (no flush)"}
 
 
@@ -187,10 +190,12 @@ def bench_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = _workload(args)
+    f64 = args.precision == "f64"
     stream = torch.cuda.current_stream()
-    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol)
+    extra = dict(precision=pk.AP_PIC_FP64_PLAIN) if f64 else {}
+    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, **extra)
     g.load(w.x, w.v)
-    sort_every = w.sort_every
+    sort_every = 0 if f64 else w.sort_every
 
     def hot_step(k):
         g.push_deposit()
@@ -228,8 +233,8 @@ def bench_ours(args):
     peak, peak_kind = _peaks()
     pd_ms, pd_n = stages["push_deposit"]
     avg_ms = pd_ms / max(pd_n, 1)
-    alg_bytes = (w.np_ * _bytes_per_particle(w.ndim, w.nv)
-                 + w.cells * _grid_bytes_per_node(w.ndim))
+    alg_bytes = (w.np_ * _bytes_per_particle(w.ndim, w.nv, f64)
+                 + w.cells * _grid_bytes_per_node(w.ndim, f64))
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     breakdown = {k: (v[0] / max(v[1], 1)) for k, v in stages.items() if v[1]}
 
@@ -238,7 +243,7 @@ def bench_ours(args):
     g.solve_field()
     fs = g.get_timing()["field"]
     g.set_timing(False)
-    e2e = run_e2e(args, w, pk, torch, stream) if not args.no_e2e else None
+    e2e = run_e2e(args, w, pk, torch, stream, extra) if not args.no_e2e else None
     g.close()
 
     cpu = None
@@ -253,11 +258,12 @@ def bench_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": _config(args, w),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if f64 else "f32", "data": "synthetic", "config": _config(args, w),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_particle_pass (gather+Boris+move+deposit)",
+                         "kernel": ("k_plain_pass" if f64 else "k_particle_pass")
+                         + " (gather+Boris+move+deposit)",
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                          "peak_kind": peak_kind},
             "stage_ms_per_call": breakdown,
@@ -272,14 +278,14 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, w, pk, torch, stream):
+def run_e2e(args, w, pk, torch, stream, extra):
     """Load from pinned host memory, run the full cycle (with field solves) for
     e2e_steps steps reading the diagnostics back every step, then read rho."""
     import ctypes
 
     xs = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
     vs = torch.from_numpy(np.ascontiguousarray(w.v)).pin_memory()
-    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol)
+    g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, **extra)
     steps = args.e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -308,7 +314,9 @@ def main():
     ap.add_argument("--workload", default="two_stream_2d")
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--ppc", type=int, default=64)
-    ap.add_argument("--cg-rtol", type=float, default=1e-6)
+    ap.add_argument("--cg-rtol", type=float, default=0.0, help="0: the form's default")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32",
+                    help="f32: cell + FP32 offset form (the product); f64: FP64 plain form")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -86,10 +86,12 @@ typedef struct {
                               be 3 when B0 != 0                                    */
     int sort_every;        /* ap_pic_step sorts by cell every this many steps (0:
                               never); ignored by AP_PIC_FP64_PLAIN                 */
-    int fx_bits;           /* fixed-point fraction bits S of the charge
-                              accumulator (0: 40); capped at 62 - bitlen(np) so the
-                              int64 sum can never overflow                         */
-    double cg_rtol;        /* field-solve relative residual target (0: 1e-7)      */
+    int fx_bits;           /* fixed-point fraction bits S of the charge accumulator:
+                              each particle deposits exactly 2^S.  FP32 form: 0 means
+                              24 (the precision of its FP32 weights), at most 25 (a
+                              warp's per-corner sum must fit int32).  Always capped
+                              at 62 - bitlen(np) so the int64 sum cannot overflow  */
+    double cg_rtol;        /* field-solve relative residual target (0: 1e-6)      */
     int cg_maxit;          /* field-solve iteration cap (0: 20000)                 */
     int brick[3];          /* sort brick in cells per axis (0: library default)    */
     int diag_every;        /* diagnostics every this many steps (0: every step)    */

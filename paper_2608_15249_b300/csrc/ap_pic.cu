@@ -24,8 +24,12 @@ void apk::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed
 
 namespace {
 
-constexpr int DEFAULT_FX_BITS = 40;
-constexpr double DEFAULT_CG_RTOL = 1e-7;
+constexpr int DEFAULT_FX_BITS = 24;   // FP32 cell+offset form: matches the FP32 weights
+constexpr int MAX_FX_BITS_F32 = 25;   // a warp's 32 corner quanta must sum inside int32
+constexpr int DEFAULT_FX_BITS_F64 = 40;  // FP64 plain form: FP64 weights
+constexpr int MAX_FX_BITS_F64 = 52;
+constexpr double DEFAULT_CG_RTOL_F64 = 1e-10;
+constexpr double DEFAULT_CG_RTOL = 1e-6;
 constexpr int DEFAULT_CG_MAXIT = 20000;
 constexpr int64_t LOAD_CHUNK = int64_t(1) << 23;  // particles per host->device load chunk
 
@@ -58,6 +62,10 @@ struct ap_pic {
     double dV = 1.0, V = 1.0;
     int64_t step = 0;
     bool loaded = false;
+
+    bool plain = false;            // AP_PIC_FP64_PLAIN
+    ParticlesF64 p64{};
+    FieldBufsF64 f64{};
 
     // particles (FP32 cell + offset form)
     ParticlesF32 p{};
@@ -217,6 +225,34 @@ static GridParams grid_params(const ap_pic *h, double step_h)
     }
     g.magnetised = (c.B0[0] != 0.0 || c.B0[1] != 0.0 || c.B0[2] != 0.0) ? 1 : 0;
     g.fx_bits = h->fx_bits;
+    g.div0 = make_fastdiv((uint32_t)g.n[0]);
+    g.div1 = make_fastdiv((uint32_t)g.n[1]);
+    return g;
+}
+
+static GridParamsF64 grid_params_f64(const ap_pic *h, double step_h)
+{
+    GridParamsF64 g{};
+    const ap_pic_config &c = h->cfg;
+    g.ndim = h->ndim;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < h->ndim ? c.n[a] : 1;
+        g.dx[a] = c.dx[a];
+        g.inv_dx[a] = 1.0 / c.dx[a];
+        g.L[a] = g.n[a] * c.dx[a];
+        g.E0[a] = c.E0[a];
+    }
+    g.dt = c.dt;
+    const double qm = c.q / c.m;
+    g.qmh2 = qm * step_h * 0.5;
+    double tt = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        g.t[a] = qm * c.B0[a] * step_h * 0.5;
+        tt += g.t[a] * g.t[a];
+    }
+    for (int a = 0; a < 3; ++a) g.s[a] = 2.0 * g.t[a] / (1.0 + tt);
+    g.magnetised = (c.B0[0] != 0.0 || c.B0[1] != 0.0 || c.B0[2] != 0.0) ? 1 : 0;
+    g.fx_bits = h->fx_bits;
     return g;
 }
 
@@ -283,8 +319,6 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
         return fail(h, AP_PIC_ERR_UNSUPPORTED, "only periodic boundaries are implemented");
     if (c->precision != AP_PIC_FP32_CELLOFF && c->precision != AP_PIC_FP64_PLAIN)
         return fail(h, AP_PIC_ERR_ARG, "unknown precision %d", c->precision);
-    if (c->precision == AP_PIC_FP64_PLAIN)
-        return fail(h, AP_PIC_ERR_UNSUPPORTED, "FP64 plain form not built in this library");
     if (c->nv < c->ndim || c->nv > 3) return fail(h, AP_PIC_ERR_ARG, "need ndim <= nv <= 3");
     const bool mag = c->B0[0] != 0.0 || c->B0[1] != 0.0 || c->B0[2] != 0.0;
     if (mag && c->nv != 3) return fail(h, AP_PIC_ERR_ARG, "B0 != 0 needs nv = 3");
@@ -292,9 +326,12 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
         if (!isfinite(c->E0[a]) || !isfinite(c->B0[a]))
             return fail(h, AP_PIC_ERR_ARG, "E0 and B0 must be finite");
     if (c->sort_every < 0) return fail(h, AP_PIC_ERR_ARG, "sort_every must be >= 0");
-    if (c->fx_bits == 0) c->fx_bits = DEFAULT_FX_BITS;
-    if (c->fx_bits < 8 || c->fx_bits > 52) return fail(h, AP_PIC_ERR_ARG, "fx_bits in [8, 52]");
-    if (c->cg_rtol == 0.0) c->cg_rtol = DEFAULT_CG_RTOL;
+    const bool plain = c->precision == AP_PIC_FP64_PLAIN;
+    if (c->fx_bits == 0) c->fx_bits = plain ? DEFAULT_FX_BITS_F64 : DEFAULT_FX_BITS;
+    const int fx_max = plain ? MAX_FX_BITS_F64 : MAX_FX_BITS_F32;
+    if (c->fx_bits < 8 || c->fx_bits > fx_max)
+        return fail(h, AP_PIC_ERR_ARG, "fx_bits must be in [8, %d] for this form", fx_max);
+    if (c->cg_rtol == 0.0) c->cg_rtol = plain ? DEFAULT_CG_RTOL_F64 : DEFAULT_CG_RTOL;
     if (!(c->cg_rtol > 0.0)) return fail(h, AP_PIC_ERR_ARG, "cg_rtol must be > 0");
     if (c->cg_maxit == 0) c->cg_maxit = DEFAULT_CG_MAXIT;
     if (c->cg_maxit < 1) return fail(h, AP_PIC_ERR_ARG, "cg_maxit must be >= 1");
@@ -315,8 +352,60 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
 
 // ---- create / destroy ------------------------------------------------------------------------
 
+static ap_pic_status create_pinned(ap_pic *h)
+{
+    CU(h, cudaMallocHost(&h->h_done, 64));
+    CU(h, cudaMallocHost(&h->h_diag, 64));
+    CU(h, cudaMallocHost(&h->h_accsum, 64));
+    CU(h, cudaMallocHost(&h->h_err, 64));
+    CU(h, cudaMallocHost(&h->h_iters, 64));
+    return AP_PIC_OK;
+}
+
+static ap_pic_status create_grid_f64(ap_pic *h)
+{
+    FieldBufsF64 &f = h->f64;
+    f.ndim = h->ndim;
+    f.cells = h->cells;
+    for (int a = 0; a < 3; ++a) {
+        f.n[a] = h->cfg.n[a];
+        f.dx[a] = h->cfg.dx[a];
+    }
+    f.nblocks = field_blocks(h->cells);
+    const size_t c = (size_t)h->cells;
+    TRY(alloc_n(h, &f.acc, c));
+    TRY(alloc_n(h, &f.rho, c));
+    TRY(alloc_n(h, &f.b, c));
+    TRY(alloc_n(h, &f.phi, c));
+    TRY(alloc_n(h, &f.r, c));
+    TRY(alloc_n(h, &f.p, c));
+    TRY(alloc_n(h, &f.q, c));
+    TRY(alloc_n(h, &f.E, c * h->ndim));
+    for (int k = 0; k < 3; ++k) TRY(alloc_n(h, &f.part[k], (size_t)f.nblocks));
+    TRY(alloc_n(h, &f.scal, 8));
+    TRY(alloc_n(h, &f.done, 1));
+    TRY(alloc_n(h, &f.iters, 1));
+    TRY(alloc_n(h, &f.isum_part, (size_t)f.nblocks));
+    TRY(alloc_n(h, &f.fe_part, (size_t)f.nblocks));
+    TRY(alloc_n(h, &h->d_diag, 8));
+    TRY(alloc_n(h, &h->d_accsum, 1));
+    TRY(alloc_n(h, &h->d_err, 1));
+    CU(h, cudaMemsetAsync(f.acc, 0, c * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.phi, 0, c * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.E, 0, c * h->ndim * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.isum_part, 0, (size_t)f.nblocks * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.fe_part, 0, (size_t)f.nblocks * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.scal, 0, 64, h->stream));
+    CU(h, cudaMemsetAsync(f.iters, 0, 4, h->stream));
+    CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
+    CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
+    CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+    return create_pinned(h);
+}
+
 static ap_pic_status create_grid(ap_pic *h)
 {
+    if (h->plain) return create_grid_f64(h);
     FieldBufs &f = h->f;
     f.ndim = h->ndim;
     f.cells = h->cells;
@@ -354,16 +443,14 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
     CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
     CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
-    CU(h, cudaMallocHost(&h->h_done, 64));
-    CU(h, cudaMallocHost(&h->h_diag, 64));
-    CU(h, cudaMallocHost(&h->h_accsum, 64));
-    CU(h, cudaMallocHost(&h->h_err, 64));
-    CU(h, cudaMallocHost(&h->h_iters, 64));
-    return AP_PIC_OK;
+    return create_pinned(h);
 }
 
 static void free_particles(ap_pic *h)
 {
+    dev_free(h, h->p64.x);
+    dev_free(h, h->p64.v);
+    h->p64 = ParticlesF64{};
     dev_free(h, h->p.cell);
     dev_free(h, h->p.off);
     dev_free(h, h->p.v);
@@ -405,6 +492,7 @@ extern "C" ap_pic_status ap_pic_create(const ap_pic_config *cfg, const ap_pic_al
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->ndim = h->cfg.ndim;
     h->nv = h->cfg.nv;
+    h->plain = h->cfg.precision == AP_PIC_FP64_PLAIN;
     h->cells = 1;
     h->dV = 1.0;
     for (int a = 0; a < h->ndim; ++a) {
@@ -456,6 +544,19 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
     free_particles(h);
     h->np = np;
     const size_t n = (size_t)(np > 0 ? np : 1);
+    // fixed-point scale: S <= 62 - bitlen(np) keeps |sum| < 2^62 whatever the clustering
+    const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
+    h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
+    h->dpart.nblocks = particle_pass_blocks(np > 0 ? np : 1, h->ndim);
+    TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
+    CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
+    if (h->plain) {
+        TRY(alloc_n(h, &h->p64.x, n * h->ndim));
+        TRY(alloc_n(h, &h->p64.v, n * h->nv));
+        h->p64.np = np;
+        h->p64.nv = h->nv;
+        return AP_PIC_OK;
+    }
     ParticlesF32 *ps[2] = {&h->p, &h->p_alt};
     for (ParticlesF32 *q : ps) {
         TRY(alloc_n(h, &q->cell, n));
@@ -473,12 +574,6 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
     h->sort.scan_tmp_len = sort_scan_tmp_len(hl);
     TRY(alloc_n(h, &h->sort.scan_tmp, h->sort.scan_tmp_len));
     h->sort.capacity = np;
-    h->dpart.nblocks = particle_pass_blocks(np > 0 ? np : 1);
-    TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
-    CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
-    // fixed-point scale: S <= 62 - bitlen(np) keeps |sum| < 2^62 whatever the clustering
-    const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
-    h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
     return AP_PIC_OK;
 }
 
@@ -497,13 +592,23 @@ static ap_pic_status convert_rho(ap_pic *h)
     const double scale = h->cfg.q * h->cfg.weight / h->dV * ldexp(1.0, -h->fx_bits);
     const double mean_e = h->cfg.q * h->cfg.weight * (double)h->np / h->V;
     const int mk = stage_begin(h, AP_PIC_STAGE_RHO);
-    CU(h, launch_rho_convert(h->f, scale, bg_density(h), mean_e, false, h->stream));
+    if (h->plain)
+        CU(h, launch_plain_rho_convert(h->f64, scale, bg_density(h), mean_e, h->stream));
+    else
+        CU(h, launch_rho_convert(h->f, scale, bg_density(h), mean_e, false, h->stream));
     stage_end(h, mk);
     return AP_PIC_OK;
 }
 
 static ap_pic_status deposit_only(ap_pic *h)
 {
+    if (h->plain) {
+        CU(h, cudaMemsetAsync(h->f64.acc, 0, (size_t)h->cells * 8, h->stream));
+        const GridParamsF64 g = grid_params_f64(h, h->cfg.dt);
+        CU(h, launch_plain_pass(g, h->p64, h->f64.E, h->f64.acc, false, false, true,
+                                DiagPartials{}, h->d_err, h->stream));
+        return convert_rho(h);
+    }
     CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
     const GridParams g = grid_params(h, h->cfg.dt);
     CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, false, false, true, DiagPartials{},
@@ -513,26 +618,35 @@ static ap_pic_status deposit_only(ap_pic *h)
 
 static ap_pic_status solve_field(ap_pic *h)
 {
-    FieldBufs &f = h->f;
     const double rtol = h->cfg.cg_rtol;
     const int maxit = h->cfg.cg_maxit;
     const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
-    CU(h, launch_cg_init(f, rtol, h->stream));
+    int *d_done = h->plain ? h->f64.done : h->f.done;
+    int *d_iters = h->plain ? h->f64.iters : h->f.iters;
+    double *d_scal = h->plain ? h->f64.scal : h->f.scal;
+    if (h->plain) CU(h, launch_plain_cg_init(h->f64, rtol, h->stream));
+    else CU(h, launch_cg_init(h->f, rtol, h->stream));
     int it = 0, chunk = 8;
     while (true) {
-        CU(h, cudaMemcpyAsync(h->h_done, f.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CU(h, cudaMemcpyAsync(h->h_done, d_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CU(h, cudaStreamSynchronize(h->stream));
         if (*h->h_done || it >= maxit) break;
-        CU(h, launch_cg_iters(f, it, chunk, maxit, rtol, h->stream));
+        if (h->plain) CU(h, launch_plain_cg_iters(h->f64, it, chunk, maxit, rtol, h->stream));
+        else CU(h, launch_cg_iters(h->f, it, chunk, maxit, rtol, h->stream));
         it += chunk;
         if (chunk < 64) chunk *= 2;
     }
-    CU(h, launch_cg_finish(f, rtol, h->d_err, h->stream));
-    CU(h, launch_efield(f, h->stream));
+    if (h->plain) {
+        CU(h, launch_plain_cg_finish(h->f64, rtol, h->d_err, h->stream));
+        CU(h, launch_plain_efield(h->f64, h->stream));
+    } else {
+        CU(h, launch_cg_finish(h->f, rtol, h->d_err, h->stream));
+        CU(h, launch_efield(h->f, h->stream));
+    }
     stage_end(h, mk);
-    CU(h, cudaMemcpyAsync(h->h_iters, f.iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(h->h_iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     double rel = 0.0;
-    CU(h, cudaMemcpyAsync(h->h_diag + 7, f.scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+    CU(h, cudaMemcpyAsync(h->h_diag + 7, d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
                           h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     rel = h->h_diag[7];
@@ -547,7 +661,7 @@ static ap_pic_status solve_field(ap_pic *h)
 
 static ap_pic_status sort_particles(ap_pic *h)
 {
-    if (h->np == 0) return AP_PIC_OK;
+    if (h->np == 0 || h->plain) return AP_PIC_OK;
     const GridParams g = grid_params(h, h->cfg.dt);
     int slot = 0;
     const int mk = stage_begin(h, AP_PIC_STAGE_SORT);
@@ -564,7 +678,12 @@ static ap_pic_status sort_particles(ap_pic *h)
 static ap_pic_status finalize_diag(ap_pic *h, bool have_particles)
 {
     const int mk = stage_begin(h, AP_PIC_STAGE_DIAG);
-    CU(h, launch_diag_finalize(h->dpart, have_particles, h->f, h->d_diag, h->d_accsum, h->stream));
+    if (h->plain)
+        CU(h, launch_plain_diag_finalize(h->dpart, have_particles, h->f64, h->d_diag, h->d_accsum,
+                                         h->stream));
+    else
+        CU(h, launch_diag_finalize(h->dpart, have_particles, h->f, h->d_diag, h->d_accsum,
+                                   h->stream));
     stage_end(h, mk);
     h->diag_valid = true;
     return AP_PIC_OK;
@@ -579,6 +698,12 @@ static ap_pic_status field_update(ap_pic *h)
 
 static ap_pic_status half_push(ap_pic *h)
 {
+    if (h->plain) {
+        const GridParamsF64 g = grid_params_f64(h, -0.5 * h->cfg.dt);
+        CU(h, launch_plain_pass(g, h->p64, h->f64.E, h->f64.acc, true, false, false,
+                                DiagPartials{}, h->d_err, h->stream));
+        return AP_PIC_OK;
+    }
     const GridParams g = grid_params(h, -0.5 * h->cfg.dt);
     CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, false, false, DiagPartials{},
                                h->d_err, h->stream));
@@ -609,19 +734,24 @@ extern "C" ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, con
     TRY(alloc_n(h, &dx_buf, (size_t)chunk * h->ndim));
     TRY(alloc_n(h, &dv_buf, (size_t)chunk * h->nv));
     const GridParams g = grid_params(h, h->cfg.dt);
+    const GridParamsF64 g64 = grid_params_f64(h, h->cfg.dt);
     for (int64_t first = 0; first < np; first += chunk) {
         const int64_t cnt = np - first < chunk ? np - first : chunk;
         CU(h, cudaMemcpyAsync(dx_buf, x + first * h->ndim, (size_t)cnt * h->ndim * 8,
                               cudaMemcpyHostToDevice, h->stream));
         CU(h, cudaMemcpyAsync(dv_buf, v + first * h->nv, (size_t)cnt * h->nv * 8,
                               cudaMemcpyHostToDevice, h->stream));
-        CU(h, launch_load_convert(g, h->cfg.dx, dx_buf, dv_buf, h->p, first, cnt, h->d_err,
-                                  h->stream));
+        if (h->plain)
+            CU(h, launch_plain_load(g64, dx_buf, dv_buf, h->p64, first, cnt, h->d_err, h->stream));
+        else
+            CU(h, launch_load_convert(g, h->cfg.dx, dx_buf, dv_buf, h->p, first, cnt, h->d_err,
+                                      h->stream));
     }
     CU(h, cudaStreamSynchronize(h->stream));
     dev_free(h, dx_buf);
     dev_free(h, dv_buf);
-    CU(h, cudaMemsetAsync(h->f.phi, 0, (size_t)h->cells * 4, h->stream));
+    if (h->plain) CU(h, cudaMemsetAsync(h->f64.phi, 0, (size_t)h->cells * 8, h->stream));
+    else CU(h, cudaMemsetAsync(h->f.phi, 0, (size_t)h->cells * 4, h->stream));
     return after_load(h, flags);
 }
 
@@ -631,6 +761,8 @@ extern "C" ap_pic_status ap_pic_load_state(ap_pic *h, int64_t np, const int32_t 
     if (!h) return AP_PIC_ERR_ARG;
     if (np < 0 || np >= (int64_t(1) << 31)) return fail(h, AP_PIC_ERR_ARG, "np out of range");
     if (np > 0 && (!cell || !off || !v)) return fail(h, AP_PIC_ERR_ARG, "cell, off, v required");
+    if (h->plain)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "ap_pic_load_state needs the FP32 cell+offset form");
     TRY(alloc_particles(h, np));
     if (np > 0) {
         // the alternate buffers double as staging for the row-major host layout
@@ -658,6 +790,12 @@ static ap_pic_status need_loaded(ap_pic *h)
 extern "C" ap_pic_status ap_pic_gather_push(ap_pic *h)
 {
     TRY(need_loaded(h));
+    if (h->plain) {
+        const GridParamsF64 g = grid_params_f64(h, h->cfg.dt);
+        CU(h, launch_plain_pass(g, h->p64, h->f64.E, h->f64.acc, true, true, false, h->dpart,
+                                h->d_err, h->stream));
+        return AP_PIC_OK;
+    }
     const GridParams g = grid_params(h, h->cfg.dt);
     CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, true, false, h->dpart, h->d_err,
                                h->stream));
@@ -672,6 +810,15 @@ extern "C" ap_pic_status ap_pic_deposit(ap_pic *h)
 
 static ap_pic_status push_deposit(ap_pic *h, bool diag)
 {
+    if (h->plain) {
+        CU(h, cudaMemsetAsync(h->f64.acc, 0, (size_t)h->cells * 8, h->stream));
+        const GridParamsF64 g = grid_params_f64(h, h->cfg.dt);
+        const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
+        CU(h, launch_plain_pass(g, h->p64, h->f64.E, h->f64.acc, true, true, true,
+                                diag ? h->dpart : DiagPartials{}, h->d_err, h->stream));
+        stage_end(h, mk);
+        return convert_rho(h);
+    }
     CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
     const GridParams g = grid_params(h, h->cfg.dt);
     const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
@@ -720,20 +867,27 @@ extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
 extern "C" ap_pic_status ap_pic_get_rho(ap_pic *h, double *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
-    CU(h, cudaMemcpyAsync(out, h->f.rho, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(out, h->plain ? h->f64.rho : h->f.rho, (size_t)h->cells * 8,
+                          cudaMemcpyDeviceToHost, h->stream));
     return sync_check(h);
 }
 
 extern "C" ap_pic_status ap_pic_get_rho_fx(ap_pic *h, int64_t *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
-    CU(h, cudaMemcpyAsync(out, h->f.acc, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(out, h->plain ? h->f64.acc : h->f.acc, (size_t)h->cells * 8,
+                          cudaMemcpyDeviceToHost, h->stream));
     return sync_check(h);
 }
 
 extern "C" ap_pic_status ap_pic_get_E(ap_pic *h, double *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
+    if (h->plain) {
+        CU(h, cudaMemcpyAsync(out, h->f64.E, (size_t)h->cells * h->ndim * 8,
+                              cudaMemcpyDeviceToHost, h->stream));
+        return sync_check(h);
+    }
     double *tmp = nullptr;
     TRY(alloc_n(h, &tmp, (size_t)h->cells * h->ndim));
     CU(h, launch_e_to_f64(h->f, tmp, h->stream));
@@ -747,17 +901,60 @@ extern "C" ap_pic_status ap_pic_get_E(ap_pic *h, double *out)
 extern "C" ap_pic_status ap_pic_get_phi(ap_pic *h, double *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
-    double *tmp = nullptr;
-    TRY(alloc_n(h, &tmp, (size_t)h->cells));
-    CU(h, launch_phi_to_f64(h->f, tmp, h->stream));
-    CU(h, cudaMemcpyAsync(out, tmp, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
-    CU(h, cudaStreamSynchronize(h->stream));
-    dev_free(h, tmp);
+    if (h->plain) {
+        CU(h, cudaMemcpyAsync(out, h->f64.phi, (size_t)h->cells * 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+    } else {
+        double *tmp = nullptr;
+        TRY(alloc_n(h, &tmp, (size_t)h->cells));
+        CU(h, launch_phi_to_f64(h->f, tmp, h->stream));
+        CU(h, cudaMemcpyAsync(out, tmp, (size_t)h->cells * 8, cudaMemcpyDeviceToHost, h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        dev_free(h, tmp);
+    }
     // phi is defined up to a constant; report the zero-mean representative
     double mean = 0.0;
     for (int64_t i = 0; i < h->cells; ++i) mean += out[i];
     mean /= (double)h->cells;
     for (int64_t i = 0; i < h->cells; ++i) out[i] -= mean;
+    return sync_check(h);
+}
+
+// FP64 plain form: positions and velocities are stored; cell and offset are
+// derived on the host with the same floor rule as the device.
+static ap_pic_status get_particles_plain(ap_pic *h, int32_t *cell, float *off, float *v, double *x)
+{
+    const int64_t np = h->np;
+    std::vector<double> xs((size_t)np * h->ndim), vs;
+    CU(h, cudaMemcpyAsync(xs.data(), h->p64.x, xs.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (v) {
+        vs.resize((size_t)np * h->nv);
+        CU(h, cudaMemcpyAsync(vs.data(), h->p64.v, vs.size() * 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < np; ++i) {
+        int64_t lin = 0, stride = 1;
+        for (int a = 0; a < h->ndim; ++a) {
+            const double xa = xs[(size_t)a * np + i];
+            const double u = xa * (1.0 / h->cfg.dx[a]);
+            double fl = floor(u);
+            double fa = u - fl;
+            int ca = (int)fl;
+            if (ca >= h->cfg.n[a] || ca < 0) {
+                ca = 0;
+                fa = 0.0;
+            }
+            lin += ca * stride;
+            stride *= h->cfg.n[a];
+            if (x) x[i * h->ndim + a] = xa;
+            if (off) off[i * h->ndim + a] = (float)fa < 1.0f ? (float)fa : 0x1.fffffep-1f;
+        }
+        if (cell) cell[i] = (int32_t)lin;
+        if (v)
+            for (int a = 0; a < h->nv; ++a) v[i * h->nv + a] = (float)vs[(size_t)a * np + i];
+    }
     return sync_check(h);
 }
 
@@ -767,6 +964,7 @@ extern "C" ap_pic_status ap_pic_get_particles(ap_pic *h, int32_t *cell, float *o
     TRY(need_loaded(h));
     const int64_t np = h->np;
     if (np == 0) return AP_PIC_OK;
+    if (h->plain) return get_particles_plain(h, cell, off, v, x);
     if (cell)
         CU(h, cudaMemcpyAsync(cell, h->p.cell, (size_t)np * 4, cudaMemcpyDeviceToHost, h->stream));
     std::vector<float> tmp;
@@ -801,8 +999,18 @@ extern "C" ap_pic_status ap_pic_get_particles(ap_pic *h, int32_t *cell, float *o
 
 extern "C" ap_pic_status ap_pic_get_velocities_f64(ap_pic *h, double *v)
 {
-    if (!h || !v) return AP_PIC_ERR_ARG;
-    return fail(h, AP_PIC_ERR_UNSUPPORTED, "only the FP64 plain form stores FP64 velocities");
+    TRY(need_loaded(h));
+    if (!v) return fail(h, AP_PIC_ERR_ARG, "v is NULL");
+    if (!h->plain)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "only the FP64 plain form stores FP64 velocities");
+    std::vector<double> vs((size_t)h->np * h->nv);
+    if (h->np)
+        CU(h, cudaMemcpyAsync(vs.data(), h->p64.v, vs.size() * 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < h->np; ++i)
+        for (int a = 0; a < h->nv; ++a) v[i * h->nv + a] = vs[(size_t)a * h->np + i];
+    return sync_check(h);
 }
 
 extern "C" ap_pic_status ap_pic_get_perm(ap_pic *h, int64_t *perm)

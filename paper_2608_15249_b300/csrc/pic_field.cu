@@ -166,10 +166,17 @@ static Lap make_lap(const FieldBufs &f)
     return L;
 }
 
-// r = b - A phi;  p = M^-1 r;  partials of r.r and b.b.
+// The periodic operator is singular (constants are its null space): FP32
+// rounding leaves r with a small constant part that CG cannot remove, and once
+// the rest has converged p would become nearly constant and p.Ap vanish.  So
+// every direction update projects r onto zero mean (its sum comes with the
+// r.r reduction; |r - m|^2 = r.r - N m^2), and a non-positive or non-finite
+// p.Ap stops the iteration instead of dividing by it.
+
+// r = b - A phi;  p = M^-1 r;  partials of r.r, b.b and sum(r).
 __global__ void __launch_bounds__(FT) k_cg_init(FieldBufs f, Lap L)
 {
-    double rr = 0.0, bb = 0.0;
+    double rr = 0.0, bb = 0.0, rs = 0.0;
     for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
          id += (int64_t)gridDim.x * FT) {
         int j[3];
@@ -180,19 +187,25 @@ __global__ void __launch_bounds__(FT) k_cg_init(FieldBufs f, Lap L)
         f.p[id] = ri * L.inv_diag;
         rr += (double)ri * ri;
         bb += (double)bi * bi;
+        rs += ri;
     }
     rr = block_sum(rr);
     bb = block_sum(bb);
+    rs = block_sum(rs);
     if (threadIdx.x == 0) {
         f.part[0][blockIdx.x] = rr;
+        f.part[1][blockIdx.x] = rs;
         f.part[2][blockIdx.x] = bb;
     }
 }
 
 __global__ void __launch_bounds__(FT) k_cg_init_fin(FieldBufs f, Lap L, double rtol)
 {
-    const double rr = reduce_partials(f.part[0], f.nblocks);
+    const double rs = reduce_partials(f.part[1], f.nblocks);
+    const double rr0 = reduce_partials(f.part[0], f.nblocks);
     const double bb = reduce_partials(f.part[2], f.nblocks);
+    const double m = rs / (double)f.cells;
+    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
     if (threadIdx.x == 0) {
         const double bn = sqrt(bb);
         f.scal[SC_BNORM] = bn;
@@ -221,30 +234,45 @@ __global__ void __launch_bounds__(FT) k_cg_matvec(FieldBufs f, Lap L)
     if (threadIdx.x == 0) f.part[0][blockIdx.x] = pq;
 }
 
-// alpha = rz / p.q;  phi += alpha p;  r -= alpha q;  partial r.r -> part[1].
+// alpha = rz / p.q;  phi += alpha p;  r -= alpha q;  partials r.r -> part[1],
+// sum(r) -> part[2].
 __global__ void __launch_bounds__(FT) k_cg_update(FieldBufs f, int it)
 {
     if (*f.done) return;
     const double pq = reduce_partials(f.part[0], f.nblocks);
     const double rz = f.scal[SC_RZ0 + (it & 1)];
-    const float alpha = (float)(rz / pq);
-    double rr = 0.0;
+    const double a64 = rz / pq;
+    if (!(pq > 0.0) || !isfinite(a64)) {  // breakdown: keep phi as it is and stop
+        if (blockIdx.x == 0 && threadIdx.x == 0) *f.done = 1;
+        return;
+    }
+    const float alpha = (float)a64;
+    double rr = 0.0, rs = 0.0;
     for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
          id += (int64_t)gridDim.x * FT) {
         f.phi[id] += alpha * f.p[id];
         const float ri = f.r[id] - alpha * f.q[id];
         f.r[id] = ri;
         rr += (double)ri * ri;
+        rs += ri;
     }
     rr = block_sum(rr);
-    if (threadIdx.x == 0) f.part[1][blockIdx.x] = rr;
+    rs = block_sum(rs);
+    if (threadIdx.x == 0) {
+        f.part[1][blockIdx.x] = rr;
+        f.part[2][blockIdx.x] = rs;
+    }
 }
 
 // beta = rz_new / rz;  p = M^-1 r + beta p;  convergence test.
 __global__ void __launch_bounds__(FT) k_cg_dir(FieldBufs f, Lap L, int it, int maxit, double rtol)
 {
     if (*f.done) return;
-    const double rr = reduce_partials(f.part[1], f.nblocks);
+    const double rs = reduce_partials(f.part[2], f.nblocks);
+    const double rr0 = reduce_partials(f.part[1], f.nblocks);
+    const double m = rs / (double)f.cells;
+    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
+    const float mf = (float)m;
     const double rz_new = rr * (double)L.inv_diag;
     const double rz = f.scal[SC_RZ0 + (it & 1)];
     const double rel = sqrt(rr) / f.scal[SC_BNORM];
@@ -258,8 +286,11 @@ __global__ void __launch_bounds__(FT) k_cg_dir(FieldBufs f, Lap L, int it, int m
     if (stop) return;
     const float beta = (float)(rz_new / rz);
     for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT)
-        f.p[id] = f.r[id] * L.inv_diag + beta * f.p[id];
+         id += (int64_t)gridDim.x * FT) {
+        const float ri = f.r[id] - mf;
+        f.r[id] = ri;
+        f.p[id] = ri * L.inv_diag + beta * f.p[id];
+    }
 }
 
 __global__ void k_cg_finish(FieldBufs f, double rtol, int *err)

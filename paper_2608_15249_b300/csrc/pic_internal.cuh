@@ -13,10 +13,40 @@ namespace apk {
 // Counts kernel launches (process-wide); every launcher calls it once per kernel.
 void note_launch(int n = 1);
 
+// Division by a loop-invariant divisor d >= 2 through a multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, the round-up variant for unsigned operands):
+//   l = ceil(log2 d),  m = floor(2^32 (2^l - d) / d) + 1,
+//   q = (t + ((x - t) >> 1)) >> (l - 1),  t = umulhi(m, x),   valid for x < 2^31.
+struct FastDiv {
+    uint32_t d, m;
+    int l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f{d, 0u, 0};
+    if (d < 2) return f;
+    int l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(f.m, x);
+    return (t + ((x - t) >> 1)) >> (f.l - 1);
+}
+#endif
+
 // Everything a particle kernel needs about the grid and the push, by value.
 struct GridParams {
     int ndim;
     int n[3];          // nodes per axis (unused axes 1)
+    FastDiv div0, div1; // division by n[0] and n[1] (cell index decode)
     float dtdx[3];     // dt / dx_a in FP32 (position update in cell units)
     float qmh2;        // (q/m) h / 2 for the step h of this launch
     float E0[3];       // uniform external field
@@ -61,7 +91,7 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
 
 // Number of blocks the particle pass uses for np particles (fixed, so the
 // diagnostics reduction order is deterministic).
-int particle_pass_blocks(int64_t np);
+int particle_pass_blocks(int64_t np, int ndim);
 
 // Reconstruct positions (FP64) from cell + offset for host read-back.
 cudaError_t launch_positions_f64(const GridParams &g, const double *dx, ParticlesF32 p,

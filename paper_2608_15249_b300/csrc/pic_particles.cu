@@ -21,19 +21,19 @@ constexpr int PP_THREADS = 256;
 __device__ __forceinline__ void latch(int *flags, int bit) { atomicOr(flags, bit); }
 
 template <int D>
-__device__ __forceinline__ void decode_cell(int cell, const int *n, int *c)
+__device__ __forceinline__ void decode_cell(int cell, const GridParams &g, int *c)
 {
     if (D == 1) {
         c[0] = cell;
     } else if (D == 2) {
-        int c1 = cell / n[0];
-        c[0] = cell - c1 * n[0];
+        const int c1 = (int)fdiv((uint32_t)cell, g.div0);
+        c[0] = cell - c1 * g.n[0];
         c[1] = c1;
     } else {
-        int c12 = cell / n[0];
-        c[0] = cell - c12 * n[0];
-        int c2 = c12 / n[1];
-        c[1] = c12 - c2 * n[1];
+        const int c12 = (int)fdiv((uint32_t)cell, g.div0);
+        c[0] = cell - c12 * g.n[0];
+        const int c2 = (int)fdiv((uint32_t)c12, g.div1);
+        c[1] = c12 - c2 * g.n[1];
         c[2] = c2;
     }
 }
@@ -89,45 +89,98 @@ __device__ __forceinline__ void gather_E(const float *__restrict__ E, const int 
     }
 }
 
-// Fixed-point CIC deposit of one particle at cell c, offsets f.
+// Fixed-point CIC weights of one particle: corner k (bit a of k selects the
+// upper node on axis a) gets round(W_k 2^S) for every corner but the last,
+// which takes 2^S minus the others, so the particle deposits exactly 2^S.
+// With S <= 25 every quantum, and a warp's sum of 32 of them, fits in int32.
 template <int D>
-__device__ __forceinline__ void deposit_fx(unsigned long long *__restrict__ acc, const int *c,
-                                           const float *f, const int *n, float scale,
-                                           long long one)
+__device__ __forceinline__ void cic_quanta(const float *f, float scale, int one, int *q)
 {
+    const float wx[2] = {1.0f - f[0], f[0]};
     if (D == 1) {
-        const long long q0 = __float2ll_rn((1.0f - f[0]) * scale);
-        atomicAdd(acc + c[0], (unsigned long long)q0);
-        atomicAdd(acc + up(c[0], n[0]), (unsigned long long)(one - q0));
+        q[0] = __float2int_rn(wx[0] * scale);
+        q[1] = one - q[0];
     } else if (D == 2) {
-        const int x0 = c[0], x1 = up(c[0], n[0]);
-        const int y0 = c[1] * n[0], y1 = up(c[1], n[1]) * n[0];
-        const float wx0 = 1.0f - f[0], wx1 = f[0], wy0 = 1.0f - f[1], wy1 = f[1];
-        const long long q00 = __float2ll_rn(wx0 * wy0 * scale);
-        const long long q10 = __float2ll_rn(wx1 * wy0 * scale);
-        const long long q01 = __float2ll_rn(wx0 * wy1 * scale);
-        const long long q11 = one - q00 - q10 - q01;
-        atomicAdd(acc + x0 + y0, (unsigned long long)q00);
-        atomicAdd(acc + x1 + y0, (unsigned long long)q10);
-        atomicAdd(acc + x0 + y1, (unsigned long long)q01);
-        atomicAdd(acc + x1 + y1, (unsigned long long)q11);
+        const float wy[2] = {1.0f - f[1], f[1]};
+        q[0] = __float2int_rn(wx[0] * wy[0] * scale);
+        q[1] = __float2int_rn(wx[1] * wy[0] * scale);
+        q[2] = __float2int_rn(wx[0] * wy[1] * scale);
+        q[3] = one - q[0] - q[1] - q[2];
     } else {
-        const int nxy = n[0] * n[1];
-        const int x[2] = {c[0], up(c[0], n[0])};
-        const int y[2] = {c[1] * n[0], up(c[1], n[1]) * n[0]};
-        const int z[2] = {c[2] * nxy, up(c[2], n[2]) * nxy};
-        const float wx[2] = {1.0f - f[0], f[0]};
         const float wy[2] = {1.0f - f[1], f[1]};
         const float wz[2] = {1.0f - f[2], f[2]};
-        long long rest = one;
+        int rest = one;
 #pragma unroll
-        for (int s = 0; s < 7; ++s) {
-            const int i = s & 1, j = (s >> 1) & 1, k = s >> 2;
-            const long long qs = __float2ll_rn(wx[i] * wy[j] * wz[k] * scale);
-            rest -= qs;
-            atomicAdd(acc + x[i] + y[j] + z[k], (unsigned long long)qs);
+        for (int k = 0; k < 7; ++k) {
+            q[k] = __float2int_rn(wx[k & 1] * wy[(k >> 1) & 1] * wz[k >> 2] * scale);
+            rest -= q[k];
         }
-        atomicAdd(acc + x[1] + y[1] + z[1], (unsigned long long)rest);
+        q[7] = rest;
+    }
+}
+
+// Flat node index of corner k of cell c.
+template <int D>
+__device__ __forceinline__ void corner_nodes(const int *c, const int *n, int *node)
+{
+    const int x[2] = {c[0], up(c[0], n[0])};
+    if (D == 1) {
+        node[0] = x[0];
+        node[1] = x[1];
+    } else if (D == 2) {
+        const int y[2] = {c[1] * n[0], up(c[1], n[1]) * n[0]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) node[k] = x[k & 1] + y[k >> 1];
+    } else {
+        const int nxy = n[0] * n[1];
+        const int y[2] = {c[1] * n[0], up(c[1], n[1]) * n[0]};
+        const int z[2] = {c[2] * nxy, up(c[2], n[2]) * nxy};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) node[k] = x[k & 1] + y[(k >> 1) & 1] + z[k >> 2];
+    }
+}
+
+// Warp-cooperative deposit.  Lanes hold consecutive particles of the sorted
+// array, so runs of lanes share a cell (key).  A segmented inclusive scan over
+// the lanes (five shuffle steps, fixed cost whatever the data) sums the first
+// 2^d - 1 corner quanta of each run; the run's last corner is its particle
+// count times 2^S minus those sums (the per-particle remainder rule, summed).
+// The last lane of each run issues one 64-bit atomic per corner.  Lanes with
+// key < 0 deposit nothing.  Integer sums make the result independent of how
+// lanes group and of the order of the atomics.  Must be called by all lanes.
+template <int D>
+__device__ __forceinline__ void warp_deposit(unsigned long long *__restrict__ acc, int key,
+                                             const int *node, const int *q, int one)
+{
+    constexpr int NC = 1 << D;
+    const int lane = threadIdx.x & 31;
+    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    // first lane of this lane's run: the highest head at or below this lane
+    const unsigned le = 0xffffffffu >> (31 - lane);
+    const int seg = 31 - __clz(heads & le);
+    int s[NC - 1];
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) s[k] = q[k];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const bool take = lane - d >= seg;
+#pragma unroll
+        for (int k = 0; k < NC - 1; ++k) {
+            const int y = __shfl_up_sync(0xffffffffu, s[k], d);
+            if (take) s[k] += y;
+        }
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (tail && key >= 0) {
+        long long rest = (long long)(lane - seg + 1) * one;
+#pragma unroll
+        for (int k = 0; k < NC - 1; ++k) {
+            rest -= s[k];
+            atomicAdd(acc + node[k], (unsigned long long)(long long)s[k]);
+        }
+        atomicAdd(acc + node[NC - 1], (unsigned long long)rest);
     }
 }
 
@@ -199,84 +252,97 @@ __device__ __forceinline__ double warp_sum_d(double x)
 enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8 };
 
 template <int D, int NV>
-__global__ void __launch_bounds__(PP_THREADS)
+__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     k_particle_pass(GridParams g, ParticlesF32 p, const float *__restrict__ E,
                     unsigned long long *__restrict__ acc, int mode,
                     double *__restrict__ diag_blocks, int *__restrict__ err)
 {
     const int64_t np = p.np;
     const float scale = ldexpf(1.0f, g.fx_bits);
-    const long long one = 1ll << g.fx_bits;
+    const int one = 1 << g.fx_bits;
     // FP32 running sums, folded into FP64 every 16 particles of this thread
     float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
     double dke = 0.0, dmom[3] = {0.0, 0.0, 0.0};
     int fold = 0;
     bool bad = false;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
+    // warp-uniform loop: lane i of a warp handles particle base + i
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < np; base += wstride * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < np;
         int c[3] = {0, 0, 0};
         float f[3] = {0.0f, 0.0f, 0.0f};
         float v[3] = {0.0f, 0.0f, 0.0f};
-        decode_cell<D>(p.cell[i], g.n, c);
+        bool ok = valid;
+        if (valid) {
+            decode_cell<D>(p.cell[i], g, c);
 #pragma unroll
-        for (int a = 0; a < D; ++a) f[a] = p.off[a * np + i];
-        if (mode & (PASS_PUSH | PASS_MOVE)) {
+            for (int a = 0; a < D; ++a) f[a] = p.off[a * np + i];
+            if (mode & (PASS_PUSH | PASS_MOVE)) {
 #pragma unroll
-            for (int a = 0; a < NV; ++a) v[a] = p.v[a * np + i];
-        }
-        if (mode & PASS_PUSH) {
-            float e[3] = {0.0f, 0.0f, 0.0f};
-            gather_E<D>(E, c, f, g.n, e);
+                for (int a = 0; a < NV; ++a) v[a] = p.v[a * np + i];
+            }
+            if (mode & PASS_PUSH) {
+                float e[3] = {0.0f, 0.0f, 0.0f};
+                gather_E<D>(E, c, f, g.n, e);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
-            float vn[3] = {v[0], v[1], v[2]};
-            boris(vn, e, g);
-            bool finite = true;
+                for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
+                float vn[3] = {v[0], v[1], v[2]};
+                boris(vn, e, g);
+                bool finite = true;
 #pragma unroll
-            for (int a = 0; a < NV; ++a) finite &= isfinite(vn[a]);
-            if (!finite) bad = true;
-            if (mode & PASS_DIAG) {
-                float o2 = 0.0f, n2 = 0.0f;
+                for (int a = 0; a < NV; ++a) finite &= isfinite(vn[a]);
+                if (!finite) bad = true;
+                if (mode & PASS_DIAG) {
+                    float o2 = 0.0f, n2 = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) {
+                        o2 += v[a] * v[a];
+                        n2 += vn[a] * vn[a];
+                        mom[a] += vn[a];
+                    }
+                    ke += 0.5f * (o2 + n2);
+                    if (++fold == 16) {
+                        dke += ke;
+                        ke = 0.0f;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            dmom[a] += mom[a];
+                            mom[a] = 0.0f;
+                        }
+                        fold = 0;
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < NV; ++a) {
-                    o2 += v[a] * v[a];
-                    n2 += vn[a] * vn[a];
-                    mom[a] += vn[a];
-                }
-                ke += 0.5f * (o2 + n2);
-                if (++fold == 16) {
-                    dke += ke;
-                    ke = 0.0f;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        dmom[a] += mom[a];
-                        mom[a] = 0.0f;
-                    }
-                    fold = 0;
+                    v[a] = vn[a];
+                    p.v[a * np + i] = vn[a];
                 }
             }
+            if (mode & PASS_MOVE) {
+                if (move<D>(c, f, v, g)) {
+                    p.cell[i] = encode_cell<D>(c, g.n);
 #pragma unroll
-            for (int a = 0; a < NV; ++a) {
-                v[a] = vn[a];
-                p.v[a * np + i] = vn[a];
+                    for (int a = 0; a < D; ++a) p.off[a * np + i] = f[a];
+                } else {
+                    bad = true;
+                }
             }
         }
-        if (mode & PASS_MOVE) {
-            if (move<D>(c, f, v, g)) {
-                p.cell[i] = encode_cell<D>(c, g.n);
-#pragma unroll
-                for (int a = 0; a < D; ++a) p.off[a * np + i] = f[a];
-            } else {
-                bad = true;
-            }
+        if (mode & PASS_DEPOSIT) {
+            int q[1 << D], node[1 << D];
+            cic_quanta<D>(f, scale, one, q);
+            corner_nodes<D>(c, g.n, node);
+            warp_deposit<D>(acc, ok ? encode_cell<D>(c, g.n) : -1, node, q, one);
         }
-        if (mode & PASS_DEPOSIT) deposit_fx<D>(acc, c, f, g.n, scale, one);
     }
     if (bad) latch(err, EF_NONFINITE);
     if (mode & PASS_DIAG) {
         __shared__ double red[4][PP_THREADS / 32];
         double vals[4] = {dke + ke, dmom[0] + mom[0], dmom[1] + mom[1], dmom[2] + mom[2]};
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int w = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const double s = warp_sum_d(vals[k]);
@@ -291,7 +357,7 @@ __global__ void __launch_bounds__(PP_THREADS)
     }
 }
 
-int particle_pass_blocks(int64_t np)
+int particle_pass_blocks(int64_t np, int ndim)
 {
     static int sms = 0;
     if (!sms) {
@@ -300,8 +366,10 @@ int particle_pass_blocks(int64_t np)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
+    // one resident wave: 4 blocks of 256 per SM (3 in 3D, where the pass needs more
+    // registers), each block striding over the particle array
     const int64_t need = (np + PP_THREADS - 1) / PP_THREADS;
-    const int64_t cap = (int64_t)sms * 8;
+    const int64_t cap = (int64_t)sms * (ndim == 3 ? 3 : 4);
     int64_t b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
 }
@@ -322,7 +390,7 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
     if (p.np == 0) return cudaSuccess;
     const int mode = (push ? PASS_PUSH : 0) | (mv ? PASS_MOVE : 0) |
                      (deposit ? PASS_DEPOSIT : 0) | (diag.blocks && push ? PASS_DIAG : 0);
-    const int nb = particle_pass_blocks(p.np);
+    const int nb = particle_pass_blocks(p.np, g.ndim);
     const int key = g.ndim * 10 + p.nv;
     switch (key) {
     case 11: launch_pass_t<1, 1>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
@@ -455,9 +523,9 @@ __global__ void k_positions_f64(GridParams g, double dx0, double dx1, double dx2
          i += (int64_t)gridDim.x * blockDim.x) {
         int c[3] = {0, 0, 0};
         const int cell = p.cell[i];
-        if (D == 1) decode_cell<1>(cell, g.n, c);
-        else if (D == 2) decode_cell<2>(cell, g.n, c);
-        else decode_cell<3>(cell, g.n, c);
+        if (D == 1) decode_cell<1>(cell, g, c);
+        else if (D == 2) decode_cell<2>(cell, g, c);
+        else decode_cell<3>(cell, g, c);
         for (int a = 0; a < D; ++a)
             x[i * D + a] = ((double)c[a] + (double)p.off[a * p.np + i]) * dx[a];
     }
