@@ -57,7 +57,8 @@ typedef enum {
     AP_PIC_ERR_CUDA = -4,          /* a CUDA runtime call failed               */
     AP_PIC_ERR_NOT_CONVERGED = -5, /* field solve hit cg_maxit                 */
     AP_PIC_ERR_BOUNDS = -6,        /* non-finite or out-of-range particle      */
-    AP_PIC_ERR_STATE = -7          /* call out of order (e.g. step before load) */
+    AP_PIC_ERR_STATE = -7,         /* call out of order (e.g. step before load) */
+    AP_PIC_ERR_TOO_LARGE = -8      /* size beyond a fixed capacity              */
 } ap_pic_status;
 
 enum { AP_PIC_BC_PERIODIC = 0 };
@@ -184,6 +185,33 @@ ap_pic_status ap_pic_solve_field(ap_pic *h);
 /* Per-cell sort: stable reorder of the particle arrays by the brick-major
  * cell key (ties keep their order).  FP32_CELLOFF only; a no-op for FP64_PLAIN. */
 ap_pic_status ap_pic_sort(ap_pic *h);
+
+/* Capacity (particles) of ap_pic_sort_perm_noalloc. */
+#define AP_PIC_NOALLOC_MAX_NP (1 << 20)
+
+/* The per-cell sort permutation without allocating device memory.
+ * The paper has no counterpart: this exists for callers that may not call
+ * cudaMalloc -- a host framework that owns all of the device's memory through
+ * its own pool, or a hot loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
+ * Computes the same stable brick-major permutation as ap_pic_sort: perm[r] =
+ * index in `cell` of the particle of rank r (ties keep input order).
+ *   ndim, n[3], brick[3]: grid and sort brick as in ap_pic_config (brick 0:
+ *       the library default; bricks are capped by n);
+ *   np: particles, 0 <= np <= AP_PIC_NOALLOC_MAX_NP, else AP_PIC_ERR_TOO_LARGE
+ *       with no device work;
+ *   cell: device, np int32 linear cell indices in [0, cells);
+ *   perm: device, np int32 (output); both caller-owned;
+ *   cuda_stream: cudaStream_t (NULL: legacy default stream); the call is
+ *       asynchronous on it.
+ * Scratch is one fixed array of ~16.3 MiB in device global memory, held by
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device (with that device current) looks up the array's device address
+ * and keeps it.  All calls share the array and each overwrites it: calls that
+ * overlap on the GPU race, so the caller must order them (one stream per
+ * device, or explicit synchronisation). */
+ap_pic_status ap_pic_sort_perm_noalloc(int ndim, const int n[3], const int brick[3], int64_t np,
+                                       const int32_t *cell, int32_t *perm, void *cuda_stream);
 
 /* nsteps full cycles: push+deposit (fused), sort when due, field solve,
  * diagnostics when due. */

@@ -24,8 +24,9 @@ AP_PIC_OK = 0
 STATUS = {
     0: "AP_PIC_OK", -1: "AP_PIC_ERR_ARG", -2: "AP_PIC_ERR_UNSUPPORTED", -3: "AP_PIC_ERR_NOMEM",
     -4: "AP_PIC_ERR_CUDA", -5: "AP_PIC_ERR_NOT_CONVERGED", -6: "AP_PIC_ERR_BOUNDS",
-    -7: "AP_PIC_ERR_STATE",
+    -7: "AP_PIC_ERR_STATE", -8: "AP_PIC_ERR_TOO_LARGE",
 }
+AP_PIC_NOALLOC_MAX_NP = 1 << 20
 AP_PIC_BC_PERIODIC = 0
 AP_PIC_FP32_CELLOFF = 0
 AP_PIC_FP64_PLAIN = 1
@@ -39,6 +40,7 @@ EXPORTS = [
     "ap_pic_get_phi", "ap_pic_get_rho_fx", "ap_pic_get_particles", "ap_pic_get_velocities_f64",
     "ap_pic_get_perm", "ap_pic_get_diag", "ap_pic_set_timing", "ap_pic_get_timing",
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
+    "ap_pic_sort_perm_noalloc",
 ]
 STAGES = ["push_deposit", "rho", "sort", "field", "diag"]
 NSTAGES = 8
@@ -120,6 +122,7 @@ def _declare(L):
     L.ap_pic_num_particles.restype = I64
     L.ap_pic_last_error.argtypes = [P]
     L.ap_pic_last_error.restype = ctypes.c_char_p
+    L.ap_pic_sort_perm_noalloc.argtypes = [I, P, P, I64, P, P, P]
     L.ap_pic_version.argtypes = []
     L.ap_pic_version.restype = ctypes.c_char_p
 
