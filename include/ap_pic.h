@@ -89,9 +89,11 @@ typedef struct {
                               never); ignored by AP_PIC_FP64_PLAIN                 */
     int fx_bits;           /* fixed-point fraction bits S of the charge accumulator:
                               each particle deposits exactly 2^S.  FP32 form: 0 means
-                              24 (the precision of its FP32 weights), at most 25 (a
-                              warp's per-corner sum must fit int32).  Always capped
-                              at 62 - bitlen(np) so the int64 sum cannot overflow  */
+                              22, which is also the maximum (its FP32 weights are
+                              rounded to 2^-S without a float-to-int conversion,
+                              exact up to 2^22).  FP64 plain form: 0 means 40, at
+                              most 52.  Always capped at 62 - bitlen(np) so the
+                              int64 sum cannot overflow                            */
     double cg_rtol;        /* field-solve relative residual target (0: 1e-6)      */
     int cg_maxit;          /* field-solve iteration cap (0: 20000)                 */
     int brick[3];          /* sort brick in cells per axis (0: library default)    */
@@ -124,7 +126,8 @@ typedef struct {
 enum {
     AP_PIC_EFLAG_NONFINITE = 1,     /* a particle's offset or velocity was not finite */
     AP_PIC_EFLAG_CG = 2,            /* a field solve stopped at cg_maxit              */
-    AP_PIC_EFLAG_OVERFLOW = 4       /* a particle count exceeded the fixed-point range */
+    AP_PIC_EFLAG_OVERFLOW = 4,      /* a particle count exceeded the fixed-point range */
+    AP_PIC_EFLAG_TIMEOUT = 8        /* a bounded device wait gave up (the pass stopped) */
 };
 
 typedef struct ap_pic ap_pic;

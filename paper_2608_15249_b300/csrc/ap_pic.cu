@@ -24,8 +24,8 @@ void apk::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed
 
 namespace {
 
-constexpr int DEFAULT_FX_BITS = 24;   // FP32 cell+offset form: matches the FP32 weights
-constexpr int MAX_FX_BITS_F32 = 25;   // a warp's 32 corner quanta must sum inside int32
+constexpr int DEFAULT_FX_BITS = 22;   // FP32 cell+offset form: near the FP32 weights' precision
+constexpr int MAX_FX_BITS_F32 = 22;   // the FMA rounding idiom is exact up to 2^22
 constexpr int DEFAULT_FX_BITS_F64 = 40;  // FP64 plain form: FP64 weights
 constexpr int MAX_FX_BITS_F64 = 52;
 constexpr double DEFAULT_CG_RTOL_F64 = 1e-10;
@@ -266,6 +266,8 @@ static ap_pic_status sync_check(ap_pic *h)
         return fail(h, AP_PIC_ERR_BOUNDS,
                     "a particle position or velocity was not finite or outside the box");
     if (e & EF_OVERFLOW) return fail(h, AP_PIC_ERR_BOUNDS, "fixed-point charge overflow");
+    if (e & EF_TIMEOUT)
+        return fail(h, AP_PIC_ERR_CUDA, "a device wait hit its iteration cap; results are partial");
     if (e & EF_CG)
         return fail(h, AP_PIC_ERR_NOT_CONVERGED, "field solve stopped at cg_maxit = %d",
                     h->cfg.cg_maxit);
@@ -371,6 +373,8 @@ static ap_pic_status create_grid_f64(ap_pic *h)
         f.n[a] = h->cfg.n[a];
         f.dx[a] = h->cfg.dx[a];
     }
+    f.div0 = make_fastdiv((uint32_t)f.n[0]);
+    f.div1 = make_fastdiv((uint32_t)f.n[1]);
     f.nblocks = field_blocks(h->cells);
     const size_t c = (size_t)h->cells;
     TRY(alloc_n(h, &f.acc, c));
@@ -413,6 +417,8 @@ static ap_pic_status create_grid(ap_pic *h)
         f.n[a] = h->cfg.n[a];
         f.dx[a] = h->cfg.dx[a];
     }
+    f.div0 = make_fastdiv((uint32_t)f.n[0]);
+    f.div1 = make_fastdiv((uint32_t)f.n[1]);
     f.Estride = h->ndim == 3 ? 4 : h->ndim;
     f.nblocks = field_blocks(h->cells);
     const size_t c = (size_t)h->cells;
@@ -557,12 +563,17 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
         h->p64.nv = h->nv;
         return AP_PIC_OK;
     }
+    const size_t st = (size_t)soa_stride(np);
     ParticlesF32 *ps[2] = {&h->p, &h->p_alt};
     for (ParticlesF32 *q : ps) {
-        TRY(alloc_n(h, &q->cell, n));
-        TRY(alloc_n(h, &q->off, n * h->ndim));
-        TRY(alloc_n(h, &q->v, n * h->nv));
+        TRY(alloc_n(h, &q->cell, st));
+        TRY(alloc_n(h, &q->off, st * h->ndim));
+        TRY(alloc_n(h, &q->v, st * h->nv));
+        CU(h, cudaMemsetAsync(q->cell, 0, st * 4, h->stream));
+        CU(h, cudaMemsetAsync(q->off, 0, st * h->ndim * 4, h->stream));
+        CU(h, cudaMemsetAsync(q->v, 0, st * h->nv * 4, h->stream));
         q->np = np;
+        q->stride = (int64_t)st;
         q->nv = h->nv;
     }
     for (int k = 0; k < 2; ++k) {
@@ -969,20 +980,21 @@ extern "C" ap_pic_status ap_pic_get_particles(ap_pic *h, int32_t *cell, float *o
         CU(h, cudaMemcpyAsync(cell, h->p.cell, (size_t)np * 4, cudaMemcpyDeviceToHost, h->stream));
     std::vector<float> tmp;
     if (off) {
-        tmp.resize((size_t)np * h->ndim);
+        tmp.resize((size_t)h->p.stride * h->ndim);
         CU(h, cudaMemcpyAsync(tmp.data(), h->p.off, tmp.size() * 4, cudaMemcpyDeviceToHost,
                               h->stream));
         CU(h, cudaStreamSynchronize(h->stream));
         for (int64_t i = 0; i < np; ++i)
-            for (int a = 0; a < h->ndim; ++a) off[i * h->ndim + a] = tmp[(size_t)a * np + i];
+            for (int a = 0; a < h->ndim; ++a)
+                off[i * h->ndim + a] = tmp[(size_t)a * h->p.stride + i];
     }
     if (v) {
-        tmp.resize((size_t)np * h->nv);
+        tmp.resize((size_t)h->p.stride * h->nv);
         CU(h, cudaMemcpyAsync(tmp.data(), h->p.v, tmp.size() * 4, cudaMemcpyDeviceToHost,
                               h->stream));
         CU(h, cudaStreamSynchronize(h->stream));
         for (int64_t i = 0; i < np; ++i)
-            for (int a = 0; a < h->nv; ++a) v[i * h->nv + a] = tmp[(size_t)a * np + i];
+            for (int a = 0; a < h->nv; ++a) v[i * h->nv + a] = tmp[(size_t)a * h->p.stride + i];
     }
     if (x) {
         double *dxp = nullptr;

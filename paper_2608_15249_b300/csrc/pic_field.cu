@@ -95,13 +95,22 @@ __device__ double reduce_partials(const double *__restrict__ part, int n)
     return block_sum(s);
 }
 
-// Node coordinates from a flat index (axis 0 fastest).
+// Node coordinates from a flat index (axis 0 fastest); cells < 2^30, so 32-bit
+// multiply-high division (a runtime division would issue float conversions on
+// this GPU's slow FP64 pipe).
 __device__ __forceinline__ void node_coords(int64_t id, const FieldBufs &f, int *j)
 {
-    j[0] = (int)(id % f.n[0]);
-    const int64_t r = id / f.n[0];
-    j[1] = f.ndim >= 2 ? (int)(r % f.n[1]) : 0;
-    j[2] = f.ndim >= 3 ? (int)(r / f.n[1]) : 0;
+    const uint32_t u = (uint32_t)id;
+    const uint32_t r = fdiv(u, f.div0);
+    j[0] = (int)(u - r * (uint32_t)f.n[0]);
+    if (f.ndim >= 2) {
+        const uint32_t r2 = fdiv(r, f.div1);
+        j[1] = (int)(r - r2 * (uint32_t)f.n[1]);
+        j[2] = (int)r2;
+    } else {
+        j[1] = 0;
+        j[2] = 0;
+    }
 }
 
 // (-lap_h u)[id] on the periodic grid.

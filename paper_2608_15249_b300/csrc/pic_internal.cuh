@@ -37,6 +37,7 @@ inline FastDiv make_fastdiv(uint32_t d)
 #ifdef __CUDACC__
 __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f)
 {
+    if (f.d == 1) return x;
     const uint32_t t = __umulhi(f.m, x);
     return (t + ((x - t) >> 1)) >> (f.l - 1);
 }
@@ -57,16 +58,21 @@ struct GridParams {
 };
 
 // Error bits latched in the device word (same values as AP_PIC_EFLAG_*).
-enum : int { EF_NONFINITE = 1, EF_CG = 2, EF_OVERFLOW = 4 };
+enum : int { EF_NONFINITE = 1, EF_CG = 2, EF_OVERFLOW = 4, EF_TIMEOUT = 8 };
 
 // ---- particle kernels (pic_particles.cu) --------------------------------------------------
 struct ParticlesF32 {
-    int32_t *cell;     // [np]
-    float *off;        // [ndim][np]
-    float *v;          // [nv][np]
+    int32_t *cell;     // [stride] (np used)
+    float *off;        // [ndim][stride]
+    float *v;          // [nv][stride]
     int64_t np;
+    int64_t stride;    // np rounded up to a multiple of 64: every component array starts
+                       // 256-byte aligned and may be read (TMA) up to a multiple of 16 bytes
     int nv;
 };
+
+// Component stride for np particles.
+inline int64_t soa_stride(int64_t np) { return ((np > 0 ? np : 1) + 63) / 64 * 64; }
 
 struct DiagPartials {
     double *blocks;    // [nblocks][4]: kinetic, momentum x, y, z
@@ -153,6 +159,7 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t 
 struct FieldBufs {
     int ndim;
     int n[3];
+    FastDiv div0, div1;        // division by n[0], n[1] (node coordinates)
     int64_t cells;
     double dx[3];
     unsigned long long *acc;   // int64 fixed point
@@ -194,6 +201,7 @@ cudaError_t launch_phi_to_f64(FieldBufs &f, double *out, cudaStream_t st);
 struct FieldBufsF64 {
     int ndim;
     int n[3];
+    FastDiv div0, div1;
     int64_t cells;
     double dx[3];
     unsigned long long *acc;

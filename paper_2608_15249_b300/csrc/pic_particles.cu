@@ -92,19 +92,31 @@ __device__ __forceinline__ void gather_E(const float *__restrict__ E, const int 
 // Fixed-point CIC weights of one particle: corner k (bit a of k selects the
 // upper node on axis a) gets round(W_k 2^S) for every corner but the last,
 // which takes 2^S minus the others, so the particle deposits exactly 2^S.
-// With S <= 25 every quantum, and a warp's sum of 32 of them, fits in int32.
+// Rounding uses the FMA "magic number" idiom instead of a float-to-int
+// conversion (conversions issue on the slow FP64 pipe of this GPU): for
+// |x| <= 2^22, fma(w, 2^S, 1.5 * 2^23) rounds w 2^S to the nearest integer
+// (ties to even) in the low mantissa bits, exactly once.  S <= 22 keeps every
+// quantum in that range and a warp's sum of 32 of them inside int32.
+constexpr float RND_MAGIC = 12582912.0f;     // 1.5 * 2^23
+constexpr int RND_MAGIC_BITS = 0x4B400000;   // its bit pattern
+
+__device__ __forceinline__ int round_fx(float w, float scale)
+{
+    return __float_as_int(fmaf(w, scale, RND_MAGIC)) - RND_MAGIC_BITS;
+}
+
 template <int D>
 __device__ __forceinline__ void cic_quanta(const float *f, float scale, int one, int *q)
 {
     const float wx[2] = {1.0f - f[0], f[0]};
     if (D == 1) {
-        q[0] = __float2int_rn(wx[0] * scale);
+        q[0] = round_fx(wx[0], scale);
         q[1] = one - q[0];
     } else if (D == 2) {
         const float wy[2] = {1.0f - f[1], f[1]};
-        q[0] = __float2int_rn(wx[0] * wy[0] * scale);
-        q[1] = __float2int_rn(wx[1] * wy[0] * scale);
-        q[2] = __float2int_rn(wx[0] * wy[1] * scale);
+        q[0] = round_fx(wx[0] * wy[0], scale);
+        q[1] = round_fx(wx[1] * wy[0], scale);
+        q[2] = round_fx(wx[0] * wy[1], scale);
         q[3] = one - q[0] - q[1] - q[2];
     } else {
         const float wy[2] = {1.0f - f[1], f[1]};
@@ -112,7 +124,7 @@ __device__ __forceinline__ void cic_quanta(const float *f, float scale, int one,
         int rest = one;
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            q[k] = __float2int_rn(wx[k & 1] * wy[(k >> 1) & 1] * wz[k >> 2] * scale);
+            q[k] = round_fx(wx[k & 1] * wy[(k >> 1) & 1] * wz[k >> 2], scale);
             rest -= q[k];
         }
         q[7] = rest;
@@ -140,47 +152,59 @@ __device__ __forceinline__ void corner_nodes(const int *c, const int *n, int *no
     }
 }
 
-// Warp-cooperative deposit.  Lanes hold consecutive particles of the sorted
-// array, so runs of lanes share a cell (key).  A segmented inclusive scan over
-// the lanes (five shuffle steps, fixed cost whatever the data) sums the first
-// 2^d - 1 corner quanta of each run; the run's last corner is its particle
-// count times 2^S minus those sums (the per-particle remainder rule, summed).
-// The last lane of each run issues one 64-bit atomic per corner.  Lanes with
-// key < 0 deposit nothing.  Integer sums make the result independent of how
-// lanes group and of the order of the atomics.  Must be called by all lanes.
-template <int D>
-__device__ __forceinline__ void warp_deposit(unsigned long long *__restrict__ acc, int key,
-                                             const int *node, const int *q, int one)
+// Warp-cooperative deposit of R particles per lane.  For each r, lanes hold
+// consecutive particles of the sorted array, so runs of lanes share a cell
+// (key).  A segmented inclusive scan over the lanes (five shuffle steps, fixed
+// cost whatever the data) sums the first 2^d - 1 corner quanta of each run; the
+// run's last corner is its particle count times 2^S minus those sums (the
+// per-particle remainder rule, summed).  The last lane of each run hands each
+// corner's total to emit(r, corner, value).  The R scans are interleaved step by
+// step so their shuffles overlap.  Lanes with key < 0 deposit nothing.  Integer
+// sums make the result independent of how lanes group and of the order in
+// which totals are added.  All 32 lanes must call it.
+template <int D, int R, class Emit>
+__device__ __forceinline__ void warp_deposit(const int (&key)[R], const int (&q)[R][1 << D],
+                                             int one, Emit emit)
 {
     constexpr int NC = 1 << D;
     const int lane = threadIdx.x & 31;
-    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = lane == 0 || kprev != key;
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    // first lane of this lane's run: the highest head at or below this lane
     const unsigned le = 0xffffffffu >> (31 - lane);
-    const int seg = 31 - __clz(heads & le);
-    int s[NC - 1];
+    int seg[R];
+    unsigned heads[R];
+    int s[R][NC - 1];
 #pragma unroll
-    for (int k = 0; k < NC - 1; ++k) s[k] = q[k];
+    for (int r = 0; r < R; ++r) {
+        const int kprev = __shfl_up_sync(0xffffffffu, key[r], 1);
+        heads[r] = __ballot_sync(0xffffffffu, lane == 0 || kprev != key[r]);
+        // first lane of this lane's run: the highest head at or below this lane
+        seg[r] = 31 - __clz(heads[r] & le);
+#pragma unroll
+        for (int k = 0; k < NC - 1; ++k) s[r][k] = q[r][k];
+    }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const bool take = lane - d >= seg;
 #pragma unroll
-        for (int k = 0; k < NC - 1; ++k) {
-            const int y = __shfl_up_sync(0xffffffffu, s[k], d);
-            if (take) s[k] += y;
+        for (int r = 0; r < R; ++r) {
+            const bool take = lane - d >= seg[r];
+#pragma unroll
+            for (int k = 0; k < NC - 1; ++k) {
+                const int y = __shfl_up_sync(0xffffffffu, s[r][k], d);
+                if (take) s[r][k] += y;
+            }
         }
     }
-    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (tail && key >= 0) {
-        long long rest = (long long)(lane - seg + 1) * one;
 #pragma unroll
-        for (int k = 0; k < NC - 1; ++k) {
-            rest -= s[k];
-            atomicAdd(acc + node[k], (unsigned long long)(long long)s[k]);
+    for (int r = 0; r < R; ++r) {
+        const bool tail = lane == 31 || ((heads[r] >> (lane + 1)) & 1u);
+        if (tail && key[r] >= 0) {
+            int rest = (lane - seg[r] + 1) * one;
+#pragma unroll
+            for (int k = 0; k < NC - 1; ++k) {
+                rest -= s[r][k];
+                emit(r, k, s[r][k]);
+            }
+            emit(r, NC - 1, rest);
         }
-        atomicAdd(acc + node[NC - 1], (unsigned long long)rest);
     }
 }
 
@@ -208,8 +232,10 @@ __device__ __forceinline__ void boris(float *v, const float *e, const GridParams
 
 // Position update in cell units with periodic wrap (application code in
 // Sec. 3.1): o = f + v dt/dx; shift = floor(o); f = o - shift (forced into
-// [0, 1)); cell += shift mod n.  Returns false for a non-finite or absurd
-// displacement (the particle is then left where it was).
+// [0, 1)); cell += shift mod n.  A displacement under one cell (|v dt/dx| < 1,
+// the usual case) takes shift from two compares and the fraction from one
+// exact add, with no float-to-int conversion; larger ones take floorf.
+// Returns false for an absurd displacement (the particle is then left as is).
 template <int D>
 __device__ __forceinline__ bool move(int *c, float *f, const float *v, const GridParams &g)
 {
@@ -217,12 +243,22 @@ __device__ __forceinline__ bool move(int *c, float *f, const float *v, const Gri
     int nc[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float o = f[a] + v[a] * g.dtdx[a];
-        if (!(fabsf(o) < 1.0e9f)) return false;  // also catches NaN / inf
-        const float fl = floorf(o);
-        float fr = o - fl;
-        int s = (int)fl;
-        if (fr >= 1.0f) {  // o a tiny negative number: o - floor(o) rounds up to 1
+        const float dsp = v[a] * g.dtdx[a];
+        const float o = f[a] + dsp;
+        float fr;
+        int s;
+        if (fabsf(dsp) < 1.0f) {
+            // o in (-1, 2): o - 1 is exact on [1, 2); o + 1 may round up to 1
+            const bool hi = o >= 1.0f, lo = o < 0.0f;
+            fr = hi ? o - 1.0f : (lo ? o + 1.0f : o);
+            s = hi ? 1 : (lo ? -1 : 0);
+        } else {
+            if (!(fabsf(dsp) < 1.0e6f)) return false;
+            const float fl = floorf(o);
+            fr = o - fl;
+            s = (int)fl;
+        }
+        if (fr >= 1.0f) {  // o a tiny negative number: its fraction rounded up to 1
             fr = 0.0f;
             s += 1;
         }
@@ -251,110 +287,402 @@ __device__ __forceinline__ double warp_sum_d(double x)
 
 enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8 };
 
-template <int D, int NV>
+// ---- TMA bulk-copy pipeline helpers (PTX) ---------------------------------------------------
+
+constexpr int TILE = 512;           // particles per tile (2 per thread)
+constexpr int WIN_CAP = 2048;       // nodes of a tile's shared-memory charge window
+constexpr int STAGES = 4;           // tiles in flight per CTA
+constexpr int WAIT_LIMIT = 1 << 26;   // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Polls the barrier phase with an iteration cap; false if the cap ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (int k = 0; k < WAIT_LIMIT; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1D bulk copy global -> shared, completing `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// 1D bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Waits until at most N committed bulk groups are still reading shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// The particle pass.  Persistent CTAs walk tiles of TILE consecutive particles
+// (tile t for t = blockIdx.x, + gridDim.x, ...).  One thread streams each tile's
+// record arrays (cell, offsets, velocities) into a shared-memory stage with TMA
+// bulk copies, STAGES - 1 tiles ahead of the one being computed; the updated
+// record is written back into the same stage and returned to global memory by
+// TMA bulk stores, so no thread waits on its own loads or stores.  Each thread
+// owns R = TILE / 256 particles of a tile (lane i of warp w: particles
+// r * 256 + w * 32 + i, so a warp's lanes hold consecutive sorted particles for
+// the warp-cooperative deposit) and takes all R through each phase together:
+// the field gathers are issued together and the R deposit scans interleave.
+// MODE (PASS_* bits) is a compile-time choice so each use carries only its work.
+template <int D, int NV, int MODE>
 __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     k_particle_pass(GridParams g, ParticlesF32 p, const float *__restrict__ E,
-                    unsigned long long *__restrict__ acc, int mode,
-                    double *__restrict__ diag_blocks, int *__restrict__ err)
+                    unsigned long long *__restrict__ acc, double *__restrict__ diag_blocks,
+                    int *__restrict__ err)
 {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int R = TILE / PP_THREADS;
+    constexpr int NA_MAX = 1 + D + NV;
+    constexpr bool PUSH = (MODE & PASS_PUSH) != 0, MOVE = (MODE & PASS_MOVE) != 0;
+    constexpr bool DEPOSIT = (MODE & PASS_DEPOSIT) != 0, DIAG = (MODE & PASS_DIAG) != 0;
+    constexpr bool NEED_V = PUSH || MOVE;
+    constexpr int NA = 1 + D + (NEED_V ? NV : 0);
+    constexpr bool WRITE = PUSH || MOVE;  // the record changes and goes back to global
+    float *stage_base = reinterpret_cast<float *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * NA_MAX * TILE * 4);
+    // per-tile charge window (int32 fixed point, kept zero between tiles) and the
+    // tile's box of new cells (min, max of the unwrapped offset from the tile's
+    // reference cell, per axis)
+    unsigned *s_win = reinterpret_cast<unsigned *>(bars + STAGES);
+    int *s_box = reinterpret_cast<int *>(s_win + WIN_CAP);
+
     const int64_t np = p.np;
+    const int64_t ntiles = (np + TILE - 1) / TILE;
+    const int my_tiles =
+        blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    // stage s, array a (0: cell, 1..D: offsets, D+1..: velocities)
+    auto stage_arr = [&](int st, int a) { return stage_base + ((size_t)st * NA_MAX + a) * TILE; };
+    auto tile_start = [&](int k) { return (blockIdx.x + (int64_t)k * gridDim.x) * (int64_t)TILE; };
+    auto tile_bytes = [&](int64_t start) {
+        const int64_t cnt = np - start < TILE ? np - start : TILE;
+        return (uint32_t)(((cnt + 3) / 4) * 16);
+    };
+    auto issue_load = [&](int k, int st) {
+        const int64_t start = tile_start(k);
+        const uint32_t bytes = tile_bytes(start);
+        const uint32_t bar = smem_addr(&bars[st]);
+        mbar_expect_tx(bar, bytes * (uint32_t)NA);
+        bulk_g2s(smem_addr(stage_arr(st, 0)), p.cell + start, bytes, bar);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            bulk_g2s(smem_addr(stage_arr(st, 1 + a)), p.off + a * p.stride + start, bytes, bar);
+        if (NEED_V) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a)
+                bulk_g2s(smem_addr(stage_arr(st, 1 + D + a)), p.v + a * p.stride + start, bytes,
+                         bar);
+        }
+    };
+    auto issue_store = [&](int k, int st) {
+        const int64_t start = tile_start(k);
+        const uint32_t bytes = tile_bytes(start);
+        if (MOVE) {
+            bulk_s2g(p.cell + start, smem_addr(stage_arr(st, 0)), bytes);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                bulk_s2g(p.off + a * p.stride + start, smem_addr(stage_arr(st, 1 + a)), bytes);
+        }
+        if (PUSH) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a)
+                bulk_s2g(p.v + a * p.stride + start, smem_addr(stage_arr(st, 1 + D + a)), bytes);
+        }
+        bulk_commit();
+    };
+
+    if (tid == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(&bars[st]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (DEPOSIT) {
+        for (int i = tid; i < WIN_CAP; i += PP_THREADS) s_win[i] = 0u;
+        if (tid < 3) {
+            s_box[tid] = 0x7fffffff;
+            s_box[3 + tid] = -0x7fffffff;
+        }
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < STAGES - 1 && k < my_tiles; ++k) issue_load(k, k);
+
     const float scale = ldexpf(1.0f, g.fx_bits);
     const int one = 1 << g.fx_bits;
-    // FP32 running sums, folded into FP64 every 16 particles of this thread
+    // diagnostics: FP32 sums over this thread's particles (at most a few hundred),
+    // reduced across threads and blocks in FP64
     float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
-    double dke = 0.0, dmom[3] = {0.0, 0.0, 0.0};
-    int fold = 0;
     bool bad = false;
-    // warp-uniform loop: lane i of a warp handles particle base + i
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp0 * 32; base < np; base += wstride * 32) {
-        const int64_t i = base + lane;
-        const bool valid = i < np;
-        int c[3] = {0, 0, 0};
-        float f[3] = {0.0f, 0.0f, 0.0f};
-        float v[3] = {0.0f, 0.0f, 0.0f};
-        bool ok = valid;
-        if (valid) {
-            decode_cell<D>(p.cell[i], g, c);
-#pragma unroll
-            for (int a = 0; a < D; ++a) f[a] = p.off[a * np + i];
-            if (mode & (PASS_PUSH | PASS_MOVE)) {
-#pragma unroll
-                for (int a = 0; a < NV; ++a) v[a] = p.v[a * np + i];
+
+    for (int k = 0; k < my_tiles; ++k) {
+        const int st = k % STAGES;
+        const uint32_t parity = (uint32_t)((k / STAGES) & 1);
+        const bool ok_wait = mbar_wait_bounded(smem_addr(&bars[st]), parity);
+        // the tile's reference cell (its first particle's cell before the move), read
+        // before the barrier so that no thread overwrites it first
+        int ref[3] = {0, 0, 0};
+        if (DEPOSIT && ok_wait)
+            decode_cell<D>(reinterpret_cast<const int32_t *>(stage_arr(st, 0))[0], g, ref);
+        if (__syncthreads_or(!ok_wait)) {
+            // a copy did not land within the cap: report, drain what is in flight, stop
+            if (tid == 0) {
+                latch(err, EF_TIMEOUT);
+                for (int kk = k; kk < my_tiles && kk < k + STAGES - 1; ++kk)
+                    mbar_wait_bounded(smem_addr(&bars[kk % STAGES]),
+                                      (uint32_t)((kk / STAGES) & 1));
+                bulk_wait_all();
             }
-            if (mode & PASS_PUSH) {
-                float e[3] = {0.0f, 0.0f, 0.0f};
-                gather_E<D>(E, c, f, g.n, e);
+            __syncthreads();
+            return;
+        }
+        const int cnt = (int)(np - tile_start(k) < TILE ? np - tile_start(k) : TILE);
+        int32_t *s_cell = reinterpret_cast<int32_t *>(stage_arr(st, 0));
+
+        // phase A: read the record, decode the cell, issue the field gathers
+        int c[R][3];
+        float f[R][3], v[R][3], e[R][3];
+        bool valid[R];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
-                float vn[3] = {v[0], v[1], v[2]};
-                boris(vn, e, g);
-                bool finite = true;
+        for (int r = 0; r < R; ++r) {
+            const int j = r * PP_THREADS + tid;
+            valid[r] = j < cnt;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                c[r][a] = 0;
+                f[r][a] = 0.0f;
+                v[r][a] = 0.0f;
+                e[r][a] = 0.0f;
+            }
+            if (valid[r]) {
+                decode_cell<D>(s_cell[j], g, c[r]);
+#pragma unroll
+                for (int a = 0; a < D; ++a) f[r][a] = stage_arr(st, 1 + a)[j];
+                if (NEED_V) {
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) v[r][a] = stage_arr(st, 1 + D + a)[j];
+                }
+                if (PUSH) gather_E<D>(E, c[r], f[r], g.n, e[r]);
+            }
+        }
+        // phase B: push, move, write the record back into the stage
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!valid[r]) continue;
+            const int j = r * PP_THREADS + tid;
+            bool finite = true;
+            if (PUSH) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) e[r][a] += g.E0[a];
+                float vn[3] = {v[r][0], v[r][1], v[r][2]};
+                boris(vn, e[r], g);
 #pragma unroll
                 for (int a = 0; a < NV; ++a) finite &= isfinite(vn[a]);
-                if (!finite) bad = true;
-                if (mode & PASS_DIAG) {
+                if (DIAG) {
                     float o2 = 0.0f, n2 = 0.0f;
 #pragma unroll
                     for (int a = 0; a < NV; ++a) {
-                        o2 += v[a] * v[a];
+                        o2 += v[r][a] * v[r][a];
                         n2 += vn[a] * vn[a];
                         mom[a] += vn[a];
                     }
                     ke += 0.5f * (o2 + n2);
-                    if (++fold == 16) {
-                        dke += ke;
-                        ke = 0.0f;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            dmom[a] += mom[a];
-                            mom[a] = 0.0f;
-                        }
-                        fold = 0;
-                    }
                 }
 #pragma unroll
                 for (int a = 0; a < NV; ++a) {
-                    v[a] = vn[a];
-                    p.v[a * np + i] = vn[a];
+                    v[r][a] = vn[a];
+                    stage_arr(st, 1 + D + a)[j] = vn[a];
                 }
             }
-            if (mode & PASS_MOVE) {
-                if (move<D>(c, f, v, g)) {
-                    p.cell[i] = encode_cell<D>(c, g.n);
+            if (MOVE) {
+                if (finite && move<D>(c[r], f[r], v[r], g)) {
+                    s_cell[j] = encode_cell<D>(c[r], g.n);
 #pragma unroll
-                    for (int a = 0; a < D; ++a) p.off[a * np + i] = f[a];
+                    for (int a = 0; a < D; ++a) stage_arr(st, 1 + a)[j] = f[r][a];
                 } else {
-                    bad = true;
+                    finite = false;
                 }
+            }
+            if (!finite) bad = true;
+        }
+        // phase C: deposit at the (new) positions.  The tile's particles occupy a small
+        // box of cells (they were sorted); when its nodes fit the shared-memory
+        // window, run totals are added there and each touched node goes to the
+        // global accumulator once; otherwise run totals go straight to global memory.
+        if (DEPOSIT) {
+            int q[R][1 << D], key[R], dd[R][3];
+            int lo[3], hi[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = 0x7fffffff;
+                hi[a] = -0x7fffffff;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cic_quanta<D>(f[r], scale, one, q[r]);
+                key[r] = valid[r] ? encode_cell<D>(c[r], g.n) : -1;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    int d = c[r][a] - ref[a];  // unwrapped to [-n/2, n/2]
+                    d -= (2 * d > g.n[a]) ? g.n[a] : 0;
+                    d += (2 * d < -g.n[a]) ? g.n[a] : 0;
+                    dd[r][a] = d;
+                    if (valid[r]) {
+                        lo[a] = min(lo[a], d);
+                        hi[a] = max(hi[a], d);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int wl = __reduce_min_sync(0xffffffffu, lo[a]);
+                const int wh = __reduce_max_sync(0xffffffffu, hi[a]);
+                if (lane == 0) {
+                    atomicMin(&s_box[a], wl);
+                    atomicMax(&s_box[3 + a], wh);
+                }
+            }
+            __syncthreads();
+            int W[3] = {1, 1, 1}, blo[3] = {0, 0, 0};
+            int total = 1;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                blo[a] = s_box[a];
+                W[a] = s_box[3 + a] - blo[a] + 2;  // cells lo..hi and the node above hi
+                total *= W[a];
+            }
+            const bool use_win = total <= WIN_CAP && total > 0;
+            auto emit = [&](int r, int kc, int val) {
+                if (use_win) {
+                    int idx = 0, stride = 1;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        idx += (dd[r][a] + ((kc >> a) & 1) - blo[a]) * stride;
+                        stride *= W[a];
+                    }
+                    atomicAdd(&s_win[idx], (unsigned)val);
+                } else {
+                    int node[1 << D];
+                    corner_nodes<D>(c[r], g.n, node);
+                    atomicAdd(acc + node[kc], (unsigned long long)(long long)val);
+                }
+            };
+            warp_deposit<D, R>(key, q, one, emit);
+            __syncthreads();
+            if (use_win) {
+                // flush: every touched node once to global memory, leaving the window zero.
+                // A node's tile total lies in [-TILE, TILE * 2^S] with S <= 22, so the
+                // int32 bits decode unambiguously.
+                for (int i = tid; i < total; i += PP_THREADS) {
+                    const unsigned u = s_win[i];
+                    if (u == 0u) continue;
+                    s_win[i] = 0u;
+                    const long long val =
+                        u > 0x80000400u ? (long long)u - (1ll << 32) : (long long)u;
+                    int rem = i, node = 0, stride = 1;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        const int la = rem % W[a];
+                        rem /= W[a];
+                        int x = ref[a] + blo[a] + la;
+                        x += x < 0 ? g.n[a] : 0;
+                        x -= x >= g.n[a] ? g.n[a] : 0;
+                        node += x * stride;
+                        stride *= g.n[a];
+                    }
+                    atomicAdd(acc + node, (unsigned long long)val);
+                }
+            }
+            if (tid < 3) {  // reset the box for the next tile (read by all before the sync)
+                s_box[tid] = 0x7fffffff;
+                s_box[3 + tid] = -0x7fffffff;
             }
         }
-        if (mode & PASS_DEPOSIT) {
-            int q[1 << D], node[1 << D];
-            cic_quanta<D>(f, scale, one, q);
-            corner_nodes<D>(c, g.n, node);
-            warp_deposit<D>(acc, ok ? encode_cell<D>(c, g.n) : -1, node, q, one);
+        // the stage is complete: make the generic-proxy writes visible to the bulk
+        // copies, store it back, and refill the stage consumed one tile ago
+        if (WRITE) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (WRITE) issue_store(k, st);
+            const int kn = k + STAGES - 1;
+            if (kn < my_tiles) {
+                const int sn = kn % STAGES;  // the stage of tile k - 1 (free since then)
+                if (WRITE && k >= 1) bulk_wait_read<1>();  // tile k - 1's store has read it
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_load(kn, sn);
+            }
         }
     }
+    if (tid == 0 && WRITE) bulk_wait_all();
     if (bad) latch(err, EF_NONFINITE);
-    if (mode & PASS_DIAG) {
+    if (DIAG) {
         __shared__ double red[4][PP_THREADS / 32];
-        double vals[4] = {dke + ke, dmom[0] + mom[0], dmom[1] + mom[1], dmom[2] + mom[2]};
-        const int w = threadIdx.x >> 5;
+        double vals[4] = {ke, mom[0], mom[1], mom[2]};
+        const int w = tid >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const double s = warp_sum_d(vals[k]);
-            if (lane == 0) red[k][w] = s;
+        for (int kq = 0; kq < 4; ++kq) {
+            const double sum = warp_sum_d(vals[kq]);
+            if (lane == 0) red[kq][w] = sum;
         }
         __syncthreads();
-        if (threadIdx.x < 4) {
-            double s = 0.0;
-            for (int j = 0; j < PP_THREADS / 32; ++j) s += red[threadIdx.x][j];
-            diag_blocks[blockIdx.x * 4 + threadIdx.x] = s;
+        if (tid < 4) {
+            double sum = 0.0;
+            for (int jw = 0; jw < PP_THREADS / 32; ++jw) sum += red[tid][jw];
+            diag_blocks[blockIdx.x * 4 + tid] = sum;
         }
     }
+}
+
+template <int D, int NV>
+constexpr size_t pass_smem_bytes()
+{
+    return (size_t)STAGES * (1 + D + NV) * TILE * 4 + STAGES * 8 + WIN_CAP * 4 + 8 * 4;
 }
 
 int particle_pass_blocks(int64_t np, int ndim)
@@ -366,21 +694,53 @@ int particle_pass_blocks(int64_t np, int ndim)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    // one resident wave: 4 blocks of 256 per SM (3 in 3D, where the pass needs more
-    // registers), each block striding over the particle array
-    const int64_t need = (np + PP_THREADS - 1) / PP_THREADS;
+    // one resident wave: 4 CTAs of 256 threads per SM (3 in 3D, where the pass needs
+    // more registers and shared memory), each walking tiles of TILE particles
+    const int64_t need = (np + TILE - 1) / TILE;
     const int64_t cap = (int64_t)sms * (ndim == 3 ? 3 : 4);
     int64_t b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
 }
 
-template <int D, int NV>
-static void launch_pass_t(const GridParams &g, ParticlesF32 p, const float *E,
-                          unsigned long long *acc, int mode, double *diag_blocks, int nblocks,
-                          int *err, cudaStream_t st)
+template <int D, int NV, int MODE>
+static cudaError_t launch_pass_m(const GridParams &g, ParticlesF32 p, const float *E,
+                                 unsigned long long *acc, double *diag_blocks, int nblocks,
+                                 int *err, cudaStream_t st)
 {
-    k_particle_pass<D, NV><<<nblocks, PP_THREADS, 0, st>>>(g, p, E, acc, mode, diag_blocks, err);
+    constexpr size_t smem = pass_smem_bytes<D, NV>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_particle_pass<D, NV, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_particle_pass<D, NV, MODE><<<nblocks, PP_THREADS, smem, st>>>(g, p, E, acc, diag_blocks,
+                                                                    err);
     note_launch();
+    return cudaGetLastError();
+}
+
+template <int D, int NV>
+static cudaError_t launch_pass_t(const GridParams &g, ParticlesF32 p, const float *E,
+                                 unsigned long long *acc, int mode, double *diag_blocks,
+                                 int nb, int *err, cudaStream_t st)
+{
+    constexpr int FUSED = PASS_PUSH | PASS_MOVE | PASS_DEPOSIT;
+    constexpr int GP = PASS_PUSH | PASS_MOVE;
+    switch (mode) {
+    case FUSED: return launch_pass_m<D, NV, FUSED>(g, p, E, acc, diag_blocks, nb, err, st);
+    case FUSED | PASS_DIAG:
+        return launch_pass_m<D, NV, FUSED | PASS_DIAG>(g, p, E, acc, diag_blocks, nb, err, st);
+    case GP: return launch_pass_m<D, NV, GP>(g, p, E, acc, diag_blocks, nb, err, st);
+    case GP | PASS_DIAG:
+        return launch_pass_m<D, NV, GP | PASS_DIAG>(g, p, E, acc, diag_blocks, nb, err, st);
+    case PASS_DEPOSIT:
+        return launch_pass_m<D, NV, PASS_DEPOSIT>(g, p, E, acc, diag_blocks, nb, err, st);
+    case PASS_PUSH: return launch_pass_m<D, NV, PASS_PUSH>(g, p, E, acc, diag_blocks, nb, err, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const float *E,
@@ -389,19 +749,17 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
 {
     if (p.np == 0) return cudaSuccess;
     const int mode = (push ? PASS_PUSH : 0) | (mv ? PASS_MOVE : 0) |
-                     (deposit ? PASS_DEPOSIT : 0) | (diag.blocks && push ? PASS_DIAG : 0);
+                     (deposit ? PASS_DEPOSIT : 0) | (diag.blocks && push && mv ? PASS_DIAG : 0);
     const int nb = particle_pass_blocks(p.np, g.ndim);
-    const int key = g.ndim * 10 + p.nv;
-    switch (key) {
-    case 11: launch_pass_t<1, 1>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
-    case 12: launch_pass_t<1, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
-    case 13: launch_pass_t<1, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
-    case 22: launch_pass_t<2, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
-    case 23: launch_pass_t<2, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
-    case 33: launch_pass_t<3, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
+    switch (g.ndim * 10 + p.nv) {
+    case 11: return launch_pass_t<1, 1>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 12: return launch_pass_t<1, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 13: return launch_pass_t<1, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 22: return launch_pass_t<2, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 23: return launch_pass_t<2, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 33: return launch_pass_t<3, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ---- load ------------------------------------------------------------------------------------
@@ -442,7 +800,7 @@ __global__ void k_load_convert(GridParams g, double dx0, double dx1, double dx2,
             float ff = (float)fa;
             if (ff >= 1.0f) ff = 0x1.fffffep-1f;
             c[a] = ca;
-            p.off[a * p.np + i] = ff;
+            p.off[a * p.stride + i] = ff;
         }
         int cell = c[0];
         if (D >= 2) cell += g.n[0] * c[1];
@@ -451,7 +809,7 @@ __global__ void k_load_convert(GridParams g, double dx0, double dx1, double dx2,
         for (int a = 0; a < p.nv; ++a) {
             const float va = (float)v[k * p.nv + a];
             if (!isfinite(va)) bad = true;
-            p.v[a * p.np + i] = va;
+            p.v[a * p.stride + i] = va;
         }
     }
     if (bad) latch(err, EF_NONFINITE);
@@ -491,12 +849,12 @@ __global__ void k_load_state(GridParams g, const int32_t *__restrict__ cell,
                 bad = true;
                 fa = 0.0f;
             }
-            p.off[a * p.np + i] = fa;
+            p.off[a * p.stride + i] = fa;
         }
         for (int a = 0; a < p.nv; ++a) {
             const float va = v[i * p.nv + a];
             if (!isfinite(va)) bad = true;
-            p.v[a * p.np + i] = va;
+            p.v[a * p.stride + i] = va;
         }
     }
     if (bad) latch(err, EF_NONFINITE);
@@ -527,7 +885,7 @@ __global__ void k_positions_f64(GridParams g, double dx0, double dx1, double dx2
         else if (D == 2) decode_cell<2>(cell, g, c);
         else decode_cell<3>(cell, g, c);
         for (int a = 0; a < D; ++a)
-            x[i * D + a] = ((double)c[a] + (double)p.off[a * p.np + i]) * dx[a];
+            x[i * D + a] = ((double)c[a] + (double)p.off[a * p.stride + i]) * dx[a];
     }
 }
 

@@ -283,10 +283,17 @@ __device__ double preduce(const double *__restrict__ part, int n)
 
 __device__ __forceinline__ void pcoords(int64_t id, const FieldBufsF64 &f, int *j)
 {
-    j[0] = (int)(id % f.n[0]);
-    const int64_t r = id / f.n[0];
-    j[1] = f.ndim >= 2 ? (int)(r % f.n[1]) : 0;
-    j[2] = f.ndim >= 3 ? (int)(r / f.n[1]) : 0;
+    const uint32_t u = (uint32_t)id;
+    const uint32_t r = fdiv(u, f.div0);
+    j[0] = (int)(u - r * (uint32_t)f.n[0]);
+    if (f.ndim >= 2) {
+        const uint32_t r2 = fdiv(r, f.div1);
+        j[1] = (int)(r - r2 * (uint32_t)f.n[1]);
+        j[2] = (int)r2;
+    } else {
+        j[1] = 0;
+        j[2] = 0;
+    }
 }
 
 __device__ __forceinline__ double pneg_lap(const double *__restrict__ u, int64_t id, const int *j,

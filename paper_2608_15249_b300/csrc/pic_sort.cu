@@ -28,29 +28,33 @@ size_t sort_hist_len(int64_t np) { return (size_t)RADIX * (size_t)tiles_of(np); 
 
 // ---- keys ----------------------------------------------------------------------------------
 
-__global__ void k_keys(int ndim, int n0, int n1, int b0, int b1, int b2, int nb0, int nb1,
-                       const int32_t *__restrict__ cell, int64_t np, uint32_t *__restrict__ keys)
+// (Divisions by the grid and brick sizes use the multiply-high FastDiv: a
+// runtime integer division compiles to float conversions, which issue on the
+// slow FP64 pipe of this GPU.)
+__global__ void k_keys(int ndim, FastDiv dn0, FastDiv dn1, FastDiv db0, FastDiv db1, FastDiv db2,
+                       int nb0, int nb1, const int32_t *__restrict__ cell, int64_t np,
+                       uint32_t *__restrict__ keys)
 {
-    const uint32_t bcells = (uint32_t)b0 * b1 * b2;
+    const uint32_t b0 = db0.d, b1 = db1.d;
+    const uint32_t bcells = b0 * b1 * db2.d;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cell[i];
-        int c0, c1 = 0, c2 = 0;
+        const uint32_t c = (uint32_t)cell[i];
+        uint32_t c0, c1 = 0, c2 = 0;
         if (ndim == 1) {
             c0 = c;
         } else if (ndim == 2) {
-            c1 = c / n0;
-            c0 = c - c1 * n0;
+            c1 = fdiv(c, dn0);
+            c0 = c - c1 * dn0.d;
         } else {
-            const int c12 = c / n0;
-            c0 = c - c12 * n0;
-            c2 = c12 / n1;
-            c1 = c12 - c2 * n1;
+            const uint32_t c12 = fdiv(c, dn0);
+            c0 = c - c12 * dn0.d;
+            c2 = fdiv(c12, dn1);
+            c1 = c12 - c2 * dn1.d;
         }
-        const uint32_t bid = (uint32_t)(c0 / b0) + (uint32_t)nb0 * ((uint32_t)(c1 / b1) +
-                                                                   (uint32_t)nb1 * (c2 / b2));
-        const uint32_t lid = (uint32_t)(c0 % b0) + (uint32_t)b0 * ((uint32_t)(c1 % b1) +
-                                                                  (uint32_t)b1 * (c2 % b2));
+        const uint32_t q0 = fdiv(c0, db0), q1 = fdiv(c1, db1), q2 = fdiv(c2, db2);
+        const uint32_t bid = q0 + (uint32_t)nb0 * (q1 + (uint32_t)nb1 * q2);
+        const uint32_t lid = (c0 - q0 * b0) + b0 * ((c1 - q1 * b1) + b1 * (c2 - q2 * db2.d));
         keys[i] = bid * bcells + lid;
     }
 }
@@ -253,8 +257,10 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
     const int nb1 = g.ndim >= 2 ? (g.n[1] + b1 - 1) / b1 : 1;
     int64_t kb = (np + 255) / 256;
     if (kb > 65535) kb = 65535;
-    k_keys<<<(int)kb, 256, 0, st>>>(g.ndim, g.n[0], g.n[1], b0, b1, b2, nb0, nb1, cell, np,
-                                     s.keys[0]);
+    k_keys<<<(int)kb, 256, 0, st>>>(g.ndim, make_fastdiv((uint32_t)g.n[0]),
+                                     make_fastdiv((uint32_t)g.n[1]), make_fastdiv((uint32_t)b0),
+                                     make_fastdiv((uint32_t)b1), make_fastdiv((uint32_t)b2), nb0,
+                                     nb1, cell, np, s.keys[0]);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -290,8 +296,8 @@ __global__ void k_apply_perm(const uint32_t *__restrict__ perm, ParticlesF32 src
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = perm[r];
         dst.cell[r] = src.cell[j];
-        for (int a = 0; a < ndim; ++a) dst.off[a * np + r] = src.off[a * np + j];
-        for (int a = 0; a < src.nv; ++a) dst.v[a * np + r] = src.v[a * np + j];
+        for (int a = 0; a < ndim; ++a) dst.off[a * dst.stride + r] = src.off[a * src.stride + j];
+        for (int a = 0; a < src.nv; ++a) dst.v[a * dst.stride + r] = src.v[a * src.stride + j];
     }
 }
 
