@@ -429,6 +429,7 @@ static ap_pic_status create_grid(ap_pic *h)
     TRY(alloc_n(h, &f.r, c));
     TRY(alloc_n(h, &f.p, c));
     TRY(alloc_n(h, &f.q, c));
+    TRY(alloc_n(h, &f.x, c));
     TRY(alloc_n(h, &f.E, c * f.Estride));
     for (int k = 0; k < 3; ++k) TRY(alloc_n(h, &f.part[k], (size_t)f.nblocks));
     TRY(alloc_n(h, &f.scal, 8));
@@ -627,46 +628,105 @@ static ap_pic_status deposit_only(ap_pic *h)
     return convert_rho(h);
 }
 
-static ap_pic_status solve_field(ap_pic *h)
+// CG iterations on `fb` until its device done flag is set or maxit; host checks
+// the flag after each block of iterations.  Returns the iterations taken.
+template <class LaunchIters>
+static ap_pic_status cg_loop(ap_pic *h, int *d_done, int maxit, LaunchIters launch_iters)
 {
-    const double rtol = h->cfg.cg_rtol;
-    const int maxit = h->cfg.cg_maxit;
-    const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
-    int *d_done = h->plain ? h->f64.done : h->f.done;
-    int *d_iters = h->plain ? h->f64.iters : h->f.iters;
-    double *d_scal = h->plain ? h->f64.scal : h->f.scal;
-    if (h->plain) CU(h, launch_plain_cg_init(h->f64, rtol, h->stream));
-    else CU(h, launch_cg_init(h->f, rtol, h->stream));
     int it = 0, chunk = 8;
     while (true) {
         CU(h, cudaMemcpyAsync(h->h_done, d_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CU(h, cudaStreamSynchronize(h->stream));
         if (*h->h_done || it >= maxit) break;
-        if (h->plain) CU(h, launch_plain_cg_iters(h->f64, it, chunk, maxit, rtol, h->stream));
-        else CU(h, launch_cg_iters(h->f, it, chunk, maxit, rtol, h->stream));
+        CU(h, launch_iters(it, chunk));
         it += chunk;
         if (chunk < 64) chunk *= 2;
     }
-    if (h->plain) {
-        CU(h, launch_plain_cg_finish(h->f64, rtol, h->d_err, h->stream));
-        CU(h, launch_plain_efield(h->f64, h->stream));
-    } else {
-        CU(h, launch_cg_finish(h->f, rtol, h->d_err, h->stream));
-        CU(h, launch_efield(h->f, h->stream));
-    }
-    stage_end(h, mk);
-    CU(h, cudaMemcpyAsync(h->h_iters, d_iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    double rel = 0.0;
-    CU(h, cudaMemcpyAsync(h->h_diag + 7, d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
-                          h->stream));
+    return AP_PIC_OK;
+}
+
+static ap_pic_status read_scalar(ap_pic *h, const double *d, double *out)
+{
+    CU(h, cudaMemcpyAsync(h->h_diag + 7, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
-    rel = h->h_diag[7];
-    h->last_cg_iters = *h->h_iters;
+    *out = h->h_diag[7];
+    return AP_PIC_OK;
+}
+
+static ap_pic_status read_iters(ap_pic *h, const int *d, int *out)
+{
+    CU(h, cudaMemcpyAsync(h->h_iters, d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    *out = *h->h_iters;
+    return AP_PIC_OK;
+}
+
+// FP64 plain form: one FP64 Jacobi-PCG solve.
+static ap_pic_status solve_field_f64(ap_pic *h)
+{
+    const double rtol = h->cfg.cg_rtol;
+    const int maxit = h->cfg.cg_maxit;
+    const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
+    CU(h, launch_plain_cg_init(h->f64, rtol, h->stream));
+    TRY(cg_loop(h, h->f64.done, maxit, [&](int it, int n) {
+        return launch_plain_cg_iters(h->f64, it, n, maxit, rtol, h->stream);
+    }));
+    CU(h, launch_plain_cg_finish(h->f64, rtol, h->d_err, h->stream));
+    CU(h, launch_plain_efield(h->f64, h->stream));
+    stage_end(h, mk);
+    TRY(read_iters(h, h->f64.iters, &h->last_cg_iters));
+    TRY(read_scalar(h, h->f64.scal + 3, &h->last_cg_relres));
+    if (h->last_cg_relres > rtol)
+        return fail(h, AP_PIC_ERR_NOT_CONVERGED,
+                    "field solve stopped at %d iterations, relative residual %.3e > %.3e",
+                    h->last_cg_iters, h->last_cg_relres, rtol);
+    return AP_PIC_OK;
+}
+
+// FP32 form: FP32-vector Jacobi-PCG with FP64 dots, warm-started from the previous
+// potential and stopped on its (recursive) relative residual; then one refinement
+// pass: the true residual rho - mean - A phi in FP64, a short FP32 correction solve
+// A x = r, phi += x.  The refinement removes the smooth-mode error that the FP32
+// recursion cannot see.  (The true residual itself cannot serve as the stopping
+// test: the rounding of an FP32 potential, amplified by the Laplacian, floors it.)
+static ap_pic_status solve_field(ap_pic *h)
+{
+    if (h->plain) return solve_field_f64(h);
+    constexpr double REFINE_RTOL = 1e-2;
+    const double rtol = h->cfg.cg_rtol;
+    const int maxit = h->cfg.cg_maxit;
+    const double mean_total = h->cfg.q * h->cfg.weight * (double)h->np / h->V + bg_density(h);
+    FieldBufs &f = h->f;
+    const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
+    CU(h, launch_cg_init(f, rtol, h->stream));
+    TRY(cg_loop(h, f.done, maxit, [&](int it, int n) {
+        return launch_cg_iters(f, it, n, maxit, rtol, h->stream);
+    }));
+    CU(h, launch_cg_finish(f, rtol, h->d_err, h->stream));
+    int k1 = 0, k2 = 0;
+    double rel = 0.0;
+    TRY(read_iters(h, f.iters, &k1));
+    TRY(read_scalar(h, f.scal + 3, &rel));
+    // refinement pass
+    FieldBufs inner = f;  // the correction solve A x = r: "phi" is x, "b" is r
+    inner.phi = f.x;
+    CU(h, launch_residual64(f, mean_total, h->stream));
+    CU(h, cudaMemsetAsync(f.x, 0, (size_t)h->cells * 4, h->stream));
+    CU(h, launch_cg_init(inner, REFINE_RTOL, h->stream));
+    const int budget = maxit > k1 ? maxit - k1 : 1;
+    TRY(cg_loop(h, f.done, budget, [&](int it, int n) {
+        return launch_cg_iters(inner, it, n, budget, REFINE_RTOL, h->stream);
+    }));
+    TRY(read_iters(h, f.iters, &k2));
+    CU(h, launch_add_correction(f, h->stream));
+    CU(h, launch_efield(f, h->stream));
+    stage_end(h, mk);
+    h->last_cg_iters = k1 + k2;
     h->last_cg_relres = rel;
     if (rel > rtol)
         return fail(h, AP_PIC_ERR_NOT_CONVERGED,
-                    "field solve stopped at %d iterations, relative residual %.3e > %.3e",
-                    h->last_cg_iters, rel, rtol);
+                    "field solve stopped at %d iterations, relative residual %.3e > %.3e", k1,
+                    rel, rtol);
     return AP_PIC_OK;
 }
 

@@ -341,6 +341,89 @@ cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err, cudaStream_t s
     return cudaGetLastError();
 }
 
+// ---- mixed-precision refinement -----------------------------------------------------------
+//
+// The FP32 CG above stalls near its rounding floor on large, smooth fields.  The
+// solve is therefore an iterative refinement: the true residual of the FP32
+// potential, rho - mean - A phi, is formed in FP64 from the FP64 charge density,
+// rounded to FP32 as the right-hand side of a correction solve A x = r (FP32 CG,
+// FP64 dots), and phi += x, until the FP64 residual meets the tolerance.
+
+__device__ __forceinline__ double neg_lap64(const float *__restrict__ u, int64_t id, const int *j,
+                                            const FieldBufs &f, const double *idx2)
+{
+    const double c = u[id];
+    double acc = 0.0;
+    int64_t stride = 1;
+    for (int a = 0; a < f.ndim; ++a) {
+        const int na = f.n[a];
+        const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
+        const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
+        acc += (2.0 * c - (double)u[up] - (double)u[dn]) * idx2[a];
+        stride *= na;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(FT)
+    k_residual64(FieldBufs f, double i0, double i1, double i2, double mean_total)
+{
+    const double idx2[3] = {i0, i1, i2};
+    double rr = 0.0, bb = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT) {
+        int j[3];
+        node_coords(id, f, j);
+        const double bj = f.rho[id] - mean_total;
+        const double rj = bj - neg_lap64(f.phi, id, j, f, idx2);
+        f.b[id] = (float)rj;
+        rr += rj * rj;
+        bb += bj * bj;
+    }
+    rr = block_sum(rr);
+    bb = block_sum(bb);
+    if (threadIdx.x == 0) {
+        f.part[0][blockIdx.x] = rr;
+        f.part[2][blockIdx.x] = bb;
+    }
+}
+
+__global__ void __launch_bounds__(FT) k_residual_fin(FieldBufs f)
+{
+    const double rr = reduce_partials(f.part[0], f.nblocks);
+    const double bb = reduce_partials(f.part[2], f.nblocks);
+    if (threadIdx.x == 0) {
+        const double bn = sqrt(bb);
+        f.scal[SCAL_BNORM64] = bn;
+        f.scal[SCAL_TRUE_REL] = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+    }
+}
+
+cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st)
+{
+    double i2[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < f.ndim; ++a) i2[a] = 1.0 / (f.dx[a] * f.dx[a]);
+    k_residual64<<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], mean_total);
+    note_launch();
+    k_residual_fin<<<1, FT, 0, st>>>(f);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(FT) k_add_correction(FieldBufs f)
+{
+    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * FT)
+        f.phi[id] += f.x[id];
+}
+
+cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st)
+{
+    k_add_correction<<<f.nblocks, FT, 0, st>>>(f);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ---- E = -grad phi ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(FT) k_efield(FieldBufs f, float h0, float h1, float h2)

@@ -166,6 +166,7 @@ struct FieldBufs {
     double *rho;               // total charge density (FP64)
     float *b;                  // rho - mean(rho), FP32
     float *phi, *r, *p, *q;    // CG vectors
+    float *x;                  // correction of the refinement step
     float *E;                  // interleaved, stride Estride floats per node
     int Estride;
     double *part[3];           // reduction partials (ping-pong + spare), nblocks each
@@ -189,6 +190,12 @@ cudaError_t launch_cg_init(FieldBufs &f, double rtol, cudaStream_t st);
 cudaError_t launch_cg_iters(FieldBufs &f, int first, int count, int maxit, double rtol,
                             cudaStream_t st);
 cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err_flags, cudaStream_t st);
+// Refinement: b = (float)(rho - mean - A phi) computed in FP64, and its relative norm
+// |rho - mean - A phi| / |rho - mean| into scal[SCAL_TRUE_REL].
+cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st);
+// phi += x
+cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
+enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5 };
 cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
 // Finalise diagnostics: reduce particle partials, accumulator sum, field energy
 // into out[0..7] = {kinetic, px, py, pz, field_energy, acc_sum (as bits), -, -}.

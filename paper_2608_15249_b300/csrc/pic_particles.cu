@@ -290,7 +290,8 @@ enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8 };
 // ---- TMA bulk-copy pipeline helpers (PTX) ---------------------------------------------------
 
 constexpr int TILE = 512;           // particles per tile (2 per thread)
-constexpr int WIN_CAP = 2048;       // nodes of a tile's shared-memory charge window
+constexpr int WIN_BITS = 11;        // a tile's shared-memory charge window: 2^11 nodes
+constexpr int WIN_CAP = 1 << WIN_BITS;
 constexpr int STAGES = 4;           // tiles in flight per CTA
 constexpr int WAIT_LIMIT = 1 << 26;   // bounded mbarrier polling
 
@@ -553,8 +554,8 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
         }
         // phase C: deposit at the (new) positions.  The tile's particles occupy a small
         // box of cells (they were sorted); when its nodes fit the shared-memory
-        // window, run totals are added there and each touched node goes to the
-        // global accumulator once; otherwise run totals go straight to global memory.
+        // window, every corner is added there and each touched node goes to the
+        // global accumulator once; otherwise warp-summed runs go to global memory.
         if (DEPOSIT) {
             int q[R][1 << D], key[R], dd[R][3];
             int lo[3], hi[3];
@@ -589,23 +590,24 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
                 }
             }
             __syncthreads();
-            int W[3] = {1, 1, 1}, blo[3] = {0, 0, 0};
-            int total = 1;
+            // window extents rounded up to powers of two: index = sum of shifted offsets
+            int sh[3] = {0, 0, 0}, bits[3] = {0, 0, 0}, blo[3] = {0, 0, 0};
+            int tot_bits = 0;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 blo[a] = s_box[a];
-                W[a] = s_box[3 + a] - blo[a] + 2;  // cells lo..hi and the node above hi
-                total *= W[a];
+                const int w = s_box[3 + a] - blo[a] + 2;  // cells lo..hi and the node above
+                sh[a] = tot_bits;
+                bits[a] = 32 - __clz(w - 1);              // ceil(log2 w)
+                tot_bits += bits[a];
             }
-            const bool use_win = total <= WIN_CAP && total > 0;
+            const bool use_win = tot_bits <= WIN_BITS && s_box[3] >= s_box[0];
             auto emit = [&](int r, int kc, int val) {
                 if (use_win) {
-                    int idx = 0, stride = 1;
+                    int idx = 0;
 #pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        idx += (dd[r][a] + ((kc >> a) & 1) - blo[a]) * stride;
-                        stride *= W[a];
-                    }
+                    for (int a = 0; a < D; ++a)
+                        idx += (dd[r][a] + ((kc >> a) & 1) - blo[a]) << sh[a];
                     atomicAdd(&s_win[idx], (unsigned)val);
                 } else {
                     int node[1 << D];
@@ -613,23 +615,36 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
                     atomicAdd(acc + node[kc], (unsigned long long)(long long)val);
                 }
             };
-            warp_deposit<D, R>(key, q, one, emit);
+            if (use_win) {
+                // shared-memory atomics absorb the same-cell contention of sorted
+                // particles cheaply, so each lane adds its own corners
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (valid[r]) {
+#pragma unroll
+                        for (int kc = 0; kc < (1 << D); ++kc) emit(r, kc, q[r][kc]);
+                    }
+            } else {
+                // box too large for the window (particles far from sorted order): sum
+                // runs of equal cells across the warp first, then global atomics
+                warp_deposit<D, R>(key, q, one, emit);
+            }
             __syncthreads();
             if (use_win) {
                 // flush: every touched node once to global memory, leaving the window zero.
                 // A node's tile total lies in [-TILE, TILE * 2^S] with S <= 22, so the
                 // int32 bits decode unambiguously.
+                const int total = 1 << tot_bits;
                 for (int i = tid; i < total; i += PP_THREADS) {
                     const unsigned u = s_win[i];
                     if (u == 0u) continue;
                     s_win[i] = 0u;
                     const long long val =
                         u > 0x80000400u ? (long long)u - (1ll << 32) : (long long)u;
-                    int rem = i, node = 0, stride = 1;
+                    int node = 0, stride = 1;
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
-                        const int la = rem % W[a];
-                        rem /= W[a];
+                        const int la = (i >> sh[a]) & ((1 << bits[a]) - 1);
                         int x = ref[a] + blo[a] + la;
                         x += x < 0 ? g.n[a] : 0;
                         x -= x >= g.n[a] ? g.n[a] : 0;

@@ -38,6 +38,10 @@ def small_cases():
         "2d": plasma.maxwellian_box(2, (40, 36), ppc=16, nv=2, dt=0.1, seed=33),
         "2d_two_stream": plasma.two_stream_2d(n=(64, 48), ppc=8, mode=(2, 1), seed=34),
         "3d_mag": plasma.magnetized_3d(n=(16, 12, 10), ppc=8, seed=35),
+        # dilute: a tile of 512 sorted particles spans more nodes than the deposit's
+        # shared-memory window, so the warp-scan + global-atomic path runs
+        "2d_sparse": plasma.sparse_box(2, (160, 128), 1500, seed=39),
+        "3d_sparse": plasma.sparse_box(3, (40, 32, 24), 1300, seed=40),
     }
 
 
@@ -140,7 +144,7 @@ def test_one_step_from_identical_state(pk, name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["1d", "2d_two_stream", "3d_mag"])
+@pytest.mark.parametrize("name", ["1d", "2d_two_stream", "3d_mag", "2d_sparse", "3d_sparse"])
 def test_ten_steps_with_sorts(pk, name):
     """Ten cycles with a sort every 3 steps: per-particle state, rho and E stay within
     1e-5 of the oracle; particle identity is tracked through the sort permutations."""

@@ -16,6 +16,7 @@ from .plasma import (  # noqa: F401
     precision_3d,
     batch_instances,
     maxwellian_box,
+    sparse_box,
     fp32_exact,
     by_name,
 )

@@ -215,6 +215,19 @@ def maxwellian_box(ndim, n, ppc, vth=1.0, nv=3, dt=0.1, B0=(0.0, 0.0, 0.0), step
                     sort_every=sort_every, meta=dict(vth=vth, ppc=ppc))
 
 
+def sparse_box(ndim, n, npart, vth=1.0, nv=None, dt=0.1, seed=8):
+    """A dilute Maxwellian plasma (far fewer particles than cells), uniform random
+    positions: sorted tiles of particles then span large parts of the grid."""
+    rng = np.random.default_rng(seed)
+    nv = nv or ndim
+    n3, dx3, L = _box(ndim, n, (1.0,) * ndim)
+    x = _uniform_positions(rng, npart, L)
+    v = _maxwellian(rng, npart, nv, vth)
+    V = float(np.prod(L))
+    return Workload("sparse_box", ndim, n3, dx3, dt, 10, x, v, weight=V / npart,
+                    meta=dict(vth=vth))
+
+
 def magnetized_3d(n=(128, 128, 128), ppc=64, vth=1.0, wc=2.0, dt=0.05, steps=100, seed=3):
     """3D magnetised Maxwellian plasma with a uniform B0 along z such that the
     electron cyclotron frequency |q| B0 / m equals wc (in units of the plasma
