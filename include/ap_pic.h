@@ -207,7 +207,7 @@ ap_pic_status ap_pic_sort(ap_pic *h);
  *   perm: device, np int32 (output); both caller-owned;
  *   cuda_stream: cudaStream_t (NULL: legacy default stream); the call is
  *       asynchronous on it.
- * Scratch is one fixed array of ~16.3 MiB in device global memory, held by
+ * Scratch is one fixed array of ~17 MiB in device global memory, held by
  * every GPU that loads the library until the process exits.  The first call
  * on a device (with that device current) looks up the array's device address
  * and keeps it.  All calls share the array and each overwrites it: calls that

@@ -132,6 +132,10 @@ cudaError_t launch_plain_pass(const GridParamsF64 &g, ParticlesF64 p, const doub
                               DiagPartials diag, int *err_flags, cudaStream_t st);
 
 // ---- sort (pic_sort.cu) ---------------------------------------------------------------------
+constexpr int SORT_TILE = 4096;             // items per radix tile
+constexpr int SORT_MAX_DIGIT_BITS = 10;     // widest radix digit
+constexpr int SORT_MAX_RADIX = 1 << SORT_MAX_DIGIT_BITS;
+
 struct SortScratch {
     uint32_t *keys[2];
     uint32_t *idx[2];
@@ -144,8 +148,8 @@ struct SortScratch {
 size_t sort_hist_len(int64_t np);
 size_t sort_scan_tmp_len(size_t n);
 
-// Computes keys, sorts (stable LSD radix, 8-bit digits) and leaves the final
-// permutation in s.idx[*perm_slot]; returns which slot through perm_slot.
+// Computes keys, sorts (stable LSD radix, digits of up to 10 bits) and leaves the
+// final permutation in s.idx[*perm_slot].
 cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bits,
                              const int32_t *cell, int64_t np, SortScratch &s, int *perm_slot,
                              cudaStream_t st);

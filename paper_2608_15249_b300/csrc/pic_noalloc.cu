@@ -8,7 +8,7 @@
 // ap_pic_sort, but its scratch (keys, indices, digit histograms, scan
 // partials) lives in one fixed-size array in device global memory declared in
 // this file.  Every GPU that loads the library holds the array
-// (~16.3 MiB) until the process exits; the caller passes only its input and
+// (~17 MiB) until the process exits; the caller passes only its input and
 // output buffers.
 //
 // Host code cannot use the array's name as a device address (in host code it
@@ -30,9 +30,9 @@ using namespace apk;
 namespace {
 
 constexpr int64_t MAX_NP = AP_PIC_NOALLOC_MAX_NP;
-constexpr size_t TILE = 4096;                               // items per sort tile
+constexpr size_t TILE = SORT_TILE;                          // items per sort tile
 constexpr size_t MAX_TILES = (size_t)(MAX_NP + TILE - 1) / TILE;
-constexpr size_t HIST_WORDS = 256 * MAX_TILES;              // per-tile digit histograms
+constexpr size_t HIST_WORDS = (size_t)SORT_MAX_RADIX * MAX_TILES;  // per-tile digit histograms
 constexpr size_t SCAN_WORDS = 256;                          // scan partials (checked below)
 constexpr size_t SCRATCH_WORDS = 4 * (size_t)MAX_NP + HIST_WORDS + SCAN_WORDS;
 constexpr int MAX_DEVICES = 64;

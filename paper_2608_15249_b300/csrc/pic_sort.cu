@@ -6,11 +6,14 @@
 //   key = brick_id * (b0 b1 b2) + local_id,
 //   brick_id = c0/b0 + nb0 (c1/b1 + nb1 c2/b2),   nb_a = ceil(n_a / b_a),
 //   local_id = c0%b0 + b0 (c1%b1 + b1 c2%b2).
-// Sort: least-significant-digit radix sort over (key, index) pairs with 8-bit
-// digits.  Each pass is stable (per-tile digit histograms, a device-wide
+// Sort: least-significant-digit radix sort over (key, index) pairs with digits
+// of up to 10 bits (as few passes as the key width allows: two 9-bit passes for
+// an 18-bit key).  Each pass is stable (per-tile digit histograms, a device-wide
 // exclusive scan in digit-major order, and a scatter whose in-tile ranks keep
 // input order), so the result is the unique stable permutation.  The
 // particle record is then gathered through the permutation.
+#include <type_traits>
+
 #include "pic_internal.cuh"
 
 namespace apk {
@@ -19,12 +22,14 @@ constexpr int ST_THREADS = 256;
 constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int ST_ITEMS = 16;
 constexpr int ST_TILE = ST_THREADS * ST_ITEMS;  // 4096 items per tile
-constexpr int RADIX = 256;
-constexpr int NO_DIGIT = RADIX;                 // marks an item past the end
+static_assert(ST_TILE == SORT_TILE, "tile size shared with the scratch sizing");
+constexpr int MAX_DIGIT_BITS = SORT_MAX_DIGIT_BITS;
+constexpr int MAX_RADIX = SORT_MAX_RADIX;
+constexpr int NO_DIGIT = -1;                    // marks an item past the end
 
 static int64_t tiles_of(int64_t np) { return (np + ST_TILE - 1) / ST_TILE; }
 
-size_t sort_hist_len(int64_t np) { return (size_t)RADIX * (size_t)tiles_of(np); }
+size_t sort_hist_len(int64_t np) { return (size_t)MAX_RADIX * (size_t)tiles_of(np); }
 
 // ---- keys ----------------------------------------------------------------------------------
 
@@ -61,12 +66,13 @@ __global__ void k_keys(int ndim, FastDiv dn0, FastDiv dn1, FastDiv db0, FastDiv 
 
 // ---- per-tile digit histogram ----------------------------------------------------------------
 
+template <int RADIX>
 __global__ void __launch_bounds__(ST_THREADS)
     k_hist(const uint32_t *__restrict__ keys, int64_t np, int shift, uint32_t *__restrict__ hist,
            int64_t ntiles)
 {
     __shared__ uint32_t h[RADIX];
-    h[threadIdx.x] = 0;
+    for (int j = threadIdx.x; j < RADIX; j += ST_THREADS) h[j] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * ST_TILE;
     const int lane = threadIdx.x & 31;
@@ -78,21 +84,24 @@ __global__ void __launch_bounds__(ST_THREADS)
         if (d != NO_DIGIT && lane == __ffs(m) - 1) atomicAdd(&h[d], (uint32_t)__popc(m));
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int j = threadIdx.x; j < RADIX; j += ST_THREADS)
+        hist[(int64_t)j * ntiles + blockIdx.x] = h[j];
 }
 
 // ---- stable scatter --------------------------------------------------------------------------
 
 // Warp w of a tile owns the contiguous items [w*512, (w+1)*512) of the tile and
 // walks them in 16 rounds of 32, so (warp, round, lane) order is input order.
+template <int RADIX>
 __global__ void __launch_bounds__(ST_THREADS)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
               int shift, const uint32_t *__restrict__ offs, int64_t ntiles,
               uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
 {
-    __shared__ uint32_t wcount[ST_WARPS][RADIX];
+    extern __shared__ uint32_t wcount_flat[];  // [ST_WARPS][RADIX]
+    auto wcount = [&](int w, int d) -> uint32_t & { return wcount_flat[w * RADIX + d]; };
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < ST_WARPS * RADIX; j += ST_THREADS) (&wcount[0][0])[j] = 0;
+    for (int j = threadIdx.x; j < ST_WARPS * RADIX; j += ST_THREADS) wcount_flat[j] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * ST_TILE + (int64_t)w * (ST_ITEMS * 32);
     const unsigned lt = (1u << lane) - 1u;
@@ -106,19 +115,18 @@ __global__ void __launch_bounds__(ST_THREADS)
         dig[r] = d;
         const unsigned m = __match_any_sync(0xffffffffu, d);
         uint32_t before = 0;
-        if (d != NO_DIGIT) before = wcount[w][d];
+        if (d != NO_DIGIT) before = wcount(w, d);
         rank[r] = before + (uint32_t)__popc(m & lt);
         __syncwarp();
-        if (d != NO_DIGIT && (m & lt) == 0) wcount[w][d] = before + (uint32_t)__popc(m);
+        if (d != NO_DIGIT && (m & lt) == 0) wcount(w, d) = before + (uint32_t)__popc(m);
         __syncwarp();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;  // ST_THREADS == RADIX
+    for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
         uint32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
         for (int ww = 0; ww < ST_WARPS; ++ww) {
-            const uint32_t t = wcount[ww][d];
-            wcount[ww][d] = run;
+            const uint32_t t = wcount(ww, d);
+            wcount(ww, d) = run;
             run += t;
         }
     }
@@ -127,7 +135,7 @@ __global__ void __launch_bounds__(ST_THREADS)
     for (int r = 0; r < ST_ITEMS; ++r) {
         if (dig[r] == NO_DIGIT) continue;
         const int64_t i = base + r * 32 + lane;
-        const uint32_t pos = wcount[w][dig[r]] + rank[r];
+        const uint32_t pos = wcount(w, dig[r]) + rank[r];
         if (keys_out) keys_out[pos] = key[r];
         idx_out[pos] = idx_in ? idx_in[i] : (uint32_t)i;
     }
@@ -265,20 +273,38 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t ntiles = tiles_of(np);
-    const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
+    const int passes = key_bits <= 0 ? 1 : (key_bits + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
+    const int dbits = key_bits <= 0 ? 8 : (key_bits + passes - 1) / passes;  // <= 10
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        k_hist<<<(unsigned)ntiles, ST_THREADS, 0, st>>>(s.keys[cur], np, shift, s.hist, ntiles);
-        note_launch();
-        e = launch_exclusive_scan_u32(s.hist, s.hist, (size_t)RADIX * ntiles, s.scan_tmp, st);
-        if (e != cudaSuccess) return e;
+        const int shift = dbits * pass;
         const bool last = pass == passes - 1;
-        k_scatter<<<(unsigned)ntiles, ST_THREADS, 0, st>>>(
-            s.keys[cur], pass == 0 ? nullptr : s.idx[cur], np, shift, s.hist, ntiles,
-            last ? nullptr : s.keys[cur ^ 1], s.idx[cur ^ 1]);
-        note_launch();
-        e = cudaGetLastError();
+        const uint32_t *idx_in = pass == 0 ? nullptr : s.idx[cur];
+        uint32_t *keys_out = last ? nullptr : s.keys[cur ^ 1];
+        const size_t hist_len = ((size_t)1 << (dbits < 8 ? 8 : dbits)) * ntiles;
+        auto run = [&](auto radix_tag) -> cudaError_t {
+            constexpr int RADIX = decltype(radix_tag)::value;
+            k_hist<RADIX><<<(unsigned)ntiles, ST_THREADS, 0, st>>>(s.keys[cur], np, shift, s.hist,
+                                                                  ntiles);
+            note_launch();
+            cudaError_t e2 = launch_exclusive_scan_u32(s.hist, s.hist, hist_len, s.scan_tmp, st);
+            if (e2 != cudaSuccess) return e2;
+            const size_t smem = (size_t)ST_WARPS * RADIX * 4;
+            static bool configured = false;
+            if (!configured) {
+                e2 = cudaFuncSetAttribute(k_scatter<RADIX>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e2 != cudaSuccess) return e2;
+                configured = true;
+            }
+            k_scatter<RADIX><<<(unsigned)ntiles, ST_THREADS, smem, st>>>(
+                s.keys[cur], idx_in, np, shift, s.hist, ntiles, keys_out, s.idx[cur ^ 1]);
+            note_launch();
+            return cudaGetLastError();
+        };
+        if (dbits <= 8) e = run(std::integral_constant<int, 256>{});
+        else if (dbits == 9) e = run(std::integral_constant<int, 512>{});
+        else e = run(std::integral_constant<int, 1024>{});
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -288,16 +314,46 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
 
 // ---- gather the record through the permutation ----------------------------------------------
 
-__global__ void k_apply_perm(const uint32_t *__restrict__ perm, ParticlesF32 src, ParticlesF32 dst,
-                             int ndim)
+// dst[r] = src[perm[r]].  Each thread gathers 4 records, all loads issued before
+// any store, so enough independent loads are in flight to cover the latency of
+// the near-sorted gather.
+template <int D, int NV>
+__global__ void __launch_bounds__(256) k_apply_perm(const uint32_t *__restrict__ perm,
+                                                    ParticlesF32 src, ParticlesF32 dst)
 {
+    constexpr int K = 4;
     const int64_t np = src.np;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < np;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = perm[r];
-        dst.cell[r] = src.cell[j];
-        for (int a = 0; a < ndim; ++a) dst.off[a * dst.stride + r] = src.off[a * src.stride + j];
-        for (int a = 0; a < src.nv; ++a) dst.v[a * dst.stride + r] = src.v[a * src.stride + j];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * K;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x) * K + threadIdx.x; base < np;
+         base += stride) {
+        uint32_t j[K];
+        bool ok[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t r = base + (int64_t)k * blockDim.x;
+            ok[k] = r < np;
+            j[k] = ok[k] ? __ldg(perm + r) : 0u;
+        }
+        int32_t c[K];
+        float o[K][D], v[K][NV];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            c[k] = __ldg(src.cell + j[k]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) o[k][a] = __ldg(src.off + a * src.stride + j[k]);
+#pragma unroll
+            for (int a = 0; a < NV; ++a) v[k][a] = __ldg(src.v + a * src.stride + j[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!ok[k]) continue;
+            const int64_t r = base + (int64_t)k * blockDim.x;
+            dst.cell[r] = c[k];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dst.off[a * dst.stride + r] = o[k][a];
+#pragma unroll
+            for (int a = 0; a < NV; ++a) dst.v[a * dst.stride + r] = v[k][a];
+        }
     }
 }
 
@@ -305,9 +361,17 @@ cudaError_t launch_apply_perm(const uint32_t *perm, ParticlesF32 src, ParticlesF
                               cudaStream_t st)
 {
     if (src.np <= 0) return cudaSuccess;
-    int64_t nb = (src.np + 255) / 256;
+    int64_t nb = (src.np + 1023) / 1024;
     if (nb > 65535) nb = 65535;
-    k_apply_perm<<<(int)nb, 256, 0, st>>>(perm, src, dst, ndim);
+    switch (ndim * 10 + src.nv) {
+    case 11: k_apply_perm<1, 1><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    case 12: k_apply_perm<1, 2><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    case 13: k_apply_perm<1, 3><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    case 22: k_apply_perm<2, 2><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    case 23: k_apply_perm<2, 3><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    case 33: k_apply_perm<3, 3><<<(int)nb, 256, 0, st>>>(perm, src, dst); break;
+    default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }
