@@ -263,6 +263,69 @@ ap_pic_status ap_pic_get_timing(ap_pic *h, double *ms, int64_t *count);
 /* Kernels this library has launched in the process so far (all handles). */
 int64_t ap_pic_kernel_launches(void);
 
+/* ---- batch: many independent instances advanced together ----------------------------
+ * The serving form of the same cycle: `count` periodic instances of uneven grid
+ * and particle counts (each 1D or 2D, nv = 2, B0 = 0, FP32 cell + offset form)
+ * share one particle arena and one set of grid arenas.  Each step runs one
+ * persistent particle pass per dimension class over the tiles of every
+ * instance, the charge conversion, and the field solve of every instance in
+ * lockstep (same Jacobi-PCG and refinement as a single instance; an instance
+ * that has converged skips its work); the front of the step (particle pass to
+ * the first block of CG iterations) is captured once as a CUDA graph and
+ * replayed.  Instance i of a batch computes what a single instance with cfgs[i]
+ * computes, within the single instance's tolerance. */
+typedef struct ap_pic_batch ap_pic_batch;
+
+typedef struct {
+    int pass_ctas_per_sm;   /* CTAs per SM of the persistent particle pass (1..8)     */
+    int item_cells;         /* nodes per work item of the grid kernels (multiple of
+                               256, 256..65536; set before loading)                  */
+    int sort_every;         /* steps between sorts (0: never)                         */
+    int cg_iters_per_graph; /* CG iterations in each replayed block (1..256)          */
+    int use_graph;          /* 1: capture and replay the step front as a CUDA graph   */
+} ap_pic_batch_tuning;
+
+void ap_pic_batch_default_tuning(ap_pic_batch_tuning *t);
+
+/* cfgs: `count` configurations (validated as for ap_pic_create, plus the batch
+ * limits above; cg_rtol and cg_maxit are taken from cfgs[0]).  Allocates no
+ * device memory yet (that happens at ap_pic_batch_load).  The batch enqueues its
+ * work on a stream of its own, ordered after `cuda_stream` on entry to each call
+ * and making `cuda_stream` wait for it on exit. */
+ap_pic_status ap_pic_batch_create(int count, const ap_pic_config *cfgs,
+                                  const ap_pic_allocator *alloc, void *cuda_stream,
+                                  ap_pic_batch **out);
+ap_pic_status ap_pic_batch_destroy(ap_pic_batch *b);
+
+/* Loads every instance at once: np[i] particles, x[i] host FP64 (np[i] x ndim_i),
+ * v[i] host FP64 (np[i] x 2); then sorts, deposits, solves and (unless
+ * AP_PIC_LOAD_NO_HALFPUSH) applies the initial half push, as ap_pic_load. */
+ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np, const double *const *x,
+                                const double *const *v, unsigned flags);
+
+/* nsteps cycles of every instance (sort every tuning.sort_every steps). */
+ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps);
+
+ap_pic_status ap_pic_batch_set_tuning(ap_pic_batch *b, const ap_pic_batch_tuning *t);
+ap_pic_status ap_pic_batch_get_tuning(const ap_pic_batch *b, ap_pic_batch_tuning *t);
+
+/* Picks pass_ctas_per_sm, cg_iters_per_graph and sort_every for this batch by
+ * timing `steps_per_trial` steps of each candidate (the batch advances while it
+ * is tuned).  With a non-NULL cache_path, a result stored there for the same
+ * batch shape and GPU is reused, and a new one is written back. */
+ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_trial, const char *cache_path);
+
+/* Per-instance read-back (host buffers; each synchronises), as the single-instance
+ * calls of the same names. */
+ap_pic_status ap_pic_batch_get_rho(ap_pic_batch *b, int i, double *rho);
+ap_pic_status ap_pic_batch_get_E(ap_pic_batch *b, int i, double *E);
+ap_pic_status ap_pic_batch_get_particles(ap_pic_batch *b, int i, int32_t *cell, float *off,
+                                         float *v, double *x);
+ap_pic_status ap_pic_batch_get_perm(ap_pic_batch *b, int i, int64_t *perm);
+ap_pic_status ap_pic_batch_get_diag(ap_pic_batch *b, int i, ap_pic_diag *out);
+int64_t ap_pic_batch_num_particles(const ap_pic_batch *b, int i);
+const char *ap_pic_batch_last_error(const ap_pic_batch *b);
+
 /* Number of particles loaded (0 before ap_pic_load). */
 int64_t ap_pic_num_particles(const ap_pic *h);
 

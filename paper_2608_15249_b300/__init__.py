@@ -41,6 +41,11 @@ EXPORTS = [
     "ap_pic_get_perm", "ap_pic_get_diag", "ap_pic_set_timing", "ap_pic_get_timing",
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
     "ap_pic_sort_perm_noalloc",
+    "ap_pic_batch_default_tuning", "ap_pic_batch_create", "ap_pic_batch_destroy",
+    "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_set_tuning",
+    "ap_pic_batch_get_tuning", "ap_pic_batch_autotune", "ap_pic_batch_get_rho",
+    "ap_pic_batch_get_E", "ap_pic_batch_get_particles", "ap_pic_batch_get_perm",
+    "ap_pic_batch_get_diag", "ap_pic_batch_num_particles", "ap_pic_batch_last_error",
 ]
 STAGES = ["push_deposit", "rho", "sort", "field", "diag"]
 NSTAGES = 8
@@ -78,6 +83,15 @@ class ap_pic_diag(ctypes.Structure):
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k == "momentum" else getattr(self, k))
                 for k, _ in self._fields_}
+
+
+class ap_pic_batch_tuning(ctypes.Structure):
+    _fields_ = [("pass_ctas_per_sm", ctypes.c_int), ("item_cells", ctypes.c_int),
+                ("sort_every", ctypes.c_int), ("cg_iters_per_graph", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -123,6 +137,24 @@ def _declare(L):
     L.ap_pic_last_error.argtypes = [P]
     L.ap_pic_last_error.restype = ctypes.c_char_p
     L.ap_pic_sort_perm_noalloc.argtypes = [I, P, P, I64, P, P, P]
+    tunp = ctypes.POINTER(ap_pic_batch_tuning)
+    L.ap_pic_batch_default_tuning.argtypes = [tunp]
+    L.ap_pic_batch_default_tuning.restype = None
+    L.ap_pic_batch_create.argtypes = [I, P, ctypes.POINTER(ap_pic_allocator), P, ctypes.POINTER(P)]
+    L.ap_pic_batch_destroy.argtypes = [P]
+    L.ap_pic_batch_load.argtypes = [P, P, P, P, U]
+    L.ap_pic_batch_step.argtypes = [P, I]
+    L.ap_pic_batch_set_tuning.argtypes = [P, tunp]
+    L.ap_pic_batch_get_tuning.argtypes = [P, tunp]
+    L.ap_pic_batch_autotune.argtypes = [P, I, ctypes.c_char_p]
+    for name in ("ap_pic_batch_get_rho", "ap_pic_batch_get_E", "ap_pic_batch_get_perm"):
+        getattr(L, name).argtypes = [P, I, P]
+    L.ap_pic_batch_get_particles.argtypes = [P, I, P, P, P, P]
+    L.ap_pic_batch_get_diag.argtypes = [P, I, ctypes.POINTER(ap_pic_diag)]
+    L.ap_pic_batch_num_particles.argtypes = [P, I]
+    L.ap_pic_batch_num_particles.restype = I64
+    L.ap_pic_batch_last_error.argtypes = [P]
+    L.ap_pic_batch_last_error.restype = ctypes.c_char_p
     L.ap_pic_version.argtypes = []
     L.ap_pic_version.restype = ctypes.c_char_p
 
@@ -359,6 +391,131 @@ def from_workload(w, stream=None, **over) -> Pic:
               E0=w.E0, nv=w.nv, sort_every=w.sort_every)
     kw.update(over)
     return Pic(make_config(**kw), stream=stream)
+
+
+class Batch:
+    """Many independent instances advanced together (the C ABI's ap_pic_batch_*)."""
+
+    def __init__(self, cfgs, stream=None, use_torch_allocator=True):
+        self._lib = lib()
+        self.cfgs = list(cfgs)
+        self.count = len(self.cfgs)
+        arr = (ap_pic_config * self.count)(*self.cfgs)
+        self._alloc = _TorchAllocator() if use_torch_allocator else None
+        allocp = ctypes.byref(self._alloc.struct) if self._alloc else None
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:  # noqa: BLE001
+                stream = 0
+        h = ctypes.c_void_p()
+        st = self._lib.ap_pic_batch_create(self.count, arr, allocp, ctypes.c_void_p(stream or 0),
+                                           ctypes.byref(h))
+        self.h = h
+        if st != AP_PIC_OK:
+            msg = self.last_error()
+            self._lib.ap_pic_batch_destroy(h)
+            self.h = None
+            raise PicError(st, msg)
+
+    def last_error(self):
+        return self._lib.ap_pic_batch_last_error(self.h).decode() if self.h else ""
+
+    def _check(self, st):
+        if st != AP_PIC_OK:
+            raise PicError(st, self.last_error())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ap_pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def load(self, xs, vs, half_push=True):
+        xs = [np.ascontiguousarray(x, dtype=np.float64) for x in xs]
+        vs = [np.ascontiguousarray(v, dtype=np.float64) for v in vs]
+        nps = (ctypes.c_int64 * self.count)(*[x.shape[0] for x in xs])
+        xp = (ctypes.c_void_p * self.count)(*[x.ctypes.data for x in xs])
+        vp = (ctypes.c_void_p * self.count)(*[v.ctypes.data for v in vs])
+        self._keep = (xs, vs)
+        flags = 0 if half_push else AP_PIC_LOAD_NO_HALFPUSH
+        self._check(self._lib.ap_pic_batch_load(self.h, nps, xp, vp, flags))
+        self._keep = None
+        return self
+
+    def step(self, nsteps=1):
+        self._check(self._lib.ap_pic_batch_step(self.h, int(nsteps)))
+
+    def get_tuning(self):
+        t = ap_pic_batch_tuning()
+        self._check(self._lib.ap_pic_batch_get_tuning(self.h, ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, **kw):
+        t = self.get_tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._check(self._lib.ap_pic_batch_set_tuning(self.h, ctypes.byref(t)))
+
+    def autotune(self, steps_per_trial=4, cache_path=None):
+        cp = cache_path.encode() if cache_path else None
+        self._check(self._lib.ap_pic_batch_autotune(self.h, int(steps_per_trial), cp))
+        return self.get_tuning().as_dict()
+
+    def num_particles(self, i):
+        return int(self._lib.ap_pic_batch_num_particles(self.h, i))
+
+    def _cells(self, i):
+        c = self.cfgs[i]
+        return int(np.prod([c.n[a] for a in range(c.ndim)]))
+
+    def get_rho(self, i):
+        out = np.empty(self._cells(i), np.float64)
+        self._check(self._lib.ap_pic_batch_get_rho(self.h, i, _ptr(out)))
+        return out
+
+    def get_E(self, i):
+        out = np.empty(self.cfgs[i].ndim * self._cells(i), np.float64)
+        self._check(self._lib.ap_pic_batch_get_E(self.h, i, _ptr(out)))
+        return out
+
+    def get_particles(self, i):
+        n, nd = self.num_particles(i), self.cfgs[i].ndim
+        cell = np.empty(n, np.int32)
+        off = np.empty((n, nd), np.float32)
+        v = np.empty((n, 2), np.float32)
+        x = np.empty((n, nd), np.float64)
+        self._check(self._lib.ap_pic_batch_get_particles(self.h, i, _ptr(cell), _ptr(off),
+                                                         _ptr(v), _ptr(x)))
+        return cell, off, v, x
+
+    def get_perm(self, i):
+        out = np.empty(self.num_particles(i), np.int64)
+        self._check(self._lib.ap_pic_batch_get_perm(self.h, i, _ptr(out)))
+        return out
+
+    def get_diag(self, i):
+        d = ap_pic_diag()
+        self._check(self._lib.ap_pic_batch_get_diag(self.h, i, ctypes.byref(d)))
+        return d.as_dict()
+
+
+def batch_from_workloads(ws, stream=None, **over):
+    """A Batch configured for a list of `workloads.Workload` (not loaded yet)."""
+    cfgs = []
+    for w in ws:
+        kw = dict(ndim=w.ndim, n=w.n, dx=w.dx, dt=w.dt, q=w.q, m=w.m, weight=w.weight,
+                  E0=w.E0, nv=w.nv, sort_every=w.sort_every)
+        kw.update(over)
+        cfgs.append(make_config(**kw))
+    return Batch(cfgs, stream=stream)
 
 
 def kernel_launches() -> int:

@@ -23,6 +23,9 @@ struct FastDiv {
     int l;
 };
 
+#ifdef __CUDACC__
+__host__ __device__
+#endif
 inline FastDiv make_fastdiv(uint32_t d)
 {
     FastDiv f{d, 0u, 0};
@@ -95,6 +98,24 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
                                  unsigned long long *acc, bool push, bool move, bool deposit,
                                  DiagPartials diag, int *err_flags, cudaStream_t st);
 
+// A tile of a batch: particles [start, start + count) of the arena, all of
+// instance `inst` (count <= 512; start a multiple of 4).
+struct BatchTile {
+    int64_t start;
+    int count;
+    int inst;
+};
+
+// The particle pass over the tiles of many instances (one dimension class: ndim
+// 1 or 2 with nv = 2).  inst_params: device array of per-instance tile
+// parameters (make_tile_params); diag_tiles: [ntiles][4] per-tile sums or NULL.
+cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
+                              const void *inst_params, ParticlesF32 p, bool push, bool mv,
+                              bool deposit, double *diag_tiles, int nblocks, int *err,
+                              cudaStream_t st);
+size_t batch_tile_params_bytes();
+void make_tile_params(void *dst, const GridParams &g, const float *E, unsigned long long *acc);
+
 // Number of blocks the particle pass uses for np particles (fixed, so the
 // diagnostics reduction order is deterministic).
 int particle_pass_blocks(int64_t np, int ndim);
@@ -152,6 +173,9 @@ size_t sort_scan_tmp_len(size_t n);
 // final permutation in s.idx[*perm_slot].
 cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bits,
                              const int32_t *cell, int64_t np, SortScratch &s, int *perm_slot,
+                             cudaStream_t st);
+// The radix passes alone, on keys already in s.keys[0] (key_bits wide).
+cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm_slot,
                              cudaStream_t st);
 // dst[r] = src[perm[r]] for the SoA particle record.
 cudaError_t launch_apply_perm(const uint32_t *perm, ParticlesF32 src, ParticlesF32 dst,

@@ -361,6 +361,39 @@ __device__ __forceinline__ void bulk_wait_read()
 
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Parameters of the tile being processed.
+struct TileParams {
+    GridParams g;
+    const float *E;
+    unsigned long long *acc;
+};
+
+// One instance: tiles of TILE consecutive particles of [0, np).
+struct SingleSrc {
+    static constexpr bool PER_TILE_DIAG = false;
+    TileParams tp;
+    int64_t np;
+    __device__ int64_t ntiles() const { return (np + TILE - 1) / TILE; }
+    __device__ int64_t start(int64_t t) const { return t * TILE; }
+    __device__ int count(int64_t t) const { return np - t * TILE < TILE ? (int)(np - t * TILE) : TILE; }
+    __device__ void load_params(int64_t, TileParams *) const {}
+    __device__ const TileParams &params(const TileParams &) const { return tp; }
+};
+
+// Many instances packed in one arena: tile t covers particles
+// [tiles[t].start, + tiles[t].count) of instance tiles[t].inst.
+struct BatchSrc {
+    static constexpr bool PER_TILE_DIAG = true;
+    const BatchTile *tiles;
+    const TileParams *inst;  // per instance: parameters, field and accumulator
+    int64_t nt;
+    __device__ int64_t ntiles() const { return nt; }
+    __device__ int64_t start(int64_t t) const { return tiles[t].start; }
+    __device__ int count(int64_t t) const { return tiles[t].count; }
+    __device__ void load_params(int64_t t, TileParams *dst) const { *dst = inst[tiles[t].inst]; }
+    __device__ const TileParams &params(const TileParams &s) const { return s; }
+};
+
 // The particle pass.  Persistent CTAs walk tiles of TILE consecutive particles
 // (tile t for t = blockIdx.x, + gridDim.x, ...).  One thread streams each tile's
 // record arrays (cell, offsets, velocities) into a shared-memory stage with TMA
@@ -372,10 +405,12 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // the warp-cooperative deposit) and takes all R through each phase together:
 // the field gathers are issued together and the R deposit scans interleave.
 // MODE (PASS_* bits) is a compile-time choice so each use carries only its work.
-template <int D, int NV, int MODE>
+// Src supplies the tiles: one instance (SingleSrc) or the tiles of many
+// independent instances packed in one particle arena (BatchSrc, whose tiles each
+// carry their instance's parameters, field and charge accumulator).
+template <int D, int NV, int MODE, class Src>
 __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
-    k_particle_pass(GridParams g, ParticlesF32 p, const float *__restrict__ E,
-                    unsigned long long *__restrict__ acc, double *__restrict__ diag_blocks,
+    k_particle_pass(Src src, ParticlesF32 p, double *__restrict__ diag_blocks,
                     int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -393,23 +428,25 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     // reference cell, per axis)
     unsigned *s_win = reinterpret_cast<unsigned *>(bars + STAGES);
     int *s_box = reinterpret_cast<int *>(s_win + WIN_CAP);
+    // the current tile's parameters (copied by one thread for a batch), its
+    // reference cell, and per-warp diagnostic partials of a batch tile
+    __shared__ TileParams s_tp;
+    __shared__ int s_ref_cell;
+    __shared__ float s_diag[PP_THREADS / 32][4];
 
-    const int64_t np = p.np;
-    const int64_t ntiles = (np + TILE - 1) / TILE;
+    const int64_t ntiles = src.ntiles();
     const int my_tiles =
         blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     const int tid = threadIdx.x, lane = tid & 31;
 
     // stage s, array a (0: cell, 1..D: offsets, D+1..: velocities)
     auto stage_arr = [&](int st, int a) { return stage_base + ((size_t)st * NA_MAX + a) * TILE; };
-    auto tile_start = [&](int k) { return (blockIdx.x + (int64_t)k * gridDim.x) * (int64_t)TILE; };
-    auto tile_bytes = [&](int64_t start) {
-        const int64_t cnt = np - start < TILE ? np - start : TILE;
-        return (uint32_t)(((cnt + 3) / 4) * 16);
-    };
+    auto tile_of = [&](int k) { return (int64_t)blockIdx.x + (int64_t)k * gridDim.x; };
+    auto tile_bytes = [&](int64_t t) { return (uint32_t)(((src.count(t) + 3) / 4) * 16); };
     auto issue_load = [&](int k, int st) {
-        const int64_t start = tile_start(k);
-        const uint32_t bytes = tile_bytes(start);
+        const int64_t t = tile_of(k);
+        const int64_t start = src.start(t);
+        const uint32_t bytes = tile_bytes(t);
         const uint32_t bar = smem_addr(&bars[st]);
         mbar_expect_tx(bar, bytes * (uint32_t)NA);
         bulk_g2s(smem_addr(stage_arr(st, 0)), p.cell + start, bytes, bar);
@@ -424,8 +461,9 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
         }
     };
     auto issue_store = [&](int k, int st) {
-        const int64_t start = tile_start(k);
-        const uint32_t bytes = tile_bytes(start);
+        const int64_t t = tile_of(k);
+        const int64_t start = src.start(t);
+        const uint32_t bytes = tile_bytes(t);
         if (MOVE) {
             bulk_s2g(p.cell + start, smem_addr(stage_arr(st, 0)), bytes);
 #pragma unroll
@@ -455,22 +493,20 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     if (tid == 0)
         for (int k = 0; k < STAGES - 1 && k < my_tiles; ++k) issue_load(k, k);
 
-    const float scale = ldexpf(1.0f, g.fx_bits);
-    const int one = 1 << g.fx_bits;
-    // diagnostics: FP32 sums over this thread's particles (at most a few hundred),
-    // reduced across threads and blocks in FP64
+    // diagnostics: FP32 sums over this thread's particles (at most a few hundred, or
+    // one batch tile), reduced across threads and blocks in FP64
     float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
     bool bad = false;
 
     for (int k = 0; k < my_tiles; ++k) {
         const int st = k % STAGES;
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
+        const int64_t t = tile_of(k);
+        if (tid == 0) src.load_params(t, &s_tp);  // the previous tile is finished
         const bool ok_wait = mbar_wait_bounded(smem_addr(&bars[st]), parity);
-        // the tile's reference cell (its first particle's cell before the move), read
+        // the tile's reference cell (its first particle's cell before the move), kept
         // before the barrier so that no thread overwrites it first
-        int ref[3] = {0, 0, 0};
-        if (DEPOSIT && ok_wait)
-            decode_cell<D>(reinterpret_cast<const int32_t *>(stage_arr(st, 0))[0], g, ref);
+        if (tid == 0 && ok_wait) s_ref_cell = reinterpret_cast<const int32_t *>(stage_arr(st, 0))[0];
         if (__syncthreads_or(!ok_wait)) {
             // a copy did not land within the cap: report, drain what is in flight, stop
             if (tid == 0) {
@@ -483,8 +519,16 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
             __syncthreads();
             return;
         }
-        const int cnt = (int)(np - tile_start(k) < TILE ? np - tile_start(k) : TILE);
+        const TileParams &tp = src.params(s_tp);
+        const GridParams &g = tp.g;
+        const float *__restrict__ E = tp.E;
+        unsigned long long *__restrict__ acc = tp.acc;
+        const float scale = ldexpf(1.0f, g.fx_bits);
+        const int one = 1 << g.fx_bits;
+        const int cnt = src.count(t);
         int32_t *s_cell = reinterpret_cast<int32_t *>(stage_arr(st, 0));
+        int ref[3] = {0, 0, 0};
+        if (DEPOSIT) decode_cell<D>(s_ref_cell, g, ref);
 
         // phase A: read the record, decode the cell, issue the field gathers
         int c[R][3];
@@ -659,10 +703,28 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
                 s_box[3 + tid] = -0x7fffffff;
             }
         }
+        if (DIAG && Src::PER_TILE_DIAG) {
+            // this tile's sums, per warp, then per tile below (fixed order)
+            float vals[4] = {ke, mom[0], mom[1], mom[2]};
+#pragma unroll
+            for (int kq = 0; kq < 4; ++kq) {
+                float x = vals[kq];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) s_diag[tid >> 5][kq] = x;
+            }
+            ke = 0.0f;
+            mom[0] = mom[1] = mom[2] = 0.0f;
+        }
         // the stage is complete: make the generic-proxy writes visible to the bulk
         // copies, store it back, and refill the stage consumed one tile ago
         if (WRITE) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (DIAG && Src::PER_TILE_DIAG && tid < 4) {
+            double sum = 0.0;
+            for (int jw = 0; jw < PP_THREADS / 32; ++jw) sum += (double)s_diag[jw][tid];
+            diag_blocks[t * 4 + tid] = sum;
+        }
         if (tid == 0) {
             if (WRITE) issue_store(k, st);
             const int kn = k + STAGES - 1;
@@ -676,7 +738,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     }
     if (tid == 0 && WRITE) bulk_wait_all();
     if (bad) latch(err, EF_NONFINITE);
-    if (DIAG) {
+    if (DIAG && !Src::PER_TILE_DIAG) {
         __shared__ double red[4][PP_THREADS / 32];
         double vals[4] = {ke, mom[0], mom[1], mom[2]};
         const int w = tid >> 5;
@@ -717,45 +779,47 @@ int particle_pass_blocks(int64_t np, int ndim)
     return (int)(b < 1 ? 1 : b);
 }
 
-template <int D, int NV, int MODE>
-static cudaError_t launch_pass_m(const GridParams &g, ParticlesF32 p, const float *E,
-                                 unsigned long long *acc, double *diag_blocks, int nblocks,
+template <int D, int NV, int MODE, class Src>
+static cudaError_t launch_pass_m(const Src &src, ParticlesF32 p, double *diag_blocks, int nblocks,
                                  int *err, cudaStream_t st)
 {
     constexpr size_t smem = pass_smem_bytes<D, NV>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_particle_pass<D, NV, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_particle_pass<D, NV, MODE, Src>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_particle_pass<D, NV, MODE><<<nblocks, PP_THREADS, smem, st>>>(g, p, E, acc, diag_blocks,
-                                                                    err);
+    k_particle_pass<D, NV, MODE, Src><<<nblocks, PP_THREADS, smem, st>>>(src, p, diag_blocks, err);
     note_launch();
     return cudaGetLastError();
 }
 
-template <int D, int NV>
-static cudaError_t launch_pass_t(const GridParams &g, ParticlesF32 p, const float *E,
-                                 unsigned long long *acc, int mode, double *diag_blocks,
+template <int D, int NV, class Src>
+static cudaError_t launch_pass_t(const Src &src, ParticlesF32 p, int mode, double *diag_blocks,
                                  int nb, int *err, cudaStream_t st)
 {
     constexpr int FUSED = PASS_PUSH | PASS_MOVE | PASS_DEPOSIT;
     constexpr int GP = PASS_PUSH | PASS_MOVE;
     switch (mode) {
-    case FUSED: return launch_pass_m<D, NV, FUSED>(g, p, E, acc, diag_blocks, nb, err, st);
+    case FUSED: return launch_pass_m<D, NV, FUSED>(src, p, diag_blocks, nb, err, st);
     case FUSED | PASS_DIAG:
-        return launch_pass_m<D, NV, FUSED | PASS_DIAG>(g, p, E, acc, diag_blocks, nb, err, st);
-    case GP: return launch_pass_m<D, NV, GP>(g, p, E, acc, diag_blocks, nb, err, st);
+        return launch_pass_m<D, NV, FUSED | PASS_DIAG>(src, p, diag_blocks, nb, err, st);
+    case GP: return launch_pass_m<D, NV, GP>(src, p, diag_blocks, nb, err, st);
     case GP | PASS_DIAG:
-        return launch_pass_m<D, NV, GP | PASS_DIAG>(g, p, E, acc, diag_blocks, nb, err, st);
-    case PASS_DEPOSIT:
-        return launch_pass_m<D, NV, PASS_DEPOSIT>(g, p, E, acc, diag_blocks, nb, err, st);
-    case PASS_PUSH: return launch_pass_m<D, NV, PASS_PUSH>(g, p, E, acc, diag_blocks, nb, err, st);
+        return launch_pass_m<D, NV, GP | PASS_DIAG>(src, p, diag_blocks, nb, err, st);
+    case PASS_DEPOSIT: return launch_pass_m<D, NV, PASS_DEPOSIT>(src, p, diag_blocks, nb, err, st);
+    case PASS_PUSH: return launch_pass_m<D, NV, PASS_PUSH>(src, p, diag_blocks, nb, err, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+static int pass_mode(bool push, bool mv, bool deposit, bool diag)
+{
+    return (push ? PASS_PUSH : 0) | (mv ? PASS_MOVE : 0) | (deposit ? PASS_DEPOSIT : 0) |
+           (diag && push && mv ? PASS_DIAG : 0);
 }
 
 cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const float *E,
@@ -763,18 +827,51 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
                                  DiagPartials diag, int *err, cudaStream_t st)
 {
     if (p.np == 0) return cudaSuccess;
-    const int mode = (push ? PASS_PUSH : 0) | (mv ? PASS_MOVE : 0) |
-                     (deposit ? PASS_DEPOSIT : 0) | (diag.blocks && push && mv ? PASS_DIAG : 0);
+    const int mode = pass_mode(push, mv, deposit, diag.blocks != nullptr);
     const int nb = particle_pass_blocks(p.np, g.ndim);
+    SingleSrc src;
+    src.tp.g = g;
+    src.tp.E = E;
+    src.tp.acc = acc;
+    src.np = p.np;
     switch (g.ndim * 10 + p.nv) {
-    case 11: return launch_pass_t<1, 1>(g, p, E, acc, mode, diag.blocks, nb, err, st);
-    case 12: return launch_pass_t<1, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st);
-    case 13: return launch_pass_t<1, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
-    case 22: return launch_pass_t<2, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st);
-    case 23: return launch_pass_t<2, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
-    case 33: return launch_pass_t<3, 3>(g, p, E, acc, mode, diag.blocks, nb, err, st);
+    case 11: return launch_pass_t<1, 1>(src, p, mode, diag.blocks, nb, err, st);
+    case 12: return launch_pass_t<1, 2>(src, p, mode, diag.blocks, nb, err, st);
+    case 13: return launch_pass_t<1, 3>(src, p, mode, diag.blocks, nb, err, st);
+    case 22: return launch_pass_t<2, 2>(src, p, mode, diag.blocks, nb, err, st);
+    case 23: return launch_pass_t<2, 3>(src, p, mode, diag.blocks, nb, err, st);
+    case 33: return launch_pass_t<3, 3>(src, p, mode, diag.blocks, nb, err, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
+                              const void *inst_params, ParticlesF32 p, bool push, bool mv,
+                              bool deposit, double *diag_tiles, int nblocks, int *err,
+                              cudaStream_t st)
+{
+    if (ntiles == 0) return cudaSuccess;
+    const int mode = pass_mode(push, mv, deposit, diag_tiles != nullptr);
+    BatchSrc src;
+    src.tiles = tiles;
+    src.inst = static_cast<const TileParams *>(inst_params);
+    src.nt = ntiles;
+    const int nb = nblocks < ntiles ? nblocks : (int)ntiles;
+    switch (ndim * 10 + p.nv) {
+    case 12: return launch_pass_t<1, 2>(src, p, mode, diag_tiles, nb, err, st);
+    case 22: return launch_pass_t<2, 2>(src, p, mode, diag_tiles, nb, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t batch_tile_params_bytes() { return sizeof(TileParams); }
+
+void make_tile_params(void *dst, const GridParams &g, const float *E, unsigned long long *acc)
+{
+    TileParams *t = static_cast<TileParams *>(dst);
+    t->g = g;
+    t->E = E;
+    t->acc = acc;
 }
 
 // ---- load ------------------------------------------------------------------------------------

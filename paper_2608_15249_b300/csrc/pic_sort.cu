@@ -272,8 +272,18 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t ntiles = tiles_of(np);
-    const int passes = key_bits <= 0 ? 1 : (key_bits + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
+    return launch_sort_keys(key_bits, np, s, perm_slot, st);
+}
+
+cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm_slot,
+                             cudaStream_t st)
+{
+    if (np <= 0) {
+        *perm_slot = 0;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaSuccess;
+    const int64_t ntiles = tiles_of(np);    const int passes = key_bits <= 0 ? 1 : (key_bits + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
     const int dbits = key_bits <= 0 ? 8 : (key_bits + passes - 1) / passes;  // <= 10
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
