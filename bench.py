@@ -305,6 +305,136 @@ def run_e2e(args, w, pk, torch, stream, extra):
                     "+ diagnostics read each step + final rho read"}
 
 
+def _per_instance_rate(pk, torch, stream, ws, steps, **over):
+    """Particle-steps/s of push_deposit run instance by instance (one handle each)
+    over `ws`: total particle-steps / total CUDA-event time."""
+    ps, secs = 0, 0.0
+    for w in ws:
+        g = pk.from_workload(w, stream=stream.cuda_stream, **over)
+        g.load(w.x, w.v)
+        for _ in range(3):
+            g.push_deposit()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.push_deposit()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs += e0.elapsed_time(e1) * 1e-3
+        ps += w.np_ * steps
+        g.close()
+    return ps / secs
+
+
+def bench_batch(args):
+    """The batched serving workload: `--instances` independent periodic 1D/2D
+    instances (n per axis log-uniform in [32, 1024], 1k-200k electrons log-uniform,
+    Maxwellian with a 1 % random mode, dt = 0.1) advanced together.  The value is
+    the batch's particle-steps/s of gather + push + move + deposit (the shared
+    particle pass and the charge conversion of every instance, with the sort at the
+    tuned cadence); the field solve, the full step, and the same metric run instance
+    by instance (FP64 plain and FP32 forms) on an unbiased sample of the instances
+    are reported beside it."""
+    import torch
+
+    import paper_2608_15249_b300 as pk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ws = workloads.batch_instances(count=args.instances, seed=5)
+    total = sum(w.np_ for w in ws)
+    nodes = sum(w.cells for w in ws)
+    stream = torch.cuda.current_stream()
+    bt = pk.batch_from_workloads(ws, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    bt.load([w.x for w in ws], [w.v for w in ws])
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t0
+    tuning = (bt.autotune(steps_per_trial=3) if not args.no_autotune
+              else bt.get_tuning().as_dict())
+    sort_every = tuning["sort_every"]
+
+    def hot_step(k):
+        bt.push_deposit()
+        if sort_every and k % sort_every == 0:
+            bt.sort()
+
+    for k in range(1, args.warmup + 1):
+        hot_step(k)
+    torch.cuda.synchronize()
+    launches0 = pk.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ev0.record(stream)
+        for k in range(args.warmup + 1, args.warmup + args.steps + 1):
+            hot_step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = pk.kernel_launches() - launches0
+    value = total * args.steps / (ms * 1e-3)
+    # push_deposit alone (no sort) for the roofline
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        bt.push_deposit()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pd_ms = e0.elapsed_time(e1) / 10
+    alg_bytes = sum(w.np_ * _bytes_per_particle(w.ndim, 2)
+                    + w.cells * (4 * w.ndim + 8 + 8 + 12) for w in ws)
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (pd_ms * 1e-3) / 1e9
+    # the field solve of every instance, and the full step
+    e0.record(stream)
+    for _ in range(args.solve_reps):
+        bt.solve_field()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1) / args.solve_reps
+    e0.record(stream)
+    bt.step(args.full_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1) / args.full_steps
+    iters = [bt.get_diag(i)["cg_iters"] for i in range(len(ws))]
+    bt.close()
+    # the same metric instance by instance, on every k-th instance
+    sample = ws[:: args.plain_stride]
+    f64_rate = _per_instance_rate(pk, torch, stream, sample, args.plain_steps,
+                                  precision=pk.AP_PIC_FP64_PLAIN)
+    f32_rate = _per_instance_rate(pk, torch, stream, sample, args.plain_steps)
+    line = {
+        "metric": METRIC + ", batched", "value": value,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(ws)} periodic 1D/2D instances, "
+                               f"{total} electrons, {nodes} nodes, sort every {sort_every}",
+                   "instances": len(ws), "particles": total, "nodes": nodes,
+                   "tuning": tuning, "load_seconds": load_s,
+                   "l2": "particle state larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "batch push_deposit (k_particle_pass per dimension class "
+                               "+ memset + k_b_convert)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": pd_ms,
+                     "peak_kind": peak_kind},
+        "field_solve_ms": solve_ms,
+        "full_step_ms": full_ms,
+        "full_step_particle_steps_per_s": total / (full_ms * 1e-3),
+        "cg_iters_last_solve": {"max": max(iters), "median": statistics.median(iters)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "per_instance": {
+            "sample": f"every {args.plain_stride}th instance ({len(sample)}), "
+                      f"{args.plain_steps} push_deposit calls each",
+            "fp64_plain": f64_rate, "fp32": f32_rate, "unit": UNIT,
+            "batched_over_fp64_plain": value / f64_rate},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,11 +453,19 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--ref-sample", type=int, default=1 << 16)
+    ap.add_argument("--instances", type=int, default=1024, help="--workload batch")
+    ap.add_argument("--plain-stride", type=int, default=8, help="--workload batch")
+    ap.add_argument("--plain-steps", type=int, default=10, help="--workload batch")
+    ap.add_argument("--solve-reps", type=int, default=3, help="--workload batch")
+    ap.add_argument("--full-steps", type=int, default=3, help="--workload batch")
+    ap.add_argument("--no-autotune", action="store_true", help="--workload batch")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batch":
+        bench_batch(args)
     else:
         bench_ours(args)
 

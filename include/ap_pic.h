@@ -306,6 +306,19 @@ ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np, const double
 /* nsteps cycles of every instance (sort every tuning.sort_every steps). */
 ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps);
 
+/* The parts of a step, for timing them apart (a step is push_deposit, a sort
+ * when due, then solve_field; none of these advances the step counter):
+ *   push_deposit: one particle pass of every instance (gather, push, move,
+ *                 deposit, Sec. 3.1 steps of Listing 1) and the charge conversion;
+ *   sort:         the stable sort of every instance's particles by brick-major key;
+ *   solve_field:  the Jacobi-PCG solve of every instance, its refinement pass, E
+ *                 and the diagnostics.
+ * Stream-ordered and asynchronous like ap_pic_batch_step; errors latched on the
+ * device surface at the next read-back. */
+ap_pic_status ap_pic_batch_push_deposit(ap_pic_batch *b);
+ap_pic_status ap_pic_batch_sort(ap_pic_batch *b);
+ap_pic_status ap_pic_batch_solve_field(ap_pic_batch *b);
+
 ap_pic_status ap_pic_batch_set_tuning(ap_pic_batch *b, const ap_pic_batch_tuning *t);
 ap_pic_status ap_pic_batch_get_tuning(const ap_pic_batch *b, ap_pic_batch_tuning *t);
 

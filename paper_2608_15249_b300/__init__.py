@@ -42,7 +42,8 @@ EXPORTS = [
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
     "ap_pic_sort_perm_noalloc",
     "ap_pic_batch_default_tuning", "ap_pic_batch_create", "ap_pic_batch_destroy",
-    "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_set_tuning",
+    "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_push_deposit", "ap_pic_batch_sort",
+    "ap_pic_batch_solve_field", "ap_pic_batch_set_tuning",
     "ap_pic_batch_get_tuning", "ap_pic_batch_autotune", "ap_pic_batch_get_rho",
     "ap_pic_batch_get_E", "ap_pic_batch_get_particles", "ap_pic_batch_get_perm",
     "ap_pic_batch_get_diag", "ap_pic_batch_num_particles", "ap_pic_batch_last_error",
@@ -144,6 +145,9 @@ def _declare(L):
     L.ap_pic_batch_destroy.argtypes = [P]
     L.ap_pic_batch_load.argtypes = [P, P, P, P, U]
     L.ap_pic_batch_step.argtypes = [P, I]
+    for name in ("ap_pic_batch_push_deposit", "ap_pic_batch_sort", "ap_pic_batch_solve_field"):
+        getattr(L, name).argtypes = [P]
+        getattr(L, name).restype = I
     L.ap_pic_batch_set_tuning.argtypes = [P, tunp]
     L.ap_pic_batch_get_tuning.argtypes = [P, tunp]
     L.ap_pic_batch_autotune.argtypes = [P, I, ctypes.c_char_p]
@@ -452,6 +456,15 @@ class Batch:
 
     def step(self, nsteps=1):
         self._check(self._lib.ap_pic_batch_step(self.h, int(nsteps)))
+
+    def push_deposit(self):
+        self._check(self._lib.ap_pic_batch_push_deposit(self.h))
+
+    def sort(self):
+        self._check(self._lib.ap_pic_batch_sort(self.h))
+
+    def solve_field(self):
+        self._check(self._lib.ap_pic_batch_solve_field(self.h))
 
     def get_tuning(self):
         t = ap_pic_batch_tuning()

@@ -90,6 +90,18 @@ __device__ double bblock_sum(double x)
     return r;
 }
 
+// An instance's done flag read once per block and broadcast, so that every thread
+// of the block takes the same branch even while another block of the instance
+// sets the flag in the same launch (the item loops below synchronise the block).
+__device__ int block_flag(const int *p)
+{
+    __shared__ int s;
+    __syncthreads();  // the previous broadcast has been read by every thread
+    if (threadIdx.x == 0) s = *reinterpret_cast<const volatile int *>(p);
+    __syncthreads();
+    return s;
+}
+
 // Sum of instance `in`'s item partials (stride `stride` doubles per item, field
 // `k`), in a fixed order; valid in every thread of the block.
 __device__ double inst_sum(const double *__restrict__ part, int stride, int k, const BInst &in)
@@ -151,10 +163,14 @@ struct BCG {
     double *scal;     // [ninst][8]: 0 bnorm, 1-2 rz ping-pong, 3 relres
     int *done;        // [ninst]
     int *iters;       // [ninst]
-    int *active;      // [1]: instances not done
 };
 
 #define ITEM_LOOP for (int it_ = blockIdx.x; it_ < nitems; it_ += gridDim.x)
+// Over the items listed in act[0..nact) (every item when act is null): the CG
+// iterations walk only the items of instances that have not converged.
+#define ACT_LOOP                                                                               \
+    for (int k_ = blockIdx.x, it_ = 0; k_ < nact && ((it_ = act ? act[k_] : k_), true);      \
+         k_ += gridDim.x)
 
 __global__ void __launch_bounds__(BT)
     k_b_convert(const CellItem *__restrict__ items, int nitems, const BInst *__restrict__ inst,
@@ -235,13 +251,13 @@ __global__ void __launch_bounds__(BT)
 }
 
 __global__ void __launch_bounds__(BT)
-    k_b_cg_matvec(const CellItem *__restrict__ items, int nitems, const BInst *__restrict__ inst,
+    k_b_cg_matvec(const CellItem *__restrict__ items, const int *__restrict__ act, int nact, const BInst *__restrict__ inst,
                   BArena A, BCG cg)
 {
-    ITEM_LOOP
+    ACT_LOOP
     {
         const CellItem ci = items[it_];
-        if (cg.done[ci.inst]) continue;
+        if (block_flag(cg.done + ci.inst)) continue;
         const BInst in = inst[ci.inst];
         double pq = 0.0;
         for (int k = threadIdx.x; k < ci.count; k += BT) {
@@ -258,13 +274,13 @@ __global__ void __launch_bounds__(BT)
 }
 
 __global__ void __launch_bounds__(BT)
-    k_b_cg_update(const CellItem *__restrict__ items, int nitems, const BInst *__restrict__ inst,
+    k_b_cg_update(const CellItem *__restrict__ items, const int *__restrict__ act, int nact, const BInst *__restrict__ inst,
                   BArena A, float *__restrict__ x, BCG cg, int it)
 {
-    ITEM_LOOP
+    ACT_LOOP
     {
         const CellItem ci = items[it_];
-        if (cg.done[ci.inst]) continue;
+        if (block_flag(cg.done + ci.inst)) continue;
         const BInst in = inst[ci.inst];
         const double pq = inst_sum(cg.part, 4, 3, in);
         const double a64 = cg.scal[ci.inst * 8 + 1 + (it & 1)] / pq;
@@ -292,13 +308,13 @@ __global__ void __launch_bounds__(BT)
 }
 
 __global__ void __launch_bounds__(BT)
-    k_b_cg_dir(const CellItem *__restrict__ items, int nitems, const BInst *__restrict__ inst,
+    k_b_cg_dir(const CellItem *__restrict__ items, const int *__restrict__ act, int nact, const BInst *__restrict__ inst,
                BArena A, BCG cg, int it, int maxit, double rtol)
 {
-    ITEM_LOOP
+    ACT_LOOP
     {
         const CellItem ci = items[it_];
-        if (cg.done[ci.inst]) continue;
+        if (block_flag(cg.done + ci.inst)) continue;
         const BInst in = inst[ci.inst];
         const double rr0 = inst_sum(cg.part, 4, 0, in);
         const double rs = inst_sum(cg.part, 4, 1, in);
@@ -327,21 +343,6 @@ __global__ void __launch_bounds__(BT)
             A.r[a] = ri;
             A.p[a] = ri * in.inv_diag + beta * A.p[a];
         }
-    }
-}
-
-__global__ void k_b_count_active(const int *__restrict__ done, int ninst, int *active)
-{
-    int c = 0;
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x) c += done[i] ? 0 : 1;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    __shared__ int red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int j = 0; j < (int)(blockDim.x + 31) / 32; ++j) t += red[j];
-        *active = t;
     }
 }
 
@@ -516,6 +517,8 @@ struct BatchGrid {
     double *ipart;
     long long *ipart_ll;
     int nblocks;
+    const int *act;  // items the CG iterations walk (null: all), nact of them
+    int nact;
 };
 
 }  // namespace apk
@@ -584,7 +587,9 @@ struct ap_pic_batch {
     double *d_diag = nullptr;     // [count][8]
     long long *d_isum = nullptr;  // [count]
     int *d_err = nullptr;
-    int *h_active = nullptr;
+    int *h_done = nullptr;   // pinned: per-instance CG done flags
+    int *h_act = nullptr;    // pinned: the active item list, uploaded to d_act
+    int *d_act = nullptr;
     int *h_err = nullptr;
     int pass_blocks = 0;
     int sms = 148;
@@ -756,7 +761,7 @@ extern "C" ap_pic_status ap_pic_batch_create(int count, const ap_pic_config *cfg
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     if (b->sms <= 0) b->sms = 148;
-    BCU(b, cudaMallocHost(&b->h_active, 64));
+    BCU(b, cudaMallocHost(&b->h_done, sizeof(int) * (size_t)count));
     BCU(b, cudaMallocHost(&b->h_err, 64));
     return AP_PIC_OK;
 }
@@ -770,7 +775,8 @@ extern "C" ap_pic_status ap_pic_batch_destroy(ap_pic_batch *b)
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
-    if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->h_done) cudaFreeHost(b->h_done);
+    if (b->h_act) cudaFreeHost(b->h_act);
     if (b->h_err) cudaFreeHost(b->h_err);
     delete b;
     return AP_PIC_OK;
@@ -861,44 +867,67 @@ ap_pic_status batch_convert(ap_pic_batch *b)
     return AP_PIC_OK;
 }
 
-// CG iterations [first, first + n) for the solve A x = rhs.
+// CG iterations [first, first + n) for the solve A x = rhs, over the active items.
 void cg_iters(ap_pic_batch *b, float *x, int first, int n, int maxit, double rtol)
 {
     BatchGrid &G = b->G;
-    const int nb = grid_blocks(b);
+    const int cap = b->sms * 4;
+    const int nb = G.nact < cap ? G.nact : cap;
+    if (nb == 0) return;
     for (int it = first; it < first + n && it < maxit; ++it) {
-        k_b_cg_matvec<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, G.cg);
-        k_b_cg_update<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, x, G.cg, it);
-        k_b_cg_dir<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, G.cg, it, maxit, rtol);
+        k_b_cg_matvec<<<nb, BT, 0, b->stream>>>(G.items, G.act, G.nact, G.inst, G.A, G.cg);
+        k_b_cg_update<<<nb, BT, 0, b->stream>>>(G.items, G.act, G.nact, G.inst, G.A, x, G.cg, it);
+        k_b_cg_dir<<<nb, BT, 0, b->stream>>>(G.items, G.act, G.nact, G.inst, G.A, G.cg, it, maxit,
+                                             rtol);
         note_launch(3);
     }
 }
 
+// Starts a solve on every item (the CG kernels then walk all items until the
+// first host check narrows the list).
 void cg_start(ap_pic_batch *b, float *x, const float *rhs, double rtol)
 {
     BatchGrid &G = b->G;
+    G.act = nullptr;
+    G.nact = G.nitems;
     k_b_cg_init<<<grid_blocks(b), BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, x, rhs, G.cg);
     const int nbi = b->count < b->sms * 4 ? b->count : b->sms * 4;
     k_b_cg_init_fin<<<nbi, BT, 0, b->stream>>>(G.inst, G.ninst, G.cg, rtol);
     note_launch(2);
 }
 
-void count_active(ap_pic_batch *b)
-{
-    k_b_count_active<<<1, 1024, 0, b->stream>>>(b->G.cg.done, b->G.ninst, b->G.cg.active);
-    note_launch();
-}
-
-// Runs CG blocks until every instance is done (host check per block).
+// Runs CG blocks until every instance is done.  Before each block the host reads
+// the done flags and, when instances have finished, narrows the item list to
+// those of the instances still iterating, so that the launches (sized to the
+// list) cost nothing for converged instances.
 ap_pic_status cg_finish(ap_pic_batch *b, float *x, int first, int maxit, double rtol)
 {
+    BatchGrid &G = b->G;
     int it = first;
+    // the solve's first iterations (possibly replayed from a graph) walked every item
+    G.act = nullptr;
+    G.nact = G.nitems;
+    int listed = b->count;  // instances in the current list
     while (true) {
-        count_active(b);
-        BCU(b, cudaMemcpyAsync(b->h_active, b->G.cg.active, sizeof(int), cudaMemcpyDeviceToHost,
-                               b->stream));
+        BCU(b, cudaMemcpyAsync(b->h_done, G.cg.done, sizeof(int) * (size_t)b->count,
+                               cudaMemcpyDeviceToHost, b->stream));
         BCU(b, cudaStreamSynchronize(b->stream));
-        if (*b->h_active == 0 || it >= maxit) break;
+        int active = 0;
+        for (int i = 0; i < b->count; ++i) active += b->h_done[i] ? 0 : 1;
+        if (active == 0 || it >= maxit) break;
+        if (active < listed) {
+            int m = 0;
+            for (int i = 0; i < b->count; ++i) {
+                if (b->h_done[i]) continue;
+                const BInst &in = b->binst[i];
+                for (int j = 0; j < in.nitems; ++j) b->h_act[m++] = in.item0 + j;
+            }
+            BCU(b, cudaMemcpyAsync(b->d_act, b->h_act, sizeof(int) * (size_t)m,
+                                   cudaMemcpyHostToDevice, b->stream));
+            G.act = b->d_act;
+            G.nact = m;
+            listed = active;
+        }
         const int n = b->tune.cg_iters_per_graph;
         cg_iters(b, x, it, n, maxit, rtol);
         it += n;
@@ -1135,7 +1164,12 @@ extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
     BTRY(balloc(b, &G.cg.scal, (size_t)n * 8));
     BTRY(balloc(b, &G.cg.done, (size_t)n));
     BTRY(balloc(b, &G.cg.iters, (size_t)n));
-    BTRY(balloc(b, &G.cg.active, 1));
+    BTRY(balloc(b, &b->d_act, (size_t)G.nitems + 1));
+    if (b->h_act) cudaFreeHost(b->h_act);
+    b->h_act = nullptr;
+    BCU(b, cudaMallocHost(&b->h_act, sizeof(int) * ((size_t)G.nitems + 1)));
+    G.act = nullptr;
+    G.nact = G.nitems;
     BTRY(balloc(b, &G.fepart, (size_t)G.nitems + 1));
     BTRY(balloc(b, &G.ipart, (size_t)G.nitems + 1));
     BTRY(balloc(b, &G.ipart_ll, (size_t)G.nitems + 1));
@@ -1244,6 +1278,38 @@ extern "C" ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps)
         BTRY(step_back(b, b->tune.cg_iters_per_graph));
         b->step = k;
     }
+    return leave(b);
+}
+
+// The parts of a step on their own (a step is push_deposit, a sort when due,
+// solve_field); none of them advances the step counter.
+extern "C" ap_pic_status ap_pic_batch_push_deposit(ap_pic_batch *b)
+{
+    BTRY(need_loaded(b, 0));
+    BTRY(enter(b));
+    BCU(b, cudaMemsetAsync(b->G.A.acc, 0, (size_t)b->total_nodes * 8, b->stream));
+    BTRY(batch_pass(b, true, true, true, true));
+    BTRY(batch_convert(b));
+    return leave(b);
+}
+
+extern "C" ap_pic_status ap_pic_batch_sort(ap_pic_batch *b)
+{
+    BTRY(need_loaded(b, 0));
+    BTRY(enter(b));
+    BTRY(batch_sort(b));
+    return leave(b);
+}
+
+extern "C" ap_pic_status ap_pic_batch_solve_field(ap_pic_batch *b)
+{
+    BTRY(need_loaded(b, 0));
+    BTRY(enter(b));
+    BatchGrid &G = b->G;
+    const int first = b->tune.cg_iters_per_graph;
+    cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
+    cg_iters(b, G.A.phi, 0, first, b->cfg[0].cg_maxit, b->cfg[0].cg_rtol);
+    BTRY(step_back(b, first));
     return leave(b);
 }
 

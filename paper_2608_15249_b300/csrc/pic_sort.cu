@@ -283,7 +283,8 @@ cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm
         return cudaSuccess;
     }
     cudaError_t e = cudaSuccess;
-    const int64_t ntiles = tiles_of(np);    const int passes = key_bits <= 0 ? 1 : (key_bits + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
+    const int64_t ntiles = tiles_of(np);
+    const int passes = key_bits <= 0 ? 1 : (key_bits + MAX_DIGIT_BITS - 1) / MAX_DIGIT_BITS;
     const int dbits = key_bits <= 0 ? 8 : (key_bits + passes - 1) / passes;  // <= 10
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {

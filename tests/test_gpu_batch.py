@@ -127,3 +127,70 @@ def test_batch_autotune_and_cache(pk, tmp_path):
         d = bt.get_diag(i)
         assert d["charge_fx_sum"] == w.np_ * (1 << d["fx_bits"])
     bt.close()
+
+
+def test_batch_many_instances_many_items(pk):
+    """Many instances split into many small cell items, converging at different CG
+    iterations while their blocks share launches: every instance stays finite with
+    exact charge, and a sample matches the oracle after a few steps."""
+    rng = np.random.default_rng(79)
+    ws = []
+    for i in range(40):
+        if i % 3 == 0:
+            ws.append(plasma.maxwellian_box(1, (int(rng.integers(32, 300)),), ppc=12, nv=2,
+                                            seed=100 + i))
+        else:
+            n = (int(rng.integers(40, 140)), int(rng.integers(40, 140)))
+            ppc = [0.05, 1, 3][i % 3]
+            ws.append(plasma.sparse_box(2, n, max(64, int(ppc * n[0] * n[1])), nv=2,
+                                        seed=100 + i))
+    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7)
+    bt.set_tuning(item_cells=256, sort_every=2, cg_iters_per_graph=8)
+    bt.load([w.x for w in ws], [w.v for w in ws])
+    check = list(range(0, len(ws), 7))
+    sims = {i: _oracle(ws[i]).load(ws[i].x, ws[i].v) for i in check}
+    ident = {i: bt.get_perm(i).copy() for i in check}
+    for k in range(1, 5):
+        bt.step(1)
+        for s in sims.values():
+            s.step(1)
+        if k % 2 == 0:
+            ident = {i: ident[i][bt.get_perm(i)] for i in check}
+    for i, w in enumerate(ws):
+        d = bt.get_diag(i)
+        assert d["error_flags"] == 0 and d["charge_fx_sum"] == w.np_ * (1 << d["fx_bits"]), i
+        assert np.all(np.isfinite(bt.get_E(i))), i
+    for i in check:
+        w, sim = ws[i], sims[i]
+        _, _, v, x = bt.get_particles(i)
+        L = np.asarray(w.L[: w.ndim])
+        dist = np.abs(x - sim.x[ident[i]])
+        dist = np.minimum(dist, L - dist)
+        assert dist.max() <= TOL, (i, dist.max())
+        assert rel(v, sim.v[ident[i]], np.abs(sim.v).max()) <= TOL, i
+        assert rel(bt.get_E(i), sim.E, np.abs(sim.E).max()) <= TOL, i
+    bt.close()
+
+
+def test_batch_step_parts_equal_step(pk):
+    """push_deposit, a sort when due and solve_field, called apart, give bit for bit
+    what the step gives."""
+    ws = instances()
+    a = pk.batch_from_workloads(ws)
+    b = pk.batch_from_workloads(ws)
+    for t in (a, b):
+        t.set_tuning(sort_every=2)
+        t.load([w.x for w in ws], [w.v for w in ws])
+    a.step(4)
+    for k in range(1, 5):
+        b.push_deposit()
+        if k % 2 == 0:
+            b.sort()
+        b.solve_field()
+    for i in range(len(ws)):
+        np.testing.assert_array_equal(a.get_rho(i), b.get_rho(i))
+        np.testing.assert_array_equal(a.get_E(i), b.get_E(i))
+        for x, y in zip(a.get_particles(i), b.get_particles(i)):
+            np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
