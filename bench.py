@@ -7,8 +7,9 @@ sort at its cadence, on the 2D two-stream workload: 512 x 512 nodes, dx = 1,
 64 electrons per cell (16,777,216), beams at +-3 v_te with v_te = 1, dt = 0.1,
 sort every 20 steps.  One step of the timed loop = one pass of those stages
 over every particle; particle state (335 MB) is larger than L2, so no L2
-flush is needed between steps.  The field solve (CG + E) is run and timed
-separately, and it is inside the end-to-end number.
+flush is needed between steps.  The field solve (Jacobi-PCG + E, and the
+spectral solve) is run and timed separately; the end-to-end number runs the
+full cycle with the spectral solve (and, for a few steps, with the CG).
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
@@ -238,13 +239,35 @@ def bench_ours(args):
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     breakdown = {k: (v[0] / max(v[1], 1)) for k, v in stages.items() if v[1]}
 
-    # field solve timed separately, then the end-to-end job through host buffers
+    # field solve timed separately (the CG, and the spectral solve where the form has
+    # it), then the end-to-end job through host buffers
     g.set_timing(True)
     g.solve_field()
     fs = g.get_timing()["field"]
     g.set_timing(False)
-    e2e = run_e2e(args, w, pk, torch, stream, extra) if not args.no_e2e else None
     g.close()
+    field_ms = {"cg": fs[0] / max(fs[1], 1)}
+    if not f64:
+        gf = pk.from_workload(w, stream=stream.cuda_stream, solver=pk.AP_PIC_SOLVER_FFT)
+        gf.load(w.x, w.v)
+        gf.solve_field()
+        gf.set_timing(True)
+        for _ in range(10):
+            gf.solve_field()
+        ff = gf.get_timing()["field"]
+        gf.set_timing(False)
+        gf.close()
+        field_ms["fft"] = ff[0] / max(ff[1], 1)
+    e2e = None
+    if not args.no_e2e:
+        solver = "cg" if f64 else args.e2e_solver
+        e2e = run_e2e(args, w, pk, torch, stream, dict(extra, solver=_SOLVERS[solver]),
+                      args.e2e_steps)
+        e2e["solver"] = solver
+        if solver != "cg":
+            other = run_e2e(args, w, pk, torch, stream, extra, args.e2e_steps_cg)
+            e2e["cg"] = {"value": other["value"], "steps": other["steps"],
+                         "seconds": other["seconds"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -267,7 +290,7 @@ def bench_ours(args):
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                          "peak_kind": peak_kind},
             "stage_ms_per_call": breakdown,
-            "field_solve_ms": fs[0] / max(fs[1], 1),
+            "field_solve_ms": field_ms,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -278,7 +301,10 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, w, pk, torch, stream, extra):
+_SOLVERS = {"cg": 0, "fft": 1}
+
+
+def run_e2e(args, w, pk, torch, stream, extra, steps):
     """Load from pinned host memory, run the full cycle (with field solves) for
     e2e_steps steps reading the diagnostics back every step, then read rho."""
     import ctypes
@@ -286,7 +312,6 @@ def run_e2e(args, w, pk, torch, stream, extra):
     xs = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
     vs = torch.from_numpy(np.ascontiguousarray(w.v)).pin_memory()
     g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, **extra)
-    steps = args.e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.load_ptr(w.np_, xs.data_ptr(), vs.data_ptr())
@@ -301,7 +326,7 @@ def run_e2e(args, w, pk, torch, stream, extra):
     return {"value": w.np_ * steps / (t1 - t0), "unit": UNIT,
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h + rho.nbytes / steps,
             "steps": steps, "seconds": t1 - t0,
-            "what": "load from pinned host + full cycle (push, deposit, sort, CG, E) per step "
+            "what": "load from pinned host + full cycle (push, deposit, sort, field solve, E) per step "
                     "+ diagnostics read each step + final rho read"}
 
 
@@ -448,6 +473,8 @@ def main():
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32",
                     help="f32: cell + FP32 offset form (the product); f64: FP64 plain form")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--e2e-solver", choices=["cg", "fft"], default="fft")
+    ap.add_argument("--e2e-steps-cg", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)

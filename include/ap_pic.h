@@ -68,6 +68,17 @@ enum {
     AP_PIC_FP64_PLAIN = 1     /* FP64 positions/velocities, no sort, no tiling     */
 };
 
+/* Field solver of the FP32 form (the FP64 plain form always uses the CG). */
+enum {
+    AP_PIC_SOLVER_CG = 0,   /* Jacobi-preconditioned CG (D02, Sec. 2.2), default        */
+    AP_PIC_SOLVER_FFT = 1   /* spectral solve of the same discrete equation: phi_hat =
+                               rho_hat / K^2 with K^2 the Fourier symbol of the (2d+1)-
+                               point Laplacian; exact, no iteration.  Every n[a] must be
+                               <= AP_PIC_FFT_MAX_N (other lengths than powers of two use
+                               Bluestein's chirp-z form)                               */
+};
+#define AP_PIC_FFT_MAX_N 4096
+
 /* ap_pic_load flags */
 enum { AP_PIC_LOAD_NO_HALFPUSH = 1u };
 
@@ -98,6 +109,8 @@ typedef struct {
     int cg_maxit;          /* field-solve iteration cap (0: 20000)                 */
     int brick[3];          /* sort brick in cells per axis (0: library default)    */
     int diag_every;        /* diagnostics every this many steps (0: every step)    */
+    int solver;            /* AP_PIC_SOLVER_CG (default) or AP_PIC_SOLVER_FFT; both
+                              end with one FP64-residual refinement pass           */
 } ap_pic_config;
 
 typedef struct {

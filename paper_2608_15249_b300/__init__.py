@@ -30,6 +30,9 @@ AP_PIC_NOALLOC_MAX_NP = 1 << 20
 AP_PIC_BC_PERIODIC = 0
 AP_PIC_FP32_CELLOFF = 0
 AP_PIC_FP64_PLAIN = 1
+AP_PIC_SOLVER_CG = 0
+AP_PIC_SOLVER_FFT = 1
+AP_PIC_FFT_MAX_N = 4096
 AP_PIC_LOAD_NO_HALFPUSH = 1
 
 # Every symbol the header declares (checked by the CPU test of the library's exports).
@@ -60,7 +63,7 @@ class ap_pic_config(ctypes.Structure):
         ("E0", ctypes.c_double * 3), ("B0", ctypes.c_double * 3), ("bc", ctypes.c_int),
         ("precision", ctypes.c_int), ("nv", ctypes.c_int), ("sort_every", ctypes.c_int),
         ("fx_bits", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
-        ("brick", ctypes.c_int * 3), ("diag_every", ctypes.c_int),
+        ("brick", ctypes.c_int * 3), ("diag_every", ctypes.c_int), ("solver", ctypes.c_int),
     ]
 
 
@@ -176,7 +179,8 @@ def _ptr(a: Optional[np.ndarray]):
 def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
                 rho_background=None, E0=(0, 0, 0), B0=(0, 0, 0), nv=None,
                 precision=AP_PIC_FP32_CELLOFF, sort_every=20, fx_bits=0, cg_rtol=0.0,
-                cg_maxit=0, brick=(0, 0, 0), diag_every=0) -> ap_pic_config:
+                cg_maxit=0, brick=(0, 0, 0), diag_every=0,
+                solver=AP_PIC_SOLVER_CG) -> ap_pic_config:
     c = ap_pic_config()
     lib().ap_pic_config_default(ctypes.byref(c))
     c.ndim = ndim
@@ -197,6 +201,7 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
     c.cg_rtol = float(cg_rtol)
     c.cg_maxit = int(cg_maxit)
     c.diag_every = int(diag_every)
+    c.solver = int(solver)
     return c
 
 

@@ -87,6 +87,11 @@ struct ap_pic {
     int *h_err = nullptr;
     int *h_iters = nullptr;
 
+    // spectral field solve (AP_PIC_SOLVER_FFT)
+    bool use_fft = false;
+    FftPlan fft{};
+    bool relres_on_device = false;  // last_cg_relres is in f.scal[SCAL_TRUE_REL]
+
     int last_cg_iters = 0;
     double last_cg_relres = 0.0;
     bool diag_valid = false;
@@ -338,6 +343,16 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
     if (c->cg_maxit == 0) c->cg_maxit = DEFAULT_CG_MAXIT;
     if (c->cg_maxit < 1) return fail(h, AP_PIC_ERR_ARG, "cg_maxit must be >= 1");
     if (c->diag_every < 0) return fail(h, AP_PIC_ERR_ARG, "diag_every must be >= 0");
+    if (c->solver != AP_PIC_SOLVER_CG && c->solver != AP_PIC_SOLVER_FFT)
+        return fail(h, AP_PIC_ERR_ARG, "unknown solver %d", c->solver);
+    if (c->solver == AP_PIC_SOLVER_FFT) {
+        if (plain)
+            return fail(h, AP_PIC_ERR_UNSUPPORTED, "the FP64 plain form solves with the CG only");
+        for (int a = 0; a < c->ndim; ++a)
+            if (!fft_length_ok(c->n[a]))
+                return fail(h, AP_PIC_ERR_UNSUPPORTED, "FFT solver needs n[%d] <= %d", a,
+                            FFT_MAX_N);
+    }
     if (c->diag_every == 0) c->diag_every = 1;
     // default sort brick: 64 cells in 1D, 8 x 8 in 2D, 8 x 8 x 8 in 3D (capped by n)
     for (int a = 0; a < 3; ++a) {
@@ -407,6 +422,52 @@ static ap_pic_status create_grid_f64(ap_pic *h)
     return create_pinned(h);
 }
 
+// Tables of the spectral solve: per axis the Laplacian's Fourier eigenvalues (and
+// for lengths other than powers of two the Bluestein chirp and filter), one
+// twiddle table for the longest transform, and the complex work array.
+static ap_pic_status create_fft(ap_pic *h)
+{
+    static bool configured = false;
+    if (!configured) {
+        CU(h, fft_configure());
+        configured = true;
+    }
+    FftPlan &P = h->fft;
+    P.ndim = h->ndim;
+    P.cells = h->cells;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (P.sms <= 0) P.sms = 148;
+    size_t total = 0;
+    size_t off[3] = {0, 0, 0};
+    P.log2M = 1;
+    for (int a = 0; a < h->ndim; ++a) {
+        off[a] = total;
+        total += fft_axis_table_floats(h->cfg.n[a]);
+        const int l = fft_log2m(h->cfg.n[a]);
+        if (l > P.log2M) P.log2M = l;
+    }
+    std::vector<float> host(total + fft_twiddle_floats(P.log2M), 0.0f);
+    float *dev_tab = nullptr;
+    TRY(alloc_n(h, &dev_tab, host.size()));
+    int64_t inner = 1;
+    for (int a = 0; a < h->ndim; ++a) {
+        fft_axis_tables(h->cfg.n[a], h->cfg.dx[a], host.data() + off[a], dev_tab + off[a],
+                        &P.ax[a]);
+        P.ax[a].inner = inner;
+        inner *= h->cfg.n[a];
+    }
+    fft_twiddles(P.log2M, host.data() + total);
+    P.tw = reinterpret_cast<const float2 *>(dev_tab + total);
+    CU(h, cudaMemcpyAsync(dev_tab, host.data(), host.size() * sizeof(float),
+                          cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    TRY(alloc_n(h, &P.Z, (size_t)h->cells));
+    h->use_fft = true;
+    return AP_PIC_OK;
+}
+
 static ap_pic_status create_grid(ap_pic *h)
 {
     if (h->plain) return create_grid_f64(h);
@@ -450,6 +511,7 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
     CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
     CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+    if (h->cfg.solver == AP_PIC_SOLVER_FFT) TRY(create_fft(h));
     return create_pinned(h);
 }
 
@@ -689,9 +751,28 @@ static ap_pic_status solve_field_f64(ap_pic *h)
 // A x = r, phi += x.  The refinement removes the smooth-mode error that the FP32
 // recursion cannot see.  (The true residual itself cannot serve as the stopping
 // test: the rounding of an FP32 potential, amplified by the Laplacian, floors it.)
+static ap_pic_status solve_field_fft(ap_pic *h)
+{
+    const double mean_total = h->cfg.q * h->cfg.weight * (double)h->np / h->V + bg_density(h);
+    FieldBufs &f = h->f;
+    const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
+    CU(h, launch_fft_poisson(h->fft, f.b, f.phi, h->stream));
+    // refinement pass: the FP64 residual of the FP32 solve, solved again and added
+    CU(h, launch_residual64(f, mean_total, h->stream));
+    CU(h, launch_fft_poisson(h->fft, f.b, f.x, h->stream));
+    CU(h, launch_add_correction(f, h->stream));
+    CU(h, launch_efield(f, h->stream));
+    stage_end(h, mk);
+    h->last_cg_iters = 0;
+    h->relres_on_device = true;  // the first solve's true residual, read with the diagnostics
+    return AP_PIC_OK;
+}
+
 static ap_pic_status solve_field(ap_pic *h)
 {
     if (h->plain) return solve_field_f64(h);
+    if (h->use_fft) return solve_field_fft(h);
+    h->relres_on_device = false;
     constexpr double REFINE_RTOL = 1e-2;
     const double rtol = h->cfg.cg_rtol;
     const int maxit = h->cfg.cg_maxit;
@@ -1108,7 +1189,11 @@ extern "C" ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out)
     CU(h, cudaMemcpyAsync(h->h_accsum, h->d_accsum, sizeof(long long), cudaMemcpyDeviceToHost,
                           h->stream));
     CU(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->relres_on_device)
+        CU(h, cudaMemcpyAsync(h->h_diag + 7, h->f.scal + SCAL_TRUE_REL, sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
+    if (h->relres_on_device) h->last_cg_relres = h->h_diag[7];
     const double mw = h->cfg.m * h->cfg.weight;
     out->step = h->step;
     out->t = (double)h->step * h->cfg.dt;

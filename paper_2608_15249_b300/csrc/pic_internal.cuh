@@ -225,6 +225,36 @@ cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st);
 cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
 enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5 };
 cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
+
+// ---- spectral Poisson solve (pic_fft.cu) ------------------------------------------------------
+constexpr int FFT_MAX_N = 4096;  // longest axis (power-of-two or Bluestein length <= 8192)
+struct FftAxis {
+    int n;                 // nodes on the axis
+    int log2m;             // transform length m = 2^log2m in shared memory
+    int bluestein;         // 1: n is not a power of two (chirp-z form, m >= 2n - 1)
+    const float *lam;      // (2 sin(pi k / n) / dx)^2, k < n
+    const float2 *chirp;   // exp(-i pi j^2 / n), j < n
+    const float2 *bhat;    // length-m DFT of the chirp filter
+    int64_t inner;         // stride of the axis (product of the lower axes' n)
+};
+struct FftPlan {
+    int ndim;
+    int64_t cells;
+    FftAxis ax[3];
+    float2 *Z;             // complex work array [cells]
+    const float2 *tw;      // exp(-2 pi i t / M), t < M / 2
+    int log2M;             // M: the longest transform length
+    int sms;
+};
+bool fft_length_ok(int n);
+int fft_log2m(int n);  // log2 of the transform length of an axis of n nodes
+size_t fft_axis_table_floats(int n);
+void fft_axis_tables(int n, double dx, float *host, float *dev, FftAxis *ax);
+size_t fft_twiddle_floats(int log2M);
+void fft_twiddles(int log2M, float *host);
+cudaError_t fft_configure();
+// phi = the zero-mean solution of -lap_h phi = b (b's mean is ignored).
+cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st);
 // Finalise diagnostics: reduce particle partials, accumulator sum, field energy
 // into out[0..7] = {kinetic, px, py, pz, field_energy, acc_sum (as bits), -, -}.
 cudaError_t launch_diag_finalize(const DiagPartials &pd, bool have_particles, FieldBufs &f,

@@ -70,3 +70,39 @@ def test_config_defaults_and_validation(libpath):
     h = ctypes.c_void_p()
     assert pk.lib().ap_pic_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == -2
     pk.lib().ap_pic_destroy(h)
+    # the solver: unknown values are rejected; the spectral solve needs the FP32 form
+    # and every axis within its longest transform
+    for bad, want in ((dict(solver=7), -1),
+                      (dict(solver=pk.AP_PIC_SOLVER_FFT, precision=pk.AP_PIC_FP64_PLAIN), -2),
+                      (dict(solver=pk.AP_PIC_SOLVER_FFT, n=(pk.AP_PIC_FFT_MAX_N + 1,)), -2)):
+        kw = dict(ndim=1, n=(8,))
+        kw.update(bad)
+        cfg = pk.make_config(**kw)
+        h = ctypes.c_void_p()
+        assert pk.lib().ap_pic_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == want
+        pk.lib().ap_pic_destroy(h)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the C compiler's size and field offsets."""
+    import paper_2608_15249_b300 as pk
+    structs = {"ap_pic_config": pk.ap_pic_config, "ap_pic_diag": pk.ap_pic_diag,
+               "ap_pic_batch_tuning": pk.ap_pic_batch_tuning,
+               "ap_pic_allocator": pk.ap_pic_allocator}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ap_pic.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                        text=True, check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
