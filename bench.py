@@ -370,7 +370,8 @@ def bench_batch(args):
     total = sum(w.np_ for w in ws)
     nodes = sum(w.cells for w in ws)
     stream = torch.cuda.current_stream()
-    bt = pk.batch_from_workloads(ws, stream=stream.cuda_stream)
+    bt = pk.batch_from_workloads(ws, stream=stream.cuda_stream,
+                                 solver=_SOLVERS[args.batch_solver])
     t0 = time.perf_counter()
     bt.load([w.x for w in ws], [w.v for w in ws])
     torch.cuda.synchronize()
@@ -416,7 +417,7 @@ def bench_batch(args):
         bt.solve_field()
     e1.record(stream)
     torch.cuda.synchronize()
-    solve_ms = e0.elapsed_time(e1) / args.solve_reps
+    solve_ms = {args.batch_solver: e0.elapsed_time(e1) / args.solve_reps}
     e0.record(stream)
     bt.step(args.full_steps)
     e1.record(stream)
@@ -424,6 +425,20 @@ def bench_batch(args):
     full_ms = e0.elapsed_time(e1) / args.full_steps
     iters = [bt.get_diag(i)["cg_iters"] for i in range(len(ws))]
     bt.close()
+    if args.batch_solver != "cg" and args.cg_solve_reps > 0:
+        # the lockstep Jacobi-PCG of the same batch, for comparison
+        bc = pk.batch_from_workloads(ws, stream=stream.cuda_stream)
+        bc.load([w.x for w in ws], [w.v for w in ws])
+        for _ in range(3):
+            bc.push_deposit()
+        e0.record(stream)
+        for _ in range(args.cg_solve_reps):
+            bc.solve_field()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solve_ms["cg"] = e0.elapsed_time(e1) / args.cg_solve_reps
+        iters = [bc.get_diag(i)["cg_iters"] for i in range(len(ws))]
+        bc.close()
     # the same metric instance by instance, on every k-th instance
     sample = ws[:: args.plain_stride]
     f64_rate = _per_instance_rate(pk, torch, stream, sample, args.plain_steps,
@@ -437,7 +452,7 @@ def bench_batch(args):
         "config": {"workload": f"batch of {len(ws)} periodic 1D/2D instances, "
                                f"{total} electrons, {nodes} nodes, sort every {sort_every}",
                    "instances": len(ws), "particles": total, "nodes": nodes,
-                   "tuning": tuning, "load_seconds": load_s,
+                   "tuning": tuning, "solver": args.batch_solver, "load_seconds": load_s,
                    "l2": "particle state larger than L2 (no flush)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -448,7 +463,8 @@ def bench_batch(args):
         "field_solve_ms": solve_ms,
         "full_step_ms": full_ms,
         "full_step_particle_steps_per_s": total / (full_ms * 1e-3),
-        "cg_iters_last_solve": {"max": max(iters), "median": statistics.median(iters)},
+        "cg_iters_last_solve": {"max": max(iters), "median": statistics.median(iters),
+                                "what": "the CG refinement's correction solve"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "per_instance": {
@@ -486,6 +502,9 @@ def main():
     ap.add_argument("--solve-reps", type=int, default=3, help="--workload batch")
     ap.add_argument("--full-steps", type=int, default=3, help="--workload batch")
     ap.add_argument("--no-autotune", action="store_true", help="--workload batch")
+    ap.add_argument("--batch-solver", choices=["cg", "fft"], default="fft",
+                    help="--workload batch")
+    ap.add_argument("--cg-solve-reps", type=int, default=1, help="--workload batch")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

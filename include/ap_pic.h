@@ -281,11 +281,13 @@ int64_t ap_pic_kernel_launches(void);
  * and particle counts (each 1D or 2D, nv = 2, B0 = 0, FP32 cell + offset form)
  * share one particle arena and one set of grid arenas.  Each step runs one
  * persistent particle pass per dimension class over the tiles of every
- * instance, the charge conversion, and the field solve of every instance in
- * lockstep (same Jacobi-PCG and refinement as a single instance; an instance
- * that has converged skips its work); the front of the step (particle pass to
- * the first block of CG iterations) is captured once as a CUDA graph and
- * replayed.  Instance i of a batch computes what a single instance with cfgs[i]
+ * instance, the charge conversion, and the field solve of every instance:
+ * with cfgs[0].solver = AP_PIC_SOLVER_CG in lockstep (same Jacobi-PCG and
+ * refinement as a single instance; an instance that has converged drops out),
+ * with AP_PIC_SOLVER_FFT the spectral solve of every instance in three passes.
+ * The front of the step (particle pass to the first block of CG iterations, or
+ * the whole field update with the spectral solve) is captured once as a CUDA
+ * graph and replayed.  Instance i of a batch computes what a single instance with cfgs[i]
  * computes, within the single instance's tolerance. */
 typedef struct ap_pic_batch ap_pic_batch;
 
@@ -301,7 +303,7 @@ typedef struct {
 void ap_pic_batch_default_tuning(ap_pic_batch_tuning *t);
 
 /* cfgs: `count` configurations (validated as for ap_pic_create, plus the batch
- * limits above; cg_rtol and cg_maxit are taken from cfgs[0]).  Allocates no
+ * limits above; solver, cg_rtol and cg_maxit are taken from cfgs[0]).  Allocates no
  * device memory yet (that happens at ap_pic_batch_load).  The batch enqueues its
  * work on a stream of its own, ordered after `cuda_stream` on entry to each call
  * and making `cuda_stream` wait for it on exit. */

@@ -13,12 +13,14 @@
 //     is deterministic.
 // The field solve is the same Jacobi-preconditioned CG as the single instance
 // (FP32 vectors, FP64 dots, null-space projection, breakdown guard), run for
-// all instances in lockstep; an instance that has converged skips its work.
+// all instances in lockstep (an instance that has converged drops out of the
+// launches), or the spectral solve of every instance in three passes of jobs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -603,6 +605,18 @@ struct ap_pic_batch {
     int64_t graph_launches = 0;  // kernels per replay (for the launch counter)
 
     int last_iters_max = 0;
+
+    // spectral field solve (cfgs[0].solver == AP_PIC_SOLVER_FFT): three passes of
+    // jobs (x forward of 2D grids and the whole 1D solves; y forward, scale and
+    // inverse; x inverse), tables shared by instances of equal (n, dx)
+    bool use_fft = false;
+    FftGrid *d_fft_grids = nullptr;
+    FftJob *d_fft_jobs[3] = {nullptr, nullptr, nullptr};
+    int fft_njobs[3] = {0, 0, 0};
+    size_t fft_smem[3] = {0, 0, 0};
+    float2 *fft_Z = nullptr;
+    const float2 *fft_tw = nullptr;
+    int fft_log2M = 1;
 };
 
 namespace {
@@ -699,6 +713,93 @@ ap_pic_status upload_tile_params(ap_pic_batch *b, double factor)
     return AP_PIC_OK;
 }
 
+// Tables and job lists of the spectral solve (grids already placed in the arenas).
+ap_pic_status setup_fft(ap_pic_batch *b)
+{
+    static bool configured = false;
+    if (!configured) {
+        BCU(b, fft_configure());
+        configured = true;
+    }
+    const int n = b->count;
+    using Key = std::pair<int, double>;
+    std::map<Key, size_t> at;  // float offset of the tables of an (n, dx) axis
+    size_t total = 0;
+    int log2M = 1;
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < b->cfg[i].ndim; ++a) {
+            const Key key(b->cfg[i].n[a], b->cfg[i].dx[a]);
+            if (at.count(key)) continue;
+            at[key] = total;
+            total += fft_axis_table_floats(key.first);
+            const int l = fft_log2m(key.first);
+            log2M = l > log2M ? l : log2M;
+        }
+    std::vector<float> host(total + fft_twiddle_floats(log2M), 0.0f);
+    float *dev = nullptr;
+    BTRY(balloc(b, &dev, host.size()));
+    std::map<Key, FftAxis> axes;
+    for (const auto &kv : at) {
+        FftAxis ax{};
+        fft_axis_tables(kv.first.first, kv.first.second, host.data() + kv.second,
+                        dev + kv.second, &ax);
+        axes[kv.first] = ax;
+    }
+    fft_twiddles(log2M, host.data() + total);
+    b->fft_tw = reinterpret_cast<const float2 *>(dev + total);
+    b->fft_log2M = log2M;
+    // one grid per instance; jobs of W lines (W * m <= 4096 elements of shared memory)
+    std::vector<FftGrid> grids((size_t)n);
+    std::vector<FftJob> jobs[3];
+    for (int k = 0; k < 3; ++k) b->fft_smem[k] = 0;
+    for (int i = 0; i < n; ++i) {
+        const ap_pic_config &c = b->cfg[i];
+        FftGrid &g = grids[(size_t)i];
+        g.node0 = b->node0[i];
+        g.ndim = c.ndim;
+        int64_t inner = 1;
+        for (int a = 0; a < c.ndim; ++a) {
+            g.ax[a] = axes[Key(c.n[a], c.dx[a])];
+            g.ax[a].inner = inner;
+            inner *= c.n[a];
+        }
+        g.div_n0 = make_fastdiv((uint32_t)c.n[0]);
+        g.inv_cells = (float)(1.0 / (double)b->cells[i]);
+        auto add = [&](int pass, int axis) {
+            const int64_t lines = b->cells[i] / c.n[axis];
+            const int log2m = g.ax[axis].log2m;
+            int W = 32;
+            while (W > 1 && (((int64_t)W << log2m) > 4096 || W / 2 >= lines)) W >>= 1;
+            for (int64_t l0 = 0; l0 < lines; l0 += W)
+                jobs[pass].push_back(
+                    FftJob{i, axis, l0, (int)(lines - l0 < W ? lines - l0 : W), W});
+            const size_t sm = fft_smem_bytes(W, log2m);
+            if (sm > b->fft_smem[pass]) b->fft_smem[pass] = sm;
+        };
+        add(0, 0);
+        if (c.ndim == 2) {
+            add(1, 1);
+            add(2, 0);
+        }
+    }
+    BTRY(balloc(b, &b->d_fft_grids, grids.size()));
+    BCU(b, cudaMemcpyAsync(b->d_fft_grids, grids.data(), grids.size() * sizeof(FftGrid),
+                           cudaMemcpyHostToDevice, b->stream));
+    for (int k = 0; k < 3; ++k) {
+        b->fft_njobs[k] = (int)jobs[k].size();
+        BTRY(balloc(b, &b->d_fft_jobs[k], jobs[k].size() + 1));
+        if (!jobs[k].empty())
+            BCU(b, cudaMemcpyAsync(b->d_fft_jobs[k], jobs[k].data(),
+                                   jobs[k].size() * sizeof(FftJob), cudaMemcpyHostToDevice,
+                                   b->stream));
+    }
+    BCU(b, cudaMemcpyAsync(dev, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           b->stream));
+    BTRY(balloc(b, &b->fft_Z, (size_t)(b->total_nodes > 0 ? b->total_nodes : 1)));
+    BCU(b, cudaStreamSynchronize(b->stream));  // the host tables go out of scope
+    return AP_PIC_OK;
+}
+
 }  // namespace
 
 extern "C" void ap_pic_batch_default_tuning(ap_pic_batch_tuning *t)
@@ -749,12 +850,19 @@ extern "C" ap_pic_status ap_pic_batch_create(int count, const ap_pic_config *cfg
             return bfail(b, AP_PIC_ERR_ARG, "bad dt, m or weight");
         if (c.fx_bits == 0) c.fx_bits = 22;
         if (c.fx_bits < 8 || c.fx_bits > 22) return bfail(b, AP_PIC_ERR_ARG, "fx_bits in [8, 22]");
+        if (b->cfg[0].solver == AP_PIC_SOLVER_FFT)
+            for (int a = 0; a < c.ndim; ++a)
+                if (!fft_length_ok(c.n[a]))
+                    return bfail(b, AP_PIC_ERR_UNSUPPORTED, "FFT solver needs n <= 4096");
         for (int a = 0; a < c.ndim; ++a) {
             if (c.brick[a] == 0) c.brick[a] = c.ndim == 1 ? 64 : 8;
             if (c.brick[a] > c.n[a]) c.brick[a] = c.n[a];
         }
         for (int a = c.ndim; a < 3; ++a) c.brick[a] = 1;
     }
+    if (b->cfg[0].solver != AP_PIC_SOLVER_CG && b->cfg[0].solver != AP_PIC_SOLVER_FFT)
+        return bfail(b, AP_PIC_ERR_ARG, "unknown solver");
+    b->use_fft = b->cfg[0].solver == AP_PIC_SOLVER_FFT;
     if (b->cfg[0].cg_rtol == 0.0) b->cfg[0].cg_rtol = 1e-6;
     if (b->cfg[0].cg_maxit == 0) b->cfg[0].cg_maxit = 20000;
     int dev = 0;
@@ -936,20 +1044,39 @@ ap_pic_status cg_finish(ap_pic_batch *b, float *x, int first, int maxit, double 
     return AP_PIC_OK;
 }
 
+ap_pic_status field_fft(ap_pic_batch *b);
+
 // The part of a step that does not depend on host decisions: particle pass,
-// charge conversion, start of the CG and its first block of iterations.
+// charge conversion, start of the CG and its first block of iterations (with the
+// spectral solve: the whole field update).
 ap_pic_status step_front(ap_pic_batch *b, bool diag)
 {
     BatchGrid &G = b->G;
     BCU(b, cudaMemsetAsync(G.A.acc, 0, (size_t)b->total_nodes * 8, b->stream));
     BTRY(batch_pass(b, true, true, true, diag));
     BTRY(batch_convert(b));
+    if (b->use_fft) return field_fft(b);
     cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
     cg_iters(b, G.A.phi, 0, b->tune.cg_iters_per_graph, b->cfg[0].cg_maxit, b->cfg[0].cg_rtol);
     return AP_PIC_OK;
 }
 
-// Finish the field: remaining CG blocks, one refinement pass, E, diagnostics.
+// E from the potential, and the per-instance diagnostics.
+ap_pic_status field_finish(ap_pic_batch *b)
+{
+    BatchGrid &G = b->G;
+    const int nb = grid_blocks(b);
+    k_b_efield<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, G.fepart);
+    k_b_isum<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.A, G.ipart_ll);
+    const int nbi = b->count < b->sms * 4 ? b->count : b->sms * 4;
+    k_b_diag<<<nbi, BT, 0, b->stream>>>(G.inst, G.ninst, b->d_tdiag1, b->d_tdiag2, G.fepart,
+                                        G.ipart_ll, b->d_diag, b->d_isum, 1);
+    note_launch(3);
+    BCU(b, cudaGetLastError());
+    return AP_PIC_OK;
+}
+
+// Finish the CG field: remaining CG blocks, one refinement pass, E, diagnostics.
 ap_pic_status step_back(ap_pic_batch *b, int first_iter)
 {
     BatchGrid &G = b->G;
@@ -965,14 +1092,40 @@ ap_pic_status step_back(ap_pic_batch *b, int first_iter)
     cg_iters(b, G.A.x, 0, 8, maxit, 1e-2);
     BTRY(cg_finish(b, G.A.x, 8, maxit, 1e-2));
     k_b_add_correction<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.A);
-    k_b_efield<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, G.fepart);
-    k_b_isum<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.A, G.ipart_ll);
-    const int nbi = b->count < b->sms * 4 ? b->count : b->sms * 4;
-    k_b_diag<<<nbi, BT, 0, b->stream>>>(G.inst, G.ninst, b->d_tdiag1, b->d_tdiag2, G.fepart,
-                                        G.ipart_ll, b->d_diag, b->d_isum, 1);
-    note_launch(4);
-    BCU(b, cudaGetLastError());
+    note_launch();
+    return field_finish(b);
+}
+
+// The spectral solve of every instance: x forward of the 2D grids (and the whole
+// solve of the 1D ones), y forward / scale / inverse, x inverse.
+ap_pic_status fft_solve(ap_pic_batch *b, const float *rhs, float *out)
+{
+    const int blocks = b->sms * 4;
+    BCU(b, launch_fft_jobs(b->d_fft_jobs[0], b->fft_njobs[0], b->d_fft_grids, b->fft_Z, rhs,
+                           nullptr, out, b->fft_tw, b->fft_log2M, FFT_FWD, b->fft_smem[0], blocks,
+                           b->stream));
+    BCU(b, launch_fft_jobs(b->d_fft_jobs[1], b->fft_njobs[1], b->d_fft_grids, b->fft_Z, nullptr,
+                           nullptr, nullptr, b->fft_tw, b->fft_log2M, FFT_FWD_SCALE_INV,
+                           b->fft_smem[1], blocks, b->stream));
+    BCU(b, launch_fft_jobs(b->d_fft_jobs[2], b->fft_njobs[2], b->d_fft_grids, b->fft_Z, nullptr,
+                           out, nullptr, b->fft_tw, b->fft_log2M, FFT_INV, b->fft_smem[2], blocks,
+                           b->stream));
     return AP_PIC_OK;
+}
+
+// The spectral field of every instance: solve, the FP64-residual refinement
+// (residual, solve, add), E and diagnostics.  No host decision, so it can be captured.
+ap_pic_status field_fft(ap_pic_batch *b)
+{
+    BatchGrid &G = b->G;
+    const int nb = grid_blocks(b);
+    BTRY(fft_solve(b, G.A.b, G.A.phi));
+    k_b_residual64<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A);
+    note_launch();
+    BTRY(fft_solve(b, G.A.b, G.A.x));
+    k_b_add_correction<<<nb, BT, 0, b->stream>>>(G.items, G.nitems, G.A);
+    note_launch();
+    return field_finish(b);
 }
 
 ap_pic_status batch_sort(ap_pic_batch *b)
@@ -1164,6 +1317,10 @@ extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
     BTRY(balloc(b, &G.cg.scal, (size_t)n * 8));
     BTRY(balloc(b, &G.cg.done, (size_t)n));
     BTRY(balloc(b, &G.cg.iters, (size_t)n));
+    BCU(b, cudaMemsetAsync(G.cg.scal, 0, (size_t)n * 64, b->stream));
+    BCU(b, cudaMemsetAsync(G.cg.done, 0, (size_t)n * 4, b->stream));
+    BCU(b, cudaMemsetAsync(G.cg.iters, 0, (size_t)n * 4, b->stream));
+    if (b->use_fft) BTRY(setup_fft(b));
     BTRY(balloc(b, &b->d_act, (size_t)G.nitems + 1));
     if (b->h_act) cudaFreeHost(b->h_act);
     b->h_act = nullptr;
@@ -1210,8 +1367,12 @@ extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
     BCU(b, cudaMemsetAsync(G.A.acc, 0, nn * 8, b->stream));
     BTRY(batch_pass(b, false, false, true, false));
     BTRY(batch_convert(b));
-    cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
-    BTRY(step_back(b, 0));
+    if (b->use_fft) {
+        BTRY(field_fft(b));
+    } else {
+        cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
+        BTRY(step_back(b, 0));
+    }
     if (!(flags & AP_PIC_LOAD_NO_HALFPUSH)) {
         BTRY(upload_tile_params(b, -0.5));
         BTRY(batch_pass(b, true, false, false, false));
@@ -1275,7 +1436,7 @@ extern "C" ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps)
             BTRY(step_front(b, true));
         }
         if (b->tune.sort_every > 0 && k % b->tune.sort_every == 0) BTRY(batch_sort(b));
-        BTRY(step_back(b, b->tune.cg_iters_per_graph));
+        if (!b->use_fft) BTRY(step_back(b, b->tune.cg_iters_per_graph));
         b->step = k;
     }
     return leave(b);
@@ -1306,6 +1467,10 @@ extern "C" ap_pic_status ap_pic_batch_solve_field(ap_pic_batch *b)
     BTRY(need_loaded(b, 0));
     BTRY(enter(b));
     BatchGrid &G = b->G;
+    if (b->use_fft) {
+        BTRY(field_fft(b));
+        return leave(b);
+    }
     const int first = b->tune.cg_iters_per_graph;
     cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
     cg_iters(b, G.A.phi, 0, first, b->cfg[0].cg_maxit, b->cfg[0].cg_rtol);

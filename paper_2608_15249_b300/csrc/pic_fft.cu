@@ -94,40 +94,53 @@ __device__ void dif(float2 *buf, int W, int log2m, const float2 *tws, bool inver
     }
 }
 
-enum : int { FFT_FWD = 0, FFT_INV = 1, FFT_FWD_SCALE_INV = 2 };
-
-// One axis of the transform.  Lines l in [0, inner * outer): inner index i = l % inner,
-// outer index o = l / inner, element j at o * n * inner + i + j * inner.
-struct AxisArgs {
-    FftAxis ax;
-    const float2 *tw;    // exp(-2 pi i t / M), t < M / 2
-    int log2M;
-    int W;               // lines per CTA (power of two)
-    int64_t lines;
-    int mode;
+// W lines along one axis of one grid.  Lines l in [0, inner * outer): inner index
+// i = l % inner, outer index o = l / inner, element j at o * n * inner + i + j * inner
+// (relative to the grid's first node).
+struct LineJob {
+    float2 *Z;             // the grid's complex work array
     const float *in_real;  // non-null: the input is this real array (first forward pass)
-    float *out_real;       // non-null: write Re * 1 into this array (last inverse pass)
-    // scaling of the last axis: eigenvalues of the lower axes and their sizes
+    float *out_real;       // non-null: write the real part here (last inverse pass)
+    FftAxis ax;
+    int64_t l0;            // first line
+    int nl;                // lines of this job (<= W)
+    int W;                 // lines per job (power of two, <= 32): shared-memory layout
+    int mode;
+    // scaling of the last axis: eigenvalues of the lower axes
     const float *lam0, *lam1;
-    FastDiv div_n0;        // coordinates of the inner index (3D: i = k0 + n0 k1)
+    FastDiv div_n0;        // 3D: inner index i = k0 + n0 k1
     float inv_cells;
 };
 
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z, AxisArgs A)
+// 1 / (N K^2) for element k of the last axis of a line whose inner index is i.
+__device__ __forceinline__ float spectral_scale(const LineJob &J, int k, int i)
 {
-    extern __shared__ __align__(16) float2 fsm[];
-    __shared__ int64_t s_base[32];  // first element of each of the CTA's lines
+    float K2 = J.ax.lam[k];
+    if (J.lam0) {
+        uint32_t k0 = (uint32_t)i;
+        if (J.lam1) {
+            const uint32_t k1 = fdiv((uint32_t)i, J.div_n0);
+            k0 = (uint32_t)i - k1 * (uint32_t)J.div_n0.d;
+            K2 += J.lam1[k1];
+        }
+        K2 += J.lam0[k0];
+    }
+    return K2 > 0.0f ? J.inv_cells / K2 : 0.0f;
+}
+
+// The transform of one job by the whole CTA (fsm: W * m + m / 2 complex).
+__device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int log2M, float2 *fsm)
+{
+    __shared__ int64_t s_base[32];  // first element of each of the job's lines
     __shared__ int s_inner[32];     // its inner index (the coordinates of the lower axes)
-    const FftAxis &ax = A.ax;
-    const int n = ax.n, log2m = ax.log2m, m = 1 << log2m, W = A.W;
+    const FftAxis &ax = J.ax;
+    const int n = ax.n, log2m = ax.log2m, m = 1 << log2m, W = J.W, nl = J.nl;
     float2 *buf = fsm;
     float2 *tws = fsm + ((size_t)W << log2m);
-    for (int t = threadIdx.x; t < m / 2; t += blockDim.x) tws[t] = A.tw[(size_t)t << (A.log2M - log2m)];
-    const int64_t l0 = (int64_t)blockIdx.x * W;
-    const int nl = (int)((A.lines - l0) < W ? (A.lines - l0) : W);
+    for (int t = threadIdx.x; t < m / 2; t += blockDim.x) tws[t] = tw[(size_t)t << (log2M - log2m)];
     const int64_t inner = ax.inner;
     if (threadIdx.x < nl) {
-        const int64_t l = l0 + threadIdx.x;
+        const int64_t l = J.l0 + threadIdx.x;
         const int64_t o = l / inner, i = l - o * inner;
         s_base[threadIdx.x] = o * (int64_t)n * inner + i;
         s_inner[threadIdx.x] = (int)i;
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
         }
     };
     const bool blue = ax.bluestein != 0;
-    const bool inv_in = A.mode == FFT_INV;
+    const bool inv_in = J.mode == FFT_INV;
     // ---- load (scattered to bit-reversed positions, for the DIT) ----------------------------
     if (blue) {
         // zero the padding of Bluestein lines
@@ -159,7 +172,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
         coords(e, &t, &j);
         if (t >= nl) continue;
         const int64_t a = addr(t, j);
-        float2 x = A.in_real ? make_float2(A.in_real[a], 0.0f) : Z[a];
+        float2 x = J.in_real ? make_float2(J.in_real[a], 0.0f) : J.Z[a];
         if (blue) {
             if (inv_in) x = cconj(x);
             x = cmul(x, ax.chirp[j]);
@@ -173,8 +186,6 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
     __syncthreads();
 
     // ---- transform -----------------------------------------------------------------------------
-    // After this block, line t holds its result at position pos(j) (natural or
-    // bit-reversed), with a per-element factor applied on the way out.
     const float inv_m = 1.0f / (float)m;
     if (blue) {
         // forward DFT via the chirp-z convolution (an inverse is the conjugate of the
@@ -184,8 +195,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
             buf[e] = cmul(buf[e], ax.bhat[e & (m - 1)]);
         __syncthreads();
         dif(buf, W, log2m, tws, true);  // conv * m, bit-reversed
-        if (A.mode == FFT_FWD_SCALE_INV) {
-            // X_k = w_k c_k / m; Y_k = s_k X_k; then the inverse input conj(Y_k) w_k in place
+        if (J.mode == FFT_FWD_SCALE_INV) {
+            // X_k = w_k c_k / m and Y_k = s_k X_k, then the inverse's input conj(Y_k) w_k,
+            // all at position brev(k) of the line, which only this thread touches
             for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
                 const int t = e >> log2m, p = e & (m - 1);
                 const int k = brev(p, log2m);
@@ -193,28 +205,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
                 if (k < n) {
                     const float2 w = ax.chirp[k];
                     float2 X = cmul(w, buf[e]);
-                    X.x *= inv_m;
-                    X.y *= inv_m;
-                    // element (t, k): its coordinates in the lower axes come from the line
-                    const int i = s_inner[t < nl ? t : 0];
-                    float K2 = ax.lam[k];
-                    if (A.lam0) {
-                        uint32_t k1 = 0, k0 = (uint32_t)i;
-                        if (A.lam1) {
-                            k1 = fdiv((uint32_t)i, A.div_n0);
-                            k0 = (uint32_t)i - k1 * (uint32_t)A.div_n0.d;
-                            K2 += A.lam1[k1];
-                        }
-                        K2 += A.lam0[k0];
-                    }
-                    const float s = K2 > 0.0f ? A.inv_cells / K2 : 0.0f;
+                    const float s = inv_m * spectral_scale(J, k, s_inner[t < nl ? t : 0]);
                     X.x *= s;
                     X.y *= s;
                     v = cmul(cconj(X), w);
                 }
-                // position p of line t was read only by this thread; write it back
-                buf[e] = make_float2(0.f, 0.f);
-                if (k < n) buf[((size_t)t << log2m) + brev(k, log2m)] = v;
+                buf[e] = v;
             }
             __syncthreads();
             dit(buf, W, log2m, tws, false);
@@ -224,25 +220,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
             dif(buf, W, log2m, tws, true);
         }
     } else {
-        if (A.mode == FFT_INV) {
+        if (J.mode == FFT_INV) {
             dif(buf, W, log2m, tws, true);  // bit-reversed result
         } else {
             dit(buf, W, log2m, tws, false);  // natural-order spectrum
-            if (A.mode == FFT_FWD_SCALE_INV) {
+            if (J.mode == FFT_FWD_SCALE_INV) {
                 for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
                     const int t = e >> log2m, k = e & (m - 1);
-                    const int i = s_inner[t < nl ? t : 0];
-                    float K2 = ax.lam[k];
-                    if (A.lam0) {
-                        uint32_t k1 = 0, k0 = (uint32_t)i;
-                        if (A.lam1) {
-                            k1 = fdiv((uint32_t)i, A.div_n0);
-                            k0 = (uint32_t)i - k1 * (uint32_t)A.div_n0.d;
-                            K2 += A.lam1[k1];
-                        }
-                        K2 += A.lam0[k0];
-                    }
-                    const float s = K2 > 0.0f ? A.inv_cells / K2 : 0.0f;
+                    const float s = spectral_scale(J, k, s_inner[t < nl ? t : 0]);
                     buf[e].x *= s;
                     buf[e].y *= s;
                 }
@@ -254,8 +239,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
 
     // ---- store ---------------------------------------------------------------------------------
     // natural order after a forward power-of-two pass; bit-reversed after a DIF
-    const bool rev_out = blue || A.mode != FFT_FWD;
-    const bool conj_out = blue && A.mode != FFT_FWD;
+    const bool rev_out = blue || J.mode != FFT_FWD;
+    const bool conj_out = blue && J.mode != FFT_FWD;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int t, j;
         coords(e, &t, &j);
@@ -269,8 +254,47 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(float2 *__restrict__ Z
             if (conj_out) v = cconj(v);
         }
         const int64_t a = addr(t, j);
-        if (A.out_real) A.out_real[a] = v.x;
-        else Z[a] = v;
+        if (J.out_real) J.out_real[a] = v.x;
+        else J.Z[a] = v;
+    }
+    __syncthreads();  // the shared buffers are reused by the CTA's next job
+}
+
+// One axis of one grid: CTA b takes lines [b W, b W + W).
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_axis(LineJob J, const float2 *__restrict__ tw,
+                                                        int log2M, int64_t lines)
+{
+    extern __shared__ __align__(16) float2 fsm[];
+    J.l0 = (int64_t)blockIdx.x * J.W;
+    J.nl = (int)((lines - J.l0) < J.W ? (lines - J.l0) : J.W);
+    fft_lines(J, tw, log2M, fsm);
+}
+
+// Many grids (a batch): CTAs walk a list of jobs, each W lines of one grid's axis.
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_jobs(const FftJob *__restrict__ jobs, int njobs, const FftGrid *__restrict__ grids,
+               float2 *Z, const float *in_real, float *out_real, float *out_1d,
+               const float2 *__restrict__ tw, int log2M, int mode)
+{
+    extern __shared__ __align__(16) float2 fsm[];
+    for (int q = blockIdx.x; q < njobs; q += gridDim.x) {
+        const FftJob jb = jobs[q];
+        const FftGrid &G = grids[jb.grid];
+        LineJob J;
+        J.Z = Z + G.node0;
+        J.in_real = in_real ? in_real + G.node0 : nullptr;
+        float *out = G.ndim == 1 ? out_1d : out_real;
+        J.out_real = out ? out + G.node0 : nullptr;
+        J.ax = G.ax[jb.axis];
+        J.l0 = jb.l0;
+        J.nl = jb.nl;
+        J.W = jb.W;
+        J.mode = (G.ndim == 1) ? FFT_FWD_SCALE_INV : mode;
+        J.lam0 = jb.axis >= 1 ? G.ax[0].lam : nullptr;
+        J.lam1 = nullptr;
+        J.div_n0 = G.div_n0;
+        J.inv_cells = G.inv_cells;
+        fft_lines(J, tw, log2M, fsm);
     }
 }
 
@@ -373,16 +397,16 @@ void fft_twiddles(int log2M, float *host)
     }
 }
 
-// Lines per CTA: enough CTAs to fill the GPU twice when the axis allows, at most
-// 32 lines and 8192 elements of shared memory.
-static int lines_per_cta(int64_t lines, int log2m, int sms)
+// Lines per job: enough jobs to fill the GPU twice when the axis allows, at most
+// 32 lines and `cap` elements of shared memory.
+int lines_per_cta(int64_t lines, int log2m, int sms, int cap)
 {
     int W = 32;
-    while (W > 1 && (((int64_t)W << log2m) > 8192 || lines / W < 2 * (int64_t)sms)) W >>= 1;
+    while (W > 1 && (((int64_t)W << log2m) > cap || lines / W < 2 * (int64_t)sms)) W >>= 1;
     return W;
 }
 
-static size_t axis_smem(int W, int log2m)
+size_t fft_smem_bytes(int W, int log2m)
 {
     return (((size_t)W << log2m) + ((size_t)1 << (log2m - 1))) * sizeof(float2);
 }
@@ -390,29 +414,32 @@ static size_t axis_smem(int W, int log2m)
 cudaError_t fft_configure()
 {
     // W * m <= 8192 elements plus m / 2 twiddles
-    return cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((8192 + 4096) * sizeof(float2)));
+    const int most = (int)((8192 + 4096) * sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         most);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fft_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st)
 {
     const int d = P.ndim;
     auto run = [&](int a, int mode, const float *in, float *out) -> cudaError_t {
-        AxisArgs A{};
-        A.ax = P.ax[a];
-        A.tw = P.tw;
-        A.log2M = P.log2M;
-        A.lines = P.cells / A.ax.n;
-        A.W = lines_per_cta(A.lines, A.ax.log2m, P.sms);
-        A.mode = mode;
-        A.in_real = in;
-        A.out_real = out;
-        A.lam0 = a >= 1 ? P.ax[0].lam : nullptr;
-        A.lam1 = a >= 2 ? P.ax[1].lam : nullptr;
-        A.div_n0 = make_fastdiv((uint32_t)P.ax[0].n);
-        A.inv_cells = (float)(1.0 / (double)P.cells);
-        const int64_t grid = (A.lines + A.W - 1) / A.W;
-        k_fft_axis<<<(unsigned)grid, FFT_THREADS, axis_smem(A.W, A.ax.log2m), st>>>(P.Z, A);
+        LineJob J{};
+        J.Z = P.Z;
+        J.in_real = in;
+        J.out_real = out;
+        J.ax = P.ax[a];
+        const int64_t lines = P.cells / J.ax.n;
+        J.W = lines_per_cta(lines, J.ax.log2m, P.sms, 8192);
+        J.mode = mode;
+        J.lam0 = a >= 1 ? P.ax[0].lam : nullptr;
+        J.lam1 = a >= 2 ? P.ax[1].lam : nullptr;
+        J.div_n0 = make_fastdiv((uint32_t)P.ax[0].n);
+        J.inv_cells = (float)(1.0 / (double)P.cells);
+        const int64_t grid = (lines + J.W - 1) / J.W;
+        k_fft_axis<<<(unsigned)grid, FFT_THREADS, fft_smem_bytes(J.W, J.ax.log2m), st>>>(
+            J, P.tw, P.log2M, lines);
         note_launch();
         return cudaGetLastError();
     };
@@ -425,6 +452,18 @@ cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cud
     for (int a = d - 2; a >= 1; --a)
         if ((e = run(a, FFT_INV, nullptr, nullptr)) != cudaSuccess) return e;
     return run(0, FFT_INV, nullptr, phi);
+}
+
+cudaError_t launch_fft_jobs(const FftJob *jobs, int njobs, const FftGrid *grids, float2 *Z,
+                            const float *in_real, float *out_real, float *out_1d,
+                            const float2 *tw, int log2M, int mode, size_t smem, int blocks,
+                            cudaStream_t st)
+{
+    if (njobs == 0) return cudaSuccess;
+    k_fft_jobs<<<blocks < njobs ? blocks : njobs, FFT_THREADS, smem, st>>>(
+        jobs, njobs, grids, Z, in_real, out_real, out_1d, tw, log2M, mode);
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace apk

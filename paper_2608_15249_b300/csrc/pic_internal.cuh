@@ -246,6 +246,29 @@ struct FftPlan {
     int log2M;             // M: the longest transform length
     int sms;
 };
+enum : int { FFT_FWD = 0, FFT_INV = 1, FFT_FWD_SCALE_INV = 2 };
+// A grid of a batch for the spectral solve, and a job: W lines of one of its axes.
+struct FftGrid {
+    int64_t node0;         // first node in the batch's grid arenas
+    int ndim;
+    FftAxis ax[2];
+    FastDiv div_n0;
+    float inv_cells;
+};
+struct FftJob {
+    int grid, axis;
+    int64_t l0;
+    int nl, W;
+};
+int lines_per_cta(int64_t lines, int log2m, int sms, int cap);
+size_t fft_smem_bytes(int W, int log2m);
+// Runs `jobs` (one pass of a batch's transform: every job in the same mode, except
+// that 1D grids always take the fused forward / scale / inverse form and write their
+// real result to out_1d).
+cudaError_t launch_fft_jobs(const FftJob *jobs, int njobs, const FftGrid *grids, float2 *Z,
+                            const float *in_real, float *out_real, float *out_1d,
+                            const float2 *tw, int log2M, int mode, size_t smem, int blocks,
+                            cudaStream_t st);
 bool fft_length_ok(int n);
 int fft_log2m(int n);  // log2 of the transform length of an axis of n nodes
 size_t fft_axis_table_floats(int n);

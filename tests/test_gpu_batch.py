@@ -63,10 +63,10 @@ def test_batch_load_matches_oracle(pk):
     bt.close()
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_batch_steps_match_oracle(pk, use_graph):
+@pytest.mark.parametrize("use_graph,solver", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_batch_steps_match_oracle(pk, use_graph, solver):
     ws = instances()
-    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7)
+    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7, solver=solver)
     bt.set_tuning(use_graph=use_graph, sort_every=2)
     bt.load([w.x for w in ws], [w.v for w in ws])
     sims = [_oracle(w).load(w.x, w.v) for w in ws]
@@ -93,11 +93,12 @@ def test_batch_steps_match_oracle(pk, use_graph):
     bt.close()
 
 
-def test_batch_graph_replay_equals_direct_launches(pk):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_batch_graph_replay_equals_direct_launches(pk, solver):
     ws = instances()[:4]
     out = []
     for use_graph in (1, 0):
-        bt = pk.batch_from_workloads(ws)
+        bt = pk.batch_from_workloads(ws, solver=solver)
         bt.set_tuning(use_graph=use_graph)
         bt.load([w.x for w in ws], [w.v for w in ws])
         bt.step(5)
@@ -129,7 +130,8 @@ def test_batch_autotune_and_cache(pk, tmp_path):
     bt.close()
 
 
-def test_batch_many_instances_many_items(pk):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_batch_many_instances_many_items(pk, solver):
     """Many instances split into many small cell items, converging at different CG
     iterations while their blocks share launches: every instance stays finite with
     exact charge, and a sample matches the oracle after a few steps."""
@@ -144,7 +146,7 @@ def test_batch_many_instances_many_items(pk):
             ppc = [0.05, 1, 3][i % 3]
             ws.append(plasma.sparse_box(2, n, max(64, int(ppc * n[0] * n[1])), nv=2,
                                         seed=100 + i))
-    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7)
+    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7, solver=solver)
     bt.set_tuning(item_cells=256, sort_every=2, cg_iters_per_graph=8)
     bt.load([w.x for w in ws], [w.v for w in ws])
     check = list(range(0, len(ws), 7))
@@ -172,12 +174,13 @@ def test_batch_many_instances_many_items(pk):
     bt.close()
 
 
-def test_batch_step_parts_equal_step(pk):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_batch_step_parts_equal_step(pk, solver):
     """push_deposit, a sort when due and solve_field, called apart, give bit for bit
     what the step gives."""
     ws = instances()
-    a = pk.batch_from_workloads(ws)
-    b = pk.batch_from_workloads(ws)
+    a = pk.batch_from_workloads(ws, solver=solver)
+    b = pk.batch_from_workloads(ws, solver=solver)
     for t in (a, b):
         t.set_tuning(sort_every=2)
         t.load([w.x for w in ws], [w.v for w in ws])
