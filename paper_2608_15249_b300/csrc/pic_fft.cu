@@ -46,12 +46,29 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 
 __device__ __forceinline__ int brev(int j, int log2m) { return (int)(__brev((unsigned)j) >> (32 - log2m)); }
 
-// W lines of length m in shared memory (line t at buf + t * m), input in
-// bit-reversed order -> DFT (sign -1, or +1 when inverse) in natural order.
-// tws[t] = exp(-2 pi i t / m), t < m / 2.
-__device__ void dit(float2 *buf, int W, int log2m, const float2 *tws, bool inverse)
+// Shared-memory layout of W lines of length m = 2^log2m: line t starts at t * ls and
+// element i sits at i + (i >> ps), one padding slot per m / 32 elements, so the 32
+// elements a warp scatters to bit-reversed positions (m / 32 apart) land in
+// different banks.  Twiddles follow the lines, stage by stage: stage s (butterfly
+// span 2h, h = 2^s) holds exp(-2 pi i k / 2h), k < h, at offset h - 1.
+struct SLayout {
+    int log2m, ps, ls;
+    __device__ int at(int t, int i) const { return t * ls + i + (i >> ps); }
+};
+
+__device__ __forceinline__ SLayout slayout(int log2m)
 {
-    const int half = 1 << (log2m - 1);
+    SLayout L;
+    L.log2m = log2m;
+    L.ps = log2m >= 5 ? log2m - 5 : 30;
+    L.ls = (1 << log2m) + (log2m >= 5 ? 32 : 0);
+    return L;
+}
+
+// W lines in bit-reversed order -> DFT (sign -1, or +1 when inverse) in natural order.
+__device__ void dit(float2 *buf, int W, const SLayout &S, const float2 *tws, bool inverse)
+{
+    const int log2m = S.log2m, half = 1 << (log2m - 1);
     const int nb = W * half;
     for (int s = 0; s < log2m; ++s) {
         const int h = 1 << s;
@@ -60,21 +77,21 @@ __device__ void dit(float2 *buf, int W, int log2m, const float2 *tws, bool inver
             const int bb = b & (half - 1);
             const int k = bb & (h - 1);
             const int i0 = ((bb >> s) << (s + 1)) + k;
-            float2 *L = buf + ((size_t)t << log2m);
-            float2 w = tws[k << (log2m - 1 - s)];
+            float2 w = tws[h - 1 + k];
             if (inverse) w.y = -w.y;
-            const float2 u = L[i0], v = cmul(w, L[i0 + h]);
-            L[i0] = cadd(u, v);
-            L[i0 + h] = csub(u, v);
+            const int a0 = S.at(t, i0), a1 = S.at(t, i0 + h);
+            const float2 u = buf[a0], v = cmul(w, buf[a1]);
+            buf[a0] = cadd(u, v);
+            buf[a1] = csub(u, v);
         }
         __syncthreads();
     }
 }
 
 // Natural-order input -> DFT in bit-reversed order (decimation in frequency).
-__device__ void dif(float2 *buf, int W, int log2m, const float2 *tws, bool inverse)
+__device__ void dif(float2 *buf, int W, const SLayout &S, const float2 *tws, bool inverse)
 {
-    const int half = 1 << (log2m - 1);
+    const int log2m = S.log2m, half = 1 << (log2m - 1);
     const int nb = W * half;
     for (int s = log2m - 1; s >= 0; --s) {
         const int h = 1 << s;
@@ -83,12 +100,12 @@ __device__ void dif(float2 *buf, int W, int log2m, const float2 *tws, bool inver
             const int bb = b & (half - 1);
             const int k = bb & (h - 1);
             const int i0 = ((bb >> s) << (s + 1)) + k;
-            float2 *L = buf + ((size_t)t << log2m);
-            float2 w = tws[k << (log2m - 1 - s)];
+            float2 w = tws[h - 1 + k];
             if (inverse) w.y = -w.y;
-            const float2 u = L[i0], v = L[i0 + h];
-            L[i0] = cadd(u, v);
-            L[i0 + h] = cmul(csub(u, v), w);
+            const int a0 = S.at(t, i0), a1 = S.at(t, i0 + h);
+            const float2 u = buf[a0], v = buf[a1];
+            buf[a0] = cadd(u, v);
+            buf[a1] = cmul(csub(u, v), w);
         }
         __syncthreads();
     }
@@ -128,16 +145,21 @@ __device__ __forceinline__ float spectral_scale(const LineJob &J, int k, int i)
     return K2 > 0.0f ? J.inv_cells / K2 : 0.0f;
 }
 
-// The transform of one job by the whole CTA (fsm: W * m + m / 2 complex).
+// The transform of one job by the whole CTA (fsm: fft_smem_bytes(W, log2m)).
 __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int log2M, float2 *fsm)
 {
     __shared__ int64_t s_base[32];  // first element of each of the job's lines
     __shared__ int s_inner[32];     // its inner index (the coordinates of the lower axes)
     const FftAxis &ax = J.ax;
     const int n = ax.n, log2m = ax.log2m, m = 1 << log2m, W = J.W, nl = J.nl;
+    const SLayout S = slayout(log2m);
     float2 *buf = fsm;
-    float2 *tws = fsm + ((size_t)W << log2m);
-    for (int t = threadIdx.x; t < m / 2; t += blockDim.x) tws[t] = tw[(size_t)t << (log2M - log2m)];
+    float2 *tws = fsm + (size_t)W * S.ls;
+    // stage tables: entry h - 1 + k = exp(-2 pi i k / 2h) = tw[k M / 2h]
+    for (int q = threadIdx.x; q < m - 1; q += blockDim.x) {
+        const int s = 31 - __clz(q + 1), k = q + 1 - (1 << s);
+        tws[q] = tw[(size_t)k << (log2M - 1 - s)];
+    }
     const int64_t inner = ax.inner;
     if (threadIdx.x < nl) {
         const int64_t l = J.l0 + threadIdx.x;
@@ -164,7 +186,7 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
     // ---- load (scattered to bit-reversed positions, for the DIT) ----------------------------
     if (blue) {
         // zero the padding of Bluestein lines
-        for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) buf[e] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < W * S.ls; e += blockDim.x) buf[e] = make_float2(0.f, 0.f);
         __syncthreads();
     }
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -176,11 +198,11 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
         if (blue) {
             if (inv_in) x = cconj(x);
             x = cmul(x, ax.chirp[j]);
-            buf[((size_t)t << log2m) + brev(j, log2m)] = x;
+            buf[S.at(t, brev(j, log2m))] = x;
         } else if (inv_in) {
-            buf[((size_t)t << log2m) + j] = x;  // natural order for the DIF
+            buf[S.at(t, j)] = x;  // natural order for the DIF
         } else {
-            buf[((size_t)t << log2m) + brev(j, log2m)] = x;
+            buf[S.at(t, brev(j, log2m))] = x;
         }
     }
     __syncthreads();
@@ -190,49 +212,55 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
     if (blue) {
         // forward DFT via the chirp-z convolution (an inverse is the conjugate of the
         // forward DFT of the conjugate input)
-        dit(buf, W, log2m, tws, false);
-        for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x)
-            buf[e] = cmul(buf[e], ax.bhat[e & (m - 1)]);
+        dit(buf, W, S, tws, false);
+        for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
+            const int a = S.at(e >> log2m, e & (m - 1));
+            buf[a] = cmul(buf[a], ax.bhat[e & (m - 1)]);
+        }
         __syncthreads();
-        dif(buf, W, log2m, tws, true);  // conv * m, bit-reversed
+        dif(buf, W, S, tws, true);  // conv * m, bit-reversed
         if (J.mode == FFT_FWD_SCALE_INV) {
             // X_k = w_k c_k / m and Y_k = s_k X_k, then the inverse's input conj(Y_k) w_k,
             // all at position brev(k) of the line, which only this thread touches
             for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
                 const int t = e >> log2m, p = e & (m - 1);
                 const int k = brev(p, log2m);
+                const int a = S.at(t, p);
                 float2 v = make_float2(0.f, 0.f);
                 if (k < n) {
                     const float2 w = ax.chirp[k];
-                    float2 X = cmul(w, buf[e]);
+                    float2 X = cmul(w, buf[a]);
                     const float s = inv_m * spectral_scale(J, k, s_inner[t < nl ? t : 0]);
                     X.x *= s;
                     X.y *= s;
                     v = cmul(cconj(X), w);
                 }
-                buf[e] = v;
+                buf[a] = v;
             }
             __syncthreads();
-            dit(buf, W, log2m, tws, false);
-            for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x)
-                buf[e] = cmul(buf[e], ax.bhat[e & (m - 1)]);
+            dit(buf, W, S, tws, false);
+            for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
+                const int a = S.at(e >> log2m, e & (m - 1));
+                buf[a] = cmul(buf[a], ax.bhat[e & (m - 1)]);
+            }
             __syncthreads();
-            dif(buf, W, log2m, tws, true);
+            dif(buf, W, S, tws, true);
         }
     } else {
         if (J.mode == FFT_INV) {
-            dif(buf, W, log2m, tws, true);  // bit-reversed result
+            dif(buf, W, S, tws, true);  // bit-reversed result
         } else {
-            dit(buf, W, log2m, tws, false);  // natural-order spectrum
+            dit(buf, W, S, tws, false);  // natural-order spectrum
             if (J.mode == FFT_FWD_SCALE_INV) {
                 for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
                     const int t = e >> log2m, k = e & (m - 1);
                     const float s = spectral_scale(J, k, s_inner[t < nl ? t : 0]);
-                    buf[e].x *= s;
-                    buf[e].y *= s;
+                    const int a = S.at(t, k);
+                    buf[a].x *= s;
+                    buf[a].y *= s;
                 }
                 __syncthreads();
-                dif(buf, W, log2m, tws, true);
+                dif(buf, W, S, tws, true);
             }
         }
     }
@@ -245,8 +273,7 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
         int t, j;
         coords(e, &t, &j);
         if (t >= nl) continue;
-        const size_t p = ((size_t)t << log2m) + (rev_out ? brev(j, log2m) : j);
-        float2 v = buf[p];
+        float2 v = buf[S.at(t, rev_out ? brev(j, log2m) : j)];
         if (blue) {
             v = cmul(ax.chirp[j], v);
             v.x *= inv_m;
@@ -408,13 +435,17 @@ int lines_per_cta(int64_t lines, int log2m, int sms, int cap)
 
 size_t fft_smem_bytes(int W, int log2m)
 {
-    return (((size_t)W << log2m) + ((size_t)1 << (log2m - 1))) * sizeof(float2);
+    // W padded lines, then m - 1 stage twiddles
+    const size_t m = (size_t)1 << log2m;
+    const size_t ls = m + (log2m >= 5 ? 32 : 0);
+    return ((size_t)W * ls + m) * sizeof(float2);
 }
 
 cudaError_t fft_configure()
 {
-    // W * m <= 8192 elements plus m / 2 twiddles
-    const int most = (int)((8192 + 4096) * sizeof(float2));
+    // W * m <= 8192 elements (+ 32 padding slots per line, W <= 32) plus m <= 8192
+    // stage twiddles
+    const int most = (int)((8192 + 32 * 32 + 8192) * sizeof(float2));
     cudaError_t e = cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          most);
     if (e != cudaSuccess) return e;
