@@ -8,9 +8,9 @@ push (gather + Boris) -> position update with periodic wrap -> field update.
 It shares no code with the CUDA path.
 
 Parity status per function (details in the repository's design notes):
-  locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris, move,
-  sort_key, counting_sort, kinetic, field_energy, momentum: pinned by the
-  tests under tests/test_oracle_*.py.
+  locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris,
+  higuera_cary, move, sort_key, counting_sort, kinetic, kinetic_rel,
+  field_energy, momentum: pinned by the tests under tests/test_oracle_*.py.
 """
 
 from __future__ import annotations
@@ -58,6 +58,10 @@ def _declare(L):
     L.orc_field_energy.argtypes = [i, _I32, _D, _D]
     L.orc_field_energy.restype = d
     L.orc_momentum.argtypes = [i, i64, _D, d, _D]
+    L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
+    L.orc_hc.restype = None
+    L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
+    L.orc_kinetic_rel.restype = d
 
 
 def _dp(a: np.ndarray):
@@ -185,6 +189,34 @@ def counting_sort(key, nkeys):
     return perm
 
 
+def higuera_cary(ndim, u, Ep, E0, B0, qm, h, c=None):
+    """In-place Higuera-Cary advance of the momentum per mass u = gamma v by step h
+    (Sec. 2.2 A_Pusher); c=None is the non-relativistic limit."""
+    assert u.dtype == np.float64 and u.flags.c_contiguous
+    npart, nv = u.shape
+    Epp = _dp(np.ascontiguousarray(Ep, dtype=np.float64)) if Ep is not None else None
+    e0 = (ctypes.c_double * 3)(*(list(E0) + [0.0] * 3)[:3])
+    b0 = (ctypes.c_double * 3)(*(list(B0) + [0.0] * 3)[:3])
+    keep = Ep  # noqa: F841  (keep the array alive during the call)
+    lib().orc_hc(ndim, nv, npart, _dp(u), Epp, e0, b0, float(qm), float(h), _inv_c2(c))
+    return u
+
+
+def _inv_c2(c):
+    return 0.0 if c is None or c == math.inf else 1.0 / (float(c) * float(c))
+
+
+def lorentz_gamma(u, c=None):
+    """gamma = sqrt(1 + |u|^2 / c^2) per particle."""
+    u = np.asarray(u, dtype=np.float64)
+    return np.sqrt(1.0 + np.sum(u * u, axis=1) * _inv_c2(c))
+
+
+def kinetic_rel(u, mw, c=None):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_kinetic_rel(u.shape[1], u.shape[0], _dp(u), float(mw), _inv_c2(c))
+
+
 def kinetic(v, mw):
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib().orc_kinetic(v.shape[1], v.shape[0], _dp(v), float(mw))
@@ -213,7 +245,7 @@ class Simulation:
 
     def __init__(self, ndim, n, dx, dt, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0),
                  E0=(0, 0, 0), rho_background: Optional[float] = None, rtol=1e-12,
-                 maxit=200000):
+                 maxit=200000, pusher="boris", c=None):
         self.ndim = ndim
         self.n = tuple(list(n)[:3]) + (1,) * (3 - len(n))
         self.dx = tuple(list(dx)[:3]) + (1.0,) * (3 - len(dx))
@@ -222,6 +254,10 @@ class Simulation:
         self.E0 = tuple(E0) + (0.0,) * (3 - len(E0))
         self.rho_background = rho_background
         self.rtol, self.maxit = rtol, maxit
+        # "boris", or "hc" (Higuera-Cary): v then holds u = gamma v, positions move
+        # with u / gamma, and the kinetic energy is the relativistic one
+        assert pusher in ("boris", "hc")
+        self.pusher, self.c = pusher, c
         self.cells = _cells(ndim, self.n)
         self.dV = float(np.prod(self.dx[:ndim]))
         self.V = self.dV * self.cells
@@ -248,21 +284,38 @@ class Simulation:
         if half_push:
             Ep = gather(self.ndim, self.n, self.dx, self.x, self.E)
             v0 = self.v.copy()
-            boris(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, -0.5 * self.dt)
-            self.ke = kinetic(v0, self.m * self.w)
+            self._advance(Ep, -0.5 * self.dt)
+            self.ke = self._kinetic(v0)
         return self
 
+    def _advance(self, Ep, h):
+        if self.pusher == "hc":
+            higuera_cary(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, h, self.c)
+        else:
+            boris(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, h)
+
+    def _kinetic(self, v):
+        if self.pusher == "hc":
+            return kinetic_rel(v, self.m * self.w, self.c)
+        return kinetic(v, self.m * self.w)
+
     def push(self):
-        """Gather (C01) + Boris (A01) by one full step; returns the
-        time-centred kinetic energy (mean of the two half-step energies)."""
+        """Gather (C01) + the pusher (A01 Boris, or Higuera-Cary) by one full step;
+        returns the time-centred kinetic energy (mean of the two half-step energies)."""
         Ep = gather(self.ndim, self.n, self.dx, self.x, self.E)
-        ke_old = kinetic(self.v, self.m * self.w)
-        boris(self.ndim, self.v, Ep, self.E0, self.B0, self.q / self.m, self.dt)
-        self.ke = 0.5 * (ke_old + kinetic(self.v, self.m * self.w))
+        ke_old = self._kinetic(self.v)
+        self._advance(Ep, self.dt)
+        self.ke = 0.5 * (ke_old + self._kinetic(self.v))
         return self.ke
 
+    def velocity(self):
+        """dx/dt of each particle: v, or u / gamma with the Higuera-Cary pusher."""
+        if self.pusher == "hc":
+            return np.ascontiguousarray(self.v / lorentz_gamma(self.v, self.c)[:, None])
+        return self.v
+
     def move(self):
-        move(self.ndim, self.n, self.dx, self.x, self.v, self.dt)
+        move(self.ndim, self.n, self.dx, self.x, self.velocity(), self.dt)
 
     def step(self, nsteps=1):
         for _ in range(nsteps):

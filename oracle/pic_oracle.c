@@ -278,6 +278,61 @@ void orc_boris(int ndim, int nv, int64_t np, double *v, const double *Ep, const 
     }
 }
 
+/* Higuera-Cary advance (A_Pusher, Sec. 2.2, the relativistic pusher the paper
+ * cites besides Boris) of the momentum per mass u = gamma v by a step h, with
+ * eps = (q/m) h / 2, tau = eps B and 1/c^2 = inv_c2 (0: the non-relativistic limit):
+ *   u- = u + eps E
+ *   sigma = gamma-^2 - tau^2,  gamma-^2 = 1 + |u-|^2 / c^2
+ *   gamma_bar^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + (u- . tau)^2 / c^2))) / 2
+ *   t = tau / gamma_bar,  s = 1 / (1 + t . t)
+ *   u+ = s (u- + (u- . t) t + u- x t)
+ *   u = u+ + eps E + u+ x t
+ * gamma_bar is the Lorentz factor of the mean momentum (u- + u+) / 2, so the
+ * rotation is the implicit midpoint one, u+ - u- = (u- + u+) x tau / gamma_bar. */
+void orc_hc(int ndim, int nv, int64_t np, double *u, const double *Ep, const double *E0,
+            const double *B0, double qm, double h, double inv_c2)
+{
+    const double eps = 0.5 * qm * h;
+    double tau[3], tau2 = 0.0;
+    for (int a = 0; a < 3; ++a) { tau[a] = eps * B0[a]; tau2 += tau[a] * tau[a]; }
+    for (int64_t p = 0; p < np; ++p) {
+        double E[3], um[3], up[3], t[3];
+        for (int a = 0; a < 3; ++a) {
+            E[a] = E0[a] + (a < ndim && Ep ? Ep[p * ndim + a] : 0.0);
+            um[a] = (a < nv ? u[p * nv + a] : 0.0) + eps * E[a];
+        }
+        const double um2 = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+        const double ustar = um[0] * tau[0] + um[1] * tau[1] + um[2] * tau[2];
+        const double sigma = 1.0 + um2 * inv_c2 - tau2;
+        const double gbar = sqrt(0.5 * (sigma + sqrt(sigma * sigma +
+                                                     4.0 * (tau2 + ustar * ustar * inv_c2))));
+        double tt = 0.0;
+        for (int a = 0; a < 3; ++a) { t[a] = tau[a] / gbar; tt += t[a] * t[a]; }
+        const double s = 1.0 / (1.0 + tt);
+        const double ut = um[0] * t[0] + um[1] * t[1] + um[2] * t[2];
+        up[0] = s * (um[0] + ut * t[0] + (um[1] * t[2] - um[2] * t[1]));
+        up[1] = s * (um[1] + ut * t[1] + (um[2] * t[0] - um[0] * t[2]));
+        up[2] = s * (um[2] + ut * t[2] + (um[0] * t[1] - um[1] * t[0]));
+        const double un[3] = {up[0] + eps * E[0] + (up[1] * t[2] - up[2] * t[1]),
+                              up[1] + eps * E[1] + (up[2] * t[0] - up[0] * t[2]),
+                              up[2] + eps * E[2] + (up[0] * t[1] - up[1] * t[0])};
+        for (int a = 0; a < nv && a < 3; ++a) u[p * nv + a] = un[a];
+    }
+}
+
+/* Relativistic kinetic energy m w sum (gamma - 1) c^2 = m w sum |u|^2 / (gamma + 1)
+ * (the second form has no cancellation; at inv_c2 = 0 it is (1/2) m w sum |u|^2). */
+double orc_kinetic_rel(int nv, int64_t np, const double *u, double mw, double inv_c2)
+{
+    double s = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        double u2 = 0.0;
+        for (int a = 0; a < nv; ++a) u2 += u[p * nv + a] * u[p * nv + a];
+        s += u2 / (sqrt(1.0 + u2 * inv_c2) + 1.0);
+    }
+    return mw * s;
+}
+
 /* Position update with periodic boundaries (application code in Sec. 3.1):
  * x_a += v_a dt on the ndim spatial axes, then x_a -= L_a floor(x_a / L_a);
  * a result that rounds to L_a is set to 0. */

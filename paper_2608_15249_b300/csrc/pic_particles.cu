@@ -292,7 +292,7 @@ enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8 };
 constexpr int TILE = 512;           // particles per tile (2 per thread)
 constexpr int WIN_BITS = 11;        // a tile's shared-memory charge window: 2^11 nodes
 constexpr int WIN_CAP = 1 << WIN_BITS;
-constexpr int STAGES = 4;           // tiles in flight per CTA
+constexpr int STAGES = 3;           // tiles in flight per CTA
 constexpr int WAIT_LIMIT = 1 << 26;   // bounded mbarrier polling
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -409,7 +409,7 @@ struct BatchSrc {
 // independent instances packed in one particle arena (BatchSrc, whose tiles each
 // carry their instance's parameters, field and charge accumulator).
 template <int D, int NV, int MODE, class Src>
-__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
+__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
     k_particle_pass(Src src, ParticlesF32 p, double *__restrict__ diag_blocks,
                     int *__restrict__ err)
 {
@@ -771,10 +771,10 @@ int particle_pass_blocks(int64_t np, int ndim)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    // one resident wave: 4 CTAs of 256 threads per SM (3 in 3D, where the pass needs
+    // one resident wave: 5 CTAs of 256 threads per SM (3 in 3D, where the pass needs
     // more registers and shared memory), each walking tiles of TILE particles
     const int64_t need = (np + TILE - 1) / TILE;
-    const int64_t cap = (int64_t)sms * (ndim == 3 ? 3 : 4);
+    const int64_t cap = (int64_t)sms * (ndim == 3 ? 3 : 5);
     int64_t b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
 }

@@ -1,5 +1,5 @@
 """Pins of the oracle's particle steps: the Boris push (Sec. 2.2 A_Pusher, module A01
-in Sec. 3.1), the position update with periodic wrap (application code in Sec. 3.1)
+in Sec. 3.1) and the Higuera-Cary push the same module lists, the position update with periodic wrap (application code in Sec. 3.1)
 and the per-cell sort (a layout step the paper does not name)."""
 
 import math
@@ -78,6 +78,116 @@ def test_boris_is_time_reversible(orc):
     orc.boris(3, v, Ep, (0.1, 0, 0), (0.2, 0.5, 1.0), -1.0, 0.07)
     orc.boris(3, v, Ep, (0.1, 0, 0), (0.2, 0.5, 1.0), -1.0, -0.07)
     np.testing.assert_allclose(v, v0, atol=1e-14)
+
+
+# ---- Higuera-Cary (the relativistic pusher of Sec. 2.2 A_Pusher) ---------------------------
+
+def _rand_fields(seed, n=16):
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((n, 3)) * 2.0
+    Ep = rng.standard_normal((n, 3)) * 0.3
+    return u, Ep
+
+
+def test_hc_is_the_implicit_midpoint_rotation(orc):
+    """The defining relation: with u-/u+ the momenta before/after the rotation,
+    u+ - u- = (u- + u+) x tau / gamma(mean momentum), tau = (q/m) B h / 2."""
+    u, Ep = _rand_fields(31)
+    E0, B0, qm, h, c = (0.05, -0.1, 0.2), (0.3, -0.2, 1.5), -1.0, 0.08, 2.0
+    u0 = u.copy()
+    orc.higuera_cary(3, u, Ep, E0, B0, qm, h, c)
+    eps = 0.5 * qm * h
+    E = Ep + np.array(E0)
+    um, up = u0 + eps * E, u - eps * E
+    ub = 0.5 * (um + up)
+    gb = np.sqrt(1.0 + np.sum(ub * ub, axis=1) / c ** 2)
+    rhs = np.cross(um + up, eps * np.array(B0)[None, :] / gb[:, None])
+    np.testing.assert_allclose(up - um, rhs, rtol=0, atol=1e-13)
+
+
+def test_hc_nonrelativistic_limit_is_boris(orc):
+    u, Ep = _rand_fields(32)
+    v = u.copy()
+    args = ((0.05, -0.1, 0.2), (0.3, -0.2, 1.5), -1.0, 0.08)
+    orc.higuera_cary(3, u, Ep, *args, c=None)
+    orc.boris(3, v, Ep, *args)
+    np.testing.assert_allclose(u, v, rtol=0, atol=1e-14)
+    # and a very large c approaches it
+    u2 = _rand_fields(32)[0]
+    orc.higuera_cary(3, u2, Ep, *args, c=1e7)
+    np.testing.assert_allclose(u2, v, rtol=0, atol=1e-10)
+
+
+def test_hc_pure_B_keeps_momentum_and_turns_at_the_midpoint_gamma(orc):
+    """In pure B |u| (hence gamma) is kept; per step u turns by 2 atan(|tau| / gamma_bar)
+    about B, gamma_bar the Lorentz factor of the mean momentum, in the electron's sense."""
+    c, wc, h = 2.0, 1.5, 0.05
+    u = np.array([[3.0, 1.0, 0.0]])
+    s0 = np.linalg.norm(u)
+    for _ in range(1000):
+        orc.higuera_cary(3, u, None, (0, 0, 0), (0.3, -0.2, 1.1), -1.0, h, c)
+    assert abs(np.linalg.norm(u) - s0) < 1e-12 * s0
+    u = np.array([[3.0, 1.0, 0.0]])
+    u0 = u[0].copy()
+    orc.higuera_cary(3, u, None, (0, 0, 0), (0, 0, wc), -1.0, h, c)
+    ub = 0.5 * (u0 + u[0])
+    gb = math.sqrt(1.0 + ub.dot(ub) / c ** 2)
+    ang = math.atan2(u0[0] * u[0, 1] - u0[1] * u[0, 0], u0.dot(u[0]))
+    assert abs(ang - 2 * math.atan(0.5 * wc * h / gb)) < 1e-14
+    # gamma_bar < gamma: the relativistic gyro-frequency is below the classical one
+    assert gb < math.sqrt(1.0 + u0.dot(u0) / c ** 2)
+
+
+def test_hc_relativistic_ExB_drift_is_exact(orc):
+    """A particle moving with the E x B drift, u = gamma_d E x B / |B|^2, is a fixed
+    point of the Higuera-Cary step at any step size (the property that sets it apart
+    from Boris, which is also checked here to miss it)."""
+    c, Ey, Bz, qm = 1.0, 0.5, 1.0, -1.0
+    E, B = np.array([0.0, Ey, 0.0]), np.array([0.0, 0.0, Bz])
+    vd = np.cross(E, B) / B.dot(B)
+    ud = vd / math.sqrt(1.0 - vd.dot(vd) / c ** 2)
+    for h in (0.05, 0.5, 2.0):
+        u = ud[None, :].copy()
+        for _ in range(10):
+            orc.higuera_cary(3, u, None, tuple(E), tuple(B), qm, h, c)
+        np.testing.assert_allclose(u[0], ud, rtol=0, atol=1e-14)
+        v = ud[None, :].copy()
+        orc.boris(3, v, None, tuple(E), tuple(B), qm, h)
+        assert np.abs(v[0] - ud).max() > 1e-3
+
+
+def test_hc_without_B_is_leapfrog_in_momentum(orc):
+    u, Ep = _rand_fields(33)
+    want = u + (-1.0) * 0.1 * Ep
+    orc.higuera_cary(3, u, Ep, (0, 0, 0), (0, 0, 0), -1.0, 0.1, 0.7)
+    np.testing.assert_allclose(u, want, rtol=0, atol=1e-14)
+
+
+def test_relativistic_kinetic_energy(orc):
+    u, _ = _rand_fields(34)
+    c, mw = 1.7, 2.5
+    gamma = np.sqrt(1.0 + np.sum(u * u, axis=1) / c ** 2)
+    assert abs(orc.kinetic_rel(u, mw, c) - mw * c ** 2 * np.sum(gamma - 1.0)) < 1e-12 * mw * c ** 2
+    assert abs(orc.kinetic_rel(u, mw, None) - orc.kinetic(u, mw)) < 1e-12
+
+
+def test_hc_simulation_moves_with_u_over_gamma(orc):
+    """In a uniform external E (no self-field: negligible weight) the momentum grows
+    by q E dt / m per step and the position advances by u / gamma dt (the
+    relativistic velocity), wrapped into the box."""
+    c, dt, Ex = 1.5, 0.1, 0.4
+    sim = orc.Simulation(1, (64,), (1.0,), dt, weight=1e-12, E0=(Ex, 0, 0), pusher="hc", c=c)
+    x0 = np.array([[10.0]])
+    sim.load(x0, np.array([[0.0, 0.0, 0.0]]), half_push=False)
+    x = 10.0
+    u = 0.0
+    for _ in range(50):
+        u += -1.0 * Ex * dt
+        x += u / math.sqrt(1.0 + u * u / c ** 2) * dt
+        sim.step(1)
+    assert abs(sim.v[0, 0] - u) < 1e-12
+    assert abs(sim.x[0, 0] - (x % 64.0)) < 1e-9
+    assert abs(sim.velocity()[0, 0]) < c
 
 
 def test_move_wraps(orc):
