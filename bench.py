@@ -173,7 +173,9 @@ def _config(args, w):
             "grid": list(w.n[: w.ndim]), "particles": w.np_, "ppc": args.ppc,
             "sort_every": w.sort_every, "parallelism": f"replicas x{args.gpus}",
             "storage": "FP64 plain" if args.precision == "f64" else "int32 cell + FP32 offset",
-            "l2": "particle state larger than L2 (no flush)"}
+            "l2": "particle state larger than L2 (no flush)",
+            "pusher": args.pusher if args.pusher == "boris"
+            else f"higuera-cary, c = {args.c_light or 'infinite'}"}
 
 
 def bench_ours(args):
@@ -194,6 +196,8 @@ def bench_ours(args):
     f64 = args.precision == "f64"
     stream = torch.cuda.current_stream()
     extra = dict(precision=pk.AP_PIC_FP64_PLAIN) if f64 else {}
+    if args.pusher == "hc":
+        extra.update(pusher=pk.AP_PIC_PUSHER_HIGUERA_CARY, c_light=args.c_light)
     g = pk.from_workload(w, stream=stream.cuda_stream, cg_rtol=args.cg_rtol, **extra)
     g.load(w.x, w.v)
     sort_every = 0 if f64 else w.sort_every
@@ -490,6 +494,9 @@ def main():
                     help="f32: cell + FP32 offset form (the product); f64: FP64 plain form")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--e2e-solver", choices=["cg", "fft"], default="fft")
+    ap.add_argument("--pusher", choices=["boris", "hc"], default="boris",
+                    help="hc: Higuera-Cary (velocities read as momenta per mass)")
+    ap.add_argument("--c-light", type=float, default=0.0, help="with --pusher hc; 0: infinite")
     ap.add_argument("--e2e-steps-cg", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

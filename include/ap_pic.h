@@ -79,6 +79,16 @@ enum {
 };
 #define AP_PIC_FFT_MAX_N 4096
 
+/* Particle pusher (A_Pusher, Sec. 2.2, which lists the Boris and Higuera-Cary
+ * pushers).  With AP_PIC_PUSHER_HIGUERA_CARY the stored (and loaded) velocities
+ * are the momenta per mass u = gamma v, positions advance with u / gamma, and the
+ * kinetic energy is m w sum (gamma - 1) c^2; the FP32 form only. */
+enum {
+    AP_PIC_PUSHER_BORIS = 0,          /* Boris / leapfrog (A01), default          */
+    AP_PIC_PUSHER_HIGUERA_CARY = 1    /* relativistic, volume-preserving, exact
+                                         E x B drift                            */
+};
+
 /* ap_pic_load flags */
 enum { AP_PIC_LOAD_NO_HALFPUSH = 1u };
 
@@ -111,6 +121,9 @@ typedef struct {
     int diag_every;        /* diagnostics every this many steps (0: every step)    */
     int solver;            /* AP_PIC_SOLVER_CG (default) or AP_PIC_SOLVER_FFT; both
                               end with one FP64-residual refinement pass           */
+    int pusher;            /* AP_PIC_PUSHER_BORIS (default) or _HIGUERA_CARY        */
+    double c_light;        /* speed of light in the run's units, for the Higuera-
+                              Cary pusher (0: infinite, the non-relativistic limit) */
 } ap_pic_config;
 
 typedef struct {

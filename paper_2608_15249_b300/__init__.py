@@ -33,6 +33,8 @@ AP_PIC_FP64_PLAIN = 1
 AP_PIC_SOLVER_CG = 0
 AP_PIC_SOLVER_FFT = 1
 AP_PIC_FFT_MAX_N = 4096
+AP_PIC_PUSHER_BORIS = 0
+AP_PIC_PUSHER_HIGUERA_CARY = 1
 AP_PIC_LOAD_NO_HALFPUSH = 1
 
 # Every symbol the header declares (checked by the CPU test of the library's exports).
@@ -64,6 +66,7 @@ class ap_pic_config(ctypes.Structure):
         ("precision", ctypes.c_int), ("nv", ctypes.c_int), ("sort_every", ctypes.c_int),
         ("fx_bits", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
         ("brick", ctypes.c_int * 3), ("diag_every", ctypes.c_int), ("solver", ctypes.c_int),
+        ("pusher", ctypes.c_int), ("c_light", ctypes.c_double),
     ]
 
 
@@ -180,7 +183,8 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
                 rho_background=None, E0=(0, 0, 0), B0=(0, 0, 0), nv=None,
                 precision=AP_PIC_FP32_CELLOFF, sort_every=20, fx_bits=0, cg_rtol=0.0,
                 cg_maxit=0, brick=(0, 0, 0), diag_every=0,
-                solver=AP_PIC_SOLVER_CG) -> ap_pic_config:
+                solver=AP_PIC_SOLVER_CG, pusher=AP_PIC_PUSHER_BORIS,
+                c_light=0.0) -> ap_pic_config:
     c = ap_pic_config()
     lib().ap_pic_config_default(ctypes.byref(c))
     c.ndim = ndim
@@ -202,6 +206,8 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
     c.cg_maxit = int(cg_maxit)
     c.diag_every = int(diag_every)
     c.solver = int(solver)
+    c.pusher = int(pusher)
+    c.c_light = float(c_light)
     return c
 
 

@@ -232,6 +232,8 @@ static GridParams grid_params(const ap_pic *h, double step_h)
     g.fx_bits = h->fx_bits;
     g.div0 = make_fastdiv((uint32_t)g.n[0]);
     g.div1 = make_fastdiv((uint32_t)g.n[1]);
+    g.pusher = c.pusher;
+    g.inv_c2 = c.c_light > 0.0 ? (float)(1.0 / (c.c_light * c.c_light)) : 0.0f;
     return g;
 }
 
@@ -343,6 +345,12 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
     if (c->cg_maxit == 0) c->cg_maxit = DEFAULT_CG_MAXIT;
     if (c->cg_maxit < 1) return fail(h, AP_PIC_ERR_ARG, "cg_maxit must be >= 1");
     if (c->diag_every < 0) return fail(h, AP_PIC_ERR_ARG, "diag_every must be >= 0");
+    if (c->pusher != AP_PIC_PUSHER_BORIS && c->pusher != AP_PIC_PUSHER_HIGUERA_CARY)
+        return fail(h, AP_PIC_ERR_ARG, "unknown pusher %d", c->pusher);
+    if (!(c->c_light >= 0.0) || !isfinite(c->c_light))
+        return fail(h, AP_PIC_ERR_ARG, "c_light must be >= 0 and finite (0: infinite)");
+    if (c->pusher == AP_PIC_PUSHER_HIGUERA_CARY && plain)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "the FP64 plain form pushes with Boris only");
     if (c->solver != AP_PIC_SOLVER_CG && c->solver != AP_PIC_SOLVER_FFT)
         return fail(h, AP_PIC_ERR_ARG, "unknown solver %d", c->solver);
     if (c->solver == AP_PIC_SOLVER_FFT) {

@@ -850,6 +850,8 @@ extern "C" ap_pic_status ap_pic_batch_create(int count, const ap_pic_config *cfg
             return bfail(b, AP_PIC_ERR_ARG, "bad dt, m or weight");
         if (c.fx_bits == 0) c.fx_bits = 22;
         if (c.fx_bits < 8 || c.fx_bits > 22) return bfail(b, AP_PIC_ERR_ARG, "fx_bits in [8, 22]");
+        if (c.pusher != AP_PIC_PUSHER_BORIS)
+            return bfail(b, AP_PIC_ERR_UNSUPPORTED, "batch instances push with Boris only");
         if (b->cfg[0].solver == AP_PIC_SOLVER_FFT)
             for (int a = 0; a < c.ndim; ++a)
                 if (!fft_length_ok(c.n[a]))

@@ -58,6 +58,8 @@ struct GridParams {
     float s[3];        // Boris s = 2 t / (1 + |t|^2)
     int fx_bits;       // S
     int magnetised;    // B0 != 0
+    int pusher;        // AP_PIC_PUSHER_*
+    float inv_c2;      // 1 / c^2 of the Higuera-Cary pusher (0: non-relativistic)
 };
 
 // Error bits latched in the device word (same values as AP_PIC_EFLAG_*).

@@ -12,6 +12,8 @@
 // the order of the atomics.
 #include <math.h>
 
+#include <type_traits>
+
 #include "pic_internal.cuh"
 
 namespace apk {
@@ -285,7 +287,49 @@ __device__ __forceinline__ double warp_sum_d(double x)
     return x;
 }
 
-enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8 };
+enum : int { PASS_PUSH = 1, PASS_MOVE = 2, PASS_DEPOSIT = 4, PASS_DIAG = 8, PASS_HC = 16 };
+
+// Higuera-Cary advance (A_Pusher, Sec. 2.2) of the momentum per mass u = gamma v
+// in FP32, with eps = qmh2 and tau = t (the Boris t vector, (q/m) B h / 2):
+//   u- = u + eps E;  sigma = 1 + |u-|^2 / c^2 - |tau|^2;
+//   gamma_bar^2 = (sigma + sqrt(sigma^2 + 4 (|tau|^2 + (u-.tau)^2 / c^2))) / 2;
+//   t = tau / gamma_bar;  s = 1 / (1 + |t|^2);  u+ = s (u- + (u-.t) t + u- x t);
+//   u = u+ + eps E + u+ x t.
+// gamma_bar is the Lorentz factor of the mean momentum, so the turn is the
+// implicit midpoint rotation; it keeps the relativistic E x B drift exact.
+__device__ __forceinline__ void hc_push(float *u, const float *e, const GridParams &g)
+{
+    float um[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) um[a] = u[a] + g.qmh2 * e[a];
+    const float tau2 = g.t[0] * g.t[0] + g.t[1] * g.t[1] + g.t[2] * g.t[2];
+    const float um2 = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+    const float ustar = um[0] * g.t[0] + um[1] * g.t[1] + um[2] * g.t[2];
+    const float sigma = 1.0f + um2 * g.inv_c2 - tau2;
+    const float gbar2 =
+        0.5f * (sigma + sqrtf(sigma * sigma + 4.0f * (tau2 + ustar * ustar * g.inv_c2)));
+    const float ig = rsqrtf(gbar2);
+    const float t[3] = {g.t[0] * ig, g.t[1] * ig, g.t[2] * ig};
+    const float s = 1.0f / (1.0f + tau2 * ig * ig);
+    const float ut = um[0] * t[0] + um[1] * t[1] + um[2] * t[2];
+    const float up[3] = {s * (um[0] + ut * t[0] + (um[1] * t[2] - um[2] * t[1])),
+                         s * (um[1] + ut * t[1] + (um[2] * t[0] - um[0] * t[2])),
+                         s * (um[2] + ut * t[2] + (um[0] * t[1] - um[1] * t[0]))};
+    u[0] = up[0] + g.qmh2 * e[0] + (up[1] * t[2] - up[2] * t[1]);
+    u[1] = up[1] + g.qmh2 * e[1] + (up[2] * t[0] - up[0] * t[2]);
+    u[2] = up[2] + g.qmh2 * e[2] + (up[0] * t[1] - up[1] * t[0]);
+}
+
+// 2 |u|^2 / (gamma + 1): twice the relativistic kinetic energy per mass,
+// (gamma - 1) c^2, without cancellation.
+template <int NV>
+__device__ __forceinline__ float twice_ke_rel(const float *u, float inv_c2)
+{
+    float u2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) u2 += u[a] * u[a];
+    return 2.0f * u2 / (sqrtf(1.0f + u2 * inv_c2) + 1.0f);
+}
 
 // ---- TMA bulk-copy pipeline helpers (PTX) ---------------------------------------------------
 
@@ -418,6 +462,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
     constexpr int NA_MAX = 1 + D + NV;
     constexpr bool PUSH = (MODE & PASS_PUSH) != 0, MOVE = (MODE & PASS_MOVE) != 0;
     constexpr bool DEPOSIT = (MODE & PASS_DEPOSIT) != 0, DIAG = (MODE & PASS_DIAG) != 0;
+    constexpr bool HC = (MODE & PASS_HC) != 0;  // Higuera-Cary push, move at u / gamma
     constexpr bool NEED_V = PUSH || MOVE;
     constexpr int NA = 1 + D + (NEED_V ? NV : 0);
     constexpr bool WRITE = PUSH || MOVE;  // the record changes and goes back to global
@@ -566,17 +611,24 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) e[r][a] += g.E0[a];
                 float vn[3] = {v[r][0], v[r][1], v[r][2]};
-                boris(vn, e[r], g);
+                if (HC) hc_push(vn, e[r], g);
+                else boris(vn, e[r], g);
 #pragma unroll
                 for (int a = 0; a < NV; ++a) finite &= isfinite(vn[a]);
                 if (DIAG) {
                     float o2 = 0.0f, n2 = 0.0f;
+                    if (HC) {
+                        o2 = twice_ke_rel<NV>(v[r], g.inv_c2);
+                        n2 = twice_ke_rel<NV>(vn, g.inv_c2);
+                    } else {
 #pragma unroll
-                    for (int a = 0; a < NV; ++a) {
-                        o2 += v[r][a] * v[r][a];
-                        n2 += vn[a] * vn[a];
-                        mom[a] += vn[a];
+                        for (int a = 0; a < NV; ++a) {
+                            o2 += v[r][a] * v[r][a];
+                            n2 += vn[a] * vn[a];
+                        }
                     }
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) mom[a] += vn[a];
                     ke += 0.5f * (o2 + n2);
                 }
 #pragma unroll
@@ -586,7 +638,17 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
                 }
             }
             if (MOVE) {
-                if (finite && move<D>(c[r], f[r], v[r], g)) {
+                // dx/dt: v, or u / gamma for the relativistic pusher
+                float w[3] = {v[r][0], v[r][1], v[r][2]};
+                if (HC) {
+                    float u2 = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < NV; ++a) u2 += v[r][a] * v[r][a];
+                    const float ig = rsqrtf(1.0f + u2 * g.inv_c2);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) w[a] *= ig;
+                }
+                if (finite && move<D>(c[r], f[r], w, g)) {
                     s_cell[j] = encode_cell<D>(c[r], g.n);
 #pragma unroll
                     for (int a = 0; a < D; ++a) stage_arr(st, 1 + a)[j] = f[r][a];
@@ -803,6 +865,20 @@ static cudaError_t launch_pass_t(const Src &src, ParticlesF32 p, int mode, doubl
 {
     constexpr int FUSED = PASS_PUSH | PASS_MOVE | PASS_DEPOSIT;
     constexpr int GP = PASS_PUSH | PASS_MOVE;
+    if constexpr (std::is_same<Src, SingleSrc>::value) {
+        // the relativistic pusher (single instances only)
+        constexpr int H = PASS_HC;
+        switch (mode) {
+        case FUSED | H: return launch_pass_m<D, NV, FUSED | H>(src, p, diag_blocks, nb, err, st);
+        case FUSED | PASS_DIAG | H:
+            return launch_pass_m<D, NV, FUSED | PASS_DIAG | H>(src, p, diag_blocks, nb, err, st);
+        case GP | H: return launch_pass_m<D, NV, GP | H>(src, p, diag_blocks, nb, err, st);
+        case GP | PASS_DIAG | H:
+            return launch_pass_m<D, NV, GP | PASS_DIAG | H>(src, p, diag_blocks, nb, err, st);
+        case PASS_PUSH | H: return launch_pass_m<D, NV, PASS_PUSH | H>(src, p, diag_blocks, nb, err, st);
+        default: break;
+        }
+    }
     switch (mode) {
     case FUSED: return launch_pass_m<D, NV, FUSED>(src, p, diag_blocks, nb, err, st);
     case FUSED | PASS_DIAG:
@@ -827,7 +903,8 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
                                  DiagPartials diag, int *err, cudaStream_t st)
 {
     if (p.np == 0) return cudaSuccess;
-    const int mode = pass_mode(push, mv, deposit, diag.blocks != nullptr);
+    const int mode = pass_mode(push, mv, deposit, diag.blocks != nullptr) |
+                     (push && g.pusher == AP_PIC_PUSHER_HIGUERA_CARY ? PASS_HC : 0);
     const int nb = particle_pass_blocks(p.np, g.ndim);
     SingleSrc src;
     src.tp.g = g;

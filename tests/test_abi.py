@@ -74,7 +74,10 @@ def test_config_defaults_and_validation(libpath):
     # and every axis within its longest transform
     for bad, want in ((dict(solver=7), -1),
                       (dict(solver=pk.AP_PIC_SOLVER_FFT, precision=pk.AP_PIC_FP64_PLAIN), -2),
-                      (dict(solver=pk.AP_PIC_SOLVER_FFT, n=(pk.AP_PIC_FFT_MAX_N + 1,)), -2)):
+                      (dict(solver=pk.AP_PIC_SOLVER_FFT, n=(pk.AP_PIC_FFT_MAX_N + 1,)), -2),
+                      (dict(pusher=5), -1), (dict(c_light=-1.0), -1),
+                      (dict(pusher=pk.AP_PIC_PUSHER_HIGUERA_CARY,
+                            precision=pk.AP_PIC_FP64_PLAIN), -2)):
         kw = dict(ndim=1, n=(8,))
         kw.update(bad)
         cfg = pk.make_config(**kw)
