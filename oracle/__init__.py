@@ -10,7 +10,8 @@ It shares no code with the CUDA path.
 Parity status per function (details in the repository's design notes):
   locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris,
   higuera_cary, move, sort_key, counting_sort, kinetic, kinetic_rel,
-  field_energy, momentum: pinned by the tests under tests/test_oracle_*.py.
+  field_energy, momentum, rng24, mcc: pinned by the tests under
+  tests/test_oracle_*.py.
 """
 
 from __future__ import annotations
@@ -58,6 +59,16 @@ def _declare(L):
     L.orc_field_energy.argtypes = [i, _I32, _D, _D]
     L.orc_field_energy.restype = d
     L.orc_momentum.argtypes = [i, i64, _D, d, _D]
+    u32, u64 = ctypes.c_uint32, ctypes.c_uint64
+    L.orc_rng24.argtypes = [u64, u64, u64, i]
+    L.orc_rng24.restype = u32
+    L.orc_rng24_fill.argtypes = [u64, u64, u64, i64, i, ctypes.POINTER(ctypes.c_uint32)]
+    L.orc_rng24_fill.restype = None
+    L.orc_mcc_threshold.argtypes = [d, d, d, d, d]
+    L.orc_mcc_threshold.restype = u32
+    L.orc_mcc.argtypes = [i64, _D, ctypes.POINTER(ctypes.c_uint32), u64, u64, d, d, d, d, d, d,
+                          d, d, _I64]
+    L.orc_mcc.restype = None
     L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
     L.orc_hc.restype = None
     L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
@@ -217,6 +228,41 @@ def kinetic_rel(u, mw, c=None):
     return lib().orc_kinetic_rel(u.shape[1], u.shape[0], _dp(u), float(mw), _inv_c2(c))
 
 
+def rng24(seed, step, pid, k):
+    """The counter-based 24-bit draw k of particle `pid` at `step` (SplitMix64 output
+    function); what both the oracle and the CUDA path draw."""
+    return int(lib().orc_rng24(int(seed), int(step), int(pid), int(k)))
+
+
+def rng24_fill(seed, step, id0, n, k):
+    out = np.empty(n, np.uint32)
+    lib().orc_rng24_fill(int(seed), int(step), int(id0), int(n), int(k),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return out
+
+
+def mcc_threshold(ng, sig_el, sig_exc, vmax, dt):
+    return int(lib().orc_mcc_threshold(float(ng), float(sig_el), float(sig_exc), float(vmax),
+                                       float(dt)))
+
+
+MCC_FIELDS = ("density", "sigma_el", "sigma_exc", "eps_exc", "mass_ratio", "vmax", "seed")
+
+
+def mcc(v, ids, step, p, m, dt):
+    """In-place null-collision step (Sec. 2.2 G_collision) of velocities v (np x 3)
+    with particle ids; p: dict with MCC_FIELDS.  Returns the counts (elastic,
+    excitation, bound exceeded)."""
+    assert v.dtype == np.float64 and v.flags.c_contiguous and v.shape[1] == 3
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    counts = np.zeros(3, np.int64)
+    lib().orc_mcc(v.shape[0], _dp(v), ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                  int(step), int(p["seed"]), float(p["density"]), float(p["sigma_el"]),
+                  float(p["sigma_exc"]), float(p["eps_exc"]), float(p["mass_ratio"]),
+                  float(p["vmax"]), float(m), float(dt), _i64p(counts))
+    return counts
+
+
 def kinetic(v, mw):
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib().orc_kinetic(v.shape[1], v.shape[0], _dp(v), float(mw))
@@ -245,7 +291,7 @@ class Simulation:
 
     def __init__(self, ndim, n, dx, dt, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0),
                  E0=(0, 0, 0), rho_background: Optional[float] = None, rtol=1e-12,
-                 maxit=200000, pusher="boris", c=None):
+                 maxit=200000, pusher="boris", c=None, collisions=None):
         self.ndim = ndim
         self.n = tuple(list(n)[:3]) + (1,) * (3 - len(n))
         self.dx = tuple(list(dx)[:3]) + (1.0,) * (3 - len(dx))
@@ -258,6 +304,10 @@ class Simulation:
         # with u / gamma, and the kinetic energy is the relativistic one
         assert pusher in ("boris", "hc")
         self.pusher, self.c = pusher, c
+        # null-collision Monte Carlo after each move (dict with MCC_FIELDS, or None);
+        # particle ids are the load order
+        self.collisions = collisions
+        self.mcc_counts = np.zeros(3, np.int64)
         self.cells = _cells(ndim, self.n)
         self.dV = float(np.prod(self.dx[:ndim]))
         self.V = self.dV * self.cells
@@ -280,6 +330,7 @@ class Simulation:
     def load(self, x, v, half_push=True):
         self.x = np.array(x, dtype=np.float64, order="C")
         self.v = np.array(v, dtype=np.float64, order="C")
+        self.ids = np.arange(self.x.shape[0], dtype=np.uint32)
         self.update_field()
         if half_push:
             Ep = gather(self.ndim, self.n, self.dx, self.x, self.E)
@@ -317,10 +368,19 @@ class Simulation:
     def move(self):
         move(self.ndim, self.n, self.dx, self.x, self.velocity(), self.dt)
 
+    def collide(self):
+        """Null-collision step of this time step (the step count it draws with is
+        the step being completed, 1 for the first)."""
+        self.mcc_counts = mcc(self.v, self.ids, self.step_count + 1, self.collisions, self.m,
+                              self.dt)
+        return self.mcc_counts
+
     def step(self, nsteps=1):
         for _ in range(nsteps):
             self.push()
             self.move()
+            if self.collisions is not None:
+                self.collide()
             self.update_field()
             self.t += self.dt
             self.step_count += 1
@@ -341,4 +401,5 @@ class Simulation:
         perm = counting_sort(key, num_keys(self.ndim, self.n, brick))
         self.x = np.ascontiguousarray(self.x[perm])
         self.v = np.ascontiguousarray(self.v[perm])
+        self.ids = np.ascontiguousarray(self.ids[perm])
         return perm

@@ -419,3 +419,97 @@ void orc_momentum(int nv, int64_t np, const double *v, double mw, double *out)
         for (int a = 0; a < nv; ++a) out[a] += v[p * nv + a];
     for (int a = 0; a < nv; ++a) out[a] *= mw;
 }
+
+/* ---- null-collision Monte Carlo (G_collision, Sec. 2.2, after Vahedi and Surendra) --------- */
+
+/* Counter-based uniform numbers: the output function of SplitMix64 (Steele, Lea and
+ * Flood 2014) applied to seed + (counter + 1) * 0x9E3779B97F4A7C15, counter =
+ * step * 2^34 + id * 4 + k; the draw is the top 24 bits. */
+uint32_t orc_rng24(uint64_t seed, uint64_t step, uint64_t id, int k)
+{
+    const uint64_t ctr = (step << 34) | (id << 2) | (uint64_t)k;
+    uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)(z >> 40);
+}
+
+/* out[i] = draw k of particle id0 + i at step (for statistical checks). */
+void orc_rng24_fill(uint64_t seed, uint64_t step, uint64_t id0, int64_t n, int k, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_rng24(seed, step, id0 + (uint64_t)i, k);
+}
+
+/* The candidate threshold of the null-collision method: a particle is a candidate
+ * when its first draw r0 < round(P 2^24), P = 1 - exp(-nu' dt), nu' = n_g (sig_el +
+ * sig_exc) vmax the bounding total collision frequency. */
+uint32_t orc_mcc_threshold(double ng, double sig_el, double sig_exc, double vmax, double dt)
+{
+    const double nu_max = ng * (sig_el + sig_exc) * vmax;
+    const double P = 1.0 - exp(-nu_max * dt);
+    return (uint32_t)floor(P * 16777216.0 + 0.5);
+}
+
+/* One null-collision step of the electrons (3 velocity components, ids `id`) against
+ * a uniform neutral background of density ng with constant cross sections: elastic
+ * sig_el (isotropic, recoil loss 2 m/M per unit of 1 - cos chi) and excitation
+ * sig_exc above the threshold energy eps_exc (the electron loses eps_exc, then
+ * scatters isotropically).  For a candidate (draw 0 below the threshold) draw 1
+ * selects elastic if u1 < nu_el / nu', excitation if u1 < (nu_el + nu_exc) / nu',
+ * else a null collision; nu_j = ng sig_j |v|.  Draws 2 and 3 give the scattering
+ * angles: cos chi = 1 - 2 u2, phi = 2 pi u3; the new direction is
+ * vhat cos chi + sin chi (e1 cos phi + e2 sin phi) with (e1, e2) the orthonormal
+ * basis perpendicular to vhat of Duff et al. (2017).  counts: elastic, excitation,
+ * candidates whose frequency exceeded nu'. */
+void orc_mcc(int64_t np, double *v, const uint32_t *id, uint64_t step, uint64_t seed,
+             double ng, double sig_el, double sig_exc, double eps_exc, double mass_ratio,
+             double vmax, double m, double dt, int64_t *counts)
+{
+    const uint32_t thr = orc_mcc_threshold(ng, sig_el, sig_exc, vmax, dt);
+    const double nu_max = ng * (sig_el + sig_exc) * vmax;
+    const double inv24 = 1.0 / 16777216.0;
+    for (int64_t p = 0; p < np; ++p) {
+        if (orc_rng24(seed, step, id[p], 0) >= thr) continue;
+        double *vp = v + 3 * p;
+        const double v2 = vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2];
+        const double speed = sqrt(v2);
+        const double energy = 0.5 * m * v2;
+        const double nu_el = ng * sig_el * speed;
+        const double nu_exc = energy >= eps_exc ? ng * sig_exc * speed : 0.0;
+        if (nu_el + nu_exc > nu_max) counts[2] += 1;
+        const double u1 = ((double)orc_rng24(seed, step, id[p], 1) + 0.5) * inv24;
+        double snew;
+        if (u1 < nu_el / nu_max) {
+            const double u2 = ((double)orc_rng24(seed, step, id[p], 2) + 0.5) * inv24;
+            const double cchi = 1.0 - 2.0 * u2;
+            snew = speed * sqrt(1.0 - 2.0 * mass_ratio * (1.0 - cchi));
+            counts[0] += 1;
+        } else if (u1 < (nu_el + nu_exc) / nu_max) {
+            const double s2 = v2 - 2.0 * eps_exc / m;
+            snew = sqrt(s2 > 0.0 ? s2 : 0.0);
+            counts[1] += 1;
+        } else {
+            continue;  /* null collision */
+        }
+        const double u2 = ((double)orc_rng24(seed, step, id[p], 2) + 0.5) * inv24;
+        const double u3 = (double)orc_rng24(seed, step, id[p], 3) * inv24;
+        const double cchi = 1.0 - 2.0 * u2;
+        const double schi = sqrt(1.0 - cchi * cchi > 0.0 ? 1.0 - cchi * cchi : 0.0);
+        const double phi = 6.283185307179586476925 * u3;  /* 2 pi u3 */
+        double n[3] = {1.0, 0.0, 0.0};
+        if (speed > 0.0) {
+            n[0] = vp[0] / speed;
+            n[1] = vp[1] / speed;
+            n[2] = vp[2] / speed;
+        }
+        const double sgn = n[2] >= 0.0 ? 1.0 : -1.0;
+        const double a = -1.0 / (sgn + n[2]);
+        const double b = n[0] * n[1] * a;
+        const double e1[3] = {1.0 + sgn * n[0] * n[0] * a, sgn * b, -sgn * n[0]};
+        const double e2[3] = {b, sgn + n[1] * n[1] * a, -n[1]};
+        const double cp = cos(phi), sp = sin(phi);
+        for (int k = 0; k < 3; ++k)
+            vp[k] = snew * (n[k] * cchi + schi * (e1[k] * cp + e2[k] * sp));
+    }
+}
