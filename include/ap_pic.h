@@ -147,6 +147,9 @@ typedef struct {
     int cg_iters;           /* iterations of the last field solve                 */
     double cg_relres;       /* its final relative residual                        */
     int error_flags;        /* latched device error bits (AP_PIC_EFLAG_*)         */
+    int64_t mcc_counts[3];  /* collisions of the last collision pass: elastic,
+                               excitation, and candidates whose frequency exceeded
+                               the null-collision bound (0 without collisions)      */
 } ap_pic_diag;
 
 enum {
@@ -288,6 +291,36 @@ ap_pic_status ap_pic_get_timing(ap_pic *h, double *ms, int64_t *count);
 
 /* Kernels this library has launched in the process so far (all handles). */
 int64_t ap_pic_kernel_launches(void);
+
+/* ---- null-collision Monte Carlo (G_collision, Sec. 2.2) --------------------------------
+ * Electrons against a uniform neutral background of density `density`, with
+ * constant cross sections: isotropic elastic scattering (energy loss
+ * 2 (m/M) (1 - cos chi) of E) and excitation above `eps_exc` (loses eps_exc, then
+ * scatters isotropically).  The null-collision method bounds the total frequency by
+ * nu' = density (sigma_el + sigma_exc) vmax: a fraction 1 - exp(-nu' dt) of the
+ * particles are candidates each step, and a candidate of speed v takes process j
+ * with probability density sigma_j v / nu' (else a null collision); candidates
+ * faster than vmax are counted in ap_pic_diag.mcc_counts[2].  Random draws come from
+ * a counter-based generator keyed by (seed, step, particle id, draw): the output
+ * function of SplitMix64 on seed + (counter + 1) 0x9E3779B97F4A7C15, counter =
+ * step 2^34 + id 4 + draw, top 24 bits; particle ids are the load order and follow
+ * the sort.  FP32 cell + offset form, nv = 3, Boris pusher. */
+typedef struct {
+    double density;     /* neutral density n_g (>= 0)                                */
+    double sigma_el;    /* elastic cross section (>= 0)                              */
+    double sigma_exc;   /* excitation cross section above eps_exc (>= 0)             */
+    double eps_exc;     /* excitation threshold energy (>= 0)                        */
+    double mass_ratio;  /* m / M of electron and neutral, in [0, 0.25]               */
+    double vmax;        /* speed bound of the null-collision frequency (> 0)         */
+    uint64_t seed;      /* generator key                                             */
+} ap_pic_mcc;
+
+/* Enables (c non-NULL) or disables collisions; before ap_pic_load (the ids are
+ * allocated at load).  ap_pic_step then runs one collision pass after each
+ * particle pass, drawing with the step number being completed (1 for the first). */
+ap_pic_status ap_pic_set_collisions(ap_pic *h, const ap_pic_mcc *c);
+/* One collision pass now, drawing with step number (steps taken + 1). */
+ap_pic_status ap_pic_collide(ap_pic *h);
 
 /* ---- batch: many independent instances advanced together ----------------------------
  * The serving form of the same cycle: `count` periodic instances of uneven grid

@@ -455,10 +455,11 @@ uint32_t orc_mcc_threshold(double ng, double sig_el, double sig_exc, double vmax
  * a uniform neutral background of density ng with constant cross sections: elastic
  * sig_el (isotropic, recoil loss 2 m/M per unit of 1 - cos chi) and excitation
  * sig_exc above the threshold energy eps_exc (the electron loses eps_exc, then
- * scatters isotropically).  For a candidate (draw 0 below the threshold) draw 1
- * selects elastic if u1 < nu_el / nu', excitation if u1 < (nu_el + nu_exc) / nu',
- * else a null collision; nu_j = ng sig_j |v|.  Draws 2 and 3 give the scattering
- * angles: cos chi = 1 - 2 u2, phi = 2 pi u3; the new direction is
+ * scatters isotropically).  For a candidate (draw 0 below the threshold) draw 1,
+ * u1 = r1 / 2^24, selects elastic if u1 < nu_el / nu', excitation if
+ * u1 < (nu_el + nu_exc) / nu', else a null collision; nu_j = ng sig_j |v|.  Draws 2
+ * and 3 give the scattering angles: cos chi = 1 - 2 u2 with u2 = (r2 + 1/2) / 2^24,
+ * phi = 2 pi u3 with u3 = r3 / 2^24; the new direction is
  * vhat cos chi + sin chi (e1 cos phi + e2 sin phi) with (e1, e2) the orthonormal
  * basis perpendicular to vhat of Duff et al. (2017).  counts: elastic, excitation,
  * candidates whose frequency exceeded nu'. */
@@ -478,7 +479,7 @@ void orc_mcc(int64_t np, double *v, const uint32_t *id, uint64_t step, uint64_t 
         const double nu_el = ng * sig_el * speed;
         const double nu_exc = energy >= eps_exc ? ng * sig_exc * speed : 0.0;
         if (nu_el + nu_exc > nu_max) counts[2] += 1;
-        const double u1 = ((double)orc_rng24(seed, step, id[p], 1) + 0.5) * inv24;
+        const double u1 = (double)orc_rng24(seed, step, id[p], 1) * inv24;
         double snew;
         if (u1 < nu_el / nu_max) {
             const double u2 = ((double)orc_rng24(seed, step, id[p], 2) + 0.5) * inv24;

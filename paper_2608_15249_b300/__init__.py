@@ -45,7 +45,7 @@ EXPORTS = [
     "ap_pic_get_phi", "ap_pic_get_rho_fx", "ap_pic_get_particles", "ap_pic_get_velocities_f64",
     "ap_pic_get_perm", "ap_pic_get_diag", "ap_pic_set_timing", "ap_pic_get_timing",
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
-    "ap_pic_sort_perm_noalloc",
+    "ap_pic_sort_perm_noalloc", "ap_pic_set_collisions", "ap_pic_collide",
     "ap_pic_batch_default_tuning", "ap_pic_batch_create", "ap_pic_batch_destroy",
     "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_push_deposit", "ap_pic_batch_sort",
     "ap_pic_batch_solve_field", "ap_pic_batch_set_tuning",
@@ -85,11 +85,19 @@ class ap_pic_diag(ctypes.Structure):
         ("total_charge", ctypes.c_double), ("kinetic", ctypes.c_double),
         ("field_energy", ctypes.c_double), ("momentum", ctypes.c_double * 3),
         ("cg_iters", ctypes.c_int), ("cg_relres", ctypes.c_double), ("error_flags", ctypes.c_int),
+        ("mcc_counts", ctypes.c_int64 * 3),
     ]
 
     def as_dict(self):
-        return {k: (list(getattr(self, k)) if k == "momentum" else getattr(self, k))
+        return {k: (list(getattr(self, k)) if k in ("momentum", "mcc_counts") else getattr(self, k))
                 for k, _ in self._fields_}
+
+
+class ap_pic_mcc(ctypes.Structure):
+    _fields_ = [("density", ctypes.c_double), ("sigma_el", ctypes.c_double),
+                ("sigma_exc", ctypes.c_double), ("eps_exc", ctypes.c_double),
+                ("mass_ratio", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
 
 
 class ap_pic_batch_tuning(ctypes.Structure):
@@ -136,6 +144,8 @@ def _declare(L):
     L.ap_pic_get_particles.argtypes = [P, P, P, P, P]
     L.ap_pic_get_diag.argtypes = [P, ctypes.POINTER(ap_pic_diag)]
     L.ap_pic_set_timing.argtypes = [P, I]
+    L.ap_pic_set_collisions.argtypes = [P, ctypes.POINTER(ap_pic_mcc)]
+    L.ap_pic_collide.argtypes = [P]
     L.ap_pic_get_timing.argtypes = [P, P, P]
     L.ap_pic_kernel_launches.argtypes = []
     L.ap_pic_kernel_launches.restype = I64
@@ -332,6 +342,20 @@ class Pic:
 
     def solve_field(self):
         self._check(self._lib.ap_pic_solve_field(self.h))
+
+    def set_collisions(self, density=None, sigma_el=0.0, sigma_exc=0.0, eps_exc=0.0,
+                       mass_ratio=0.0, vmax=1.0, seed=0):
+        """Null-collision Monte Carlo (before load); density=None disables it."""
+        if density is None:
+            self._check(self._lib.ap_pic_set_collisions(self.h, None))
+            return self
+        c = ap_pic_mcc(float(density), float(sigma_el), float(sigma_exc), float(eps_exc),
+                       float(mass_ratio), float(vmax), int(seed))
+        self._check(self._lib.ap_pic_set_collisions(self.h, ctypes.byref(c)))
+        return self
+
+    def collide(self):
+        self._check(self._lib.ap_pic_collide(self.h))
 
     def sort(self):
         self._check(self._lib.ap_pic_sort(self.h))

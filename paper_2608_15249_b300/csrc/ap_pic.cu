@@ -87,6 +87,11 @@ struct ap_pic {
     int *h_err = nullptr;
     int *h_iters = nullptr;
 
+    // null-collision Monte Carlo (ap_pic_set_collisions)
+    bool mcc_on = false;
+    MccParams mccp{};
+    unsigned long long *d_mcc = nullptr;  // [3] counts of the last collision pass
+
     // spectral field solve (AP_PIC_SOLVER_FFT)
     bool use_fft = false;
     FftPlan fft{};
@@ -519,6 +524,8 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
     CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
     CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+    TRY(alloc_n(h, &h->d_mcc, 3));
+    CU(h, cudaMemsetAsync(h->d_mcc, 0, 24, h->stream));
     if (h->cfg.solver == AP_PIC_SOLVER_FFT) TRY(create_fft(h));
     return create_pinned(h);
 }
@@ -646,6 +653,8 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
         q->np = np;
         q->stride = (int64_t)st;
         q->nv = h->nv;
+        q->id = nullptr;
+        if (h->mcc_on) TRY(alloc_n(h, &q->id, st));
     }
     for (int k = 0; k < 2; ++k) {
         TRY(alloc_n(h, &h->sort.keys[k], n));
@@ -907,6 +916,7 @@ extern "C" ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, con
             CU(h, launch_load_convert(g, h->cfg.dx, dx_buf, dv_buf, h->p, first, cnt, h->d_err,
                                       h->stream));
     }
+    if (h->mcc_on) CU(h, launch_iota(h->p.id, np, h->stream));  // ids: the load order
     CU(h, cudaStreamSynchronize(h->stream));
     dev_free(h, dx_buf);
     dev_free(h, dv_buf);
@@ -935,6 +945,7 @@ extern "C" ap_pic_status ap_pic_load_state(ap_pic *h, int64_t np, const int32_t 
         const GridParams g = grid_params(h, h->cfg.dt);
         CU(h, launch_load_state(g, h->p_alt.cell, h->p_alt.off, h->p_alt.v, h->p, h->d_err,
                                 h->stream));
+        if (h->mcc_on) CU(h, launch_iota(h->p.id, np, h->stream));
     }
     CU(h, cudaMemsetAsync(h->f.phi, 0, (size_t)h->cells * 4, h->stream));
     return after_load(h, flags);
@@ -1006,6 +1017,39 @@ extern "C" ap_pic_status ap_pic_sort(ap_pic *h)
     return sort_particles(h);
 }
 
+extern "C" ap_pic_status ap_pic_set_collisions(ap_pic *h, const ap_pic_mcc *c)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    if (h->loaded || h->np > 0)
+        return fail(h, AP_PIC_ERR_STATE, "set collisions before loading particles");
+    if (!c) {
+        h->mcc_on = false;
+        return AP_PIC_OK;
+    }
+    if (h->plain) return fail(h, AP_PIC_ERR_UNSUPPORTED, "collisions need the FP32 form");
+    if (h->nv != 3) return fail(h, AP_PIC_ERR_ARG, "collisions need nv = 3");
+    if (h->cfg.pusher != AP_PIC_PUSHER_BORIS)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "collisions need the Boris pusher");
+    const double vals[5] = {c->density, c->sigma_el, c->sigma_exc, c->eps_exc, c->mass_ratio};
+    for (double x : vals)
+        if (!(x >= 0.0) || !isfinite(x))
+            return fail(h, AP_PIC_ERR_ARG, "collision parameters must be >= 0 and finite");
+    if (c->mass_ratio > 0.25) return fail(h, AP_PIC_ERR_ARG, "mass_ratio must be <= 0.25");
+    if (!(c->vmax > 0.0) || !isfinite(c->vmax)) return fail(h, AP_PIC_ERR_ARG, "vmax must be > 0");
+    h->mccp = make_mcc_params(c->density, c->sigma_el, c->sigma_exc, c->eps_exc, c->mass_ratio,
+                              c->vmax, h->cfg.m, h->cfg.dt, c->seed);
+    h->mcc_on = true;
+    return AP_PIC_OK;
+}
+
+extern "C" ap_pic_status ap_pic_collide(ap_pic *h)
+{
+    TRY(need_loaded(h));
+    if (!h->mcc_on) return fail(h, AP_PIC_ERR_STATE, "collisions are not enabled");
+    CU(h, launch_mcc(h->p, h->mccp, (uint64_t)(h->step + 1), h->d_mcc, h->stream));
+    return AP_PIC_OK;
+}
+
 extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
 {
     TRY(need_loaded(h));
@@ -1014,6 +1058,7 @@ extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
         const int64_t k = h->step + 1;
         const bool diag = (k % h->cfg.diag_every) == 0;
         TRY(push_deposit(h, diag));
+        if (h->mcc_on) CU(h, launch_mcc(h->p, h->mccp, (uint64_t)k, h->d_mcc, h->stream));
         if (h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0) TRY(sort_particles(h));
         TRY(solve_field(h));
         if (diag) TRY(finalize_diag(h, true));
@@ -1197,6 +1242,9 @@ extern "C" ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out)
     CU(h, cudaMemcpyAsync(h->h_accsum, h->d_accsum, sizeof(long long), cudaMemcpyDeviceToHost,
                           h->stream));
     CU(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->d_mcc)
+        CU(h, cudaMemcpyAsync(h->h_accsum + 1, h->d_mcc, 3 * sizeof(long long),
+                              cudaMemcpyDeviceToHost, h->stream));
     if (h->relres_on_device)
         CU(h, cudaMemcpyAsync(h->h_diag + 7, h->f.scal + SCAL_TRUE_REL, sizeof(double),
                               cudaMemcpyDeviceToHost, h->stream));
@@ -1215,6 +1263,7 @@ extern "C" ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out)
     out->cg_iters = h->last_cg_iters;
     out->cg_relres = h->last_cg_relres;
     out->error_flags = *h->h_err;
+    for (int k = 0; k < 3; ++k) out->mcc_counts[k] = h->d_mcc ? h->h_accsum[1 + k] : 0;
     return AP_PIC_OK;
 }
 

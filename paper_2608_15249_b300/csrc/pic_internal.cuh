@@ -74,6 +74,7 @@ struct ParticlesF32 {
     int64_t stride;    // np rounded up to a multiple of 64: every component array starts
                        // 256-byte aligned and may be read (TMA) up to a multiple of 16 bytes
     int nv;
+    uint32_t *id;      // [stride] particle ids (load order), only with collisions; else null
 };
 
 // Component stride for np particles.
@@ -227,6 +228,25 @@ cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st);
 cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
 enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5 };
 cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
+
+// ---- null-collision Monte Carlo (pic_mcc.cu) ---------------------------------------------------
+struct MccParams {
+    uint64_t seed;
+    uint32_t thr;          // candidate iff draw 0 < thr = round((1 - exp(-nu' dt)) 2^24)
+    float ng_sig_el, ng_sig_exc;  // n_g sigma_j: nu_j = n_g sigma_j |v|
+    float nu_max;          // nu' = n_g (sigma_el + sigma_exc) vmax
+    float eps_exc;         // excitation threshold energy
+    float two_eps_over_m;  // 2 eps_exc / m
+    float two_mass_ratio;  // 2 m / M
+    float half_m;          // m / 2
+};
+MccParams make_mcc_params(double density, double sigma_el, double sigma_exc, double eps_exc,
+                          double mass_ratio, double vmax, double m, double dt, uint64_t seed);
+// One null-collision pass over the particles (nv = 3, ids set) for time step `step`;
+// counts[0..2] = elastic, excitation, candidates above the bound (zeroed first).
+cudaError_t launch_mcc(ParticlesF32 p, const MccParams &c, uint64_t step,
+                       unsigned long long *counts, cudaStream_t st);
+cudaError_t launch_iota(uint32_t *id, int64_t np, cudaStream_t st);
 
 // ---- spectral Poisson solve (pic_fft.cu) ------------------------------------------------------
 constexpr int FFT_MAX_N = 4096;  // longest axis (power-of-two or Bluestein length <= 8192)

@@ -1,0 +1,163 @@
+// pic_mcc.cu -- null-collision Monte Carlo of the electrons against a uniform
+// neutral background (the G_collision module of Sec. 2.2, which implements the
+// null-collision method), with constant cross sections: isotropic elastic
+// scattering with the recoil loss 2 m/M (1 - cos chi), and excitation above a
+// threshold energy (the electron loses the threshold, then scatters isotropically).
+//
+// The method bounds the total collision frequency by nu' = n_g (sig_el + sig_exc)
+// vmax, makes a fraction P = 1 - exp(-nu' dt) of the particles candidates, and lets a
+// candidate of speed v undergo process j with probability nu_j(v) / nu', the rest
+// being null collisions.  Random numbers come from a counter-based generator keyed
+// by (seed, step, particle id, draw), so a particle's draws do not depend on where
+// the sort has put it: the output function of SplitMix64 (Steele, Lea and Flood,
+// 2014) applied to seed + (counter + 1) * 0x9E3779B97F4A7C15 with counter =
+// step * 2^34 + id * 4 + draw; a draw is the top 24 bits.  The candidate test is an
+// integer compare against round(P 2^24).
+//
+// One streaming pass: each thread reads a particle's id, draws once and, for the
+// few candidates, reads and rewrites its velocity; collision counts are summed per
+// warp and added to three device counters.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pic_internal.cuh"
+
+namespace apk {
+
+namespace {
+
+constexpr int MCC_THREADS = 256;
+
+__device__ __forceinline__ uint32_t draw24(uint64_t seed, uint64_t step, uint32_t id, int k)
+{
+    const uint64_t ctr = (step << 34) | ((uint64_t)id << 2) | (uint64_t)k;
+    uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)(z >> 40);
+}
+
+__global__ void __launch_bounds__(MCC_THREADS)
+    k_mcc(ParticlesF32 p, MccParams c, uint64_t step, unsigned long long *__restrict__ counts)
+{
+    int n_el = 0, n_exc = 0, n_over = 0;
+    const float inv24 = 1.0f / 16777216.0f;
+    for (int64_t i = (int64_t)blockIdx.x * MCC_THREADS + threadIdx.x; i < p.np;
+         i += (int64_t)gridDim.x * MCC_THREADS) {
+        const uint32_t id = p.id[i];
+        if (draw24(c.seed, step, id, 0) >= c.thr) continue;
+        float *vp[3] = {p.v + i, p.v + p.stride + i, p.v + 2 * p.stride + i};
+        const float v[3] = {*vp[0], *vp[1], *vp[2]};
+        const float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const float speed = sqrtf(v2);
+        const float energy = c.half_m * v2;
+        const float nu_el = c.ng_sig_el * speed;
+        const float nu_exc = energy >= c.eps_exc ? c.ng_sig_exc * speed : 0.0f;
+        if (nu_el + nu_exc > c.nu_max) ++n_over;
+        const float u1 = (float)draw24(c.seed, step, id, 1) * inv24;
+        const float u2 = ((float)draw24(c.seed, step, id, 2) + 0.5f) * inv24;
+        const float cchi = 1.0f - 2.0f * u2;
+        float snew;
+        if (u1 < nu_el / c.nu_max) {
+            snew = speed * sqrtf(1.0f - c.two_mass_ratio * (1.0f - cchi));
+            ++n_el;
+        } else if (u1 < (nu_el + nu_exc) / c.nu_max) {
+            snew = sqrtf(fmaxf(v2 - c.two_eps_over_m, 0.0f));
+            ++n_exc;
+        } else {
+            continue;  // null collision
+        }
+        // new direction: vhat cos chi + sin chi (e1 cos phi + e2 sin phi), with the
+        // orthonormal basis (e1, e2) perpendicular to vhat of Duff et al. (2017)
+        const float u3 = (float)draw24(c.seed, step, id, 3) * inv24;
+        float sp, cp;
+        sincospif(2.0f * u3, &sp, &cp);
+        const float schi = sqrtf(fmaxf(1.0f - cchi * cchi, 0.0f));
+        float n[3] = {1.0f, 0.0f, 0.0f};
+        if (speed > 0.0f) {
+            const float is = 1.0f / speed;
+            n[0] = v[0] * is;
+            n[1] = v[1] * is;
+            n[2] = v[2] * is;
+        }
+        const float sgn = n[2] >= 0.0f ? 1.0f : -1.0f;
+        const float a = -1.0f / (sgn + n[2]);
+        const float b = n[0] * n[1] * a;
+        const float e1[3] = {1.0f + sgn * n[0] * n[0] * a, sgn * b, -sgn * n[0]};
+        const float e2[3] = {b, sgn + n[1] * n[1] * a, -n[1]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) *vp[k] = snew * (n[k] * cchi + schi * (e1[k] * cp + e2[k] * sp));
+    }
+    n_el = __reduce_add_sync(0xffffffffu, n_el);
+    n_exc = __reduce_add_sync(0xffffffffu, n_exc);
+    n_over = __reduce_add_sync(0xffffffffu, n_over);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_el) atomicAdd(counts + 0, (unsigned long long)n_el);
+        if (n_exc) atomicAdd(counts + 1, (unsigned long long)n_exc);
+        if (n_over) atomicAdd(counts + 2, (unsigned long long)n_over);
+    }
+}
+
+__global__ void __launch_bounds__(MCC_THREADS) k_iota(uint32_t *__restrict__ id, int64_t np)
+{
+    for (int64_t i = (int64_t)blockIdx.x * MCC_THREADS + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * MCC_THREADS)
+        id[i] = (uint32_t)i;
+}
+
+int mcc_blocks(int64_t np)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const int64_t need = (np + MCC_THREADS - 1) / MCC_THREADS;
+    const int64_t cap = (int64_t)sms * 8;
+    const int64_t b = need < cap ? need : cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+MccParams make_mcc_params(double density, double sigma_el, double sigma_exc, double eps_exc,
+                          double mass_ratio, double vmax, double m, double dt, uint64_t seed)
+{
+    MccParams c{};
+    const double nu_max = density * (sigma_el + sigma_exc) * vmax;
+    const double P = 1.0 - exp(-nu_max * dt);
+    c.seed = seed;
+    c.thr = (uint32_t)floor(P * 16777216.0 + 0.5);
+    c.ng_sig_el = (float)(density * sigma_el);
+    c.ng_sig_exc = (float)(density * sigma_exc);
+    c.nu_max = (float)nu_max;
+    c.eps_exc = (float)eps_exc;
+    c.two_eps_over_m = (float)(2.0 * eps_exc / m);
+    c.two_mass_ratio = (float)(2.0 * mass_ratio);
+    c.half_m = (float)(0.5 * m);
+    return c;
+}
+
+cudaError_t launch_mcc(ParticlesF32 p, const MccParams &c, uint64_t step,
+                       unsigned long long *counts, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess || p.np == 0 || c.thr == 0) return e;
+    k_mcc<<<mcc_blocks(p.np), MCC_THREADS, 0, st>>>(p, c, step, counts);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t *id, int64_t np, cudaStream_t st)
+{
+    if (np == 0) return cudaSuccess;
+    k_iota<<<mcc_blocks(np), MCC_THREADS, 0, st>>>(id, np);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace apk

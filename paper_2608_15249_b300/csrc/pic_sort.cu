@@ -346,10 +346,12 @@ __global__ void __launch_bounds__(256) k_apply_perm(const uint32_t *__restrict__
             j[k] = ok[k] ? __ldg(perm + r) : 0u;
         }
         int32_t c[K];
+        uint32_t id[K];
         float o[K][D], v[K][NV];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             c[k] = __ldg(src.cell + j[k]);
+            id[k] = src.id ? __ldg(src.id + j[k]) : 0u;
 #pragma unroll
             for (int a = 0; a < D; ++a) o[k][a] = __ldg(src.off + a * src.stride + j[k]);
 #pragma unroll
@@ -360,6 +362,7 @@ __global__ void __launch_bounds__(256) k_apply_perm(const uint32_t *__restrict__
             if (!ok[k]) continue;
             const int64_t r = base + (int64_t)k * blockDim.x;
             dst.cell[r] = c[k];
+            if (src.id) dst.id[r] = id[k];
 #pragma unroll
             for (int a = 0; a < D; ++a) dst.off[a * dst.stride + r] = o[k][a];
 #pragma unroll

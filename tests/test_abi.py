@@ -90,7 +90,7 @@ def test_binding_structs_match_the_header(tmp_path):
     """Every struct the binding mirrors has the C compiler's size and field offsets."""
     import paper_2608_15249_b300 as pk
     structs = {"ap_pic_config": pk.ap_pic_config, "ap_pic_diag": pk.ap_pic_diag,
-               "ap_pic_batch_tuning": pk.ap_pic_batch_tuning,
+               "ap_pic_batch_tuning": pk.ap_pic_batch_tuning, "ap_pic_mcc": pk.ap_pic_mcc,
                "ap_pic_allocator": pk.ap_pic_allocator}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ap_pic.h"', "int main(void){"]
     for name, cls in structs.items():
