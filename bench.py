@@ -283,6 +283,7 @@ def bench_ours(args):
         gf.set_timing(False)
         gf.close()
         field_ms["fft"] = ff[0] / max(ff[1], 1)
+    collisions = None if (f64 or args.no_collisions) else bench_collisions(args, pk, torch, stream)
     e2e = None
     if not args.no_e2e:
         solver = "cg" if f64 else args.e2e_solver
@@ -318,6 +319,7 @@ def bench_ours(args):
                          "peak_kind": peak_kind},
             "stage_ms_per_call": breakdown,
             "field_solve_ms": field_ms,
+            "collisions": collisions,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -329,6 +331,37 @@ def bench_ours(args):
 
 
 _SOLVERS = {"cg": 0, "fft": 1}
+
+# Null-collision Monte Carlo of the benchmark's size: a 2D3V Maxwellian (collisions
+# need three velocity components) on the same grid and particle count, constant
+# cross sections giving a candidate fraction of about 4 % per step.
+MCC_BENCH = dict(density=1.0, sigma_el=0.05, sigma_exc=0.02, eps_exc=1.5, mass_ratio=1e-4,
+                 vmax=6.0, seed=99)
+
+
+def bench_collisions(args, pk, torch, stream):
+    """CUDA-event time of the collision pass alone (ap_pic_collide) on 2D3V electrons."""
+    w = workloads.maxwellian_box(2, (args.n, args.n), ppc=args.ppc, nv=3, dt=0.1, seed=6)
+    g = pk.from_workload(w, stream=stream.cuda_stream).set_collisions(**MCC_BENCH)
+    g.load(w.x, w.v)
+    for _ in range(3):
+        g.collide()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        g.collide()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    counts = g.get_diag()["mcc_counts"]
+    g.close()
+    return {"ms_per_pass": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
+            "collisions_per_pass": {"elastic": counts[0], "excitation": counts[1],
+                                    "above_bound": counts[2]},
+            "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, "
+                        + ", ".join(f"{k}={v}" for k, v in MCC_BENCH.items())}
 
 
 def run_e2e(args, w, pk, torch, stream, extra, steps):
@@ -522,6 +555,7 @@ def main():
     ap.add_argument("--c-light", type=float, default=0.0, help="with --pusher hc; 0: infinite")
     ap.add_argument("--e2e-steps-cg", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-collisions", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)
     ap.add_argument("--cpu-steps", type=int, default=4)
