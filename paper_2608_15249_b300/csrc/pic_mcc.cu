@@ -14,9 +14,9 @@
 // step * 2^34 + id * 4 + draw; a draw is the top 24 bits.  The candidate test is an
 // integer compare against round(P 2^24).
 //
-// One streaming pass: each thread reads a particle's id, draws once and, for the
-// few candidates, reads and rewrites its velocity; collision counts are summed per
-// warp and added to three device counters.
+// One streaming pass: each particle's id is read and drawn once; the few candidates
+// are compacted per warp before their velocities are read and rewritten; collision
+// counts are summed per warp and added to three device counters.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -39,61 +39,101 @@ __device__ __forceinline__ uint32_t draw24(uint64_t seed, uint64_t step, uint32_
     return (uint32_t)(z >> 40);
 }
 
+// The collision of one candidate (draws 1..3), in place; returns the process
+// (0 elastic, 1 excitation, -1 null) and flags a candidate above the bound.
+__device__ __forceinline__ int collide_one(ParticlesF32 p, int64_t i, uint32_t id,
+                                           const MccParams &c, uint64_t step, bool *over)
+{
+    const float inv24 = 1.0f / 16777216.0f;
+    float *vp[3] = {p.v + i, p.v + p.stride + i, p.v + 2 * p.stride + i};
+    const float v[3] = {*vp[0], *vp[1], *vp[2]};
+    const float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const float speed = sqrtf(v2);
+    const float energy = c.half_m * v2;
+    const float nu_el = c.ng_sig_el * speed;
+    const float nu_exc = energy >= c.eps_exc ? c.ng_sig_exc * speed : 0.0f;
+    *over = nu_el + nu_exc > c.nu_max;
+    const float u1 = (float)draw24(c.seed, step, id, 1) * inv24;
+    const float u2 = ((float)draw24(c.seed, step, id, 2) + 0.5f) * inv24;
+    const float cchi = 1.0f - 2.0f * u2;
+    float snew;
+    int kind;
+    if (u1 < nu_el / c.nu_max) {
+        snew = speed * sqrtf(1.0f - c.two_mass_ratio * (1.0f - cchi));
+        kind = 0;
+    } else if (u1 < (nu_el + nu_exc) / c.nu_max) {
+        snew = sqrtf(fmaxf(v2 - c.two_eps_over_m, 0.0f));
+        kind = 1;
+    } else {
+        return -1;  // null collision
+    }
+    // new direction: vhat cos chi + sin chi (e1 cos phi + e2 sin phi), with the
+    // orthonormal basis (e1, e2) perpendicular to vhat of Duff et al. (2017)
+    const float u3 = (float)draw24(c.seed, step, id, 3) * inv24;
+    float sp, cp;
+    sincospif(2.0f * u3, &sp, &cp);
+    const float schi = sqrtf(fmaxf(1.0f - cchi * cchi, 0.0f));
+    float n[3] = {1.0f, 0.0f, 0.0f};
+    if (speed > 0.0f) {
+        const float is = 1.0f / speed;
+        n[0] = v[0] * is;
+        n[1] = v[1] * is;
+        n[2] = v[2] * is;
+    }
+    const float sgn = n[2] >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sgn + n[2]);
+    const float b = n[0] * n[1] * a;
+    const float e1[3] = {1.0f + sgn * n[0] * n[0] * a, sgn * b, -sgn * n[0]};
+    const float e2[3] = {b, sgn + n[1] * n[1] * a, -n[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *vp[k] = snew * (n[k] * cchi + schi * (e1[k] * cp + e2[k] * sp));
+    return kind;
+}
+
+// Each warp takes chunks of MCC_CHUNK particles: every lane draws for its share
+// (coalesced id reads), the candidates are packed into a per-warp list with a
+// ballot and a population count, and the list is then processed 32 at a time, so
+// the long collision path runs with full lanes instead of once per warp that
+// happens to hold a candidate.
+constexpr int MCC_CHUNK = 512;
+
 __global__ void __launch_bounds__(MCC_THREADS)
     k_mcc(ParticlesF32 p, MccParams c, uint64_t step, unsigned long long *__restrict__ counts)
 {
+    __shared__ uint32_t s_list[MCC_THREADS / 32][MCC_CHUNK];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *list = s_list[wib];
     int n_el = 0, n_exc = 0, n_over = 0;
-    const float inv24 = 1.0f / 16777216.0f;
-    for (int64_t i = (int64_t)blockIdx.x * MCC_THREADS + threadIdx.x; i < p.np;
-         i += (int64_t)gridDim.x * MCC_THREADS) {
-        const uint32_t id = p.id[i];
-        if (draw24(c.seed, step, id, 0) >= c.thr) continue;
-        float *vp[3] = {p.v + i, p.v + p.stride + i, p.v + 2 * p.stride + i};
-        const float v[3] = {*vp[0], *vp[1], *vp[2]};
-        const float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        const float speed = sqrtf(v2);
-        const float energy = c.half_m * v2;
-        const float nu_el = c.ng_sig_el * speed;
-        const float nu_exc = energy >= c.eps_exc ? c.ng_sig_exc * speed : 0.0f;
-        if (nu_el + nu_exc > c.nu_max) ++n_over;
-        const float u1 = (float)draw24(c.seed, step, id, 1) * inv24;
-        const float u2 = ((float)draw24(c.seed, step, id, 2) + 0.5f) * inv24;
-        const float cchi = 1.0f - 2.0f * u2;
-        float snew;
-        if (u1 < nu_el / c.nu_max) {
-            snew = speed * sqrtf(1.0f - c.two_mass_ratio * (1.0f - cchi));
-            ++n_el;
-        } else if (u1 < (nu_el + nu_exc) / c.nu_max) {
-            snew = sqrtf(fmaxf(v2 - c.two_eps_over_m, 0.0f));
-            ++n_exc;
-        } else {
-            continue;  // null collision
+    const int64_t nchunks = (p.np + MCC_CHUNK - 1) / MCC_CHUNK;
+    const int64_t gwarp = ((int64_t)blockIdx.x * MCC_THREADS + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * MCC_THREADS) >> 5;
+    for (int64_t ch = gwarp; ch < nchunks; ch += nwarps) {
+        const int64_t base = ch * MCC_CHUNK;
+        int m = 0;  // candidates listed so far (warp-uniform)
+#pragma unroll 4
+        for (int j = lane; j < MCC_CHUNK; j += 32) {
+            const int64_t i = base + j;
+            bool cand = false;
+            if (i < p.np) cand = draw24(c.seed, step, p.id[i], 0) < c.thr;
+            const unsigned ball = __ballot_sync(0xffffffffu, cand);
+            if (cand) list[m + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)j;
+            m += __popc(ball);
         }
-        // new direction: vhat cos chi + sin chi (e1 cos phi + e2 sin phi), with the
-        // orthonormal basis (e1, e2) perpendicular to vhat of Duff et al. (2017)
-        const float u3 = (float)draw24(c.seed, step, id, 3) * inv24;
-        float sp, cp;
-        sincospif(2.0f * u3, &sp, &cp);
-        const float schi = sqrtf(fmaxf(1.0f - cchi * cchi, 0.0f));
-        float n[3] = {1.0f, 0.0f, 0.0f};
-        if (speed > 0.0f) {
-            const float is = 1.0f / speed;
-            n[0] = v[0] * is;
-            n[1] = v[1] * is;
-            n[2] = v[2] * is;
+        __syncwarp();
+        for (int q = lane; q < m; q += 32) {
+            const int64_t i = base + list[q];
+            bool over = false;
+            const int kind = collide_one(p, i, p.id[i], c, step, &over);
+            n_el += kind == 0;
+            n_exc += kind == 1;
+            n_over += over;
         }
-        const float sgn = n[2] >= 0.0f ? 1.0f : -1.0f;
-        const float a = -1.0f / (sgn + n[2]);
-        const float b = n[0] * n[1] * a;
-        const float e1[3] = {1.0f + sgn * n[0] * n[0] * a, sgn * b, -sgn * n[0]};
-        const float e2[3] = {b, sgn + n[1] * n[1] * a, -n[1]};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) *vp[k] = snew * (n[k] * cchi + schi * (e1[k] * cp + e2[k] * sp));
+        __syncwarp();  // the list is rewritten by the next chunk
     }
     n_el = __reduce_add_sync(0xffffffffu, n_el);
     n_exc = __reduce_add_sync(0xffffffffu, n_exc);
     n_over = __reduce_add_sync(0xffffffffu, n_over);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (n_el) atomicAdd(counts + 0, (unsigned long long)n_el);
         if (n_exc) atomicAdd(counts + 1, (unsigned long long)n_exc);
         if (n_over) atomicAdd(counts + 2, (unsigned long long)n_over);
@@ -116,7 +156,8 @@ int mcc_blocks(int64_t np)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    const int64_t need = (np + MCC_THREADS - 1) / MCC_THREADS;
+    const int64_t need = (np + (int64_t)MCC_CHUNK * (MCC_THREADS / 32) - 1) /
+                         ((int64_t)MCC_CHUNK * (MCC_THREADS / 32));
     const int64_t cap = (int64_t)sms * 8;
     const int64_t b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
