@@ -10,8 +10,8 @@ It shares no code with the CUDA path.
 Parity status per function (details in the repository's design notes):
   locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris,
   higuera_cary, move, sort_key, counting_sort, kinetic, kinetic_rel,
-  field_energy, momentum, rng24, mcc: pinned by the tests under
-  tests/test_oracle_*.py.
+  field_energy, momentum, rng24, mcc, yee_b, yee_e, em_gather, boris_eb,
+  esirkepov: pinned by the tests under tests/test_oracle_*.py.
 """
 
 from __future__ import annotations
@@ -69,6 +69,20 @@ def _declare(L):
     L.orc_mcc.argtypes = [i64, _D, ctypes.POINTER(ctypes.c_uint32), u64, u64, d, d, d, d, d, d,
                           d, d, _I64]
     L.orc_mcc.restype = None
+    L.orc_yee_b.argtypes = [_I32, _D, _D, _D, d]
+    L.orc_yee_b.restype = None
+    L.orc_yee_e.argtypes = [_I32, _D, _D, _D, d, d, _D]
+    L.orc_yee_e.restype = None
+    L.orc_yee_div_e.argtypes = [_I32, _D, _D, _D]
+    L.orc_yee_div_e.restype = None
+    L.orc_yee_div_b.argtypes = [_I32, _D, _D, _D]
+    L.orc_yee_div_b.restype = None
+    L.orc_em_gather.argtypes = [_I32, _D, i64, _D, _D, _D, _D]
+    L.orc_em_gather.restype = None
+    L.orc_boris_eb.argtypes = [i64, _D, _D, d, d]
+    L.orc_boris_eb.restype = None
+    L.orc_esirkepov.argtypes = [_I32, _D, i64, _D, _D, _D, d, d, _D]
+    L.orc_esirkepov.restype = None
     L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
     L.orc_hc.restype = None
     L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
@@ -403,3 +417,135 @@ class Simulation:
         self.v = np.ascontiguousarray(self.v[perm])
         self.ids = np.ascontiguousarray(self.ids[perm])
         return perm
+
+
+# ---- electromagnetic step (E_Maxwell, Sec. 2.2): periodic 2D3V Yee grid ----------------------
+
+def _n2(n):
+    return (ctypes.c_int * 2)(int(n[0]), int(n[1]))
+
+
+def _dx2(dx):
+    return (ctypes.c_double * 2)(float(dx[0]), float(dx[1]))
+
+
+def _f(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def yee_b(n, dx, E, B, h):
+    """In-place B -= h curl E on the Yee grid ([3][cells] arrays)."""
+    assert B.dtype == np.float64 and B.flags.c_contiguous
+    E = _f(E)
+    lib().orc_yee_b(_n2(n), _dx2(dx), _dp(E), _dp(B), float(h))
+    return B
+
+
+def yee_e(n, dx, B, J, c, dt, E):
+    """In-place E += dt (c^2 curl B - J)."""
+    assert E.dtype == np.float64 and E.flags.c_contiguous
+    B, J = _f(B), _f(J)
+    lib().orc_yee_e(_n2(n), _dx2(dx), _dp(B), _dp(J), float(c) ** 2, float(dt), _dp(E))
+    return E
+
+
+def yee_div_e(n, dx, E):
+    out = np.empty(int(n[0]) * int(n[1]))
+    E = _f(E)
+    lib().orc_yee_div_e(_n2(n), _dx2(dx), _dp(E), _dp(out))
+    return out
+
+
+def yee_div_b(n, dx, B):
+    out = np.empty(int(n[0]) * int(n[1]))
+    B = _f(B)
+    lib().orc_yee_div_b(_n2(n), _dx2(dx), _dp(B), _dp(out))
+    return out
+
+
+def em_gather(n, dx, x, E, B):
+    """E and B at the particles (np x 6), CIC on each component's staggered lattice."""
+    x, E, B = _f(x), _f(E), _f(B)
+    out = np.empty((x.shape[0], 6))
+    lib().orc_em_gather(_n2(n), _dx2(dx), x.shape[0], _dp(x), _dp(E), _dp(B), _dp(out))
+    return out
+
+
+def boris_eb(v, EB, qm, h):
+    assert v.dtype == np.float64 and v.flags.c_contiguous and v.shape[1] == 3
+    EB = _f(EB)
+    lib().orc_boris_eb(v.shape[0], _dp(v), _dp(EB), float(qm), float(h))
+    return v
+
+
+def esirkepov(n, dx, x0, x1, vz, qw, dt, J):
+    """Add the charge-conserving current of the moves x0 -> x1 into J ([3][cells])."""
+    assert J.dtype == np.float64 and J.flags.c_contiguous
+    x0, x1, vz = _f(x0), _f(x1), _f(vz)
+    lib().orc_esirkepov(_n2(n), _dx2(dx), x0.shape[0], _dp(x0), _dp(x1), _dp(vz), float(qw),
+                        float(dt), _dp(J))
+    return J
+
+
+class EmSimulation:
+    """The electromagnetic PIC cycle on a periodic 2D3V Yee grid (E_Maxwell with the
+    particle modules of Sec. 2.2), FP64.  Fields E^n and B^n at integer times; each
+    step: gather E^n, B^n (+ uniform B0) -> Boris -> move -> Esirkepov current
+    J^(n+1/2) -> B -= (dt/2) curl E -> E += dt (c^2 curl B - J) -> B -= (dt/2) curl E.
+    Loading solves the Poisson equation of the loaded charge for the initial E
+    (E = -grad phi by forward differences onto the staggered points, so that
+    div E = rho exactly), B = 0, then the backward half push."""
+
+    def __init__(self, n, dx, dt, c, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0), rtol=1e-12):
+        self.n = (int(n[0]), int(n[1]))
+        self.dx = (float(dx[0]), float(dx[1]))
+        self.dt, self.c, self.q, self.m, self.w = float(dt), float(c), float(q), float(m), float(weight)
+        self.B0 = np.array(list(B0) + [0.0] * (3 - len(B0)))[:3]
+        self.rtol = rtol
+        self.cells = self.n[0] * self.n[1]
+        self.dV = self.dx[0] * self.dx[1]
+        self.V = self.dV * self.cells
+        self.step_count = 0
+
+    def _rho(self):
+        rho_e = deposit(2, self.n, self.dx, self.x, self.q * self.w)
+        return rho_e + (-self.q * self.w * self.x.shape[0] / self.V)
+
+    def load(self, x, v, half_push=True):
+        self.x = np.array(x, dtype=np.float64, order="C")
+        self.v = np.array(v, dtype=np.float64, order="C")
+        assert self.v.shape[1] == 3
+        rho = self._rho()
+        phi, _, _ = poisson(2, self.n, self.dx, rho, self.rtol, 200000)
+        ph = phi.reshape(self.n[1], self.n[0])
+        self.E = np.zeros((3, self.cells))
+        self.E[0] = (-(np.roll(ph, -1, axis=1) - ph) / self.dx[0]).ravel()
+        self.E[1] = (-(np.roll(ph, -1, axis=0) - ph) / self.dx[1]).ravel()
+        self.B = np.zeros((3, self.cells))
+        self.J = np.zeros((3, self.cells))
+        self.rho = rho
+        if half_push:
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, -0.5 * self.dt)
+        return self
+
+    def _fields_at(self, x):
+        EB = em_gather(self.n, self.dx, x, self.E, self.B)
+        EB[:, 3:] += self.B0
+        return EB
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, self.dt)
+            x0 = self.x.copy()
+            move(2, self.n + (1,), self.dx + (1.0,), self.x, self.v, self.dt)
+            self.J = np.zeros((3, self.cells))
+            esirkepov(self.n, self.dx, x0, self.x, self.v[:, 2], self.q * self.w, self.dt, self.J)
+            yee_b(self.n, self.dx, self.E, self.B, 0.5 * self.dt)
+            yee_e(self.n, self.dx, self.B, self.J, self.c, self.dt, self.E)
+            yee_b(self.n, self.dx, self.E, self.B, 0.5 * self.dt)
+            self.rho = self._rho()
+            self.step_count += 1
+        return self
+
+    def gauss_residual(self):
+        return yee_div_e(self.n, self.dx, self.E) - self.rho

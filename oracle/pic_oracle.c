@@ -514,3 +514,176 @@ void orc_mcc(int64_t np, double *v, const uint32_t *id, uint64_t step, uint64_t 
             vp[k] = snew * (n[k] * cchi + schi * (e1[k] * cp + e2[k] * sp));
     }
 }
+
+/* ---- electromagnetic step (E_Maxwell, Sec. 2.2): periodic 2D3V Yee grid ------------------ */
+/* Arrays hold three components, component-major ([3][n0 n1]); element (i, j) of a
+ * component sits at ((i + sx) dx, (j + sy) dy) with the Yee offsets
+ *   Ex (1/2, 0), Ey (0, 1/2), Ez (0, 0);  Bx (0, 1/2), By (1/2, 0), Bz (1/2, 1/2);
+ * J is staggered like E, rho lives on the nodes.  Units: eps0 = 1, mu0 = 1 / c^2. */
+static const double EM_SX[6] = {0.5, 0.0, 0.0, 0.0, 0.5, 0.5};
+static const double EM_SY[6] = {0.0, 0.5, 0.0, 0.5, 0.0, 0.5};
+
+static int64_t at2(const int *n, int i, int j)
+{
+    i %= n[0];
+    if (i < 0) i += n[0];
+    j %= n[1];
+    if (j < 0) j += n[1];
+    return (int64_t)i + (int64_t)n[0] * j;
+}
+
+/* Faraday: B -= h curl E (h = dt / 2 for each half of the split B update). */
+void orc_yee_b(const int *n, const double *dx, const double *E, double *B, double h)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    const double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = at2(n, i, j);
+            Bx[c] -= h * (Ez[at2(n, i, j + 1)] - Ez[c]) / dx[1];
+            By[c] += h * (Ez[at2(n, i + 1, j)] - Ez[c]) / dx[0];
+            Bz[c] -= h * ((Ey[at2(n, i + 1, j)] - Ey[c]) / dx[0] -
+                          (Ex[at2(n, i, j + 1)] - Ex[c]) / dx[1]);
+        }
+}
+
+/* Ampere: E += dt (c^2 curl B - J). */
+void orc_yee_e(const int *n, const double *dx, const double *B, const double *J, double c2,
+               double dt, double *E)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    const double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = at2(n, i, j);
+            const double cx = (Bz[c] - Bz[at2(n, i, j - 1)]) / dx[1];
+            const double cy = -(Bz[c] - Bz[at2(n, i - 1, j)]) / dx[0];
+            const double cz = (By[c] - By[at2(n, i - 1, j)]) / dx[0] -
+                              (Bx[c] - Bx[at2(n, i, j - 1)]) / dx[1];
+            Ex[c] += dt * (c2 * cx - J[c]);
+            Ey[c] += dt * (c2 * cy - J[cells + c]);
+            Ez[c] += dt * (c2 * cz - J[2 * cells + c]);
+        }
+}
+
+/* Discrete divergence of E at the nodes, (Ex(i+1/2) - Ex(i-1/2)) / dx + (Ey(j+1/2) - Ey(j-1/2)) / dy. */
+void orc_yee_div_e(const int *n, const double *dx, const double *E, double *div)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = at2(n, i, j);
+            div[c] = (E[c] - E[at2(n, i - 1, j)]) / dx[0] +
+                     (E[cells + c] - E[cells + at2(n, i, j - 1)]) / dx[1];
+        }
+}
+
+/* Divergence of B at the cell centres (i+1/2, j+1/2) (its z part vanishes in 2D). */
+void orc_yee_div_b(const int *n, const double *dx, const double *B, double *div)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = at2(n, i, j);
+            div[c] = (B[at2(n, i + 1, j)] - B[c]) / dx[0] +
+                     (B[cells + at2(n, i, j + 1)] - B[cells + c]) / dx[1];
+        }
+}
+
+/* E and B at the particles (np x 6: Ex Ey Ez Bx By Bz), CIC on each component's
+ * own staggered lattice. */
+void orc_em_gather(const int *n, const double *dx, int64_t np, const double *x, const double *E,
+                   const double *B, double *out)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int64_t p = 0; p < np; ++p)
+        for (int k = 0; k < 6; ++k) {
+            const double *F = (k < 3 ? E : B) + (int64_t)(k % 3) * cells;
+            const double u = x[2 * p] / dx[0] - EM_SX[k], w = x[2 * p + 1] / dx[1] - EM_SY[k];
+            const double iu = floor(u), iw = floor(w);
+            const double fu = u - iu, fw = w - iw;
+            const int i0 = (int)iu, j0 = (int)iw;
+            out[6 * p + k] = (1.0 - fw) * ((1.0 - fu) * F[at2(n, i0, j0)] + fu * F[at2(n, i0 + 1, j0)]) +
+                             fw * ((1.0 - fu) * F[at2(n, i0, j0 + 1)] + fu * F[at2(n, i0 + 1, j0 + 1)]);
+        }
+}
+
+/* Boris with per-particle fields EB (np x 6), velocities np x 3. */
+void orc_boris_eb(int64_t np, double *v, const double *EB, double qm, double h)
+{
+    for (int64_t p = 0; p < np; ++p) {
+        const double *e = EB + 6 * p, *b = EB + 6 * p + 3;
+        double t[3], s[3], tt = 0.0, vm[3], w[3];
+        for (int a = 0; a < 3; ++a) { t[a] = 0.5 * qm * h * b[a]; tt += t[a] * t[a]; }
+        for (int a = 0; a < 3; ++a) { s[a] = 2.0 * t[a] / (1.0 + tt); vm[a] = v[3 * p + a] + 0.5 * qm * h * e[a]; }
+        w[0] = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
+        w[1] = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
+        w[2] = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
+        const double vp[3] = {vm[0] + (w[1] * s[2] - w[2] * s[1]), vm[1] + (w[2] * s[0] - w[0] * s[2]),
+                              vm[2] + (w[0] * s[1] - w[1] * s[0])};
+        for (int a = 0; a < 3; ++a) v[3 * p + a] = vp[a] + 0.5 * qm * h * e[a];
+    }
+}
+
+static double cic1(double d)
+{
+    const double a = fabs(d);
+    return a < 1.0 ? 1.0 - a : 0.0;
+}
+
+/* Charge-conserving current of particles moving from x0 to x1 in one step
+ * (Esirkepov 2001, 2D3V, CIC shapes); every displacement under one cell per axis
+ * (x1 may have wrapped: the displacement is taken modulo the box).  With S0, S1 the
+ * node shapes before and after and DS = S1 - S0:
+ *   Wx = DSx (S0y + DSy / 2),  Wy = DSy (S0x + DSx / 2),
+ *   Wz = S0x S0y + DSx S0y / 2 + S0x DSy / 2 + DSx DSy / 3,
+ *   Jx(i+1/2, j) = -(qw / (dy dt)) sum_{i' <= i} Wx(i', j),
+ *   Jy(i, j+1/2) = -(qw / (dx dt)) sum_{j' <= j} Wy(i, j'),
+ *   Jz(i, j) = qw vz Wz(i, j) / (dx dy),
+ * added into J ([3][cells], staggered like E), so that rho1 - rho0 + dt div J = 0. */
+void orc_esirkepov(const int *n, const double *dx, int64_t np, const double *x0,
+                   const double *x1, const double *vz, double qw, double dt, double *J)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    const double L[2] = {n[0] * dx[0], n[1] * dx[1]};
+    for (int64_t p = 0; p < np; ++p) {
+        double u0[2], u1[2];
+        int base[2];
+        double S0[2][4], DS[2][4];
+        for (int a = 0; a < 2; ++a) {
+            double d = x1[2 * p + a] - x0[2 * p + a];
+            d -= L[a] * floor(d / L[a] + 0.5);  /* the displacement modulo the box */
+            u0[a] = x0[2 * p + a] / dx[a];
+            u1[a] = u0[a] + d / dx[a];
+            base[a] = (int)floor(u0[a]) - 1;
+            for (int k = 0; k < 4; ++k) {
+                S0[a][k] = cic1(u0[a] - (base[a] + k));
+                DS[a][k] = cic1(u1[a] - (base[a] + k)) - S0[a][k];
+            }
+        }
+        const double fx = -qw / (dx[1] * dt), fy = -qw / (dx[0] * dt);
+        const double fz = qw * vz[p] / (dx[0] * dx[1]);
+        for (int b = 0; b < 4; ++b) {
+            double run = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                run += DS[0][a] * (S0[1][b] + 0.5 * DS[1][b]);
+                J[at2(n, base[0] + a, base[1] + b)] += fx * run;
+            }
+        }
+        for (int a = 0; a < 4; ++a) {
+            double run = 0.0;
+            for (int b = 0; b < 4; ++b) {
+                run += DS[1][b] * (S0[0][a] + 0.5 * DS[0][a]);
+                J[cells + at2(n, base[0] + a, base[1] + b)] += fy * run;
+            }
+        }
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const double wz = S0[0][a] * S0[1][b] + 0.5 * DS[0][a] * S0[1][b] +
+                                  0.5 * S0[0][a] * DS[1][b] + DS[0][a] * DS[1][b] / 3.0;
+                J[2 * cells + at2(n, base[0] + a, base[1] + b)] += fz * wz;
+            }
+    }
+}
