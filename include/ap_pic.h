@@ -123,7 +123,20 @@ typedef struct {
                               end with one FP64-residual refinement pass           */
     int pusher;            /* AP_PIC_PUSHER_BORIS (default) or _HIGUERA_CARY        */
     double c_light;        /* speed of light in the run's units, for the Higuera-
-                              Cary pusher (0: infinite, the non-relativistic limit) */
+                              Cary pusher (0: infinite, the non-relativistic limit)
+                              and the electromagnetic step (required there)         */
+    int em;                /* 0: electrostatic (default); 1: the electromagnetic step
+                              (E_Maxwell, Sec. 2.2): periodic 2D3V Yee grid, E and B
+                              at integer times (B split in two half steps around
+                              the E update), Esirkepov charge-conserving current,
+                              Boris with the gathered B (+ B0).  The load's E is the
+                              Poisson field of the loaded charge, B = 0.  Needs
+                              ndim = 2, nv = 3, the FP32 form, the Boris pusher and
+                              c dt sqrt(1/dx^2 + 1/dy^2) < 1; ap_pic_step advances it
+                              (the gather_push / deposit / push_deposit /
+                              solve_field calls do not apply), ap_pic_get_E then
+                              returns the 3 staggered components and ap_pic_get_B
+                              the magnetic field                                  */
 } ap_pic_config;
 
 typedef struct {
@@ -399,6 +412,10 @@ ap_pic_status ap_pic_batch_get_perm(ap_pic_batch *b, int i, int64_t *perm);
 ap_pic_status ap_pic_batch_get_diag(ap_pic_batch *b, int i, ap_pic_diag *out);
 int64_t ap_pic_batch_num_particles(const ap_pic_batch *b, int i);
 const char *ap_pic_batch_last_error(const ap_pic_batch *b);
+
+/* The magnetic field of the electromagnetic step (em = 1): 3 x cells doubles,
+ * component-major, Bx at (i, j+1/2), By at (i+1/2, j), Bz at (i+1/2, j+1/2). */
+ap_pic_status ap_pic_get_B(ap_pic *h, double *out);
 
 /* Number of particles loaded (0 before ap_pic_load). */
 int64_t ap_pic_num_particles(const ap_pic *h);

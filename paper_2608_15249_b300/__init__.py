@@ -45,7 +45,7 @@ EXPORTS = [
     "ap_pic_get_phi", "ap_pic_get_rho_fx", "ap_pic_get_particles", "ap_pic_get_velocities_f64",
     "ap_pic_get_perm", "ap_pic_get_diag", "ap_pic_set_timing", "ap_pic_get_timing",
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
-    "ap_pic_sort_perm_noalloc", "ap_pic_set_collisions", "ap_pic_collide",
+    "ap_pic_sort_perm_noalloc", "ap_pic_set_collisions", "ap_pic_collide", "ap_pic_get_B",
     "ap_pic_batch_default_tuning", "ap_pic_batch_create", "ap_pic_batch_destroy",
     "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_push_deposit", "ap_pic_batch_sort",
     "ap_pic_batch_solve_field", "ap_pic_batch_set_tuning",
@@ -66,7 +66,7 @@ class ap_pic_config(ctypes.Structure):
         ("precision", ctypes.c_int), ("nv", ctypes.c_int), ("sort_every", ctypes.c_int),
         ("fx_bits", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
         ("brick", ctypes.c_int * 3), ("diag_every", ctypes.c_int), ("solver", ctypes.c_int),
-        ("pusher", ctypes.c_int), ("c_light", ctypes.c_double),
+        ("pusher", ctypes.c_int), ("c_light", ctypes.c_double), ("em", ctypes.c_int),
     ]
 
 
@@ -146,6 +146,7 @@ def _declare(L):
     L.ap_pic_set_timing.argtypes = [P, I]
     L.ap_pic_set_collisions.argtypes = [P, ctypes.POINTER(ap_pic_mcc)]
     L.ap_pic_collide.argtypes = [P]
+    L.ap_pic_get_B.argtypes = [P, P]
     L.ap_pic_get_timing.argtypes = [P, P, P]
     L.ap_pic_kernel_launches.argtypes = []
     L.ap_pic_kernel_launches.restype = I64
@@ -194,7 +195,7 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
                 precision=AP_PIC_FP32_CELLOFF, sort_every=20, fx_bits=0, cg_rtol=0.0,
                 cg_maxit=0, brick=(0, 0, 0), diag_every=0,
                 solver=AP_PIC_SOLVER_CG, pusher=AP_PIC_PUSHER_BORIS,
-                c_light=0.0) -> ap_pic_config:
+                c_light=0.0, em=0) -> ap_pic_config:
     c = ap_pic_config()
     lib().ap_pic_config_default(ctypes.byref(c))
     c.ndim = ndim
@@ -218,6 +219,7 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
     c.solver = int(solver)
     c.pusher = int(pusher)
     c.c_light = float(c_light)
+    c.em = int(em)
     return c
 
 
@@ -374,8 +376,16 @@ class Pic:
         return out
 
     def get_E(self):
-        out = np.empty(self.ndim * self.cells, np.float64)
+        """ndim x cells (node-centred), or 3 x cells Yee-staggered with em = 1."""
+        comps = 3 if self.cfg.em else self.ndim
+        out = np.empty(comps * self.cells, np.float64)
         self._check(self._lib.ap_pic_get_E(self.h, _ptr(out)))
+        return out
+
+    def get_B(self):
+        """3 x cells Yee-staggered magnetic field (em = 1)."""
+        out = np.empty(3 * self.cells, np.float64)
+        self._check(self._lib.ap_pic_get_B(self.h, _ptr(out)))
         return out
 
     def get_phi(self):

@@ -87,6 +87,10 @@ struct ap_pic {
     int *h_err = nullptr;
     int *h_iters = nullptr;
 
+    // electromagnetic step (cfg.em)
+    bool em = false;
+    EmBufs emb{};
+
     // null-collision Monte Carlo (ap_pic_set_collisions)
     bool mcc_on = false;
     MccParams mccp{};
@@ -358,6 +362,21 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
         return fail(h, AP_PIC_ERR_UNSUPPORTED, "the FP64 plain form pushes with Boris only");
     if (c->solver != AP_PIC_SOLVER_CG && c->solver != AP_PIC_SOLVER_FFT)
         return fail(h, AP_PIC_ERR_ARG, "unknown solver %d", c->solver);
+    if (c->em != 0 && c->em != 1) return fail(h, AP_PIC_ERR_ARG, "em must be 0 or 1");
+    if (c->em) {
+        if (c->ndim != 2 || c->nv != 3 || plain)
+            return fail(h, AP_PIC_ERR_UNSUPPORTED,
+                        "the electromagnetic step needs ndim = 2, nv = 3 and the FP32 form");
+        if (c->pusher != AP_PIC_PUSHER_BORIS)
+            return fail(h, AP_PIC_ERR_UNSUPPORTED, "the electromagnetic step pushes with Boris");
+        if (!(c->c_light > 0.0))
+            return fail(h, AP_PIC_ERR_ARG, "the electromagnetic step needs c_light > 0");
+        const double courant =
+            c->c_light * c->dt * sqrt(1.0 / (c->dx[0] * c->dx[0]) + 1.0 / (c->dx[1] * c->dx[1]));
+        if (!(courant < 1.0))
+            return fail(h, AP_PIC_ERR_ARG, "Courant number c dt sqrt(sum 1/dx^2) = %.3f >= 1",
+                        courant);
+    }
     if (c->solver == AP_PIC_SOLVER_FFT) {
         if (plain)
             return fail(h, AP_PIC_ERR_UNSUPPORTED, "the FP64 plain form solves with the CG only");
@@ -526,6 +545,18 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
     TRY(alloc_n(h, &h->d_mcc, 3));
     CU(h, cudaMemsetAsync(h->d_mcc, 0, 24, h->stream));
+    if (h->cfg.em) {
+        h->em = true;
+        TRY(alloc_n(h, &h->emb.E, c * 3));
+        TRY(alloc_n(h, &h->emb.B, c * 3));
+        TRY(alloc_n(h, &h->emb.Jf, c * 3));
+        TRY(alloc_n(h, &h->emb.J, c * 3));
+        CU(h, cudaMemsetAsync(h->emb.E, 0, c * 12, h->stream));
+        CU(h, cudaMemsetAsync(h->emb.B, 0, c * 12, h->stream));
+        CU(h, cudaMemsetAsync(h->emb.Jf, 0, c * 12, h->stream));
+        CU(h, cudaMemsetAsync(h->emb.J, 0, c * 24, h->stream));
+        for (int a = 0; a < 3; ++a) h->emb.B0[a] = (float)h->cfg.B0[a];
+    }
     if (h->cfg.solver == AP_PIC_SOLVER_FFT) TRY(create_fft(h));
     return create_pinned(h);
 }
@@ -874,6 +905,11 @@ static ap_pic_status half_push(ap_pic *h)
         return AP_PIC_OK;
     }
     const GridParams g = grid_params(h, -0.5 * h->cfg.dt);
+    if (h->em) {
+        CU(h, launch_em_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks, h->d_err,
+                             h->stream));
+        return AP_PIC_OK;
+    }
     CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, false, false, DiagPartials{},
                                h->d_err, h->stream));
     return AP_PIC_OK;
@@ -884,6 +920,14 @@ static ap_pic_status after_load(ap_pic *h, unsigned flags)
     TRY(sync_check(h));
     TRY(sort_particles(h));
     TRY(field_update(h));
+    if (h->em) {
+        // the electrostatic field of the loaded charge on the Yee lattice, B = 0
+        const GridParams g = grid_params(h, h->cfg.dt);
+        CU(h, launch_em_e_from_phi(g, h->f.phi, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->stream));
+        CU(h, cudaMemsetAsync(h->emb.B, 0, (size_t)h->cells * 12, h->stream));
+        CU(h, launch_em_energy(h->emb, h->cells, h->cfg.c_light, h->f.fe_part, h->f.nblocks,
+                               h->stream));
+    }
     TRY(finalize_diag(h, false));
     if (!(flags & AP_PIC_LOAD_NO_HALFPUSH)) TRY(half_push(h));
     h->step = 0;
@@ -961,6 +1005,7 @@ static ap_pic_status need_loaded(ap_pic *h)
 extern "C" ap_pic_status ap_pic_gather_push(ap_pic *h)
 {
     TRY(need_loaded(h));
+    if (h->em) return fail(h, AP_PIC_ERR_UNSUPPORTED, "em = 1: use ap_pic_step");
     if (h->plain) {
         const GridParamsF64 g = grid_params_f64(h, h->cfg.dt);
         CU(h, launch_plain_pass(g, h->p64, h->f64.E, h->f64.acc, true, true, false, h->dpart,
@@ -976,6 +1021,7 @@ extern "C" ap_pic_status ap_pic_gather_push(ap_pic *h)
 extern "C" ap_pic_status ap_pic_deposit(ap_pic *h)
 {
     TRY(need_loaded(h));
+    if (h->em) return fail(h, AP_PIC_ERR_UNSUPPORTED, "em = 1: use ap_pic_step");
     return deposit_only(h);
 }
 
@@ -1002,12 +1048,14 @@ static ap_pic_status push_deposit(ap_pic *h, bool diag)
 extern "C" ap_pic_status ap_pic_push_deposit(ap_pic *h)
 {
     TRY(need_loaded(h));
+    if (h->em) return fail(h, AP_PIC_ERR_UNSUPPORTED, "em = 1: use ap_pic_step");
     return push_deposit(h, true);
 }
 
 extern "C" ap_pic_status ap_pic_solve_field(ap_pic *h)
 {
     TRY(need_loaded(h));
+    if (h->em) return fail(h, AP_PIC_ERR_UNSUPPORTED, "em = 1: use ap_pic_step");
     return solve_field(h);
 }
 
@@ -1015,6 +1063,27 @@ extern "C" ap_pic_status ap_pic_sort(ap_pic *h)
 {
     TRY(need_loaded(h));
     return sort_particles(h);
+}
+
+// One electromagnetic step: particles (gather, push, move, current, charge), then
+// the field update; the diagnostics' field energy is electric plus magnetic.
+static ap_pic_status em_step(ap_pic *h, bool diag)
+{
+    CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
+    const GridParams g = grid_params(h, h->cfg.dt);
+    const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
+    CU(h, launch_em_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
+                         h->dpart.nblocks, h->d_err, h->stream));
+    stage_end(h, mk);
+    TRY(convert_rho(h));
+    const int mf = stage_begin(h, AP_PIC_STAGE_FIELD);
+    CU(h, launch_em_fields(g, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->cfg.dt, h->cfg.c_light,
+                           h->cfg.q * h->cfg.weight, h->stream));
+    if (diag)
+        CU(h, launch_em_energy(h->emb, h->cells, h->cfg.c_light, h->f.fe_part, h->f.nblocks,
+                               h->stream));
+    stage_end(h, mf);
+    return AP_PIC_OK;
 }
 
 extern "C" ap_pic_status ap_pic_set_collisions(ap_pic *h, const ap_pic_mcc *c)
@@ -1028,6 +1097,7 @@ extern "C" ap_pic_status ap_pic_set_collisions(ap_pic *h, const ap_pic_mcc *c)
     }
     if (h->plain) return fail(h, AP_PIC_ERR_UNSUPPORTED, "collisions need the FP32 form");
     if (h->nv != 3) return fail(h, AP_PIC_ERR_ARG, "collisions need nv = 3");
+    if (h->em) return fail(h, AP_PIC_ERR_UNSUPPORTED, "collisions with the electromagnetic step");
     if (h->cfg.pusher != AP_PIC_PUSHER_BORIS)
         return fail(h, AP_PIC_ERR_UNSUPPORTED, "collisions need the Boris pusher");
     const double vals[5] = {c->density, c->sigma_el, c->sigma_exc, c->eps_exc, c->mass_ratio};
@@ -1057,6 +1127,13 @@ extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         const int64_t k = h->step + 1;
         const bool diag = (k % h->cfg.diag_every) == 0;
+        if (h->em) {
+            TRY(em_step(h, diag));
+            if (h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0) TRY(sort_particles(h));
+            if (diag) TRY(finalize_diag(h, true));
+            h->step = k;
+            continue;
+        }
         TRY(push_deposit(h, diag));
         if (h->mcc_on) CU(h, launch_mcc(h->p, h->mccp, (uint64_t)k, h->d_mcc, h->stream));
         if (h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0) TRY(sort_particles(h));
@@ -1085,9 +1162,27 @@ extern "C" ap_pic_status ap_pic_get_rho_fx(ap_pic *h, int64_t *out)
     return sync_check(h);
 }
 
+// A [3][cells] FP32 device array as FP64 on the host.
+static ap_pic_status copy3_f32(ap_pic *h, const float *src, double *out)
+{
+    std::vector<float> tmp((size_t)h->cells * 3);
+    CU(h, cudaMemcpyAsync(tmp.data(), src, tmp.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < tmp.size(); ++i) out[i] = tmp[i];
+    return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_get_B(ap_pic *h, double *out)
+{
+    if (!h || !out) return AP_PIC_ERR_ARG;
+    if (!h->em) return fail(h, AP_PIC_ERR_STATE, "no magnetic field: em = 0");
+    return copy3_f32(h, h->emb.B, out);
+}
+
 extern "C" ap_pic_status ap_pic_get_E(ap_pic *h, double *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
+    if (h->em) return copy3_f32(h, h->emb.E, out);
     if (h->plain) {
         CU(h, cudaMemcpyAsync(out, h->f64.E, (size_t)h->cells * h->ndim * 8,
                               cudaMemcpyDeviceToHost, h->stream));

@@ -1,0 +1,419 @@
+// pic_em.cu -- the electromagnetic step (E_Maxwell, Sec. 2.2: finite-difference
+// time-domain updates on the Yee lattice) with its particle coupling, on a periodic
+// 2D3V grid.
+//
+// Fields live at integer times on the Yee lattice, component-major [3][cells], with
+// element (i, j) of a component at ((i + sx) dx, (j + sy) dy):
+//   Ex (1/2, 0), Ey (0, 1/2), Ez (0, 0);  Bx (0, 1/2), By (1/2, 0), Bz (1/2, 1/2);
+// the current J is staggered like E.  Units: eps0 = 1, mu0 = 1 / c^2.  A step:
+//   particles: gather E^n, B^n (+ uniform B0) on each component's lattice (CIC),
+//              Boris, move, Esirkepov current J^(n+1/2), charge at x^(n+1);
+//   fields:    B -= (dt/2) curl E;  E += dt (c^2 curl B - J);  B -= (dt/2) curl E.
+// The Esirkepov (2001) current makes rho^(n+1) - rho^n + dt div J = 0 hold exactly in
+// exact arithmetic, so Gauss's law is kept by the field update.  Current and charge
+// are accumulated in int64 fixed point (deterministic, order independent).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pic_internal.cuh"
+
+namespace apk {
+
+namespace {
+
+constexpr int EM_THREADS = 256;
+constexpr float J_SCALE = 1073741824.0f;   // 2^30: fixed point of the current weights
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Weights of a staggered CIC lattice along one axis: the particle at c + f sees the
+// lattice points (c + s) with s = 0 or 1/2; returns the lower lattice index and the
+// fraction towards the upper one.
+__device__ __forceinline__ void stagger(int c, float f, bool half, int n, int *i0, float *fr)
+{
+    if (!half) {
+        *i0 = c;
+        *fr = f;
+    } else if (f >= 0.5f) {
+        *i0 = c;
+        *fr = f - 0.5f;
+    } else {
+        *i0 = wrapi(c - 1, n);
+        *fr = f + 0.5f;
+    }
+}
+
+__device__ __forceinline__ float lattice_cic(const float *__restrict__ F, int n0, int n1, int i0,
+                                             float fx, int j0, float fy)
+{
+    const int i1 = i0 + 1 == n0 ? 0 : i0 + 1, j1 = j0 + 1 == n1 ? 0 : j0 + 1;
+    return (1.0f - fy) * ((1.0f - fx) * __ldg(F + i0 + n0 * j0) + fx * __ldg(F + i1 + n0 * j0)) +
+           fy * ((1.0f - fx) * __ldg(F + i0 + n0 * j1) + fx * __ldg(F + i1 + n0 * j1));
+}
+
+__device__ __forceinline__ float shape1(float d)
+{
+    const float a = fabsf(d);
+    return a < 1.0f ? 1.0f - a : 0.0f;
+}
+
+__device__ __forceinline__ void add_fx(unsigned long long *acc, float v)
+{
+    const long long q = __float2ll_rn(v * J_SCALE);
+    if (q) atomicAdd(acc, (unsigned long long)q);
+}
+
+template <bool MOVE>
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_push(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
+              double *__restrict__ diag_blocks, int *__restrict__ err)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    const float *Ex = em.E, *Ey = em.E + cells, *Ez = em.E + 2 * cells;
+    const float *Bx = em.B, *By = em.B + cells, *Bz = em.B + 2 * cells;
+    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
+    bool bad = false;
+    const float scale = ldexpf(1.0f, g.fx_bits);
+    const int one = 1 << g.fx_bits;
+    for (int64_t i = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; i < p.np;
+         i += (int64_t)gridDim.x * EM_THREADS) {
+        const int cell = p.cell[i];
+        int c[3] = {0, 0, 0};
+        c[1] = (int)fdiv((uint32_t)cell, g.div0);
+        c[0] = cell - c[1] * n0;
+        float f[3] = {p.off[i], p.off[p.stride + i], 0.0f};
+        float v[3] = {p.v[i], p.v[p.stride + i], p.v[2 * p.stride + i]};
+        // staggered gathers
+        int ix[2], iy[2];
+        float fx[2], fy[2];
+        stagger(c[0], f[0], false, n0, &ix[0], &fx[0]);
+        stagger(c[0], f[0], true, n0, &ix[1], &fx[1]);
+        stagger(c[1], f[1], false, n1, &iy[0], &fy[0]);
+        stagger(c[1], f[1], true, n1, &iy[1], &fy[1]);
+        float e[3], b[3];
+        e[0] = lattice_cic(Ex, n0, n1, ix[1], fx[1], iy[0], fy[0]);
+        e[1] = lattice_cic(Ey, n0, n1, ix[0], fx[0], iy[1], fy[1]);
+        e[2] = lattice_cic(Ez, n0, n1, ix[0], fx[0], iy[0], fy[0]);
+        b[0] = lattice_cic(Bx, n0, n1, ix[0], fx[0], iy[1], fy[1]) + em.B0[0];
+        b[1] = lattice_cic(By, n0, n1, ix[1], fx[1], iy[0], fy[0]) + em.B0[1];
+        b[2] = lattice_cic(Bz, n0, n1, ix[1], fx[1], iy[1], fy[1]) + em.B0[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
+        // Boris with the gathered B: t = (q/m) B h / 2, s = 2 t / (1 + t^2)
+        float t[3], s[3], vm[3];
+        float tt = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t[a] = g.qmh2 * b[a];
+            tt += t[a] * t[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s[a] = 2.0f * t[a] / (1.0f + tt);
+            vm[a] = v[a] + g.qmh2 * e[a];
+        }
+        const float w0 = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
+        const float w1 = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
+        const float w2 = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
+        const float vn[3] = {vm[0] + (w1 * s[2] - w2 * s[1]) + g.qmh2 * e[0],
+                             vm[1] + (w2 * s[0] - w0 * s[2]) + g.qmh2 * e[1],
+                             vm[2] + (w0 * s[1] - w1 * s[0]) + g.qmh2 * e[2]};
+        bool finite = isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]);
+        float o2 = 0.0f, n2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o2 += v[a] * v[a];
+            n2 += vn[a] * vn[a];
+            mom[a] += vn[a];
+            p.v[a * p.stride + i] = vn[a];
+        }
+        ke += 0.5f * (o2 + n2);
+        if constexpr (!MOVE) {
+            if (!finite) bad = true;
+        } else {
+        // move: o = f + v dt / dx, one cell at most per axis (the stencil below)
+        int cn[2];
+        float fn[2], u1[2], S0[2][4], DS[2][4];
+        int base[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float o = f[a] + vn[a] * g.dtdx[a];
+            if (!(o > -1.0f && o < 2.0f)) finite = false;
+            const bool hi = o >= 1.0f, lo = o < 0.0f;
+            float fr = hi ? o - 1.0f : (lo ? o + 1.0f : o);
+            int sh = hi ? 1 : (lo ? -1 : 0);
+            if (fr >= 1.0f) {  // o a tiny negative number: its fraction rounded up to 1
+                fr = 0.0f;
+                sh += 1;
+            }
+            cn[a] = wrapi(c[a] + sh, g.n[a]);
+            fn[a] = fr;
+            // local coordinates on the 4 lattice nodes c - 1 .. c + 2
+            base[a] = c[a] - 1;
+            const float u0 = f[a] + 1.0f;
+            u1[a] = fr + (float)sh + 1.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                S0[a][k] = shape1(u0 - (float)k);
+                DS[a][k] = shape1(u1[a] - (float)k) - S0[a][k];
+            }
+        }
+        if (!finite) {
+            bad = true;
+            continue;
+        }
+        // Esirkepov current, in units of the weights (scaled at conversion)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+            const int jj = wrapi(base[1] + bq, n1);
+            float run = 0.0f;
+#pragma unroll
+            for (int aq = 0; aq < 3; ++aq) {
+                run += DS[0][aq] * (S0[1][bq] + 0.5f * DS[1][bq]);
+                add_fx(em.J + wrapi(base[0] + aq, n0) + (int64_t)n0 * jj, run);
+            }
+        }
+#pragma unroll
+        for (int aq = 0; aq < 4; ++aq) {
+            const int ii = wrapi(base[0] + aq, n0);
+            float run = 0.0f;
+#pragma unroll
+            for (int bq = 0; bq < 3; ++bq) {
+                run += DS[1][bq] * (S0[0][aq] + 0.5f * DS[0][aq]);
+                add_fx(em.J + cells + ii + (int64_t)n0 * wrapi(base[1] + bq, n1), run);
+            }
+        }
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq)
+#pragma unroll
+            for (int aq = 0; aq < 4; ++aq) {
+                const float wz = S0[0][aq] * S0[1][bq] + 0.5f * DS[0][aq] * S0[1][bq] +
+                                 0.5f * S0[0][aq] * DS[1][bq] +
+                                 DS[0][aq] * DS[1][bq] * (1.0f / 3.0f);
+                if (wz != 0.0f)
+                    add_fx(em.J + 2 * cells + wrapi(base[0] + aq, n0) +
+                               (int64_t)n0 * wrapi(base[1] + bq, n1),
+                           vn[2] * wz);
+            }
+        // charge at the new position (int64 fixed point, exact total)
+        const float wx[2] = {1.0f - fn[0], fn[0]}, wy[2] = {1.0f - fn[1], fn[1]};
+        int qk[4], rest = one;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            qk[k] = __float2int_rn(wx[k & 1] * wy[k >> 1] * scale);
+            rest -= qk[k];
+        }
+        qk[3] = rest;
+        const int x1 = cn[0] + 1 == n0 ? 0 : cn[0] + 1, y1 = cn[1] + 1 == n1 ? 0 : cn[1] + 1;
+        const int64_t nodes[4] = {cn[0] + (int64_t)n0 * cn[1], x1 + (int64_t)n0 * cn[1],
+                                  cn[0] + (int64_t)n0 * y1, x1 + (int64_t)n0 * y1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            atomicAdd(rho_acc + nodes[k], (unsigned long long)(long long)qk[k]);
+        p.cell[i] = cn[0] + n0 * cn[1];
+        p.off[i] = fn[0];
+        p.off[p.stride + i] = fn[1];
+        }
+    }
+    if (bad) atomicOr(err, EF_NONFINITE);
+    if (diag_blocks) {
+        __shared__ double red[4][EM_THREADS / 32];
+        const float vals[4] = {ke, mom[0], mom[1], mom[2]};
+        const int w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double x = vals[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) == 0) red[k][w] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double sum = 0.0;
+            for (int j = 0; j < EM_THREADS / 32; ++j) sum += red[threadIdx.x][j];
+            diag_blocks[blockIdx.x * 4 + threadIdx.x] = sum;
+        }
+    }
+}
+
+// Node coordinates of a flat index.
+__device__ __forceinline__ void coords2(int64_t id, const GridParams &g, int *i, int *j)
+{
+    *j = (int)fdiv((uint32_t)id, g.div0);
+    *i = (int)id - *j * g.n[0];
+}
+
+__global__ void __launch_bounds__(EM_THREADS)
+    k_yee_b(GridParams g, const float *__restrict__ E, float *__restrict__ B, float hdx,
+            float hdy)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS) {
+        int i, j;
+        coords2(id, g, &i, &j);
+        const int64_t ip = (i + 1 == n0 ? 0 : i + 1) + (int64_t)n0 * j;
+        const int64_t jp = i + (int64_t)n0 * (j + 1 == n1 ? 0 : j + 1);
+        const float ez = E[2 * cells + id];
+        B[id] -= hdy * (E[2 * cells + jp] - ez);
+        B[cells + id] += hdx * (E[2 * cells + ip] - ez);
+        B[2 * cells + id] -= hdx * (E[cells + ip] - E[cells + id]) - hdy * (E[jp] - E[id]);
+    }
+}
+
+__global__ void __launch_bounds__(EM_THREADS)
+    k_yee_e(GridParams g, const float *__restrict__ B, const float *__restrict__ J,
+            float *__restrict__ E, float c2dtdx, float c2dtdy, float dt)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS) {
+        int i, j;
+        coords2(id, g, &i, &j);
+        const int64_t im = (i == 0 ? n0 - 1 : i - 1) + (int64_t)n0 * j;
+        const int64_t jm = i + (int64_t)n0 * (j == 0 ? n1 - 1 : j - 1);
+        const float bz = B[2 * cells + id];
+        E[id] += c2dtdy * (bz - B[2 * cells + jm]) - dt * J[id];
+        E[cells + id] += -c2dtdx * (bz - B[2 * cells + im]) - dt * J[cells + id];
+        E[2 * cells + id] += c2dtdx * (B[cells + id] - B[cells + im]) -
+                             c2dtdy * (B[id] - B[jm]) - dt * J[2 * cells + id];
+    }
+}
+
+// J = the fixed-point weights times their factors: Jx -(qw / (dy dt)), Jy
+// -(qw / (dx dt)), Jz qw / (dx dy); the accumulator is cleared for the next step.
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_j_convert(int64_t cells, unsigned long long *__restrict__ Jacc, float *__restrict__ J,
+                   double fx, double fy, double fz)
+{
+    const double f[3] = {fx, fy, fz};
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const long long a = (long long)Jacc[k * cells + id];
+            J[k * cells + id] = (float)(f[k] * (double)a / (double)J_SCALE);
+            Jacc[k * cells + id] = 0ull;
+        }
+}
+
+// Initial field of the load: E = -grad phi by forward differences onto the staggered
+// points (so that the discrete div E equals rho), Ez = 0.
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_e_from_phi(GridParams g, const float *__restrict__ phi, float *__restrict__ E,
+                    float idx, float idy)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS) {
+        int i, j;
+        coords2(id, g, &i, &j);
+        const int64_t ip = (i + 1 == n0 ? 0 : i + 1) + (int64_t)n0 * j;
+        const int64_t jp = i + (int64_t)n0 * (j + 1 == n1 ? 0 : j + 1);
+        E[id] = -(phi[ip] - phi[id]) * idx;
+        E[cells + id] = -(phi[jp] - phi[id]) * idy;
+        E[2 * cells + id] = 0.0f;
+    }
+}
+
+// Per-block partials of sum (|E|^2 + c^2 |B|^2) over the nodes (electric plus
+// magnetic field energy density, times 2).
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_energy(int64_t cells, const float *__restrict__ E, const float *__restrict__ B, float c2,
+                double *__restrict__ part)
+{
+    double s = 0.0;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double e = E[k * cells + id], b = B[k * cells + id];
+            s += e * e + (double)c2 * b * b;
+        }
+    __shared__ double red[EM_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int j = 0; j < EM_THREADS / 32; ++j) t += red[j];
+        part[blockIdx.x] = t;
+    }
+}
+
+int em_blocks(int64_t n)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const int64_t need = (n + EM_THREADS - 1) / EM_THREADS;
+    const int64_t cap = (int64_t)sms * 8;
+    const int64_t b = need < cap ? need : cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int em_particle_blocks(int64_t np) { return em_blocks(np); }
+
+cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
+                           unsigned long long *rho_acc, double *diag_blocks, int nblocks,
+                           int *err, cudaStream_t st)
+{
+    if (p.np == 0) return cudaSuccess;
+    if (move)
+        k_em_push<true><<<nblocks, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
+    else
+        k_em_push<false><<<nblocks, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, double dy,
+                             double dt, double c, double qw, cudaStream_t st)
+{
+    const int64_t cells = (int64_t)g.n[0] * g.n[1];
+    const int nb = em_blocks(cells);
+    k_em_j_convert<<<nb, EM_THREADS, 0, st>>>(cells, em.J, em.Jf, -qw / (dy * dt),
+                                              -qw / (dx * dt), qw / (dx * dy));
+    const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
+    k_yee_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hdx, hdy);
+    k_yee_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, em.Jf, em.E, (float)(c * c * dt / dx),
+                                       (float)(c * c * dt / dy), (float)dt);
+    k_yee_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hdx, hdy);
+    note_launch(4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_e_from_phi(const GridParams &g, const float *phi, const EmBufs &em,
+                                 double dx, double dy, cudaStream_t st)
+{
+    const int64_t cells = (int64_t)g.n[0] * g.n[1];
+    k_em_e_from_phi<<<em_blocks(cells), EM_THREADS, 0, st>>>(g, phi, em.E, (float)(1.0 / dx),
+                                                            (float)(1.0 / dy));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_energy(const EmBufs &em, int64_t cells, double c, double *part, int nblocks,
+                             cudaStream_t st)
+{
+    k_em_energy<<<nblocks, EM_THREADS, 0, st>>>(cells, em.E, em.B, (float)(c * c), part);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace apk

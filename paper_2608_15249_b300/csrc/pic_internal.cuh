@@ -229,6 +229,28 @@ cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
 enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5 };
 cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
 
+// ---- electromagnetic step (pic_em.cu) -----------------------------------------------------------
+struct EmBufs {
+    float *E, *B;              // [3][cells] Yee-staggered fields at integer time
+    float *Jf;                 // [3][cells] current of the last step (staggered like E)
+    unsigned long long *J;     // [3][cells] fixed-point current weights (2^30)
+    float B0[3];               // uniform external B added to the gathered one
+};
+int em_particle_blocks(int64_t np);
+// Gather, Boris with the gathered B, and (move) the move, Esirkepov current and the
+// charge at the new positions (into rho_acc).
+cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
+                           unsigned long long *rho_acc, double *diag_blocks, int nblocks,
+                           int *err, cudaStream_t st);
+// J from its accumulator (cleared), then B -= (dt/2) curl E; E += dt (c^2 curl B - J);
+// B -= (dt/2) curl E.
+cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, double dy,
+                             double dt, double c, double qw, cudaStream_t st);
+cudaError_t launch_em_e_from_phi(const GridParams &g, const float *phi, const EmBufs &em,
+                                 double dx, double dy, cudaStream_t st);
+cudaError_t launch_em_energy(const EmBufs &em, int64_t cells, double c, double *part, int nblocks,
+                             cudaStream_t st);
+
 // ---- null-collision Monte Carlo (pic_mcc.cu) ---------------------------------------------------
 struct MccParams {
     uint64_t seed;
