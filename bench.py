@@ -284,6 +284,7 @@ def bench_ours(args):
         gf.close()
         field_ms["fft"] = ff[0] / max(ff[1], 1)
     collisions = None if (f64 or args.no_collisions) else bench_collisions(args, pk, torch, stream)
+    em = None if (f64 or args.no_em) else bench_em(args, pk, torch, stream)
     e2e = None
     if not args.no_e2e:
         solver = "cg" if f64 else args.e2e_solver
@@ -320,6 +321,7 @@ def bench_ours(args):
             "stage_ms_per_call": breakdown,
             "field_solve_ms": field_ms,
             "collisions": collisions,
+            "electromagnetic": em,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -337,6 +339,27 @@ _SOLVERS = {"cg": 0, "fft": 1}
 # cross sections giving a candidate fraction of about 4 % per step.
 MCC_BENCH = dict(density=1.0, sigma_el=0.05, sigma_exc=0.02, eps_exc=1.5, mass_ratio=1e-4,
                  vmax=6.0, seed=99)
+
+
+def bench_em(args, pk, torch, stream, steps=20):
+    """CUDA-event time of full electromagnetic steps (particles with the Esirkepov
+    current, Yee field update, sort every 20 steps) on a 2D3V Maxwellian of the
+    benchmark's size, c = 4 v_te (Courant number 0.57)."""
+    w = workloads.maxwellian_box(2, (args.n, args.n), ppc=args.ppc, nv=3, dt=0.1, seed=7)
+    g = pk.from_workload(w, stream=stream.cuda_stream, em=1, c_light=4.0, sort_every=20)
+    g.load(w.x, w.v)
+    g.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    g.close()
+    return {"ms_per_step": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
+            "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, c = 4, dt = 0.1, "
+                        "full electromagnetic step"}
 
 
 def bench_collisions(args, pk, torch, stream):
@@ -556,6 +579,7 @@ def main():
     ap.add_argument("--e2e-steps-cg", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-collisions", action="store_true")
+    ap.add_argument("--no-em", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)
     ap.add_argument("--cpu-steps", type=int, default=4)
