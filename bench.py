@@ -341,6 +341,101 @@ MCC_BENCH = dict(density=1.0, sigma_el=0.05, sigma_exc=0.02, eps_exc=1.5, mass_r
                  vmax=6.0, seed=99)
 
 
+def _energy(g):
+    d = g.get_diag()
+    return d["kinetic"] + d["field_energy"]
+
+
+def bench_precision(args):
+    """The precision study: the FP32 cell + offset form against the FP64 plain form
+    on the GPU, both against the FP64 oracle, on the 3D Maxwellian with 1 % white
+    per-cell density noise (Jacobi-PCG field solve in every case):
+      - full size (n^3, 16 ppc): L-infinity rho and E differences FP32 vs FP64 after
+        `--prec-steps` steps, and the energy drift of each over those steps (relative
+        to the total energy after the first step);
+      - energy drift over `--drift-steps` steps on a (n/2)^3 grid;
+      - both forms against the oracle after 10 steps on a 32^3 grid."""
+    import torch
+
+    import oracle
+    import paper_2608_15249_b300 as pk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    out = {"metric": "precision study (FP32 cell+offset vs FP64 plain vs FP64 oracle)",
+           "data": "synthetic", "unit": "relative L-infinity / relative energy drift"}
+
+    def pair(w, steps, track_energy):
+        forms = {}
+        for name, over in (("f32", {}), ("f64", dict(precision=pk.AP_PIC_FP64_PLAIN))):
+            g = pk.from_workload(w, stream=stream.cuda_stream, sort_every=20, **over)
+            g.load(w.x, w.v)
+            t0 = time.perf_counter()
+            # total energy (time-centred kinetic + field) from the first step on: the
+            # load's diagnostics carry no kinetic energy yet
+            g.step(1)
+            e0 = _energy(g)
+            drift = 0.0
+            for _ in range(steps - 1):
+                g.step(1)
+                if track_energy:
+                    drift = max(drift, abs(_energy(g) - e0) / e0)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            if not track_energy:
+                drift = abs(_energy(g) - e0) / e0
+            forms[name] = {"rho": g.get_rho(), "E": g.get_E(), "drift": drift, "seconds": secs,
+                           "handle": g}
+        return forms
+
+    def linf(a, b):
+        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+    # full size, a few steps
+    n = args.n
+    w = workloads.precision_3d(n=(n, n, n), ppc=args.ppc)
+    f = pair(w, args.prec_steps, True)
+    bg = w.weight * w.np_ / float(np.prod(w.L[:3]))  # the ions: rho_e = rho - bg (q = -1)
+    rho_e_scale = float(np.max(np.abs(f["f64"]["rho"] - bg)))
+    out["full"] = {
+        "workload": f"precision_3d {n}^3, {args.ppc} ppc, {w.np_} electrons, "
+                    f"{args.prec_steps} steps, CG field solve",
+        "rho_f32_vs_f64": float(np.max(np.abs(f["f32"]["rho"] - f["f64"]["rho"]))) / rho_e_scale,
+        "E_f32_vs_f64": linf(f["f32"]["E"], f["f64"]["E"]),
+        "energy_drift": {"f32": f["f32"]["drift"], "f64": f["f64"]["drift"]},
+        "seconds": {"f32": f["f32"]["seconds"], "f64": f["f64"]["seconds"]}}
+    for v in f.values():
+        v["handle"].close()
+    del w, f
+    # long run, smaller grid
+    nd = max(8, n // 2)
+    w = workloads.precision_3d(n=(nd, nd, nd), ppc=args.ppc, seed=14)
+    f = pair(w, args.drift_steps, True)
+    out["drift"] = {
+        "workload": f"precision_3d {nd}^3, {args.ppc} ppc, {w.np_} electrons, "
+                    f"{args.drift_steps} steps, CG field solve",
+        "energy_drift_max": {"f32": f["f32"]["drift"], "f64": f["f64"]["drift"]},
+        "E_f32_vs_f64_at_end": linf(f["f32"]["E"], f["f64"]["E"]),
+        "seconds": {"f32": f["f32"]["seconds"], "f64": f["f64"]["seconds"]}}
+    for v in f.values():
+        v["handle"].close()
+    del w, f
+    # against the oracle
+    no = 32
+    w = workloads.precision_3d(n=(no, no, no), ppc=args.ppc, seed=24)
+    f = pair(w, 10, False)
+    sim = oracle.Simulation(3, w.n, w.dx, w.dt, weight=w.weight, rtol=1e-12).load(w.x, w.v)
+    sim.step(10)
+    scale = float(np.max(np.abs(sim.rho_e)))
+    out["oracle"] = {
+        "workload": f"precision_3d {no}^3, {args.ppc} ppc, {w.np_} electrons, 10 steps",
+        "rho": {k: float(np.max(np.abs(f[k]["rho"] - sim.rho))) / scale for k in ("f32", "f64")},
+        "E": {k: linf(f[k]["E"], sim.E) for k in ("f32", "f64")}}
+    for v in f.values():
+        v["handle"].close()
+    print(json.dumps(out), flush=True)
+
+
 def bench_em(args, pk, torch, stream, steps=20):
     """CUDA-event time of full electromagnetic steps (particles with the Esirkepov
     current, Yee field update, sort every 20 steps) on a 2D3V Maxwellian of the
@@ -580,6 +675,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-collisions", action="store_true")
     ap.add_argument("--no-em", action="store_true")
+    ap.add_argument("--prec-steps", type=int, default=10, help="--workload precision_study")
+    ap.add_argument("--drift-steps", type=int, default=1000, help="--workload precision_study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)
     ap.add_argument("--cpu-steps", type=int, default=4)
@@ -598,6 +695,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "precision_study":
+        bench_precision(args)
     elif args.workload == "batch":
         bench_batch(args)
     else:
