@@ -199,6 +199,17 @@ def _config(args, w):
             else f"higuera-cary, c = {args.c_light or 'infinite'}"}
 
 
+def aggregate_replicas(ms, np_per_rank, steps, world, dist=None, device=None):
+    """Max-over-ranks timed-region length and whole-job throughput of `world`
+    independent replicas: (max ms, np_per_rank * steps * world / max seconds)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, np_per_rank * steps * world / (ms * 1e-3)
+
+
 def bench_ours(args):
     import torch
 
@@ -247,13 +258,8 @@ def bench_ours(args):
     launches = pk.kernel_launches() - launches0
     stages = g.get_timing()
     g.set_timing(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_ps = w.np_ * args.steps * world
-    value = total_ps / (ms * 1e-3)
+    ms, value = aggregate_replicas(ev0.elapsed_time(ev1), w.np_, args.steps, world, dist,
+                                   device="cuda")
 
     # roofline of the dominant kernel (the fused particle pass)
     peak, peak_kind = _peaks()
