@@ -11,7 +11,8 @@ Parity status per function (details in the repository's design notes):
   locate, deposit, gather, neg_laplacian, poisson_pcg, efield, boris,
   higuera_cary, move, sort_key, counting_sort, kinetic, kinetic_rel,
   field_energy, momentum, rng24, mcc, yee_b, yee_e, em_gather, boris_eb,
-  esirkepov: pinned by the tests under tests/test_oracle_*.py.
+  esirkepov, CpmlField (cpml_b, cpml_e): pinned by the tests under
+  tests/test_oracle_*.py.
 """
 
 from __future__ import annotations
@@ -83,6 +84,11 @@ def _declare(L):
     L.orc_boris_eb.restype = None
     L.orc_esirkepov.argtypes = [_I32, _D, i64, _D, _D, _D, d, d, _D]
     L.orc_esirkepov.restype = None
+    PP = ctypes.POINTER(_D)
+    L.orc_cpml_b.argtypes = [_I32, _D, _D, _D, d, PP, PP]
+    L.orc_cpml_b.restype = None
+    L.orc_cpml_e.argtypes = [_I32, _D, _D, _D, d, d, _D, PP, PP]
+    L.orc_cpml_e.restype = None
     L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
     L.orc_hc.restype = None
     L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
@@ -549,3 +555,74 @@ class EmSimulation:
 
     def gauss_residual(self):
         return yee_div_e(self.n, self.dx, self.E) - self.rho
+
+
+# ---- convolutional PML (E_Maxwell, Sec. 2.2; Roden and Gedney 2000) ---------------------------
+
+def cpml_axis(n, npml, d, h, c, m=3, kappa_max=1.0, alpha_max=0.0):
+    """(b, c, 1/kappa) along one axis of n nodes, at integer positions i and half
+    positions i + 1/2, for an update of step h: depth = distance into a layer of npml
+    cells / npml, sigma = sigma_max depth^m with sigma_max = 0.8 (m + 1) c / d (the
+    matched value for eta = 1 / c, eps0 = 1), kappa = 1 + (kappa_max - 1) depth^m,
+    alpha = alpha_max (1 - depth) inside the layer."""
+    sigma_max = 0.8 * (m + 1) * c / d
+    out = {}
+    for name, shift in (("int", 0.0), ("half", 0.5)):
+        b, cc, ik = np.ones(n), np.zeros(n), np.ones(n)
+        if npml > 0:
+            for i in range(n):
+                x = i + shift
+                depth = max(npml - x, x - (n - 1 - npml), 0.0) / npml
+                if depth <= 0.0:
+                    continue
+                sigma = sigma_max * depth ** m
+                kappa = 1.0 + (kappa_max - 1.0) * depth ** m
+                alpha = alpha_max * (1.0 - depth)
+                b[i] = math.exp(-(sigma / kappa + alpha) * h)
+                cc[i] = sigma * (b[i] - 1.0) / (sigma * kappa + kappa * kappa * alpha)
+                ik[i] = 1.0 / kappa
+        out[name] = (b, cc, ik)
+    return out
+
+
+class CpmlField:
+    """The Yee field update of the electromagnetic step on a non-periodic 2D grid with
+    a convolutional PML of npml cells on every side, backed by a conducting wall;
+    fields only (a prescribed current J drives it).  Each step: B half step, E step,
+    B half step, as in EmSimulation."""
+
+    def __init__(self, n, dx, dt, c, npml, m=3, kappa_max=1.0, alpha_max=0.0):
+        self.n = (int(n[0]), int(n[1]))
+        self.dx = (float(dx[0]), float(dx[1]))
+        self.dt, self.c = float(dt), float(c)
+        cells = self.n[0] * self.n[1]
+        self.E = np.zeros((3, cells))
+        self.B = np.zeros((3, cells))
+        self.psi_b = [np.zeros(cells) for _ in range(4)]
+        self.psi_e = [np.zeros(cells) for _ in range(4)]
+        ax = [cpml_axis(self.n[a], npml, self.dx[a], 0.5 * self.dt, self.c, m, kappa_max, alpha_max)
+              for a in range(2)]
+        ae = [cpml_axis(self.n[a], npml, self.dx[a], self.dt, self.c, m, kappa_max, alpha_max)
+              for a in range(2)]
+        self.prof_b = [np.ascontiguousarray(v) for v in ax[0]["half"] + ax[1]["half"]]
+        self.prof_e = [np.ascontiguousarray(v) for v in ae[0]["int"] + ae[1]["int"]]
+
+    @staticmethod
+    def _pp(arrs):
+        return (_D * len(arrs))(*[a.ctypes.data_as(_D) for a in arrs])
+
+    def step(self, J=None, nsteps=1):
+        J = np.zeros_like(self.E) if J is None else _f(J)
+        for _ in range(nsteps):
+            for half in (0, 1):
+                lib().orc_cpml_b(_n2(self.n), _dx2(self.dx), _dp(self.E), _dp(self.B),
+                                 0.5 * self.dt, self._pp(self.prof_b), self._pp(self.psi_b))
+                if half == 0:
+                    lib().orc_cpml_e(_n2(self.n), _dx2(self.dx), _dp(self.B), _dp(J),
+                                     self.c ** 2, self.dt, _dp(self.E), self._pp(self.prof_e),
+                                     self._pp(self.psi_e))
+        return self
+
+    def energy(self):
+        return 0.5 * float(np.sum(self.E ** 2) + self.c ** 2 * np.sum(self.B ** 2)) * \
+            self.dx[0] * self.dx[1]

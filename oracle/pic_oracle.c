@@ -687,3 +687,79 @@ void orc_esirkepov(const int *n, const double *dx, int64_t np, const double *x0,
             }
     }
 }
+
+/* ---- convolutional PML (E_Maxwell, Sec. 2.2, the CPML the paper cites: Roden and
+ * Gedney 2000) on a 2D Yee grid with a perfectly conducting wall behind it -------------- */
+/* Non-periodic grid of n0 x n1 nodes; the Yee offsets as above; the tangential E on the
+ * outer nodes is held at zero (Ez on all four sides, Ex on j = 0 and n1 - 1, Ey on
+ * i = 0 and n0 - 1) and values outside the grid count as zero.  Inside the layers
+ * every derivative d/da of the update becomes (1 / kappa_a) d/da + psi, with
+ *   psi <- b psi + c (dF/da),   b = exp(-(sigma / kappa + alpha) h),
+ *   c = sigma (b - 1) / (sigma kappa + kappa^2 alpha)   (0 where sigma = 0),
+ * h the step of that update.  The profiles (b, c, 1 / kappa) are given per axis at
+ * integer positions (index i = position i) and half positions (index i = i + 1/2),
+ * separately for the E update (h = dt) and the B half updates (h = dt / 2).  psi
+ * arrays (all [cells]): for B: Bx_y, By_x, Bz_x, Bz_y; for E: Ex_y, Ey_x, Ez_x, Ez_y. */
+static double pec_get(const double *F, const int *n, int i, int j)
+{
+    if (i < 0 || j < 0 || i >= n[0] || j >= n[1]) return 0.0;
+    return F[(int64_t)i + (int64_t)n[0] * j];
+}
+
+void orc_cpml_b(const int *n, const double *dx, const double *E, double *B, double h,
+                const double *const *prof, double *const *psi)
+{
+    /* prof: [0] bx_half, [1] cx_half, [2] ikx_half, [3] by_half, [4] cy_half, [5] iky_half */
+    const int64_t cells = (int64_t)n[0] * n[1];
+    const double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = (int64_t)i + (int64_t)n[0] * j;
+            const double dyEz = (pec_get(Ez, n, i, j + 1) - Ez[c]) / dx[1];
+            const double dxEz = (pec_get(Ez, n, i + 1, j) - Ez[c]) / dx[0];
+            const double dxEy = (pec_get(Ey, n, i + 1, j) - Ey[c]) / dx[0];
+            const double dyEx = (pec_get(Ex, n, i, j + 1) - Ex[c]) / dx[1];
+            psi[0][c] = prof[3][j] * psi[0][c] + prof[4][j] * dyEz;
+            psi[1][c] = prof[0][i] * psi[1][c] + prof[1][i] * dxEz;
+            psi[2][c] = prof[0][i] * psi[2][c] + prof[1][i] * dxEy;
+            psi[3][c] = prof[3][j] * psi[3][c] + prof[4][j] * dyEx;
+            Bx[c] -= h * (prof[5][j] * dyEz + psi[0][c]);
+            By[c] += h * (prof[2][i] * dxEz + psi[1][c]);
+            Bz[c] -= h * ((prof[2][i] * dxEy + psi[2][c]) - (prof[5][j] * dyEx + psi[3][c]));
+        }
+}
+
+void orc_cpml_e(const int *n, const double *dx, const double *B, const double *J, double c2,
+                double dt, double *E, const double *const *prof, double *const *psi)
+{
+    /* prof: [0] bx_int, [1] cx_int, [2] ikx_int, [3] by_int, [4] cy_int, [5] iky_int */
+    const int64_t cells = (int64_t)n[0] * n[1];
+    const double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = (int64_t)i + (int64_t)n[0] * j;
+            const double dyBz = (Bz[c] - pec_get(Bz, n, i, j - 1)) / dx[1];
+            const double dxBz = (Bz[c] - pec_get(Bz, n, i - 1, j)) / dx[0];
+            const double dxBy = (By[c] - pec_get(By, n, i - 1, j)) / dx[0];
+            const double dyBx = (Bx[c] - pec_get(Bx, n, i, j - 1)) / dx[1];
+            psi[0][c] = prof[3][j] * psi[0][c] + prof[4][j] * dyBz;
+            psi[1][c] = prof[0][i] * psi[1][c] + prof[1][i] * dxBz;
+            psi[2][c] = prof[0][i] * psi[2][c] + prof[1][i] * dxBy;
+            psi[3][c] = prof[3][j] * psi[3][c] + prof[4][j] * dyBx;
+            Ex[c] += dt * (c2 * (prof[5][j] * dyBz + psi[0][c]) - J[c]);
+            Ey[c] += dt * (-c2 * (prof[2][i] * dxBz + psi[1][c]) - J[cells + c]);
+            Ez[c] += dt * (c2 * ((prof[2][i] * dxBy + psi[2][c]) - (prof[5][j] * dyBx + psi[3][c])) -
+                           J[2 * cells + c]);
+        }
+    /* the conducting wall: tangential E on the outer nodes */
+    for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+            const int64_t c = (int64_t)i + (int64_t)n[0] * j;
+            const int xb = i == 0 || i == n[0] - 1, yb = j == 0 || j == n[1] - 1;
+            if (xb || yb) Ez[c] = 0.0;
+            if (yb || i == n[0] - 1) Ex[c] = 0.0;
+            if (xb || j == n[1] - 1) Ey[c] = 0.0;
+        }
+}
