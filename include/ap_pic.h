@@ -137,6 +137,14 @@ typedef struct {
                               solve_field calls do not apply), ap_pic_get_E then
                               returns the 3 staggered components and ap_pic_get_B
                               the magnetic field                                  */
+    int em_boundary;       /* with em = 1: 0 periodic (default); 1 a convolutional
+                              PML (Roden and Gedney, the CPML of E_Maxwell) of
+                              pml_cells cells on every side, backed by a conducting
+                              wall: a non-periodic field-only grid (no particles;
+                              drive it with ap_pic_set_current).  Graded profiles,
+                              depth d in [0, 1]: sigma = 0.8 (m + 1) c / dx d^3,
+                              kappa = 1, alpha = 0                                 */
+    int pml_cells;         /* PML thickness in cells (0: 12); 2 pml_cells < n[a]    */
 } ap_pic_config;
 
 typedef struct {
@@ -412,6 +420,11 @@ ap_pic_status ap_pic_batch_get_perm(ap_pic_batch *b, int i, int64_t *perm);
 ap_pic_status ap_pic_batch_get_diag(ap_pic_batch *b, int i, ap_pic_diag *out);
 int64_t ap_pic_batch_num_particles(const ap_pic_batch *b, int i);
 const char *ap_pic_batch_last_error(const ap_pic_batch *b);
+
+/* A prescribed current density (3 x cells doubles, staggered like E) added to the
+ * particles' current in every following electromagnetic step (em = 1), until set
+ * again; NULL clears it. */
+ap_pic_status ap_pic_set_current(ap_pic *h, const double *J);
 
 /* The magnetic field of the electromagnetic step (em = 1): 3 x cells doubles,
  * component-major, Bx at (i, j+1/2), By at (i+1/2, j), Bz at (i+1/2, j+1/2). */

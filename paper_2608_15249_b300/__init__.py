@@ -46,6 +46,7 @@ EXPORTS = [
     "ap_pic_get_perm", "ap_pic_get_diag", "ap_pic_set_timing", "ap_pic_get_timing",
     "ap_pic_kernel_launches", "ap_pic_num_particles", "ap_pic_last_error", "ap_pic_version",
     "ap_pic_sort_perm_noalloc", "ap_pic_set_collisions", "ap_pic_collide", "ap_pic_get_B",
+    "ap_pic_set_current",
     "ap_pic_batch_default_tuning", "ap_pic_batch_create", "ap_pic_batch_destroy",
     "ap_pic_batch_load", "ap_pic_batch_step", "ap_pic_batch_push_deposit", "ap_pic_batch_sort",
     "ap_pic_batch_solve_field", "ap_pic_batch_set_tuning",
@@ -67,6 +68,7 @@ class ap_pic_config(ctypes.Structure):
         ("fx_bits", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
         ("brick", ctypes.c_int * 3), ("diag_every", ctypes.c_int), ("solver", ctypes.c_int),
         ("pusher", ctypes.c_int), ("c_light", ctypes.c_double), ("em", ctypes.c_int),
+        ("em_boundary", ctypes.c_int), ("pml_cells", ctypes.c_int),
     ]
 
 
@@ -147,6 +149,7 @@ def _declare(L):
     L.ap_pic_set_collisions.argtypes = [P, ctypes.POINTER(ap_pic_mcc)]
     L.ap_pic_collide.argtypes = [P]
     L.ap_pic_get_B.argtypes = [P, P]
+    L.ap_pic_set_current.argtypes = [P, P]
     L.ap_pic_get_timing.argtypes = [P, P, P]
     L.ap_pic_kernel_launches.argtypes = []
     L.ap_pic_kernel_launches.restype = I64
@@ -195,7 +198,7 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
                 precision=AP_PIC_FP32_CELLOFF, sort_every=20, fx_bits=0, cg_rtol=0.0,
                 cg_maxit=0, brick=(0, 0, 0), diag_every=0,
                 solver=AP_PIC_SOLVER_CG, pusher=AP_PIC_PUSHER_BORIS,
-                c_light=0.0, em=0) -> ap_pic_config:
+                c_light=0.0, em=0, em_boundary=0, pml_cells=0) -> ap_pic_config:
     c = ap_pic_config()
     lib().ap_pic_config_default(ctypes.byref(c))
     c.ndim = ndim
@@ -220,6 +223,8 @@ def make_config(ndim, n, dx=(1.0, 1.0, 1.0), dt=0.1, q=-1.0, m=1.0, weight=1.0,
     c.pusher = int(pusher)
     c.c_light = float(c_light)
     c.em = int(em)
+    c.em_boundary = int(em_boundary)
+    c.pml_cells = int(pml_cells)
     return c
 
 
@@ -381,6 +386,16 @@ class Pic:
         out = np.empty(comps * self.cells, np.float64)
         self._check(self._lib.ap_pic_get_E(self.h, _ptr(out)))
         return out
+
+    def set_current(self, J):
+        """Prescribed current (3 x cells, staggered like E) for the following
+        electromagnetic steps; None clears it."""
+        if J is None:
+            self._check(self._lib.ap_pic_set_current(self.h, None))
+            return
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        assert J.size == 3 * self.cells
+        self._check(self._lib.ap_pic_set_current(self.h, _ptr(J)))
 
     def get_B(self):
         """3 x cells Yee-staggered magnetic field (em = 1)."""

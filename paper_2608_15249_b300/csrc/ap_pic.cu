@@ -90,6 +90,7 @@ struct ap_pic {
     // electromagnetic step (cfg.em)
     bool em = false;
     EmBufs emb{};
+    float *jext = nullptr;  // storage of the prescribed current
 
     // null-collision Monte Carlo (ap_pic_set_collisions)
     bool mcc_on = false;
@@ -377,6 +378,14 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
             return fail(h, AP_PIC_ERR_ARG, "Courant number c dt sqrt(sum 1/dx^2) = %.3f >= 1",
                         courant);
     }
+    if (c->em_boundary != 0 && c->em_boundary != 1)
+        return fail(h, AP_PIC_ERR_ARG, "em_boundary must be 0 or 1");
+    if (c->em_boundary == 1) {
+        if (!c->em) return fail(h, AP_PIC_ERR_ARG, "the absorbing layer needs em = 1");
+        if (c->pml_cells == 0) c->pml_cells = 12;
+        if (c->pml_cells < 1 || 2 * c->pml_cells >= c->n[0] || 2 * c->pml_cells >= c->n[1])
+            return fail(h, AP_PIC_ERR_ARG, "need 1 <= pml_cells and 2 pml_cells < n");
+    }
     if (c->solver == AP_PIC_SOLVER_FFT) {
         if (plain)
             return fail(h, AP_PIC_ERR_UNSUPPORTED, "the FP64 plain form solves with the CG only");
@@ -500,6 +509,64 @@ static ap_pic_status create_fft(ap_pic *h)
     return AP_PIC_OK;
 }
 
+// Profiles of the convolutional PML along one axis of n nodes, at integer (shift 0)
+// or half (shift 1/2) positions, for an update of step hstep: depth d = distance into
+// the layer / its thickness, sigma = 0.8 (m + 1) c / dx d^m (m = 3), kappa = 1,
+// alpha = 0; b = exp(-sigma hstep), c = b - 1 (sigma (b - 1) / (sigma kappa)), 1/kappa.
+static void cpml_profile(int n, int npml, double dx, double hstep, double c, double shift,
+                         float *b, float *cc, float *ik)
+{
+    const double sigma_max = 0.8 * 4.0 * c / dx;
+    for (int i = 0; i < n; ++i) {
+        const double x = i + shift;
+        double depth = (double)npml - x;
+        const double hi = x - (double)(n - 1 - npml);
+        if (hi > depth) depth = hi;
+        depth = depth > 0.0 ? depth / npml : 0.0;
+        b[i] = 1.0f;
+        cc[i] = 0.0f;
+        ik[i] = 1.0f;
+        if (depth <= 0.0) continue;
+        const double sigma = sigma_max * depth * depth * depth;
+        const double bb = exp(-sigma * hstep);
+        b[i] = (float)bb;
+        cc[i] = (float)(bb - 1.0);
+    }
+}
+
+static ap_pic_status create_cpml(ap_pic *h)
+{
+    const int n0 = h->cfg.n[0], n1 = h->cfg.n[1], npml = h->cfg.pml_cells;
+    const double c = h->cfg.c_light, dt = h->cfg.dt;
+    std::vector<float> host(3 * (size_t)(n0 + n1) * 2);
+    float *dev = nullptr;
+    TRY(alloc_n(h, &dev, host.size()));
+    // layout: for B (half positions, h = dt/2) then E (integer positions, h = dt):
+    // bx cx ikx (n0 each), by cy iky (n1 each)
+    size_t off = 0;
+    for (int part = 0; part < 2; ++part) {
+        const double shift = part == 0 ? 0.5 : 0.0, hs = part == 0 ? 0.5 * dt : dt;
+        const float **dst = part == 0 ? h->emb.pb : h->emb.pe;
+        float *b = host.data() + off;
+        cpml_profile(n0, npml, h->cfg.dx[0], hs, c, shift, b, b + n0, b + 2 * n0);
+        for (int k = 0; k < 3; ++k) dst[k] = dev + off + (size_t)k * n0;
+        off += 3 * (size_t)n0;
+        float *by = host.data() + off;
+        cpml_profile(n1, npml, h->cfg.dx[1], hs, c, shift, by, by + n1, by + 2 * n1);
+        for (int k = 0; k < 3; ++k) dst[3 + k] = dev + off + (size_t)k * n1;
+        off += 3 * (size_t)n1;
+    }
+    CU(h, cudaMemcpyAsync(dev, host.data(), host.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 4; ++k) {
+        TRY(alloc_n(h, &h->emb.psib[k], (size_t)h->cells));
+        TRY(alloc_n(h, &h->emb.psie[k], (size_t)h->cells));
+        CU(h, cudaMemsetAsync(h->emb.psib[k], 0, (size_t)h->cells * 4, h->stream));
+        CU(h, cudaMemsetAsync(h->emb.psie[k], 0, (size_t)h->cells * 4, h->stream));
+    }
+    return AP_PIC_OK;
+}
+
 static ap_pic_status create_grid(ap_pic *h)
 {
     if (h->plain) return create_grid_f64(h);
@@ -556,6 +623,7 @@ static ap_pic_status create_grid(ap_pic *h)
         CU(h, cudaMemsetAsync(h->emb.Jf, 0, c * 12, h->stream));
         CU(h, cudaMemsetAsync(h->emb.J, 0, c * 24, h->stream));
         for (int a = 0; a < 3; ++a) h->emb.B0[a] = (float)h->cfg.B0[a];
+        if (h->cfg.em_boundary == 1) TRY(create_cpml(h));
     }
     if (h->cfg.solver == AP_PIC_SOLVER_FFT) TRY(create_fft(h));
     return create_pinned(h);
@@ -941,6 +1009,8 @@ extern "C" ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, con
     if (!h) return AP_PIC_ERR_ARG;
     if (np < 0 || np >= (int64_t(1) << 31)) return fail(h, AP_PIC_ERR_ARG, "np out of range");
     if (np > 0 && (!x || !v)) return fail(h, AP_PIC_ERR_ARG, "x and v are required");
+    if (np > 0 && h->cfg.em_boundary == 1)
+        return fail(h, AP_PIC_ERR_UNSUPPORTED, "the absorbing layer runs fields only (np = 0)");
     TRY(alloc_particles(h, np));
     const int64_t chunk = np < LOAD_CHUNK ? (np > 0 ? np : 1) : LOAD_CHUNK;
     double *dx_buf = nullptr, *dv_buf = nullptr;
@@ -1170,6 +1240,23 @@ static ap_pic_status copy3_f32(ap_pic *h, const float *src, double *out)
     CU(h, cudaStreamSynchronize(h->stream));
     for (size_t i = 0; i < tmp.size(); ++i) out[i] = tmp[i];
     return sync_check(h);
+}
+
+extern "C" ap_pic_status ap_pic_set_current(ap_pic *h, const double *J)
+{
+    if (!h) return AP_PIC_ERR_ARG;
+    if (!h->em) return fail(h, AP_PIC_ERR_STATE, "a prescribed current needs em = 1");
+    if (!J) {
+        h->emb.Jext = nullptr;
+        return AP_PIC_OK;
+    }
+    if (!h->jext) TRY(alloc_n(h, &h->jext, (size_t)h->cells * 3));
+    std::vector<float> tmp((size_t)h->cells * 3);
+    for (size_t i = 0; i < tmp.size(); ++i) tmp[i] = (float)J[i];
+    CU(h, cudaMemcpyAsync(h->jext, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));  // tmp goes out of scope
+    h->emb.Jext = h->jext;
+    return AP_PIC_OK;
 }
 
 extern "C" ap_pic_status ap_pic_get_B(ap_pic *h, double *out)

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(EM_THREADS)
 // -(qw / (dx dt)), Jz qw / (dx dy); the accumulator is cleared for the next step.
 __global__ void __launch_bounds__(EM_THREADS)
     k_em_j_convert(int64_t cells, unsigned long long *__restrict__ Jacc, float *__restrict__ J,
-                   double fx, double fy, double fz)
+                   const float *__restrict__ Jext, double fx, double fy, double fz)
 {
     const double f[3] = {fx, fy, fz};
     for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
@@ -299,9 +299,85 @@ __global__ void __launch_bounds__(EM_THREADS)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const long long a = (long long)Jacc[k * cells + id];
-            J[k * cells + id] = (float)(f[k] * (double)a / (double)J_SCALE);
+            float j = (float)(f[k] * (double)a / (double)J_SCALE);
+            if (Jext) j += Jext[k * cells + id];
+            J[k * cells + id] = j;
             Jacc[k * cells + id] = 0ull;
         }
+}
+
+// ---- convolutional PML on a non-periodic grid (Roden and Gedney) ----------------------------
+// Values outside the grid count as zero; inside the layers every derivative d/da
+// becomes (1/kappa_a) d/da + psi with psi <- b psi + c dF/da; the tangential E on the
+// outer nodes is held at zero (a conducting wall behind the layer).
+
+__device__ __forceinline__ float at_or_zero(const float *F, int n0, int n1, int i, int j)
+{
+    return (i < 0 || j < 0 || i >= n0 || j >= n1) ? 0.0f : F[i + (int64_t)n0 * j];
+}
+
+__global__ void __launch_bounds__(EM_THREADS)
+    k_cpml_b(GridParams g, EmBufs em, float h, float idx, float idy)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    const float *Ex = em.E, *Ey = em.E + cells, *Ez = em.E + 2 * cells;
+    float *Bx = em.B, *By = em.B + cells, *Bz = em.B + 2 * cells;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS) {
+        int i, j;
+        coords2(id, g, &i, &j);
+        const float dyEz = (at_or_zero(Ez, n0, n1, i, j + 1) - Ez[id]) * idy;
+        const float dxEz = (at_or_zero(Ez, n0, n1, i + 1, j) - Ez[id]) * idx;
+        const float dxEy = (at_or_zero(Ey, n0, n1, i + 1, j) - Ey[id]) * idx;
+        const float dyEx = (at_or_zero(Ex, n0, n1, i, j + 1) - Ex[id]) * idy;
+        const float p0 = em.pb[3][j] * em.psib[0][id] + em.pb[4][j] * dyEz;
+        const float p1 = em.pb[0][i] * em.psib[1][id] + em.pb[1][i] * dxEz;
+        const float p2 = em.pb[0][i] * em.psib[2][id] + em.pb[1][i] * dxEy;
+        const float p3 = em.pb[3][j] * em.psib[3][id] + em.pb[4][j] * dyEx;
+        em.psib[0][id] = p0;
+        em.psib[1][id] = p1;
+        em.psib[2][id] = p2;
+        em.psib[3][id] = p3;
+        Bx[id] -= h * (em.pb[5][j] * dyEz + p0);
+        By[id] += h * (em.pb[2][i] * dxEz + p1);
+        Bz[id] -= h * ((em.pb[2][i] * dxEy + p2) - (em.pb[5][j] * dyEx + p3));
+    }
+}
+
+__global__ void __launch_bounds__(EM_THREADS)
+    k_cpml_e(GridParams g, EmBufs em, float c2, float dt, float idx, float idy)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    const float *Bx = em.B, *By = em.B + cells, *Bz = em.B + 2 * cells;
+    float *Ex = em.E, *Ey = em.E + cells, *Ez = em.E + 2 * cells;
+    const float *J = em.Jf;
+    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
+         id += (int64_t)gridDim.x * EM_THREADS) {
+        int i, j;
+        coords2(id, g, &i, &j);
+        const float dyBz = (Bz[id] - at_or_zero(Bz, n0, n1, i, j - 1)) * idy;
+        const float dxBz = (Bz[id] - at_or_zero(Bz, n0, n1, i - 1, j)) * idx;
+        const float dxBy = (By[id] - at_or_zero(By, n0, n1, i - 1, j)) * idx;
+        const float dyBx = (Bx[id] - at_or_zero(Bx, n0, n1, i, j - 1)) * idy;
+        const float p0 = em.pe[3][j] * em.psie[0][id] + em.pe[4][j] * dyBz;
+        const float p1 = em.pe[0][i] * em.psie[1][id] + em.pe[1][i] * dxBz;
+        const float p2 = em.pe[0][i] * em.psie[2][id] + em.pe[1][i] * dxBy;
+        const float p3 = em.pe[3][j] * em.psie[3][id] + em.pe[4][j] * dyBx;
+        em.psie[0][id] = p0;
+        em.psie[1][id] = p1;
+        em.psie[2][id] = p2;
+        em.psie[3][id] = p3;
+        const bool xb = i == 0 || i == n0 - 1, yb = j == 0 || j == n1 - 1;
+        const float ex = Ex[id] + dt * (c2 * (em.pe[5][j] * dyBz + p0) - J[id]);
+        const float ey = Ey[id] + dt * (-c2 * (em.pe[2][i] * dxBz + p1) - J[cells + id]);
+        const float ez = Ez[id] + dt * (c2 * ((em.pe[2][i] * dxBy + p2) - (em.pe[5][j] * dyBx + p3)) -
+                                        J[2 * cells + id]);
+        Ex[id] = (yb || i == n0 - 1) ? 0.0f : ex;
+        Ey[id] = (xb || j == n1 - 1) ? 0.0f : ey;
+        Ez[id] = (xb || yb) ? 0.0f : ez;
+    }
 }
 
 // Initial field of the load: E = -grad phi by forward differences onto the staggered
@@ -387,8 +463,17 @@ cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, d
 {
     const int64_t cells = (int64_t)g.n[0] * g.n[1];
     const int nb = em_blocks(cells);
-    k_em_j_convert<<<nb, EM_THREADS, 0, st>>>(cells, em.J, em.Jf, -qw / (dy * dt),
+    k_em_j_convert<<<nb, EM_THREADS, 0, st>>>(cells, em.J, em.Jf, em.Jext, -qw / (dy * dt),
                                               -qw / (dx * dt), qw / (dx * dy));
+    if (em.pb[0]) {
+        // non-periodic grid with the absorbing layer
+        const float idx = (float)(1.0 / dx), idy = (float)(1.0 / dy);
+        k_cpml_b<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(0.5 * dt), idx, idy);
+        k_cpml_e<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(c * c), (float)dt, idx, idy);
+        k_cpml_b<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(0.5 * dt), idx, idy);
+        note_launch(4);
+        return cudaGetLastError();
+    }
     const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
     k_yee_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hdx, hdy);
     k_yee_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, em.Jf, em.E, (float)(c * c * dt / dx),

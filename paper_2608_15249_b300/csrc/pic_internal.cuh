@@ -234,7 +234,13 @@ struct EmBufs {
     float *E, *B;              // [3][cells] Yee-staggered fields at integer time
     float *Jf;                 // [3][cells] current of the last step (staggered like E)
     unsigned long long *J;     // [3][cells] fixed-point current weights (2^30)
+    float *Jext;               // [3][cells] prescribed current added each step, or null
     float B0[3];               // uniform external B added to the gathered one
+    // convolutional PML (non-periodic grid), null when periodic:
+    // profiles b, c, 1/kappa per axis, at half positions for the B half steps
+    // (pb[0..2] along x, pb[3..5] along y) and integer positions for the E step (pe)
+    const float *pb[6], *pe[6];
+    float *psib[4], *psie[4];  // Bx_y, By_x, Bz_x, Bz_y;  Ex_y, Ey_x, Ez_x, Ez_y
 };
 int em_particle_blocks(int64_t np);
 // Gather, Boris with the gathered B, and (move) the move, Esirkepov current and the
