@@ -23,7 +23,13 @@ namespace apk {
 namespace {
 
 constexpr int EM_THREADS = 256;
-constexpr float J_SCALE = 1073741824.0f;   // 2^30: fixed point of the current weights
+// Fixed point of the current: the Jx, Jy weights (|w| <= 1) at 2^22, rounded with the
+// FMA magic number (exact for |w 2^22| <= 2^22, no float-to-int conversion, which
+// would issue on the slow FP64 pipe); the Jz weights (weight times vz, unbounded) at
+// the same scale through a rounding conversion.
+constexpr float J_SCALE = 4194304.0f;      // 2^22
+constexpr float RND_MAGIC_F = 12582912.0f; // 1.5 * 2^23
+constexpr int RND_MAGIC_I = 0x4B400000;
 
 __device__ __forceinline__ int wrapi(int i, int n)
 {
@@ -59,6 +65,13 @@ __device__ __forceinline__ float shape1(float d)
 {
     const float a = fabsf(d);
     return a < 1.0f ? 1.0f - a : 0.0f;
+}
+
+// |v| <= 1: round(v 2^22) by the FMA magic number
+__device__ __forceinline__ void add_fx_unit(unsigned long long *acc, float v)
+{
+    const int q = __float_as_int(fmaf(v, J_SCALE, RND_MAGIC_F)) - RND_MAGIC_I;
+    if (q) atomicAdd(acc, (unsigned long long)(long long)q);
 }
 
 __device__ __forceinline__ void add_fx(unsigned long long *acc, float v)
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(EM_THREADS)
 #pragma unroll
             for (int aq = 0; aq < 3; ++aq) {
                 run += DS[0][aq] * (S0[1][bq] + 0.5f * DS[1][bq]);
-                add_fx(em.J + wrapi(base[0] + aq, n0) + (int64_t)n0 * jj, run);
+                add_fx_unit(em.J + wrapi(base[0] + aq, n0) + (int64_t)n0 * jj, run);
             }
         }
 #pragma unroll
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(EM_THREADS)
 #pragma unroll
             for (int bq = 0; bq < 3; ++bq) {
                 run += DS[1][bq] * (S0[0][aq] + 0.5f * DS[0][aq]);
-                add_fx(em.J + cells + ii + (int64_t)n0 * wrapi(base[1] + bq, n1), run);
+                add_fx_unit(em.J + cells + ii + (int64_t)n0 * wrapi(base[1] + bq, n1), run);
             }
         }
 #pragma unroll
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(EM_THREADS)
         int qk[4], rest = one;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            qk[k] = __float2int_rn(wx[k & 1] * wy[k >> 1] * scale);
+            qk[k] = __float_as_int(fmaf(wx[k & 1] * wy[k >> 1], scale, RND_MAGIC_F)) - RND_MAGIC_I;
             rest -= qk[k];
         }
         qk[3] = rest;
