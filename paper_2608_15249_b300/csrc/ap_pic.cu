@@ -87,6 +87,16 @@ struct ap_pic {
     int *h_err = nullptr;
     int *h_iters = nullptr;
 
+    // step graphs: with the spectral solve a step has no host decision, so each
+    // (buffer parity, diagnostics, sort) variant is captured once and replayed on an
+    // own non-blocking stream fenced to the caller's
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t graphs[8] = {};
+    int64_t graph_launches[8] = {};
+    int graph_slot[8] = {};
+    int parity = 0;  // flips with every sort (the ping-pong particle buffers)
+
     // electromagnetic step (cfg.em)
     bool em = false;
     EmBufs emb{};
@@ -716,6 +726,11 @@ extern "C" ap_pic_status ap_pic_destroy(ap_pic *h)
     if (h->h_accsum) cudaFreeHost(h->h_accsum);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_iters) cudaFreeHost(h->h_iters);
+    for (auto &gx : h->graphs)
+        if (gx) cudaGraphExecDestroy(gx);
+    if (h->gev_in) cudaEventDestroy(h->gev_in);
+    if (h->gev_out) cudaEventDestroy(h->gev_out);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     delete h;
     return AP_PIC_OK;
 }
@@ -936,6 +951,7 @@ static ap_pic_status sort_particles(ap_pic *h)
     CU(h, launch_sort_perm(g, h->brick, h->key_bits, h->p.cell, h->np, h->sort, &slot, h->stream));
     CU(h, launch_apply_perm(h->sort.idx[slot], h->p, h->p_alt, h->ndim, h->stream));
     stage_end(h, mk);
+    h->parity ^= 1;
     ParticlesF32 t = h->p;
     h->p = h->p_alt;
     h->p_alt = t;
@@ -1190,6 +1206,69 @@ extern "C" ap_pic_status ap_pic_collide(ap_pic *h)
     return AP_PIC_OK;
 }
 
+// A step can replay a graph when it holds no host decision and no per-step value:
+// the FP32 form with the spectral solve, no collisions (their draws take the step
+// number), not the electromagnetic step, stage timing off.
+static bool step_graphable(const ap_pic *h)
+{
+    return !h->plain && h->use_fft && !h->mcc_on && !h->em && !h->timing;
+}
+
+// One step through its captured graph (captured on first use of its variant).
+static ap_pic_status graph_step(ap_pic *h, bool diag, bool sort)
+{
+    if (!h->gstream) {
+        CU(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        CU(h, cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+        CU(h, cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    }
+    const int key = h->parity * 4 + (diag ? 2 : 0) + (sort ? 1 : 0);
+    // fence: the graph stream after the caller's work
+    CU(h, cudaEventRecord(h->gev_in, h->stream));
+    CU(h, cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+    if (!h->graphs[key]) {
+        cudaStream_t user = h->stream;
+        h->stream = h->gstream;
+        const int64_t before = ap_pic_kernel_launches();
+        cudaGraph_t graph = nullptr;
+        ap_pic_status st = AP_PIC_OK;
+        cudaError_t ce = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            st = push_deposit(h, diag);
+            if (st == AP_PIC_OK && sort) st = sort_particles(h);
+            if (st == AP_PIC_OK) st = solve_field(h);
+            if (st == AP_PIC_OK && diag) st = finalize_diag(h, true);
+            ce = cudaStreamEndCapture(h->gstream, &graph);
+        }
+        h->stream = user;
+        if (st != AP_PIC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CU(h, ce);
+        const cudaError_t ie = cudaGraphInstantiate(&h->graphs[key], graph, 0);
+        cudaGraphDestroy(graph);
+        CU(h, ie);
+        // the capture recorded the launches without running them; the host state
+        // (a sort's buffer swap) is already that of after the step
+        h->graph_launches[key] = ap_pic_kernel_launches() - before;
+        note_launch(-(int)h->graph_launches[key]);
+        h->graph_slot[key] = h->perm_slot;
+    } else if (sort) {
+        // replay of a step with a sort: the host side of the swap
+        h->parity ^= 1;
+        ParticlesF32 t = h->p;
+        h->p = h->p_alt;
+        h->p_alt = t;
+        h->perm_slot = h->graph_slot[key];
+    }
+    CU(h, cudaGraphLaunch(h->graphs[key], h->gstream));
+    note_launch((int)h->graph_launches[key]);
+    CU(h, cudaEventRecord(h->gev_out, h->gstream));
+    CU(h, cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+    return AP_PIC_OK;
+}
+
 extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
 {
     TRY(need_loaded(h));
@@ -1201,6 +1280,11 @@ extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
             TRY(em_step(h, diag));
             if (h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0) TRY(sort_particles(h));
             if (diag) TRY(finalize_diag(h, true));
+            h->step = k;
+            continue;
+        }
+        if (step_graphable(h)) {
+            TRY(graph_step(h, diag, h->cfg.sort_every > 0 && k % h->cfg.sort_every == 0));
             h->step = k;
             continue;
         }

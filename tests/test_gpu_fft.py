@@ -102,3 +102,26 @@ def test_fft_larger_grids(pk, n):
     sim = _sim(w).load(w.x, w.v, half_push=False)
     assert rel(g.get_E(), sim.E, np.abs(sim.E).max()) <= TOL
     g.close()
+
+
+def test_step_graph_replay_equals_direct_launches(pk):
+    """With the spectral solve ap_pic_step replays captured graphs (stage timing
+    turns them off): both give the same state bit for bit, through several sorts
+    (both buffer parities) and steps with and without diagnostics."""
+    w = cases()["2d_mixed"]
+    runs = []
+    for timing in (False, True):
+        g = pk.from_workload(w, solver=pk.AP_PIC_SOLVER_FFT, sort_every=2, diag_every=3)
+        g.load(w.x, w.v)
+        g.set_timing(timing)
+        g.step(9)
+        d = g.get_diag()
+        runs.append((g.get_rho_fx(), g.get_E(), g.get_particles(), g.get_perm(), d))
+        g.close()
+    a, b = runs
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    for x, y in zip(a[2], b[2]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a[3], b[3])
+    assert a[4]["step"] == b[4]["step"] == 9 and a[4]["kinetic"] == b[4]["kinetic"]
