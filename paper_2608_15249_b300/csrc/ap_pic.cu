@@ -478,11 +478,8 @@ static ap_pic_status create_grid_f64(ap_pic *h)
 // twiddle table for the longest transform, and the complex work array.
 static ap_pic_status create_fft(ap_pic *h)
 {
-    static bool configured = false;
-    if (!configured) {
-        CU(h, fft_configure());
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    CU(h, once_per_device(configured, [] { return fft_configure(); }));
     FftPlan &P = h->fft;
     P.ndim = h->ndim;
     P.cells = h->cells;

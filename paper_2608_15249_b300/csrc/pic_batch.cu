@@ -716,11 +716,8 @@ ap_pic_status upload_tile_params(ap_pic_batch *b, double factor)
 // Tables and job lists of the spectral solve (grids already placed in the arenas).
 ap_pic_status setup_fft(ap_pic_batch *b)
 {
-    static bool configured = false;
-    if (!configured) {
-        BCU(b, fft_configure());
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    BCU(b, once_per_device(configured, [] { return fft_configure(); }));
     const int n = b->count;
     using Key = std::pair<int, double>;
     std::map<Key, size_t> at;  // float offset of the tables of an (n, dx) axis
@@ -937,6 +934,18 @@ ap_pic_status leave(ap_pic_batch *b)
     return AP_PIC_OK;
 }
 
+// Runs `body` between the two fences; the exit fence is recorded on failure too,
+// so the caller's stream stays ordered after whatever the body enqueued.  The
+// body's error wins over the fence's.
+template <class F>
+ap_pic_status fenced(ap_pic_batch *b, F &&body)
+{
+    BTRY(enter(b));
+    const ap_pic_status s = body();
+    const ap_pic_status l = leave(b);
+    return s != AP_PIC_OK ? s : l;
+}
+
 ap_pic_status batch_sync_check(ap_pic_batch *b)
 {
     BCU(b, cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
@@ -1150,16 +1159,10 @@ ap_pic_status batch_sort(ap_pic_batch *b)
     return AP_PIC_OK;
 }
 
-}  // namespace
-
-// Loads every instance: x[i] (np[i] x ndim_i) and v[i] (np[i] x 2), host FP64.
-extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
-                                           const double *const *x, const double *const *v,
-                                           unsigned flags)
+// The upload and set-up of ap_pic_batch_load, inside its fences.
+ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const *x,
+                        const double *const *v, unsigned flags)
 {
-    if (!b || !np || !x || !v) return AP_PIC_ERR_ARG;
-    if (b->loaded) return bfail(b, AP_PIC_ERR_STATE, "the batch is already loaded");
-    BTRY(enter(b));
     const int n = b->count;
     b->np.assign(np, np + n);
     b->pbase.resize(n);
@@ -1382,7 +1385,19 @@ extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
     }
     b->loaded = true;
     b->step = 0;
-    BTRY(leave(b));
+    return AP_PIC_OK;
+}
+
+}  // namespace
+
+// Loads every instance: x[i] (np[i] x ndim_i) and v[i] (np[i] x 2), host FP64.
+extern "C" ap_pic_status ap_pic_batch_load(ap_pic_batch *b, const int64_t *np,
+                                           const double *const *x, const double *const *v,
+                                           unsigned flags)
+{
+    if (!b || !np || !x || !v) return AP_PIC_ERR_ARG;
+    if (b->loaded) return bfail(b, AP_PIC_ERR_STATE, "the batch is already loaded");
+    BTRY(fenced(b, [&] { return load_body(b, np, x, v, flags); }));
     return batch_sync_check(b);
 }
 
@@ -1427,21 +1442,22 @@ extern "C" ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps)
 {
     BTRY(need_loaded(b, 0));
     if (nsteps < 0) return bfail(b, AP_PIC_ERR_ARG, "nsteps must be >= 0");
-    BTRY(enter(b));
-    for (int s = 0; s < nsteps; ++s) {
-        const int64_t k = b->step + 1;
-        if (b->tune.use_graph) {
-            BTRY(ensure_graph(b));
-            BCU(b, cudaGraphLaunch(b->graphs[b->parity], b->stream));
-            note_launch((int)b->graph_launches);
-        } else {
-            BTRY(step_front(b, true));
+    return fenced(b, [&]() -> ap_pic_status {
+        for (int s = 0; s < nsteps; ++s) {
+            const int64_t k = b->step + 1;
+            if (b->tune.use_graph) {
+                BTRY(ensure_graph(b));
+                BCU(b, cudaGraphLaunch(b->graphs[b->parity], b->stream));
+                note_launch((int)b->graph_launches);
+            } else {
+                BTRY(step_front(b, true));
+            }
+            if (b->tune.sort_every > 0 && k % b->tune.sort_every == 0) BTRY(batch_sort(b));
+            if (!b->use_fft) BTRY(step_back(b, b->tune.cg_iters_per_graph));
+            b->step = k;
         }
-        if (b->tune.sort_every > 0 && k % b->tune.sort_every == 0) BTRY(batch_sort(b));
-        if (!b->use_fft) BTRY(step_back(b, b->tune.cg_iters_per_graph));
-        b->step = k;
-    }
-    return leave(b);
+        return AP_PIC_OK;
+    });
 }
 
 // The parts of a step on their own (a step is push_deposit, a sort when due,
@@ -1449,35 +1465,30 @@ extern "C" ap_pic_status ap_pic_batch_step(ap_pic_batch *b, int nsteps)
 extern "C" ap_pic_status ap_pic_batch_push_deposit(ap_pic_batch *b)
 {
     BTRY(need_loaded(b, 0));
-    BTRY(enter(b));
-    BCU(b, cudaMemsetAsync(b->G.A.acc, 0, (size_t)b->total_nodes * 8, b->stream));
-    BTRY(batch_pass(b, true, true, true, true));
-    BTRY(batch_convert(b));
-    return leave(b);
+    return fenced(b, [&]() -> ap_pic_status {
+        BCU(b, cudaMemsetAsync(b->G.A.acc, 0, (size_t)b->total_nodes * 8, b->stream));
+        BTRY(batch_pass(b, true, true, true, true));
+        return batch_convert(b);
+    });
 }
 
 extern "C" ap_pic_status ap_pic_batch_sort(ap_pic_batch *b)
 {
     BTRY(need_loaded(b, 0));
-    BTRY(enter(b));
-    BTRY(batch_sort(b));
-    return leave(b);
+    return fenced(b, [&] { return batch_sort(b); });
 }
 
 extern "C" ap_pic_status ap_pic_batch_solve_field(ap_pic_batch *b)
 {
     BTRY(need_loaded(b, 0));
-    BTRY(enter(b));
-    BatchGrid &G = b->G;
-    if (b->use_fft) {
-        BTRY(field_fft(b));
-        return leave(b);
-    }
-    const int first = b->tune.cg_iters_per_graph;
-    cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
-    cg_iters(b, G.A.phi, 0, first, b->cfg[0].cg_maxit, b->cfg[0].cg_rtol);
-    BTRY(step_back(b, first));
-    return leave(b);
+    return fenced(b, [&]() -> ap_pic_status {
+        BatchGrid &G = b->G;
+        if (b->use_fft) return field_fft(b);
+        const int first = b->tune.cg_iters_per_graph;
+        cg_start(b, G.A.phi, G.A.b, b->cfg[0].cg_rtol);
+        cg_iters(b, G.A.phi, 0, first, b->cfg[0].cg_maxit, b->cfg[0].cg_rtol);
+        return step_back(b, first);
+    });
 }
 
 extern "C" int64_t ap_pic_batch_num_particles(const ap_pic_batch *b, int i)

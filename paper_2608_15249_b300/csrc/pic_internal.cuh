@@ -6,12 +6,33 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "ap_pic.h"
 
 namespace apk {
 
 // Counts kernel launches (process-wide); every launcher calls it once per kernel.
 void note_launch(int n = 1);
+
+// Runs the set-up `f` (a kernel attribute, which is per device) once for the
+// current device, marking it in `done` (one bit per device); thread-safe.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<unsigned long long> &done, F &&f)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    static std::mutex m;
+    std::lock_guard<std::mutex> lock(m);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // Division by a loop-invariant divisor d >= 2 through a multiply-high
 // (Granlund and Montgomery, "Division by invariant integers using

@@ -846,14 +846,12 @@ static cudaError_t launch_pass_m(const Src &src, ParticlesF32 p, double *diag_bl
                                  int *err, cudaStream_t st)
 {
     constexpr size_t smem = pass_smem_bytes<D, NV>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_particle_pass<D, NV, MODE, Src>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(k_particle_pass<D, NV, MODE, Src>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     k_particle_pass<D, NV, MODE, Src><<<nblocks, PP_THREADS, smem, st>>>(src, p, diag_blocks, err);
     note_launch();
     return cudaGetLastError();

@@ -301,13 +301,12 @@ cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm
             cudaError_t e2 = launch_exclusive_scan_u32(s.hist, s.hist, hist_len, s.scan_tmp, st);
             if (e2 != cudaSuccess) return e2;
             const size_t smem = (size_t)ST_WARPS * RADIX * 4;
-            static bool configured = false;
-            if (!configured) {
-                e2 = cudaFuncSetAttribute(k_scatter<RADIX>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e2 != cudaSuccess) return e2;
-                configured = true;
-            }
+            static std::atomic<unsigned long long> configured{0};
+            e2 = once_per_device(configured, [smem] {
+                return cudaFuncSetAttribute(k_scatter<RADIX>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            });
+            if (e2 != cudaSuccess) return e2;
             k_scatter<RADIX><<<(unsigned)ntiles, ST_THREADS, smem, st>>>(
                 s.keys[cur], idx_in, np, shift, s.hist, ntiles, keys_out, s.idx[cur ^ 1]);
             note_launch();
