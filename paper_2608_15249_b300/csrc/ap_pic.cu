@@ -742,7 +742,8 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
     // fixed-point scale: S <= 62 - bitlen(np) keeps |sum| < 2^62 whatever the clustering
     const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
     h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
-    h->dpart.nblocks = particle_pass_blocks(np > 0 ? np : 1, h->ndim);
+    h->dpart.nblocks = h->plain ? plain_pass_blocks(np > 0 ? np : 1, h->ndim)
+                                : particle_pass_blocks(np > 0 ? np : 1, h->ndim, h->nv);
     TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
     CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
     if (h->plain) {

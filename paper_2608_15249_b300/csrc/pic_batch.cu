@@ -531,7 +531,7 @@ struct BatchGrid {
 
 namespace {
 
-constexpr int B_TILE = 512;      // particle tile (the shared pass's tile)
+constexpr int B_TILE = PASS_TILE;  // particle tile (the shared pass's tile)
 constexpr int64_t PAD = 64;      // instance ranges in the particle arena start on multiples of 64
 
 int bitlen_u(uint64_t x)

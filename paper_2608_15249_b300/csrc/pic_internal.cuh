@@ -140,9 +140,23 @@ cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
 size_t batch_tile_params_bytes();
 void make_tile_params(void *dst, const GridParams &g, const float *E, unsigned long long *acc);
 
-// Number of blocks the particle pass uses for np particles (fixed, so the
-// diagnostics reduction order is deterministic).
-int particle_pass_blocks(int64_t np, int ndim);
+// Particles per tile of the particle pass in 1D and 2D (3 per thread of a
+// 256-thread CTA; the batch packs its instances in tiles of the same size), and in
+// 3D (2 per thread: the 3D pass needs more registers per particle).
+constexpr int PASS_TILE = 768;
+constexpr int PASS_TILE_3D = 512;
+
+// Number of blocks the particle pass uses for np particles with nv velocity
+// components: one resident wave (the CTAs of the pass that fit an SM, times the
+// SMs), fewer for small np.  Fixed for a handle, so the diagnostics reduction
+// order is deterministic.
+int particle_pass_blocks(int64_t np, int ndim, int nv);
+
+// The same for the FP64 plain pass.
+int plain_pass_blocks(int64_t np, int ndim);
+
+// SMs of the current device (cached on first use).
+int sm_count();
 
 // Reconstruct positions (FP64) from cell + offset for host read-back.
 cudaError_t launch_positions_f64(const GridParams &g, const double *dx, ParticlesF32 p,

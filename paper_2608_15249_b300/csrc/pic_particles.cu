@@ -333,11 +333,17 @@ __device__ __forceinline__ float twice_ke_rel(const float *u, float inv_c2)
 
 // ---- TMA bulk-copy pipeline helpers (PTX) ---------------------------------------------------
 
-constexpr int TILE = 512;           // particles per tile (2 per thread)
+template <int D>
+__host__ __device__ constexpr int tile_of_dim() { return D == 3 ? PASS_TILE_3D : PASS_TILE; }
+constexpr int TILE_MAX = PASS_TILE > PASS_TILE_3D ? PASS_TILE : PASS_TILE_3D;
 constexpr int WIN_BITS = 11;        // a tile's shared-memory charge window: 2^11 nodes
 constexpr int WIN_CAP = 1 << WIN_BITS;
 constexpr int STAGES = 3;           // tiles in flight per CTA
 constexpr int WAIT_LIMIT = 1 << 26;   // bounded mbarrier polling
+// window words at or above WIN_NEG hold negative node totals (see the flush)
+constexpr unsigned WIN_NEG = 0u - (unsigned)(4 * TILE_MAX);
+static_assert((long long)TILE_MAX * (1ll << 22) < (long long)WIN_NEG,
+              "a tile's node total must stay below the negative range of the window");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -412,14 +418,15 @@ struct TileParams {
     unsigned long long *acc;
 };
 
-// One instance: tiles of TILE consecutive particles of [0, np).
+// One instance: tiles of `tile` (the pass's tile size) consecutive particles of [0, np).
 struct SingleSrc {
     static constexpr bool PER_TILE_DIAG = false;
     TileParams tp;
     int64_t np;
-    __device__ int64_t ntiles() const { return (np + TILE - 1) / TILE; }
-    __device__ int64_t start(int64_t t) const { return t * TILE; }
-    __device__ int count(int64_t t) const { return np - t * TILE < TILE ? (int)(np - t * TILE) : TILE; }
+    int tile;
+    __device__ int64_t ntiles() const { return (np + tile - 1) / tile; }
+    __device__ int64_t start(int64_t t) const { return t * tile; }
+    __device__ int count(int64_t t) const { return np - t * tile < tile ? (int)(np - t * tile) : tile; }
     __device__ void load_params(int64_t, TileParams *) const {}
     __device__ const TileParams &params(const TileParams &) const { return tp; }
 };
@@ -453,11 +460,12 @@ struct BatchSrc {
 // independent instances packed in one particle arena (BatchSrc, whose tiles each
 // carry their instance's parameters, field and charge accumulator).
 template <int D, int NV, int MODE, class Src>
-__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
+__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     k_particle_pass(Src src, ParticlesF32 p, double *__restrict__ diag_blocks,
                     int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int TILE = tile_of_dim<D>();
     constexpr int R = TILE / PP_THREADS;
     constexpr int NA_MAX = 1 + D + NV;
     constexpr bool PUSH = (MODE & PASS_PUSH) != 0, MOVE = (MODE & PASS_MOVE) != 0;
@@ -738,15 +746,16 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
             __syncthreads();
             if (use_win) {
                 // flush: every touched node once to global memory, leaving the window zero.
-                // A node's tile total lies in [-TILE, TILE * 2^S] with S <= 22, so the
-                // int32 bits decode unambiguously.
+                // A node's tile total lies in [-2 TILE, TILE * 2^S] with S <= 22 (a
+                // particle's last corner quantum is at least -2), so its 32 bits
+                // decode unambiguously: WIN_NEG and above are the negative totals.
                 const int total = 1 << tot_bits;
                 for (int i = tid; i < total; i += PP_THREADS) {
                     const unsigned u = s_win[i];
                     if (u == 0u) continue;
                     s_win[i] = 0u;
                     const long long val =
-                        u > 0x80000400u ? (long long)u - (1ll << 32) : (long long)u;
+                        u >= WIN_NEG ? (long long)u - (1ll << 32) : (long long)u;
                     int node = 0, stride = 1;
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
@@ -821,23 +830,64 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 5)
 template <int D, int NV>
 constexpr size_t pass_smem_bytes()
 {
-    return (size_t)STAGES * (1 + D + NV) * TILE * 4 + STAGES * 8 + WIN_CAP * 4 + 8 * 4;
+    return (size_t)STAGES * (1 + D + NV) * tile_of_dim<D>() * 4 + STAGES * 8 + WIN_CAP * 4 + 8 * 4;
 }
 
-int particle_pass_blocks(int64_t np, int ndim)
+int sm_count()
 {
-    static int sms = 0;
-    if (!sms) {
+    static std::atomic<int> sms{0};
+    int n = sms.load(std::memory_order_relaxed);
+    if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n <= 0) {
+            cudaGetLastError();
+            n = 148;
+        }
+        sms.store(n, std::memory_order_relaxed);
     }
-    // one resident wave: 5 CTAs of 256 threads per SM (3 in 3D, where the pass needs
-    // more registers and shared memory), each walking tiles of TILE particles
-    const int64_t need = (np + TILE - 1) / TILE;
-    const int64_t cap = (int64_t)sms * (ndim == 3 ? 3 : 5);
-    int64_t b = need < cap ? need : cap;
+    return n;
+}
+
+// CTAs of the pass resident per SM, from the occupancy calculator for the fused
+// pass with diagnostics (every mode of a (D, NV) has the same dynamic shared
+// memory, and the launch bounds give each at least this many).
+template <int D, int NV>
+int pass_ctas_per_sm()
+{
+    static std::atomic<int> cached{0};
+    int c = cached.load(std::memory_order_relaxed);
+    if (c) return c;
+    constexpr size_t smem = pass_smem_bytes<D, NV>();
+    auto k = k_particle_pass<D, NV, PASS_PUSH | PASS_MOVE | PASS_DEPOSIT | PASS_DIAG, SingleSrc>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k, PP_THREADS, smem) != cudaSuccess ||
+        c < 1) {
+        cudaGetLastError();
+        c = 1;
+    }
+    cached.store(c, std::memory_order_relaxed);
+    return c;
+}
+
+int particle_pass_blocks(int64_t np, int ndim, int nv)
+{
+    int per_sm = 1;
+    switch (ndim * 10 + nv) {
+    case 11: per_sm = pass_ctas_per_sm<1, 1>(); break;
+    case 12: per_sm = pass_ctas_per_sm<1, 2>(); break;
+    case 13: per_sm = pass_ctas_per_sm<1, 3>(); break;
+    case 22: per_sm = pass_ctas_per_sm<2, 2>(); break;
+    case 23: per_sm = pass_ctas_per_sm<2, 3>(); break;
+    default: per_sm = pass_ctas_per_sm<3, 3>(); break;
+    }
+    // one resident wave of persistent CTAs, each walking tiles of particles
+    const int64_t tile = ndim == 3 ? PASS_TILE_3D : PASS_TILE;
+    const int64_t need = (np + tile - 1) / tile;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    const int64_t b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -903,12 +953,13 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
     if (p.np == 0) return cudaSuccess;
     const int mode = pass_mode(push, mv, deposit, diag.blocks != nullptr) |
                      (push && g.pusher == AP_PIC_PUSHER_HIGUERA_CARY ? PASS_HC : 0);
-    const int nb = particle_pass_blocks(p.np, g.ndim);
+    const int nb = particle_pass_blocks(p.np, g.ndim, p.nv);
     SingleSrc src;
     src.tp.g = g;
     src.tp.E = E;
     src.tp.acc = acc;
     src.np = p.np;
+    src.tile = g.ndim == 3 ? PASS_TILE_3D : PASS_TILE;
     switch (g.ndim * 10 + p.nv) {
     case 11: return launch_pass_t<1, 1>(src, p, mode, diag.blocks, nb, err, st);
     case 12: return launch_pass_t<1, 2>(src, p, mode, diag.blocks, nb, err, st);
@@ -931,7 +982,12 @@ cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
     src.tiles = tiles;
     src.inst = static_cast<const TileParams *>(inst_params);
     src.nt = ntiles;
-    const int nb = nblocks < ntiles ? nblocks : (int)ntiles;
+    // at most one resident wave, whatever the tuning asks for
+    const int64_t wave = (int64_t)sm_count() *
+                         (ndim == 1 ? pass_ctas_per_sm<1, 2>() : pass_ctas_per_sm<2, 2>());
+    int64_t nb64 = nblocks < ntiles ? nblocks : ntiles;
+    nb64 = nb64 < wave ? nb64 : wave;
+    const int nb = (int)(nb64 < 1 ? 1 : nb64);
     switch (ndim * 10 + p.nv) {
     case 12: return launch_pass_t<1, 2>(src, p, mode, diag_tiles, nb, err, st);
     case 22: return launch_pass_t<2, 2>(src, p, mode, diag_tiles, nb, err, st);

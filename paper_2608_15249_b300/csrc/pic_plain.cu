@@ -166,6 +166,15 @@ static void launch_plain_t(const GridParamsF64 &g, ParticlesF64 p, const double 
     note_launch();
 }
 
+int plain_pass_blocks(int64_t np, int ndim)
+{
+    // one wave: 5 CTAs of 256 threads per SM (3 in 3D), 512 particles per CTA at least
+    const int64_t need = (np + 511) / 512;
+    const int64_t cap = (int64_t)sm_count() * (ndim == 3 ? 3 : 5);
+    const int64_t b = need < cap ? need : cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
 cudaError_t launch_plain_pass(const GridParamsF64 &g, ParticlesF64 p, const double *E,
                               unsigned long long *acc, bool push, bool mv, bool deposit,
                               DiagPartials diag, int *err, cudaStream_t st)
@@ -173,7 +182,7 @@ cudaError_t launch_plain_pass(const GridParamsF64 &g, ParticlesF64 p, const doub
     if (p.np == 0) return cudaSuccess;
     const int mode = (push ? 1 : 0) | (mv ? 2 : 0) | (deposit ? 4 : 0) |
                      (diag.blocks && push ? 8 : 0);
-    const int nb = particle_pass_blocks(p.np, g.ndim);
+    const int nb = plain_pass_blocks(p.np, g.ndim);
     switch (g.ndim * 10 + p.nv) {
     case 11: launch_plain_t<1, 1>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
     case 12: launch_plain_t<1, 2>(g, p, E, acc, mode, diag.blocks, nb, err, st); break;
