@@ -92,6 +92,33 @@ def _grid_bytes_per_node(ndim, f64=False):
     return (8 if f64 else 4) * ndim + 8
 
 
+def _spectral_bytes_per_node(ndim):
+    """Algorithmic bytes per node of one spectral field solve: two transform solves
+    (the solve and its refinement), each a pass per axis over the complex grid (the
+    first reads the FP32 right-hand side, 4 + 8 B; the last writes the FP32
+    potential, 8 + 4 B; the others 8 + 8 B; in 1D one real-to-real pass, 4 + 4 B),
+    the FP64 residual (8 B rho + 4 B phi + 4 B out), the correction (4 + 4 + 4 B)
+    and E = -grad phi (4 B + 4 B per axis)."""
+    solve = 8 if ndim == 1 else 12 + 16 * (2 * ndim - 3) + 12
+    return 2 * solve + 16 + 12 + 4 + 4 * ndim
+
+
+def _roofline(alg_bytes, ms, kernel, peak, peak_kind, traffic=None, **extra):
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+           "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": ms,
+           "peak_kind": peak_kind}
+    out.update(extra)
+    return out
+
+
+def _timed(fn):
+    t0 = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t0
+
+
 class Clocks:
     """nvidia-smi sampled every 100 ms while the timed region runs."""
 
@@ -289,8 +316,12 @@ def bench_ours(args):
         gf.set_timing(False)
         gf.close()
         field_ms["fft"] = ff[0] / max(ff[1], 1)
-    collisions = None if (f64 or args.no_collisions) else bench_collisions(args, pk, torch, stream)
-    em = None if (f64 or args.no_em) else bench_em(args, pk, torch, stream)
+    rows = not (f64 or args.no_rows)
+    spectral = bench_spectral(args, w, field_ms["fft"], peak, peak_kind) if rows else None
+    hc = bench_hc(args, w, pk, torch, stream, peak, peak_kind) if rows else None
+    collisions = None if (f64 or args.no_collisions) else bench_collisions(
+        args, pk, torch, stream, peak, peak_kind)
+    em = None if (f64 or args.no_em) else bench_em(args, pk, torch, stream, peak, peak_kind)
     e2e = None
     if not args.no_e2e:
         solver = "cg" if f64 else args.e2e_solver
@@ -326,6 +357,8 @@ def bench_ours(args):
                          "peak_kind": peak_kind},
             "stage_ms_per_call": breakdown,
             "field_solve_ms": field_ms,
+            "spectral_solve": spectral,
+            "higuera_cary": hc,
             "collisions": collisions,
             "electromagnetic": em,
             "gpu_launches": int(launches),
@@ -442,10 +475,16 @@ def bench_precision(args):
     print(json.dumps(out), flush=True)
 
 
-def bench_em(args, pk, torch, stream, steps=20):
+def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
     """CUDA-event time of full electromagnetic steps (particles with the Esirkepov
     current, Yee field update, sort every 20 steps) on a 2D3V Maxwellian of the
-    benchmark's size, c = 4 v_te (Courant number 0.57)."""
+    benchmark's size, c = 4 v_te (Courant number 0.57); the roofline of its particle
+    kernel (k_em_push: gather E and B, Boris, move, Esirkepov current; 48 B of
+    record read and written per particle, E and B read and the int64 current
+    written, 48 B per node) from the stage timing of separate steps; and the
+    oracle's step on a sample of the particles on the same grid."""
+    import oracle
+
     w = workloads.maxwellian_box(2, (args.n, args.n), ppc=args.ppc, nv=3, dt=0.1, seed=7)
     g = pk.from_workload(w, stream=stream.cuda_stream, em=1, c_light=4.0, sort_every=20)
     g.load(w.x, w.v)
@@ -457,17 +496,45 @@ def bench_em(args, pk, torch, stream, steps=20):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    g.set_timing(True)
+    g.step(steps)
+    st = g.get_timing()
+    g.set_timing(False)
     g.close()
-    return {"ms_per_step": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
-            "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, c = 4, dt = 0.1, "
-                        "full electromagnetic step"}
+    push_ms = st["push_deposit"][0] / max(st["push_deposit"][1], 1)
+    field_ms = st["field"][0] / max(st["field"][1], 1)
+    out = {"ms_per_step": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
+           "stage_ms": {"k_em_push": push_ms, "yee_fields": field_ms},
+           "roofline": _roofline(w.np_ * 48 + w.cells * 48, push_ms,
+                                 "k_em_push (gather E, B + Boris + move + Esirkepov current)",
+                                 peak, peak_kind),
+           "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, c = 4, dt = 0.1, "
+                       "full electromagnetic step"}
+    if not args.no_row_oracles:
+        sample = min(w.np_, 1 << 20)
+        sim = oracle.EmSimulation(w.n, w.dx, w.dt, 4.0, weight=w.weight, rtol=1e-6)
+        sim.load(w.x[:sample], w.v[:sample])
+        _, secs = _timed(lambda: sim.step(2))
+        out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": sample * 2 / secs,
+                         "sample": f"{sample} of {w.np_} particles on the full grid, 2 full "
+                                   f"electromagnetic steps ({secs:.1f} s)"}
+    return out
 
 
-def bench_collisions(args, pk, torch, stream):
-    """CUDA-event time of the collision pass alone (ap_pic_collide) on 2D3V electrons."""
+def bench_collisions(args, pk, torch, stream, peak, peak_kind):
+    """CUDA-event time of the collision pass alone (ap_pic_collide) on 2D3V electrons.
+    Repeated passes without a step draw the same numbers, so the counts reported are
+    those of the first pass.  Algorithmic bytes: every particle's id (4 B), and for
+    each candidate (a fraction P = 1 - exp(-nu' dt) of the particles) its id again
+    and its velocity read and written (4 + 24 B).  Beside it, the oracle's pass on
+    a sample of the same particles."""
+    import oracle
+
     w = workloads.maxwellian_box(2, (args.n, args.n), ppc=args.ppc, nv=3, dt=0.1, seed=6)
     g = pk.from_workload(w, stream=stream.cuda_stream).set_collisions(**MCC_BENCH)
     g.load(w.x, w.v)
+    g.collide()
+    counts = g.get_diag()["mcc_counts"]
     for _ in range(3):
         g.collide()
     torch.cuda.synchronize()
@@ -479,13 +546,90 @@ def bench_collisions(args, pk, torch, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    counts = g.get_diag()["mcc_counts"]
     g.close()
-    return {"ms_per_pass": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
-            "collisions_per_pass": {"elastic": counts[0], "excitation": counts[1],
-                                    "above_bound": counts[2]},
-            "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, "
-                        + ", ".join(f"{k}={v}" for k, v in MCC_BENCH.items())}
+    P = 1.0 - np.exp(-MCC_BENCH["density"] * (MCC_BENCH["sigma_el"] + MCC_BENCH["sigma_exc"])
+                     * MCC_BENCH["vmax"] * w.dt)
+    out = {"ms_per_pass": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
+           "collisions_first_pass": {"elastic": counts[0], "excitation": counts[1],
+                                     "above_bound": counts[2]},
+           "candidate_fraction": P,
+           "roofline": _roofline(w.np_ * 4 + P * w.np_ * 28, ms, "k_mcc", peak, peak_kind),
+           "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, "
+                       + ", ".join(f"{k}={v}" for k, v in MCC_BENCH.items())}
+    if not args.no_row_oracles:
+        v = np.array(w.v, dtype=np.float64)
+        ids = np.arange(w.np_, dtype=np.uint32)
+        (_, secs) = _timed(lambda: [oracle.mcc(v, ids, k, MCC_BENCH, w.m, w.dt)
+                                    for k in range(1, 5)])
+        out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": w.np_ * 4 / secs,
+                         "sample": f"all {w.np_} particles, 4 passes ({secs:.1f} s)"}
+    return out
+
+
+def bench_spectral(args, w, fft_ms, peak, peak_kind):
+    """Roofline of the spectral field solve (timed on the GPU beside the CG) and the
+    oracle's field solve of the same grid (FP64 Jacobi-PCG to 1e-12, whose discrete
+    potential the spectral solve reproduces) on the charge of a sample of the
+    workload's particles."""
+    import oracle
+
+    out = {"ms_per_solve": fft_ms, "nodes": w.cells,
+           "roofline": _roofline(w.cells * _spectral_bytes_per_node(w.ndim), fft_ms,
+                                 "spectral solve (k_fft_axis per axis x 2 solves, k_residual64, "
+                                 "k_add_correction, k_efield)", peak, peak_kind,
+                                 residency="the grid (a few MB) stays in L2")}
+    if not args.no_row_oracles:
+        sample = min(w.np_, 1 << 20)
+        rho = oracle.deposit(w.ndim, w.n, w.dx, w.x[:sample], w.q * w.weight * w.np_ / sample)
+        rho -= rho.mean()
+        (_, it, _), secs = _timed(lambda: oracle.poisson(w.ndim, w.n, w.dx, rho, 1e-12))
+        out["oracle"] = {"kind": "oracle", "cores": 1, "ms_per_solve": secs * 1e3,
+                         "iterations": int(it),
+                         "sample": f"one solve of the full grid, right-hand side from {sample} "
+                                   "particles"}
+    return out
+
+
+def bench_hc(args, w, pk, torch, stream, peak, peak_kind, steps=100, c=4.0):
+    """The particle pass with the Higuera-Cary pusher (c = 4 v_te) on the headline
+    workload: stage-timed push_deposit (same algorithmic bytes as the Boris pass),
+    and the oracle's Higuera-Cary gather + push + move + deposit on a sample."""
+    import oracle
+
+    g = pk.from_workload(w, stream=stream.cuda_stream, pusher=pk.AP_PIC_PUSHER_HIGUERA_CARY,
+                         c_light=c)
+    g.load(w.x, w.v)
+    for _ in range(5):
+        g.push_deposit()
+    torch.cuda.synchronize()
+    g.set_timing(True)
+    for k in range(1, steps + 1):
+        g.push_deposit()
+        if w.sort_every and k % w.sort_every == 0:
+            g.sort()
+    st = g.get_timing()
+    g.set_timing(False)
+    g.close()
+    ms = st["push_deposit"][0] / max(st["push_deposit"][1], 1)
+    alg = w.np_ * _bytes_per_particle(w.ndim, w.nv) + w.cells * _grid_bytes_per_node(w.ndim)
+    out = {"pass_ms": ms, "particle_steps_per_s": w.np_ / (ms * 1e-3), "c": c,
+           "roofline": _roofline(alg, ms, "k_particle_pass, Higuera-Cary mode", peak, peak_kind)}
+    if not args.no_row_oracles:
+        sample = min(w.np_, 1 << 20)
+        sim = oracle.Simulation(w.ndim, w.n, w.dx, w.dt, q=w.q, m=w.m, weight=w.weight, B0=w.B0,
+                                E0=w.E0, rtol=1e-6, pusher="hc", c=c)
+        sim.load(w.x[:sample], w.v[:sample])
+
+        def run():
+            for _ in range(8):
+                sim.push()
+                sim.move()
+                oracle.deposit(w.ndim, w.n, w.dx, sim.x, w.q * w.weight)
+        _, secs = _timed(run)
+        out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": sample * 8 / secs,
+                         "sample": f"{sample} of {w.np_} particles on the full grid, 8 steps of "
+                                   f"gather+push+move+deposit ({secs:.1f} s)"}
+    return out
 
 
 def run_e2e(args, w, pk, torch, stream, extra, steps):
@@ -681,6 +825,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-collisions", action="store_true")
     ap.add_argument("--no-em", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the spectral-solve and Higuera-Cary rows")
+    ap.add_argument("--no-row-oracles", action="store_true",
+                    help="skip the oracle timings beside the spectral, HC, MCC and EM rows")
     ap.add_argument("--prec-steps", type=int, default=10, help="--workload precision_study")
     ap.add_argument("--drift-steps", type=int, default=1000, help="--workload precision_study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
