@@ -479,7 +479,7 @@ def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
     """CUDA-event time of full electromagnetic steps (particles with the Esirkepov
     current, Yee field update, sort every 20 steps) on a 2D3V Maxwellian of the
     benchmark's size, c = 4 v_te (Courant number 0.57); the roofline of its particle
-    kernel (k_em_push: gather E and B, Boris, move, Esirkepov current; 48 B of
+    kernels (k_em_tile, k_em_spread: gather E and B, Boris, move, Esirkepov current; 48 B of
     record read and written per particle, E and B read and the int64 current
     written, 48 B per node) from the stage timing of separate steps; and the
     oracle's step on a sample of the particles on the same grid."""
@@ -504,9 +504,9 @@ def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
     push_ms = st["push_deposit"][0] / max(st["push_deposit"][1], 1)
     field_ms = st["field"][0] / max(st["field"][1], 1)
     out = {"ms_per_step": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
-           "stage_ms": {"k_em_push": push_ms, "yee_fields": field_ms},
+           "stage_ms": {"em_particles": push_ms, "yee_fields": field_ms},
            "roofline": _roofline(w.np_ * 48 + w.cells * 48, push_ms,
-                                 "k_em_push (gather E, B + Boris + move + Esirkepov current)",
+                                 "k_em_tile + k_em_spread (gather E, B + Boris + move + Esirkepov current)",
                                  peak, peak_kind),
            "workload": f"maxwellian 2D3V {args.n}x{args.n}, {args.ppc} ppc, c = 4, dt = 0.1, "
                        "full electromagnetic step"}

@@ -654,6 +654,8 @@ static void free_particles(ap_pic *h)
     dev_free(h, h->sort.hist);
     dev_free(h, h->sort.scan_tmp);
     dev_free(h, h->dpart.blocks);
+    dev_free(h, h->emb.tile_flag);
+    h->emb.tile_flag = nullptr;
     h->p = ParticlesF32{};
     h->p_alt = ParticlesF32{};
     h->sort = SortScratch{};
@@ -743,9 +745,15 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
     const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
     h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
     h->dpart.nblocks = h->plain ? plain_pass_blocks(np > 0 ? np : 1, h->ndim)
+                       : h->em  ? 2 * em_particle_blocks(np > 0 ? np : 1)
                                 : particle_pass_blocks(np > 0 ? np : 1, h->ndim, h->nv);
     TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
     CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
+    if (h->em) {
+        const size_t tiles = (size_t)((np + EM_PASS_TILE - 1) / EM_PASS_TILE) + 1;
+        TRY(alloc_n(h, &h->emb.tile_flag, tiles));
+        CU(h, cudaMemsetAsync(h->emb.tile_flag, 0, tiles, h->stream));
+    }
     if (h->plain) {
         TRY(alloc_n(h, &h->p64.x, n * h->ndim));
         TRY(alloc_n(h, &h->p64.v, n * h->nv));

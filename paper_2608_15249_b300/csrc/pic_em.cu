@@ -26,7 +26,8 @@ constexpr int EM_THREADS = 256;
 // Fixed point of the current: the Jx, Jy weights (|w| <= 1) at 2^22, rounded with the
 // FMA magic number (exact for |w 2^22| <= 2^22, no float-to-int conversion, which
 // would issue on the slow FP64 pipe); the Jz weights (weight times vz, unbounded) at
-// the same scale through a rounding conversion.
+// the same scale, by the magic number below 2^22 and a rounding conversion above
+// (both round to nearest, ties to even, so the two agree).
 constexpr float J_SCALE = 4194304.0f;      // 2^22
 constexpr float RND_MAGIC_F = 12582912.0f; // 1.5 * 2^23
 constexpr int RND_MAGIC_I = 0x4B400000;
@@ -34,6 +35,14 @@ constexpr int RND_MAGIC_I = 0x4B400000;
 __device__ __forceinline__ int wrapi(int i, int n)
 {
     return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// i mod n in [0, n) for any i (the remainder only off the fast path)
+__device__ __forceinline__ int wrap_any(int i, int n)
+{
+    if ((unsigned)i < (unsigned)n) return i;
+    i %= n;
+    return i < 0 ? i + n : i;
 }
 
 // Weights of a staggered CIC lattice along one axis: the particle at c + f sees the
@@ -76,138 +85,165 @@ __device__ __forceinline__ void add_fx_unit(unsigned long long *acc, float v)
 
 __device__ __forceinline__ void add_fx(unsigned long long *acc, float v)
 {
-    const long long q = __float2ll_rn(v * J_SCALE);
+    const float y = v * J_SCALE;  // exact (a power-of-two scale)
+    const long long q = fabsf(y) < J_SCALE ? (long long)(__float_as_int(y + RND_MAGIC_F) - RND_MAGIC_I)
+                                           : __float2ll_rn(y);
     if (q) atomicAdd(acc, (unsigned long long)q);
 }
 
+// Boris with the gathered fields: t = (q/m) B h / 2, s = 2 t / (1 + t^2).
+__device__ __forceinline__ void em_boris(const float *v, const float *e, const float *b,
+                                         const GridParams &g, float *vn)
+{
+    float t[3], s[3], vm[3];
+    float tt = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        t[a] = g.qmh2 * b[a];
+        tt += t[a] * t[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s[a] = 2.0f * t[a] / (1.0f + tt);
+        vm[a] = v[a] + g.qmh2 * e[a];
+    }
+    const float w0 = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
+    const float w1 = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
+    const float w2 = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
+    vn[0] = vm[0] + (w1 * s[2] - w2 * s[1]) + g.qmh2 * e[0];
+    vn[1] = vm[1] + (w2 * s[0] - w0 * s[2]) + g.qmh2 * e[1];
+    vn[2] = vm[2] + (w0 * s[1] - w1 * s[0]) + g.qmh2 * e[2];
+}
+
+// The move along one axis, at most one cell (the current stencil below assumes it):
+// o = f + v dt / dx; returns false for a longer move.  sh is the cell shift, fr the
+// new offset.  The old and new CIC supports (nodes c, c + 1 and c + sh, c + sh + 1)
+// lie in the three lattice nodes from c + m, m = min(sh, 0); S0 and DS are the
+// Esirkepov shape factors there: S0 at the old position, DS the change to the new.
+__device__ __forceinline__ bool em_move_axis(float f, float vdtdx, int *sh, int *m, float *fr,
+                                             float *S0, float *DS)
+{
+    const float o = f + vdtdx;
+    bool ok = o > -1.0f && o < 2.0f;
+    const bool hi = o >= 1.0f, lo = o < 0.0f;
+    float r = hi ? o - 1.0f : (lo ? o + 1.0f : o);
+    int s = hi ? 1 : (lo ? -1 : 0);
+    if (r >= 1.0f) {  // o a tiny negative number: its fraction rounded up to 1
+        r = 0.0f;
+        s += 1;
+    }
+    *sh = s;
+    *fr = r;
+    const int mm = s < 0 ? -1 : 0;
+    *m = mm;
+    // positions relative to node c + m: old f - m, new fr + sh - m (both in [0, 2))
+    const float u0 = f - (float)mm, u1 = r + (float)(s - mm);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S0[k] = shape1(u0 - (float)k);
+        DS[k] = shape1(u1 - (float)k) - S0[k];
+    }
+    return ok;
+}
+
+// Jz weight of lattice node (aq, bq) of the stencil (Esirkepov's W_z in 2D).
+__device__ __forceinline__ float esirkepov_wz(const float (&S0)[2][3], const float (&DS)[2][3],
+                                              int aq, int bq)
+{
+    return S0[0][aq] * S0[1][bq] + 0.5f * DS[0][aq] * S0[1][bq] + 0.5f * S0[0][aq] * DS[1][bq] +
+           DS[0][aq] * DS[1][bq] * (1.0f / 3.0f);
+}
+
+// One particle through the whole particle part of the step, reading the fields and
+// adding the current and charge in global memory (the half push of the load, with
+// MOVE false, and the particles of tiles too spread out for the shared-memory
+// windows).  A particle that is not finite or moves more than a cell is left where it
+// is and flagged.
 template <bool MOVE>
-__global__ void __launch_bounds__(EM_THREADS)
-    k_em_push(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
-              double *__restrict__ diag_blocks, int *__restrict__ err)
+__device__ __forceinline__ void em_particle_global(int64_t i, const GridParams &g, ParticlesF32 p,
+                                                   const EmBufs &em,
+                                                   unsigned long long *__restrict__ rho_acc,
+                                                   float scale, int one, float &ke, float *mom,
+                                                   bool &bad)
 {
     const int n0 = g.n[0], n1 = g.n[1];
     const int64_t cells = (int64_t)n0 * n1;
-    const float *Ex = em.E, *Ey = em.E + cells, *Ez = em.E + 2 * cells;
-    const float *Bx = em.B, *By = em.B + cells, *Bz = em.B + 2 * cells;
-    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
-    bool bad = false;
-    const float scale = ldexpf(1.0f, g.fx_bits);
-    const int one = 1 << g.fx_bits;
-    for (int64_t i = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; i < p.np;
-         i += (int64_t)gridDim.x * EM_THREADS) {
-        const int cell = p.cell[i];
-        int c[3] = {0, 0, 0};
-        c[1] = (int)fdiv((uint32_t)cell, g.div0);
-        c[0] = cell - c[1] * n0;
-        float f[3] = {p.off[i], p.off[p.stride + i], 0.0f};
-        float v[3] = {p.v[i], p.v[p.stride + i], p.v[2 * p.stride + i]};
-        // staggered gathers
-        int ix[2], iy[2];
-        float fx[2], fy[2];
-        stagger(c[0], f[0], false, n0, &ix[0], &fx[0]);
-        stagger(c[0], f[0], true, n0, &ix[1], &fx[1]);
-        stagger(c[1], f[1], false, n1, &iy[0], &fy[0]);
-        stagger(c[1], f[1], true, n1, &iy[1], &fy[1]);
-        float e[3], b[3];
-        e[0] = lattice_cic(Ex, n0, n1, ix[1], fx[1], iy[0], fy[0]);
-        e[1] = lattice_cic(Ey, n0, n1, ix[0], fx[0], iy[1], fy[1]);
-        e[2] = lattice_cic(Ez, n0, n1, ix[0], fx[0], iy[0], fy[0]);
-        b[0] = lattice_cic(Bx, n0, n1, ix[0], fx[0], iy[1], fy[1]) + em.B0[0];
-        b[1] = lattice_cic(By, n0, n1, ix[1], fx[1], iy[0], fy[0]) + em.B0[1];
-        b[2] = lattice_cic(Bz, n0, n1, ix[1], fx[1], iy[1], fy[1]) + em.B0[2];
+    const int cell = p.cell[i];
+    int c[2];
+    c[1] = (int)fdiv((uint32_t)cell, g.div0);
+    c[0] = cell - c[1] * n0;
+    const float f[2] = {p.off[i], p.off[p.stride + i]};
+    const float v[3] = {p.v[i], p.v[p.stride + i], p.v[2 * p.stride + i]};
+    // staggered gathers
+    int ix[2], iy[2];
+    float fx[2], fy[2];
+    stagger(c[0], f[0], false, n0, &ix[0], &fx[0]);
+    stagger(c[0], f[0], true, n0, &ix[1], &fx[1]);
+    stagger(c[1], f[1], false, n1, &iy[0], &fy[0]);
+    stagger(c[1], f[1], true, n1, &iy[1], &fy[1]);
+    float e[3], b[3];
+    e[0] = lattice_cic(em.E, n0, n1, ix[1], fx[1], iy[0], fy[0]);
+    e[1] = lattice_cic(em.E + cells, n0, n1, ix[0], fx[0], iy[1], fy[1]);
+    e[2] = lattice_cic(em.E + 2 * cells, n0, n1, ix[0], fx[0], iy[0], fy[0]);
+    b[0] = lattice_cic(em.B, n0, n1, ix[0], fx[0], iy[1], fy[1]) + em.B0[0];
+    b[1] = lattice_cic(em.B + cells, n0, n1, ix[1], fx[1], iy[0], fy[0]) + em.B0[1];
+    b[2] = lattice_cic(em.B + 2 * cells, n0, n1, ix[1], fx[1], iy[1], fy[1]) + em.B0[2];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
-        // Boris with the gathered B: t = (q/m) B h / 2, s = 2 t / (1 + t^2)
-        float t[3], s[3], vm[3];
-        float tt = 0.0f;
+    for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
+    float vn[3];
+    em_boris(v, e, b, g, vn);
+    bool finite = isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]);
+    float o2 = 0.0f, n2 = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            t[a] = g.qmh2 * b[a];
-            tt += t[a] * t[a];
-        }
+    for (int a = 0; a < 3; ++a) {
+        o2 += v[a] * v[a];
+        n2 += vn[a] * vn[a];
+        mom[a] += vn[a];
+        p.v[a * p.stride + i] = vn[a];
+    }
+    ke += 0.5f * (o2 + n2);
+    if constexpr (!MOVE) {
+        if (!finite) bad = true;
+    } else {
+        int sh[2], m[2];
+        float fn[2], S0[2][3], DS[2][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            s[a] = 2.0f * t[a] / (1.0f + tt);
-            vm[a] = v[a] + g.qmh2 * e[a];
-        }
-        const float w0 = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
-        const float w1 = vm[1] + (vm[2] * t[0] - vm[0] * t[2]);
-        const float w2 = vm[2] + (vm[0] * t[1] - vm[1] * t[0]);
-        const float vn[3] = {vm[0] + (w1 * s[2] - w2 * s[1]) + g.qmh2 * e[0],
-                             vm[1] + (w2 * s[0] - w0 * s[2]) + g.qmh2 * e[1],
-                             vm[2] + (w0 * s[1] - w1 * s[0]) + g.qmh2 * e[2]};
-        bool finite = isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]);
-        float o2 = 0.0f, n2 = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o2 += v[a] * v[a];
-            n2 += vn[a] * vn[a];
-            mom[a] += vn[a];
-            p.v[a * p.stride + i] = vn[a];
-        }
-        ke += 0.5f * (o2 + n2);
-        if constexpr (!MOVE) {
-            if (!finite) bad = true;
-        } else {
-        // move: o = f + v dt / dx, one cell at most per axis (the stencil below)
-        int cn[2];
-        float fn[2], u1[2], S0[2][4], DS[2][4];
-        int base[2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const float o = f[a] + vn[a] * g.dtdx[a];
-            if (!(o > -1.0f && o < 2.0f)) finite = false;
-            const bool hi = o >= 1.0f, lo = o < 0.0f;
-            float fr = hi ? o - 1.0f : (lo ? o + 1.0f : o);
-            int sh = hi ? 1 : (lo ? -1 : 0);
-            if (fr >= 1.0f) {  // o a tiny negative number: its fraction rounded up to 1
-                fr = 0.0f;
-                sh += 1;
-            }
-            cn[a] = wrapi(c[a] + sh, g.n[a]);
-            fn[a] = fr;
-            // local coordinates on the 4 lattice nodes c - 1 .. c + 2
-            base[a] = c[a] - 1;
-            const float u0 = f[a] + 1.0f;
-            u1[a] = fr + (float)sh + 1.0f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                S0[a][k] = shape1(u0 - (float)k);
-                DS[a][k] = shape1(u1[a] - (float)k) - S0[a][k];
-            }
-        }
+        for (int a = 0; a < 2; ++a)
+            finite &= em_move_axis(f[a], vn[a] * g.dtdx[a], &sh[a], &m[a], &fn[a], S0[a], DS[a]);
         if (!finite) {
             bad = true;
-            continue;
+            return;
         }
-        // Esirkepov current, in units of the weights (scaled at conversion)
+        const int cn[2] = {wrapi(c[0] + sh[0], n0), wrapi(c[1] + sh[1], n1)};
+        const int base[2] = {c[0] + m[0], c[1] + m[1]};
+        // Esirkepov current on the 3 x 3 stencil, in units of the weights (scaled at
+        // conversion); Jx on the two x edges of each row, Jy on the two y edges of
+        // each column (the third is zero: the shape changes sum to zero)
 #pragma unroll
-        for (int bq = 0; bq < 4; ++bq) {
+        for (int bq = 0; bq < 3; ++bq) {
             const int jj = wrapi(base[1] + bq, n1);
             float run = 0.0f;
 #pragma unroll
-            for (int aq = 0; aq < 3; ++aq) {
+            for (int aq = 0; aq < 2; ++aq) {
                 run += DS[0][aq] * (S0[1][bq] + 0.5f * DS[1][bq]);
                 add_fx_unit(em.J + wrapi(base[0] + aq, n0) + (int64_t)n0 * jj, run);
             }
         }
 #pragma unroll
-        for (int aq = 0; aq < 4; ++aq) {
+        for (int aq = 0; aq < 3; ++aq) {
             const int ii = wrapi(base[0] + aq, n0);
             float run = 0.0f;
 #pragma unroll
-            for (int bq = 0; bq < 3; ++bq) {
+            for (int bq = 0; bq < 2; ++bq) {
                 run += DS[1][bq] * (S0[0][aq] + 0.5f * DS[0][aq]);
                 add_fx_unit(em.J + cells + ii + (int64_t)n0 * wrapi(base[1] + bq, n1), run);
             }
         }
 #pragma unroll
-        for (int bq = 0; bq < 4; ++bq)
+        for (int bq = 0; bq < 3; ++bq)
 #pragma unroll
-            for (int aq = 0; aq < 4; ++aq) {
-                const float wz = S0[0][aq] * S0[1][bq] + 0.5f * DS[0][aq] * S0[1][bq] +
-                                 0.5f * S0[0][aq] * DS[1][bq] +
-                                 DS[0][aq] * DS[1][bq] * (1.0f / 3.0f);
+            for (int aq = 0; aq < 3; ++aq) {
+                const float wz = esirkepov_wz(S0, DS, aq, bq);
                 if (wz != 0.0f)
                     add_fx(em.J + 2 * cells + wrapi(base[0] + aq, n0) +
                                (int64_t)n0 * wrapi(base[1] + bq, n1),
@@ -231,27 +267,302 @@ __global__ void __launch_bounds__(EM_THREADS)
         p.cell[i] = cn[0] + n0 * cn[1];
         p.off[i] = fn[0];
         p.off[p.stride + i] = fn[1];
-        }
     }
+}
+
+// The four diagnostic sums of a block (time-centred 2 KE, momentum), in FP64, into
+// diag_blocks[slot * 4 ..].
+__device__ __forceinline__ void em_block_diag(float ke, const float *mom, double *diag_blocks,
+                                              int slot)
+{
+    __shared__ double red[4][EM_THREADS / 32];
+    const float vals[4] = {ke, mom[0], mom[1], mom[2]};
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double x = vals[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double sum = 0.0;
+        for (int j = 0; j < EM_THREADS / 32; ++j) sum += red[threadIdx.x][j];
+        diag_blocks[(int64_t)slot * 4 + threadIdx.x] = sum;
+    }
+}
+
+// The load's backward half push: every particle, global fields, no move.
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_half_push(GridParams g, ParticlesF32 p, EmBufs em, int *__restrict__ err)
+{
+    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; i < p.np;
+         i += (int64_t)gridDim.x * EM_THREADS)
+        em_particle_global<false>(i, g, p, em, nullptr, 0.0f, 0, ke, mom, bad);
     if (bad) atomicOr(err, EF_NONFINITE);
-    if (diag_blocks) {
-        __shared__ double red[4][EM_THREADS / 32];
-        const float vals[4] = {ke, mom[0], mom[1], mom[2]};
-        const int w = threadIdx.x >> 5;
+}
+
+// The particle part of a step, tile by tile (EMT_TILE consecutive particles, one per
+// thread; persistent CTAs take tiles blockIdx.x, + gridDim.x, ...).  The particles
+// of a tile were sorted by cell, so their old cells fill a small box; the stencils
+// of the gather (cells c - 1 .. c + 1) and of the current and charge (c - 1 .. c + 2)
+// then lie in the box widened by one cell below and two above.  When that window
+// fits EMW_CAP nodes, the CTA copies the six field components of the window into
+// shared memory, gathers from there, and accumulates Jx, Jy, Jz and the charge in
+// int32 windows with shared atomics; every touched node then goes to the int64
+// global accumulators once.  A tile whose window does not fit is flagged and left
+// for k_em_spread.
+//
+// Overflow bounds of the int32 windows (256 particles per tile): |Jx|, |Jy| weights
+// <= 1 and charge quanta <= 2^22 + 2 per particle and node give |sum| < 2^31; a Jz
+// quantum at or above 2^22 (|vz W_z| >= 1) goes straight to global memory.
+constexpr int EMT_TILE = EM_PASS_TILE;
+constexpr int EMW_CAP = 1024;
+static_assert(EMT_TILE == EM_THREADS, "one particle per thread");
+
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_tile(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
+              double *__restrict__ diag_blocks, int *__restrict__ err)
+{
+    __shared__ float s_f[6][EMW_CAP];  // Ex, Ey, Ez, Bx, By, Bz of the window
+    __shared__ int s_j[4][EMW_CAP];    // Jx, Jy, Jz, charge quanta (zero between tiles)
+    __shared__ int s_box[2][4];        // per tile parity: min d0, min d1, max d0, max d1
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k = tid; k < 4 * EMW_CAP; k += EM_THREADS) (&s_j[0][0])[k] = 0;
+    if (tid < 8) (&s_box[0][0])[tid] = (tid & 3) < 2 ? 0x7fffffff : -0x7fffffff;
+    __syncthreads();
+    const float scale = ldexpf(1.0f, g.fx_bits);
+    const int one = 1 << g.fx_bits;
+    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
+    bool bad = false;
+    const int64_t ntiles = (p.np + EMT_TILE - 1) / EMT_TILE;
+    int par = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, par ^= 1) {
+        const int64_t i = t * EMT_TILE + tid;
+        const bool valid = i < p.np;
+        // reference cell: the tile's first particle's; d = old cell - reference,
+        // unwrapped to [-n/2, n/2] per axis
+        const int ref = p.cell[t * EMT_TILE];
+        int rc[2];
+        rc[1] = (int)fdiv((uint32_t)ref, g.div0);
+        rc[0] = ref - rc[1] * n0;
+        int c[2] = {0, 0}, d[2] = {0, 0};
+        float f[2] = {0.0f, 0.0f}, v[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            const int cell = p.cell[i];
+            c[1] = (int)fdiv((uint32_t)cell, g.div0);
+            c[0] = cell - c[1] * n0;
+            f[0] = p.off[i];
+            f[1] = p.off[p.stride + i];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            double x = vals[k];
+            for (int a = 0; a < 3; ++a) v[a] = p.v[a * p.stride + i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) == 0) red[k][w] = x;
+            for (int a = 0; a < 2; ++a) {
+                int dd = c[a] - rc[a];
+                dd -= (2 * dd > g.n[a]) ? g.n[a] : 0;
+                dd += (2 * dd < -g.n[a]) ? g.n[a] : 0;
+                d[a] = dd;
+            }
+        }
+        int *box = s_box[par];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int wl = __reduce_min_sync(0xffffffffu, valid ? d[a] : 0x7fffffff);
+            const int wh = __reduce_max_sync(0xffffffffu, valid ? d[a] : -0x7fffffff);
+            if (lane == 0) {
+                atomicMin(&box[a], wl);
+                atomicMax(&box[2 + a], wh);
+            }
         }
         __syncthreads();
-        if (threadIdx.x < 4) {
-            double sum = 0.0;
-            for (int j = 0; j < EM_THREADS / 32; ++j) sum += red[threadIdx.x][j];
-            diag_blocks[blockIdx.x * 4 + threadIdx.x] = sum;
+        const int lo0 = box[0], lo1 = box[1];
+        const int W0 = box[2] - lo0 + 4, W1 = box[3] - lo1 + 4;
+        if (W0 > EMW_CAP || W1 > EMW_CAP || W0 * W1 > EMW_CAP) {
+            if (tid == 0) em.tile_flag[t] = 1;
+            __syncthreads();  // every thread has read the box
+            if (tid < 4) box[tid] = tid < 2 ? 0x7fffffff : -0x7fffffff;
+            continue;
         }
+        if (tid == 0) em.tile_flag[t] = 0;
+        // local window node (lx, ly), index ly W0 + lx, is global node
+        // (g0 + lx, g1 + ly) mod n; the fill and the flush walk it by rows (a warp per
+        // row, lanes along x)
+        const int g0 = rc[0] + lo0 - 1, g1 = rc[1] + lo1 - 1;
+        const int warp = tid >> 5;
+        auto global_node = [&](int l) -> int64_t {
+            const int ly = l / W0, lx = l - ly * W0;
+            return wrap_any(g0 + lx, n0) + (int64_t)n0 * wrap_any(g1 + ly, n1);
+        };
+        for (int ly = warp; ly < W1; ly += EM_THREADS / 32) {
+            const int64_t row = (int64_t)n0 * wrap_any(g1 + ly, n1);
+            for (int lx = lane; lx < W0; lx += 32) {
+                const int64_t gid = row + wrap_any(g0 + lx, n0);
+                const int l = ly * W0 + lx;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    s_f[k][l] = __ldg(em.E + k * cells + gid);
+                    s_f[3 + k][l] = __ldg(em.B + k * cells + gid);
+                }
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            // the old cell's local coordinates, and the staggered gathers from the window
+            const int L0 = d[0] - lo0 + 1, L1 = d[1] - lo1 + 1;
+            const bool hx = f[0] >= 0.5f, hy = f[1] >= 0.5f;
+            const int ixh = hx ? L0 : L0 - 1, iyh = hy ? L1 : L1 - 1;
+            const float fxh = hx ? f[0] - 0.5f : f[0] + 0.5f;
+            const float fyh = hy ? f[1] - 0.5f : f[1] + 0.5f;
+            auto cic = [&](int k, int ix, float fx, int iy, float fy) {
+                const float *F = s_f[k] + ix + iy * W0;
+                return (1.0f - fy) * ((1.0f - fx) * F[0] + fx * F[1]) +
+                       fy * ((1.0f - fx) * F[W0] + fx * F[W0 + 1]);
+            };
+            float e[3], b[3];
+            e[0] = cic(0, ixh, fxh, L1, f[1]);
+            e[1] = cic(1, L0, f[0], iyh, fyh);
+            e[2] = cic(2, L0, f[0], L1, f[1]);
+            b[0] = cic(3, L0, f[0], iyh, fyh) + em.B0[0];
+            b[1] = cic(4, ixh, fxh, L1, f[1]) + em.B0[1];
+            b[2] = cic(5, ixh, fxh, iyh, fyh) + em.B0[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) e[a] += g.E0[a];
+            float vn[3];
+            em_boris(v, e, b, g, vn);
+            bool finite = isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]);
+            float o2 = 0.0f, n2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o2 += v[a] * v[a];
+                n2 += vn[a] * vn[a];
+                mom[a] += vn[a];
+                p.v[a * p.stride + i] = vn[a];
+            }
+            ke += 0.5f * (o2 + n2);
+            int sh[2], m[2];
+            float fn[2], S0[2][3], DS[2][3];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                finite &= em_move_axis(f[a], vn[a] * g.dtdx[a], &sh[a], &m[a], &fn[a], S0[a],
+                                       DS[a]);
+            if (!finite) {
+                bad = true;
+            } else {
+                // the stencil's lower corner (old cell + m) in window coordinates
+                const int B0i = L0 + m[0], B1i = L1 + m[1];
+#pragma unroll
+                for (int bq = 0; bq < 3; ++bq) {
+                    int *row = s_j[0] + (B1i + bq) * W0 + B0i;
+                    float run = 0.0f;
+#pragma unroll
+                    for (int aq = 0; aq < 2; ++aq) {
+                        run += DS[0][aq] * (S0[1][bq] + 0.5f * DS[1][bq]);
+                        const int q = __float_as_int(fmaf(run, J_SCALE, RND_MAGIC_F)) - RND_MAGIC_I;
+                        if (q) atomicAdd(row + aq, q);
+                    }
+                }
+#pragma unroll
+                for (int aq = 0; aq < 3; ++aq) {
+                    int *col = s_j[1] + B1i * W0 + B0i + aq;
+                    float run = 0.0f;
+#pragma unroll
+                    for (int bq = 0; bq < 2; ++bq) {
+                        run += DS[1][bq] * (S0[0][aq] + 0.5f * DS[0][aq]);
+                        const int q = __float_as_int(fmaf(run, J_SCALE, RND_MAGIC_F)) - RND_MAGIC_I;
+                        if (q) atomicAdd(col + bq * W0, q);
+                    }
+                }
+#pragma unroll
+                for (int bq = 0; bq < 3; ++bq)
+#pragma unroll
+                    for (int aq = 0; aq < 3; ++aq) {
+                        const float y = vn[2] * esirkepov_wz(S0, DS, aq, bq) * J_SCALE;
+                        const int l = (B1i + bq) * W0 + B0i + aq;
+                        if (fabsf(y) < J_SCALE) {
+                            const int q = __float_as_int(y + RND_MAGIC_F) - RND_MAGIC_I;
+                            if (q) atomicAdd(s_j[2] + l, q);
+                        } else {
+                            atomicAdd(em.J + 2 * cells + global_node(l),
+                                      (unsigned long long)__float2ll_rn(y));
+                        }
+                    }
+                // charge at the new position
+                const float wx[2] = {1.0f - fn[0], fn[0]}, wy[2] = {1.0f - fn[1], fn[1]};
+                int qk[4], rest = one;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    qk[k] = __float_as_int(fmaf(wx[k & 1] * wy[k >> 1], scale, RND_MAGIC_F)) -
+                            RND_MAGIC_I;
+                    rest -= qk[k];
+                }
+                qk[3] = rest;
+                int *q0 = s_j[3] + (L1 + sh[1]) * W0 + L0 + sh[0];
+                atomicAdd(q0, qk[0]);
+                atomicAdd(q0 + 1, qk[1]);
+                atomicAdd(q0 + W0, qk[2]);
+                atomicAdd(q0 + W0 + 1, qk[3]);
+                const int cn0 = wrapi(c[0] + sh[0], n0), cn1 = wrapi(c[1] + sh[1], n1);
+                p.cell[i] = cn0 + n0 * cn1;
+                p.off[i] = fn[0];
+                p.off[p.stride + i] = fn[1];
+            }
+        }
+        __syncthreads();
+        // flush: every touched node once to the int64 accumulators, leaving zeros
+        for (int ly = warp; ly < W1; ly += EM_THREADS / 32)
+            for (int lx = lane; lx < W0; lx += 32) {
+            const int l = ly * W0 + lx;
+            const int qx = s_j[0][l], qy = s_j[1][l], qz = s_j[2][l], qr = s_j[3][l];
+            if ((qx | qy | qz | qr) == 0) continue;
+            const int64_t gid = wrap_any(g0 + lx, n0) + (int64_t)n0 * wrap_any(g1 + ly, n1);
+            if (qx) {
+                s_j[0][l] = 0;
+                atomicAdd(em.J + gid, (unsigned long long)(long long)qx);
+            }
+            if (qy) {
+                s_j[1][l] = 0;
+                atomicAdd(em.J + cells + gid, (unsigned long long)(long long)qy);
+            }
+            if (qz) {
+                s_j[2][l] = 0;
+                atomicAdd(em.J + 2 * cells + gid, (unsigned long long)(long long)qz);
+            }
+            if (qr) {
+                s_j[3][l] = 0;
+                atomicAdd(rho_acc + gid, (unsigned long long)(long long)qr);
+            }
+            }
+        // reset this parity's box (read by all before the barrier above); it is next
+        // used two tiles on, after the next tile's barriers
+        if (tid < 4) box[tid] = tid < 2 ? 0x7fffffff : -0x7fffffff;
     }
+    if (bad) atomicOr(err, EF_NONFINITE);
+    if (diag_blocks) em_block_diag(ke, mom, diag_blocks, blockIdx.x);
+}
+
+// The tiles that k_em_tile flagged, particle by particle through global memory; every
+// block writes its diagnostic partials (slot gridDim.x + blockIdx.x).
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_spread(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
+                double *__restrict__ diag_blocks, int *__restrict__ err)
+{
+    const float scale = ldexpf(1.0f, g.fx_bits);
+    const int one = 1 << g.fx_bits;
+    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
+    bool bad = false;
+    const int64_t ntiles = (p.np + EMT_TILE - 1) / EMT_TILE;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (!em.tile_flag[t]) continue;
+        const int64_t i = t * EMT_TILE + threadIdx.x;
+        if (i < p.np) em_particle_global<true>(i, g, p, em, rho_acc, scale, one, ke, mom, bad);
+    }
+    if (bad) atomicOr(err, EF_NONFINITE);
+    if (diag_blocks) em_block_diag(ke, mom, diag_blocks, gridDim.x + blockIdx.x);
 }
 
 // Node coordinates of a flat index.
@@ -456,18 +767,43 @@ int em_blocks(int64_t n)
 
 }  // namespace
 
-int em_particle_blocks(int64_t np) { return em_blocks(np); }
+// One resident wave of the tiled particle kernel: the CTAs of k_em_tile that fit an
+// SM (occupancy calculator) times the SMs, fewer for small np.
+int em_particle_blocks(int64_t np)
+{
+    static std::atomic<int> per_sm{0};
+    int c = per_sm.load(std::memory_order_relaxed);
+    if (!c) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_em_tile, EM_THREADS, 0) !=
+                cudaSuccess ||
+            c < 1) {
+            cudaGetLastError();
+            c = 1;
+        }
+        per_sm.store(c, std::memory_order_relaxed);
+    }
+    const int64_t need = (np + EMT_TILE - 1) / EMT_TILE;
+    const int64_t cap = (int64_t)sm_count() * c;
+    const int64_t b = need < cap ? need : cap;
+    return (int)(b < 1 ? 1 : b);
+}
 
 cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
                            unsigned long long *rho_acc, double *diag_blocks, int nblocks,
                            int *err, cudaStream_t st)
 {
     if (p.np == 0) return cudaSuccess;
-    if (move)
-        k_em_push<true><<<nblocks, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
-    else
-        k_em_push<false><<<nblocks, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
-    note_launch();
+    if (!move) {
+        k_em_half_push<<<nblocks, EM_THREADS, 0, st>>>(g, p, em, err);
+        note_launch();
+        return cudaGetLastError();
+    }
+    // nblocks diagnostic slots: the first half for the tiled kernel, the second for
+    // the spread-out tiles
+    const int nb = nblocks / 2 > 0 ? nblocks / 2 : 1;
+    k_em_tile<<<nb, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
+    k_em_spread<<<nb, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err);
+    note_launch(2);
     return cudaGetLastError();
 }
 

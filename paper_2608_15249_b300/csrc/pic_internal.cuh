@@ -276,7 +276,14 @@ struct EmBufs {
     // (pb[0..2] along x, pb[3..5] along y) and integer positions for the E step (pe)
     const float *pb[6], *pe[6];
     float *psib[4], *psie[4];  // Bx_y, By_x, Bz_x, Bz_y;  Ex_y, Ey_x, Ez_x, Ez_y
+    // per particle tile of the step kernel: 1 when its particles were too spread out
+    // for the shared-memory windows (handled particle by particle), else 0
+    unsigned char *tile_flag;
 };
+// Particles per tile of the electromagnetic step kernel (one per thread).
+constexpr int EM_PASS_TILE = 256;
+// Blocks of one resident wave of the step kernel; the handle keeps twice as many
+// diagnostic slots (the tiled kernel's and the spread-out tiles').
 int em_particle_blocks(int64_t np);
 // Gather, Boris with the gathered B, and (move) the move, Esirkepov current and the
 // charge at the new positions (into rho_acc).

@@ -64,3 +64,65 @@ def test_em_rejects_unsupported_configurations(pk):
     for bad in (dict(em=1, c_light=0.0), dict(em=1, c_light=20.0), dict(em=1, c_light=2.0, nv=2)):
         with pytest.raises(pk.PicError):
             pk.from_workload(w, **bad)
+
+
+def _window_fits(cells, n, tile=256, cap=1024):
+    """Per tile of the (sorted) particle order: does the tile's window (the box of its
+    old cells relative to its first particle's cell, widened by one node below and
+    two above) fit the kernel's shared-memory capacity?  The rule of the tiled
+    kernel, restated here to check that a test case exercises both of its paths."""
+    out = []
+    for s in range(0, len(cells), tile):
+        c = cells[s:s + tile]
+        cx, cy = c % n[0], c // n[0]
+        d = []
+        for a, ca in ((0, cx), (1, cy)):
+            dd = ca - ca[0]
+            dd = np.where(2 * dd > n[a], dd - n[a], dd)
+            dd = np.where(2 * dd < -n[a], dd + n[a], dd)
+            d.append(dd)
+        w0 = d[0].max() - d[0].min() + 4
+        w1 = d[1].max() - d[1].min() + 4
+        out.append(w0 <= cap and w1 <= cap and w0 * w1 <= cap)
+    return np.array(out)
+
+
+def test_em_windowed_and_spread_tiles_match_oracle(pk):
+    """A dense cluster (tiles whose stencils fit the shared-memory windows) in a
+    dilute background (tiles too spread out, taken particle by particle): both paths
+    against the oracle over five steps, without re-sorting."""
+    n, dx, c, dt = (64, 48), (1.0, 1.0), 3.0, 0.1
+    rng = np.random.default_rng(83)
+    L = np.array([n[0] * dx[0], n[1] * dx[1]])
+    bg = rng.uniform(0.0, 1.0, (1500, 2)) * L
+    cl = np.array([20.0, 30.0]) + rng.uniform(0.0, 4.0, (3000, 2))
+    x = np.concatenate([bg, cl])
+    v = rng.normal(0.0, 1.0, (x.shape[0], 3))
+    weight = 0.02  # a light plasma: the cluster's own field stays well below a cell per step
+    cfg = pk.make_config(2, n, dx=dx, dt=dt, nv=3, weight=weight, em=1, c_light=c,
+                         sort_every=0, cg_rtol=1e-7)
+    g = pk.Pic(cfg).load(x, v)
+    sim = oracle.EmSimulation(n, dx, dt, c=c, weight=weight).load(x, v)
+    perm = g.get_perm().copy()
+    cell, _, _, _ = g.get_particles(positions=False)
+    fits = _window_fits(np.asarray(cell, np.int64), n)
+    assert fits.any() and not fits.all(), fits
+    for _ in range(5):
+        v_prev = sim.v.copy()
+        g.step(1)
+        sim.step(1)
+    _, _, vg, xg = g.get_particles()
+    dist = np.abs(xg - sim.x[perm])
+    dist = np.minimum(dist, L - dist) / np.asarray(dx)
+    assert dist.max() <= TOL
+    assert rel(vg, sim.v[perm], np.abs(sim.v).max()) <= TOL
+    assert rel(g.get_E(), sim.E.ravel(), np.abs(sim.E).max()) <= TOL
+    assert rel(g.get_B(), sim.B.ravel(), np.abs(sim.B).max()) <= TOL
+    rho_e = oracle.deposit(2, n, dx, sim.x, -1.0 * weight)
+    assert rel(g.get_rho(), sim.rho, np.abs(rho_e).max()) <= TOL
+    d = g.get_diag()
+    assert d["charge_fx_sum"] == x.shape[0] * (1 << d["fx_bits"])
+    # kinetic energy time-centred at the last push, summed over both kernels' slots
+    ke_o = 0.5 * (0.5 * weight * float(np.sum(v_prev ** 2)) + 0.5 * weight * float(np.sum(sim.v ** 2)))
+    assert abs(d["kinetic"] - ke_o) <= 1e-5 * ke_o
+    g.close()
