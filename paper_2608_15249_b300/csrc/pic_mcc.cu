@@ -90,11 +90,14 @@ __device__ __forceinline__ int collide_one(ParticlesF32 p, int64_t i, uint32_t i
     return kind;
 }
 
-// Each warp takes chunks of MCC_CHUNK particles: every lane draws for its share
-// (coalesced id reads), the candidates are packed into a per-warp list with a
-// ballot and a population count, and the list is then processed 32 at a time, so
-// the long collision path runs with full lanes instead of once per warp that
-// happens to hold a candidate.
+// Each warp takes chunks of MCC_CHUNK particles: every lane reads its share of the
+// ids as four 16-byte loads issued together (lane l holds ids 128 r + 4 l + k), draws
+// for each, and the candidates are packed into a per-warp list with a ballot and a
+// population count; the list is then processed 32 at a time, so the long collision
+// path runs with full lanes instead of once per warp that happens to hold a
+// candidate.  (The order of the list does not matter: each candidate's collision
+// depends only on its own id and velocity.)  The last, partial chunk reads its ids
+// one by one.
 constexpr int MCC_CHUNK = 512;
 
 __global__ void __launch_bounds__(MCC_THREADS)
@@ -109,12 +112,30 @@ __global__ void __launch_bounds__(MCC_THREADS)
     const int64_t nwarps = ((int64_t)gridDim.x * MCC_THREADS) >> 5;
     for (int64_t ch = gwarp; ch < nchunks; ch += nwarps) {
         const int64_t base = ch * MCC_CHUNK;
+        uint32_t ids[MCC_CHUNK / 32];
+        const bool full = base + MCC_CHUNK <= p.np;
+        if (full) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.id + base);
+#pragma unroll
+            for (int r = 0; r < MCC_CHUNK / 128; ++r) {
+                const uint4 q = __ldg(src + r * 32 + lane);
+                ids[4 * r] = q.x;
+                ids[4 * r + 1] = q.y;
+                ids[4 * r + 2] = q.z;
+                ids[4 * r + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MCC_CHUNK / 32; ++k) {
+                const int64_t i = base + (k >> 2) * 128 + lane * 4 + (k & 3);
+                ids[k] = i < p.np ? p.id[i] : 0u;
+            }
+        }
         int m = 0;  // candidates listed so far (warp-uniform)
-#pragma unroll 4
-        for (int j = lane; j < MCC_CHUNK; j += 32) {
-            const int64_t i = base + j;
-            bool cand = false;
-            if (i < p.np) cand = draw24(c.seed, step, p.id[i], 0) < c.thr;
+#pragma unroll
+        for (int k = 0; k < MCC_CHUNK / 32; ++k) {
+            const int j = (k >> 2) * 128 + lane * 4 + (k & 3);
+            const bool cand = (full || base + j < p.np) && draw24(c.seed, step, ids[k], 0) < c.thr;
             const unsigned ball = __ballot_sync(0xffffffffu, cand);
             if (cand) list[m + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)j;
             m += __popc(ball);

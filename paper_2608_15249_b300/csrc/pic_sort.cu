@@ -36,36 +36,67 @@ size_t sort_hist_len(int64_t np) { return (size_t)MAX_RADIX * (size_t)tiles_of(n
 // (Divisions by the grid and brick sizes use the multiply-high FastDiv: a
 // runtime integer division compiles to float conversions, which issue on the
 // slow FP64 pipe of this GPU.)
-__global__ void k_keys(int ndim, FastDiv dn0, FastDiv dn1, FastDiv db0, FastDiv db1, FastDiv db2,
-                       int nb0, int nb1, const int32_t *__restrict__ cell, int64_t np,
-                       uint32_t *__restrict__ keys)
+struct KeyParams {
+    FastDiv dn0, dn1, db0, db1, db2;
+    uint32_t nb0, nb1;
+};
+
+template <int D>
+__device__ __forceinline__ uint32_t brick_key(uint32_t c, const KeyParams &k)
 {
-    const uint32_t b0 = db0.d, b1 = db1.d;
-    const uint32_t bcells = b0 * b1 * db2.d;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = (uint32_t)cell[i];
-        uint32_t c0, c1 = 0, c2 = 0;
-        if (ndim == 1) {
-            c0 = c;
-        } else if (ndim == 2) {
-            c1 = fdiv(c, dn0);
-            c0 = c - c1 * dn0.d;
-        } else {
-            const uint32_t c12 = fdiv(c, dn0);
-            c0 = c - c12 * dn0.d;
-            c2 = fdiv(c12, dn1);
-            c1 = c12 - c2 * dn1.d;
-        }
-        const uint32_t q0 = fdiv(c0, db0), q1 = fdiv(c1, db1), q2 = fdiv(c2, db2);
-        const uint32_t bid = q0 + (uint32_t)nb0 * (q1 + (uint32_t)nb1 * q2);
-        const uint32_t lid = (c0 - q0 * b0) + b0 * ((c1 - q1 * b1) + b1 * (c2 - q2 * db2.d));
-        keys[i] = bid * bcells + lid;
+    uint32_t c0, c1 = 0, c2 = 0;
+    if (D == 1) {
+        c0 = c;
+    } else if (D == 2) {
+        c1 = fdiv(c, k.dn0);
+        c0 = c - c1 * k.dn0.d;
+    } else {
+        const uint32_t c12 = fdiv(c, k.dn0);
+        c0 = c - c12 * k.dn0.d;
+        c2 = fdiv(c12, k.dn1);
+        c1 = c12 - c2 * k.dn1.d;
     }
+    const uint32_t b0 = k.db0.d, b1 = D >= 2 ? k.db1.d : 1u, b2 = D == 3 ? k.db2.d : 1u;
+    const uint32_t q0 = fdiv(c0, k.db0);
+    const uint32_t q1 = D >= 2 ? fdiv(c1, k.db1) : 0u, q2 = D == 3 ? fdiv(c2, k.db2) : 0u;
+    const uint32_t bid = q0 + k.nb0 * (q1 + k.nb1 * q2);
+    const uint32_t lid = (c0 - q0 * b0) + b0 * ((c1 - q1 * b1) + b1 * (c2 - q2 * b2));
+    return bid * (b0 * b1 * b2) + lid;
+}
+
+// Four keys per thread and iteration (16-byte loads and stores when both arrays
+// start on 16 bytes, as the library's own do; a caller's cell array may not, and
+// then goes one key at a time), persistent grid.
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_keys(KeyParams kp, const int32_t *__restrict__ cell, int64_t np, uint32_t *__restrict__ keys)
+{
+    if ((reinterpret_cast<uintptr_t>(cell) | reinterpret_cast<uintptr_t>(keys)) & 15u) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+             i += (int64_t)gridDim.x * blockDim.x)
+            keys[i] = brick_key<D>((uint32_t)cell[i], kp);
+        return;
+    }
+    const int64_t nq = np / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int4 c = __ldg(reinterpret_cast<const int4 *>(cell) + q);
+        uint4 k;
+        k.x = brick_key<D>((uint32_t)c.x, kp);
+        k.y = brick_key<D>((uint32_t)c.y, kp);
+        k.z = brick_key<D>((uint32_t)c.z, kp);
+        k.w = brick_key<D>((uint32_t)c.w, kp);
+        reinterpret_cast<uint4 *>(keys)[q] = k;
+    }
+    const int64_t t = 4 * nq + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < np) keys[t] = brick_key<D>((uint32_t)cell[t], kp);
 }
 
 // ---- per-tile digit histogram ----------------------------------------------------------------
 
+// Thread t of a tile counts the 16 consecutive keys [16 t, 16 t + 16) of the tile
+// (four 16-byte loads): runs of equal digits, which are long for the near-sorted
+// keys of a re-sort, go to the shared histogram as one atomic each.
 template <int RADIX>
 __global__ void __launch_bounds__(ST_THREADS)
     k_hist(const uint32_t *__restrict__ keys, int64_t np, int shift, uint32_t *__restrict__ hist,
@@ -74,15 +105,39 @@ __global__ void __launch_bounds__(ST_THREADS)
     __shared__ uint32_t h[RADIX];
     for (int j = threadIdx.x; j < RADIX; j += ST_THREADS) h[j] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * ST_TILE;
-    const int lane = threadIdx.x & 31;
-#pragma unroll 4
-    for (int k = 0; k < ST_ITEMS; ++k) {
-        const int64_t i = base + (int64_t)k * ST_THREADS + threadIdx.x;
-        const int d = i < np ? (int)((keys[i] >> shift) & (RADIX - 1)) : NO_DIGIT;
-        const unsigned m = __match_any_sync(0xffffffffu, d);
-        if (d != NO_DIGIT && lane == __ffs(m) - 1) atomicAdd(&h[d], (uint32_t)__popc(m));
+    const int64_t base = (int64_t)blockIdx.x * ST_TILE + (int64_t)threadIdx.x * ST_ITEMS;
+    uint32_t k[ST_ITEMS];
+    int valid = ST_ITEMS;
+    if (base + ST_ITEMS <= np) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+        for (int r = 0; r < ST_ITEMS / 4; ++r) {
+            const uint4 q = __ldg(src + r);
+            k[4 * r] = q.x;
+            k[4 * r + 1] = q.y;
+            k[4 * r + 2] = q.z;
+            k[4 * r + 3] = q.w;
+        }
+    } else {
+        valid = base < np ? (int)(np - base) : 0;
+#pragma unroll
+        for (int r = 0; r < ST_ITEMS; ++r) k[r] = r < valid ? keys[base + r] : 0u;
     }
+    int run_d = -1;
+    uint32_t run_n = 0;
+#pragma unroll
+    for (int r = 0; r < ST_ITEMS; ++r) {
+        if (r >= valid) break;
+        const int d = (int)((k[r] >> shift) & (RADIX - 1));
+        if (d == run_d) {
+            ++run_n;
+        } else {
+            if (run_n) atomicAdd(&h[run_d], run_n);
+            run_d = d;
+            run_n = 1;
+        }
+    }
+    if (run_n) atomicAdd(&h[run_d], run_n);
     __syncthreads();
     for (int j = threadIdx.x; j < RADIX; j += ST_THREADS)
         hist[(int64_t)j * ntiles + blockIdx.x] = h[j];
@@ -91,9 +146,13 @@ __global__ void __launch_bounds__(ST_THREADS)
 // ---- stable scatter --------------------------------------------------------------------------
 
 // Warp w of a tile owns the contiguous items [w*512, (w+1)*512) of the tile and
-// walks them in 16 rounds of 32, so (warp, round, lane) order is input order.
+// walks them in 16 rounds of 32, so (warp, round, lane) order is input order.  A
+// round whose 32 digits are all equal (the usual case for the near-sorted keys of
+// a re-sort) ranks by lane, against a running count of that digit kept in a
+// register; other rounds rank with a match over the lanes against the warp's
+// shared per-digit counts.
 template <int RADIX>
-__global__ void __launch_bounds__(ST_THREADS)
+__global__ void __launch_bounds__(ST_THREADS, 3)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
               int shift, const uint32_t *__restrict__ offs, int64_t ntiles,
               uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
@@ -106,21 +165,43 @@ __global__ void __launch_bounds__(ST_THREADS)
     const int64_t base = (int64_t)blockIdx.x * ST_TILE + (int64_t)w * (ST_ITEMS * 32);
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[ST_ITEMS], rank[ST_ITEMS];
-    int dig[ST_ITEMS];
 #pragma unroll
     for (int r = 0; r < ST_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
         key[r] = i < np ? keys_in[i] : 0u;
-        const int d = i < np ? (int)((key[r] >> shift) & (RADIX - 1)) : NO_DIGIT;
-        dig[r] = d;
-        const unsigned m = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d != NO_DIGIT) before = wcount(w, d);
-        rank[r] = before + (uint32_t)__popc(m & lt);
-        __syncwarp();
-        if (d != NO_DIGIT && (m & lt) == 0) wcount(w, d) = before + (uint32_t)__popc(m);
-        __syncwarp();
     }
+    auto digit = [&](int r) {
+        return base + r * 32 + lane < np ? (int)((key[r] >> shift) & (RADIX - 1)) : NO_DIGIT;
+    };
+    int cd = NO_DIGIT;  // the cached digit (warp-uniform) and its running count
+    uint32_t cc = 0;
+#pragma unroll
+    for (int r = 0; r < ST_ITEMS; ++r) {
+        const int d = digit(r);
+        const int d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0) && d0 != NO_DIGIT) {
+            if (d0 != cd) {
+                if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
+                __syncwarp();
+                cc = wcount(w, d0);
+                cd = d0;
+            }
+            rank[r] = cc + (uint32_t)lane;
+            cc += 32;
+        } else {
+            if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
+            cd = NO_DIGIT;
+            __syncwarp();
+            const unsigned m = __match_any_sync(0xffffffffu, d);
+            uint32_t before = 0;
+            if (d != NO_DIGIT) before = wcount(w, d);
+            rank[r] = before + (uint32_t)__popc(m & lt);
+            __syncwarp();
+            if (d != NO_DIGIT && (m & lt) == 0) wcount(w, d) = before + (uint32_t)__popc(m);
+            __syncwarp();
+        }
+    }
+    if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
     __syncthreads();
     for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
         uint32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
@@ -133,9 +214,10 @@ __global__ void __launch_bounds__(ST_THREADS)
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ST_ITEMS; ++r) {
-        if (dig[r] == NO_DIGIT) continue;
+        const int d = digit(r);
+        if (d == NO_DIGIT) continue;
         const int64_t i = base + r * 32 + lane;
-        const uint32_t pos = wcount(w, dig[r]) + rank[r];
+        const uint32_t pos = wcount(w, d) + rank[r];
         if (keys_out) keys_out[pos] = key[r];
         idx_out[pos] = idx_in ? idx_in[i] : (uint32_t)i;
     }
@@ -261,14 +343,21 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
         return cudaSuccess;
     }
     const int b0 = brick[0], b1 = g.ndim >= 2 ? brick[1] : 1, b2 = g.ndim >= 3 ? brick[2] : 1;
-    const int nb0 = (g.n[0] + b0 - 1) / b0;
-    const int nb1 = g.ndim >= 2 ? (g.n[1] + b1 - 1) / b1 : 1;
-    int64_t kb = (np + 255) / 256;
-    if (kb > 65535) kb = 65535;
-    k_keys<<<(int)kb, 256, 0, st>>>(g.ndim, make_fastdiv((uint32_t)g.n[0]),
-                                     make_fastdiv((uint32_t)g.n[1]), make_fastdiv((uint32_t)b0),
-                                     make_fastdiv((uint32_t)b1), make_fastdiv((uint32_t)b2), nb0,
-                                     nb1, cell, np, s.keys[0]);
+    KeyParams kp;
+    kp.dn0 = make_fastdiv((uint32_t)g.n[0]);
+    kp.dn1 = make_fastdiv((uint32_t)g.n[1]);
+    kp.db0 = make_fastdiv((uint32_t)b0);
+    kp.db1 = make_fastdiv((uint32_t)b1);
+    kp.db2 = make_fastdiv((uint32_t)b2);
+    kp.nb0 = (uint32_t)((g.n[0] + b0 - 1) / b0);
+    kp.nb1 = g.ndim >= 2 ? (uint32_t)((g.n[1] + b1 - 1) / b1) : 1u;
+    // a persistent grid of 8 CTAs per SM (fewer for small np)
+    int64_t kb = (np / 4 + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    kb = kb < 1 ? 1 : (kb > cap ? cap : kb);
+    if (g.ndim == 1) k_keys<1><<<(int)kb, 256, 0, st>>>(kp, cell, np, s.keys[0]);
+    else if (g.ndim == 2) k_keys<2><<<(int)kb, 256, 0, st>>>(kp, cell, np, s.keys[0]);
+    else k_keys<3><<<(int)kb, 256, 0, st>>>(kp, cell, np, s.keys[0]);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
