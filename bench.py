@@ -42,7 +42,7 @@ METRIC = "particle-steps/s (gather+push+deposit)"
 # workload, from the ncu capture summarised in profiles/, with the hash of the
 # kernel sources it was taken on: reported only while the sources are unchanged.
 PASS_TRAFFIC = {
-    "two_stream_2d 512x512 64ppc": {"bytes": 617555200, "sources": "36e86f900315ae58"},
+    "two_stream_2d 512x512 64ppc": {"bytes": 617822720, "sources": "7dda0771aa4c7afb"},
 }
 TRAFFIC_SOURCES = ("paper_2608_15249_b300/csrc/pic_particles.cu",
                    "paper_2608_15249_b300/csrc/pic_internal.cuh")
@@ -97,10 +97,10 @@ def _spectral_bytes_per_node(ndim):
     (the solve and its refinement), each a pass per axis over the complex grid (the
     first reads the FP32 right-hand side, 4 + 8 B; the last writes the FP32
     potential, 8 + 4 B; the others 8 + 8 B; in 1D one real-to-real pass, 4 + 4 B),
-    the FP64 residual (8 B rho + 4 B phi + 4 B out), the correction (4 + 4 + 4 B)
-    and E = -grad phi (4 B + 4 B per axis)."""
+    the refinement's last pass also reading the potential it adds to (4 B), the FP64
+    residual (8 B rho + 4 B phi + 4 B out) and E = -grad phi (4 B + 4 B per axis)."""
     solve = 8 if ndim == 1 else 12 + 16 * (2 * ndim - 3) + 12
-    return 2 * solve + 16 + 12 + 4 + 4 * ndim
+    return 2 * solve + 4 + 16 + 4 + 4 * ndim
 
 
 def _roofline(alg_bytes, ms, kernel, peak, peak_kind, traffic=None, **extra):
@@ -576,7 +576,7 @@ def bench_spectral(args, w, fft_ms, peak, peak_kind):
     out = {"ms_per_solve": fft_ms, "nodes": w.cells,
            "roofline": _roofline(w.cells * _spectral_bytes_per_node(w.ndim), fft_ms,
                                  "spectral solve (k_fft_axis per axis x 2 solves, k_residual64, "
-                                 "k_add_correction, k_efield)", peak, peak_kind,
+                                 "k_efield)", peak, peak_kind,
                                  residency="the grid (a few MB) stays in L2")}
     if not args.no_row_oracles:
         sample = min(w.np_, 1 << 20)

@@ -599,6 +599,8 @@ static ap_pic_status create_grid(ap_pic *h)
     TRY(alloc_n(h, &f.x, c));
     TRY(alloc_n(h, &f.E, c * f.Estride));
     for (int k = 0; k < 3; ++k) TRY(alloc_n(h, &f.part[k], (size_t)f.nblocks));
+    TRY(alloc_n(h, &f.ticket, 1));
+    CU(h, cudaMemsetAsync(f.ticket, 0, 4, h->stream));
     TRY(alloc_n(h, &f.scal, 8));
     TRY(alloc_n(h, &f.done, 1));
     TRY(alloc_n(h, &f.iters, 1));
@@ -894,10 +896,10 @@ static ap_pic_status solve_field_fft(ap_pic *h)
     FieldBufs &f = h->f;
     const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
     CU(h, launch_fft_poisson(h->fft, f.b, f.phi, h->stream));
-    // refinement pass: the FP64 residual of the FP32 solve, solved again and added
+    // refinement pass: the FP64 residual of the FP32 solve, solved again and added to
+    // phi by the transform's last pass
     CU(h, launch_residual64(f, mean_total, h->stream));
-    CU(h, launch_fft_poisson(h->fft, f.b, f.x, h->stream));
-    CU(h, launch_add_correction(f, h->stream));
+    CU(h, launch_fft_poisson(h->fft, f.b, f.phi, h->stream, true));
     CU(h, launch_efield(f, h->stream));
     stage_end(h, mk);
     h->last_cg_iters = 0;

@@ -545,21 +545,32 @@ __global__ void __launch_bounds__(EM_THREADS)
     if (diag_blocks) em_block_diag(ke, mom, diag_blocks, blockIdx.x);
 }
 
-// The tiles that k_em_tile flagged, particle by particle through global memory; every
-// block writes its diagnostic partials (slot gridDim.x + blockIdx.x).
+// The tiles that k_em_tile flagged, particle by particle through global memory.  A
+// block reads the flags of EM_THREADS consecutive tiles at once (one per thread) and
+// then takes the flagged ones in order; every block writes its diagnostic partials
+// (slot gridDim.x + blockIdx.x).
 __global__ void __launch_bounds__(EM_THREADS)
     k_em_spread(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
                 double *__restrict__ diag_blocks, int *__restrict__ err)
 {
+    __shared__ unsigned char s_flag[EM_THREADS];
     const float scale = ldexpf(1.0f, g.fx_bits);
     const int one = 1 << g.fx_bits;
     float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
     bool bad = false;
     const int64_t ntiles = (p.np + EMT_TILE - 1) / EMT_TILE;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (!em.tile_flag[t]) continue;
-        const int64_t i = t * EMT_TILE + threadIdx.x;
-        if (i < p.np) em_particle_global<true>(i, g, p, em, rho_acc, scale, one, ke, mom, bad);
+    for (int64_t t0 = (int64_t)blockIdx.x * EM_THREADS; t0 < ntiles;
+         t0 += (int64_t)gridDim.x * EM_THREADS) {
+        const int64_t tt = t0 + threadIdx.x;
+        const bool mine = tt < ntiles && em.tile_flag[tt];
+        s_flag[threadIdx.x] = mine ? 1 : 0;
+        if (!__syncthreads_or(mine)) continue;
+        for (int q = 0; q < EM_THREADS; ++q) {
+            if (!s_flag[q]) continue;
+            const int64_t i = (t0 + q) * EMT_TILE + threadIdx.x;
+            if (i < p.np) em_particle_global<true>(i, g, p, em, rho_acc, scale, one, ke, mom, bad);
+        }
+        __syncthreads();  // s_flag is rewritten for the next chunk
     }
     if (bad) atomicOr(err, EF_NONFINITE);
     if (diag_blocks) em_block_diag(ke, mom, diag_blocks, gridDim.x + blockIdx.x);

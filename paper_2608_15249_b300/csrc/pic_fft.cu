@@ -111,6 +111,149 @@ __device__ void dif(float2 *buf, int W, const SLayout &S, const float2 *tws, boo
     }
 }
 
+// ---- power-of-two lines: self-sorting (Stockham) mixed-radix passes ----------------------
+// A length-m transform is a sequence of passes of radix R (8, and a last 2 or 4 when
+// log2 m is not a multiple of 3).  Before a pass Ns is the product of the earlier
+// radices; group j < m / R takes x[j + r m / R] (r < R), multiplies input r by
+// exp(-+2 pi i (j mod Ns) r / (Ns R)), does an R-point DFT in registers, and writes
+// output r to y[(j - j mod Ns) R + j mod Ns + r Ns].  Input and output are in natural
+// order, so loads and stores need no bit reversal, and a 512-point line takes three
+// passes (three barriers) instead of nine radix-2 stages.  Lines sit in shared
+// memory with one padding slot per 8 elements (element i at i + i / 8), which breaks
+// the 8-element stride of the first pass's writes across banks.
+
+__device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
+__host__ __device__ inline int stockham_ls(int m) { return m + (m >> 3); }
+
+// (a - b) times exp(-+2 pi i q / 8), q = 1, 2, 3
+template <int Q>
+__device__ __forceinline__ float2 rot8(float2 d, bool inverse)
+{
+    constexpr float c = 0.70710678118654752f;
+    if (Q == 2) return inverse ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+    if (Q == 1)
+        return inverse ? make_float2(c * (d.x - d.y), c * (d.x + d.y))
+                       : make_float2(c * (d.x + d.y), c * (d.y - d.x));
+    return inverse ? make_float2(-c * (d.x + d.y), c * (d.x - d.y))
+                   : make_float2(c * (d.y - d.x), -c * (d.x + d.y));
+}
+
+// In-register R-point DFT (sign -1, or +1 when inverse), natural order in and out:
+// radix-2 decimation in frequency, then the bit-reversal permutation of registers.
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[8], bool inverse)
+{
+    if (R == 8) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float2 a = v[r], b = v[r + 4];
+            v[r] = cadd(a, b);
+            const float2 d = csub(a, b);
+            v[r + 4] = r == 0 ? d : (r == 1 ? rot8<1>(d, inverse)
+                                            : (r == 2 ? rot8<2>(d, inverse) : rot8<3>(d, inverse)));
+        }
+    }
+    if (R >= 4) {
+#pragma unroll
+        for (int h = 0; h < R; h += 4)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float2 a = v[h + r], b = v[h + r + 2];
+                v[h + r] = cadd(a, b);
+                const float2 d = csub(a, b);
+                v[h + r + 2] = r == 0 ? d : rot8<2>(d, inverse);
+            }
+    }
+#pragma unroll
+    for (int h = 0; h < R; h += 2) {
+        const float2 a = v[h], b = v[h + 1];
+        v[h] = cadd(a, b);
+        v[h + 1] = csub(a, b);
+    }
+    if (R == 8) {
+        float2 t = v[1];  // output k sits at bit-reversed register brev3(k)
+        v[1] = v[4];
+        v[4] = t;
+        t = v[3];
+        v[3] = v[6];
+        v[6] = t;
+    } else if (R == 4) {
+        const float2 t = v[1];
+        v[1] = v[2];
+        v[2] = t;
+    }
+}
+
+// One pass over W lines (line stride ls) from src to dst; tw[i] = exp(-2 pi i i / M)
+// for i < M / 2.
+template <int LOG2R>
+__device__ __forceinline__ void stockham_pass(const float2 *src, float2 *dst, int W, int log2m,
+                                              int ls, int log2ns, bool inverse,
+                                              const float2 *__restrict__ tw, int log2M)
+{
+    constexpr int R = 1 << LOG2R;
+    const int lg = log2m - LOG2R;  // log2 of the groups per line
+    const int G = W << lg;
+    const int ns = 1 << log2ns;
+    for (int q = threadIdx.x; q < G; q += blockDim.x) {
+        const int t = q >> lg, j = q & ((1 << lg) - 1);
+        const float2 *s = src + t * ls;
+        float2 *d = dst + t * ls;
+        const int k = j & (ns - 1);
+        float2 v[8];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[spad(j + (r << lg))];
+        if (log2ns > 0) {
+            // exp(-2 pi i k r / (Ns R)) = exp(-2 pi i x / M), x = k r 2^sh < M; the table
+            // holds the first half turn (M / 2 entries), and x + M / 2 is the negative
+            const int sh = log2M - log2ns - LOG2R;
+            const int half = 1 << (log2M - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const int x = (k * r) << sh;
+                float2 w = __ldg(tw + (x & (half - 1)));
+                if (x & half) {
+                    w.x = -w.x;
+                    w.y = -w.y;
+                }
+                if (inverse) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_reg<R>(v, inverse);
+        const int base = ((j - k) << LOG2R) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[spad(base + (r << log2ns))] = v[r];
+    }
+}
+
+// The whole transform of W lines held at a (natural order); returns the buffer (a
+// or b) that holds the result, in natural order.
+__device__ float2 *stockham(float2 *a, float2 *b, int W, int log2m, bool inverse,
+                            const float2 *__restrict__ tw, int log2M)
+{
+    const int ls = stockham_ls(1 << log2m);
+    int log2ns = 0;
+    for (; log2ns + 3 <= log2m; log2ns += 3) {
+        stockham_pass<3>(a, b, W, log2m, ls, log2ns, inverse, tw, log2M);
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    if (log2m - log2ns == 2) {
+        stockham_pass<2>(a, b, W, log2m, ls, log2ns, inverse, tw, log2M);
+        __syncthreads();
+        return b;
+    }
+    if (log2m - log2ns == 1) {
+        stockham_pass<1>(a, b, W, log2m, ls, log2ns, inverse, tw, log2M);
+        __syncthreads();
+        return b;
+    }
+    return a;
+}
+
 // W lines along one axis of one grid.  Lines l in [0, inner * outer): inner index
 // i = l % inner, outer index o = l / inner, element j at o * n * inner + i + j * inner
 // (relative to the grid's first node).
@@ -118,6 +261,7 @@ struct LineJob {
     float2 *Z;             // the grid's complex work array
     const float *in_real;  // non-null: the input is this real array (first forward pass)
     float *out_real;       // non-null: write the real part here (last inverse pass)
+    bool out_add;          // add the real part to out_real instead of storing it
     FftAxis ax;
     int64_t l0;            // first line
     int nl;                // lines of this job (<= W)
@@ -155,8 +299,8 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
     const SLayout S = slayout(log2m);
     float2 *buf = fsm;
     float2 *tws = fsm + (size_t)W * S.ls;
-    // stage tables: entry h - 1 + k = exp(-2 pi i k / 2h) = tw[k M / 2h]
-    for (int q = threadIdx.x; q < m - 1; q += blockDim.x) {
+    // stage tables of the radix-2 path: entry h - 1 + k = exp(-2 pi i k / 2h) = tw[k M / 2h]
+    for (int q = threadIdx.x; ax.bluestein && q < m - 1; q += blockDim.x) {
         const int s = 31 - __clz(q + 1), k = q + 1 - (1 << s);
         tws[q] = tw[(size_t)k << (log2M - 1 - s)];
     }
@@ -172,17 +316,61 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
     // thread -> (line, element) so that consecutive threads touch consecutive addresses
     const bool rows = inner == 1;
     const int total = W * n;
+    // (W is a power of two; so is n on the radix-2 path, where shifts replace the
+    // divisions, which compile to slow float conversions on this GPU)
+    const int log2W = 31 - __clz(W);
+    const bool pow2 = n == m;
     auto coords = [&](int e, int *t, int *j) {
         if (rows) {
-            *t = e / n;
+            *t = pow2 ? e >> log2m : e / n;
             *j = e - *t * n;
         } else {
             *t = e & (W - 1);
-            *j = e / W;
+            *j = e >> log2W;
         }
     };
     const bool blue = ax.bluestein != 0;
     const bool inv_in = J.mode == FFT_INV;
+    if (!blue) {
+        // power of two: Stockham passes, natural order throughout
+        const int lsS = stockham_ls(m);
+        float2 *bufA = fsm, *bufB = fsm + (size_t)W * lsS;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int t, j;
+            coords(e, &t, &j);
+            if (t >= nl) continue;
+            const int64_t a = addr(t, j);
+            bufA[t * lsS + spad(j)] = J.in_real ? make_float2(J.in_real[a], 0.0f) : J.Z[a];
+        }
+        __syncthreads();
+        float2 *res = stockham(bufA, bufB, W, log2m, inv_in, tw, log2M);
+        if (J.mode == FFT_FWD_SCALE_INV) {
+            for (int e = threadIdx.x; e < (W << log2m); e += blockDim.x) {
+                const int t = e >> log2m, k = e & (m - 1);
+                const float s = spectral_scale(J, k, s_inner[t < nl ? t : 0]);
+                float2 &x = res[t * lsS + spad(k)];
+                x.x *= s;
+                x.y *= s;
+            }
+            __syncthreads();
+            res = stockham(res, res == bufA ? bufB : bufA, W, log2m, true, tw, log2M);
+        }
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int t, j;
+            coords(e, &t, &j);
+            if (t >= nl) continue;
+            const float2 v = res[t * lsS + spad(j)];
+            const int64_t a = addr(t, j);
+            if (J.out_real) {
+                if (J.out_add) J.out_real[a] += v.x;
+                else J.out_real[a] = v.x;
+            } else {
+                J.Z[a] = v;
+            }
+        }
+        __syncthreads();  // the shared buffers are reused by the CTA's next job
+        return;
+    }
     // ---- load (scattered to bit-reversed positions, for the DIT) ----------------------------
     if (blue) {
         // zero the padding of Bluestein lines
@@ -281,8 +469,12 @@ __device__ void fft_lines(const LineJob &J, const float2 *__restrict__ tw, int l
             if (conj_out) v = cconj(v);
         }
         const int64_t a = addr(t, j);
-        if (J.out_real) J.out_real[a] = v.x;
-        else J.Z[a] = v;
+        if (J.out_real) {
+            if (J.out_add) J.out_real[a] += v.x;
+            else J.out_real[a] = v.x;
+        } else {
+            J.Z[a] = v;
+        }
     }
     __syncthreads();  // the shared buffers are reused by the CTA's next job
 }
@@ -312,6 +504,7 @@ __global__ void __launch_bounds__(FFT_THREADS)
         J.in_real = in_real ? in_real + G.node0 : nullptr;
         float *out = G.ndim == 1 ? out_1d : out_real;
         J.out_real = out ? out + G.node0 : nullptr;
+        J.out_add = false;
         J.ax = G.ax[jb.axis];
         J.l0 = jb.l0;
         J.nl = jb.nl;
@@ -435,24 +628,28 @@ int lines_per_cta(int64_t lines, int log2m, int sms, int cap)
 
 size_t fft_smem_bytes(int W, int log2m)
 {
-    // W padded lines, then m - 1 stage twiddles
+    // radix-2 / Bluestein layout: W padded lines, then m - 1 stage twiddles; Stockham
+    // layout: two buffers of W padded lines
     const size_t m = (size_t)1 << log2m;
     const size_t ls = m + (log2m >= 5 ? 32 : 0);
-    return ((size_t)W * ls + m) * sizeof(float2);
+    const size_t radix2 = ((size_t)W * ls + m) * sizeof(float2);
+    const size_t self_sorting = 2 * (size_t)W * (size_t)stockham_ls((int)m) * sizeof(float2);
+    return radix2 > self_sorting ? radix2 : self_sorting;
 }
 
 cudaError_t fft_configure()
 {
-    // W * m <= 8192 elements (+ 32 padding slots per line, W <= 32) plus m <= 8192
-    // stage twiddles
-    const int most = (int)((8192 + 32 * 32 + 8192) * sizeof(float2));
+    // the larger of W * m <= 8192 elements (+ 32 padding slots per line, W <= 32) plus
+    // m <= 8192 stage twiddles, and two Stockham buffers of 8192 + 1024 elements
+    const int most = (int)(2 * (8192 + 1024) * sizeof(float2));
     cudaError_t e = cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          most);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_fft_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
-cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st)
+cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st,
+                               bool accumulate)
 {
     const int d = P.ndim;
     auto run = [&](int a, int mode, const float *in, float *out) -> cudaError_t {
@@ -460,9 +657,10 @@ cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cud
         J.Z = P.Z;
         J.in_real = in;
         J.out_real = out;
+        J.out_add = accumulate && out != nullptr;
         J.ax = P.ax[a];
         const int64_t lines = P.cells / J.ax.n;
-        J.W = lines_per_cta(lines, J.ax.log2m, P.sms, 8192);
+        J.W = lines_per_cta(lines, J.ax.log2m, P.sms, 2048);
         J.mode = mode;
         J.lam0 = a >= 1 ? P.ax[0].lam : nullptr;
         J.lam1 = a >= 2 ? P.ax[1].lam : nullptr;

@@ -382,20 +382,31 @@ __global__ void __launch_bounds__(FT)
     }
     rr = block_sum(rr);
     bb = block_sum(bb);
+    // the last block to finish reduces the partials (in block order, so the result
+    // does not depend on which block that is) and re-arms the ticket
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
         f.part[0][blockIdx.x] = rr;
         f.part[2][blockIdx.x] = bb;
+        __threadfence();
+        s_last = atomicAdd(f.ticket, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void __launch_bounds__(FT) k_residual_fin(FieldBufs f)
-{
-    const double rr = reduce_partials(f.part[0], f.nblocks);
-    const double bb = reduce_partials(f.part[2], f.nblocks);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // (L2 loads: the partials were written by other blocks of this launch)
+    double s0 = 0.0, s2 = 0.0;
+    for (int j = threadIdx.x; j < f.nblocks; j += FT) {
+        s0 += __ldcg(f.part[0] + j);
+        s2 += __ldcg(f.part[2] + j);
+    }
+    const double trr = block_sum(s0);
+    const double tbb = block_sum(s2);
     if (threadIdx.x == 0) {
-        const double bn = sqrt(bb);
+        const double bn = sqrt(tbb);
         f.scal[SCAL_BNORM64] = bn;
-        f.scal[SCAL_TRUE_REL] = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+        f.scal[SCAL_TRUE_REL] = bn > 0.0 ? sqrt(trr) / bn : 0.0;
+        *f.ticket = 0u;
     }
 }
 
@@ -404,8 +415,6 @@ cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st)
     double i2[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < f.ndim; ++a) i2[a] = 1.0 / (f.dx[a] * f.dx[a]);
     k_residual64<<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], mean_total);
-    note_launch();
-    k_residual_fin<<<1, FT, 0, st>>>(f);
     note_launch();
     return cudaGetLastError();
 }

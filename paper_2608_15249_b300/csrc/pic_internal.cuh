@@ -242,6 +242,7 @@ struct FieldBufs {
     int *iters;                // CG iteration count
     long long *isum_part;      // int64 partials for the accumulator sum
     double *fe_part;           // field-energy partials
+    unsigned *ticket;          // blocks of k_residual64 finished (zero between launches)
 };
 
 int field_blocks(int64_t cells);
@@ -369,7 +370,9 @@ size_t fft_twiddle_floats(int log2M);
 void fft_twiddles(int log2M, float *host);
 cudaError_t fft_configure();
 // phi = the zero-mean solution of -lap_h phi = b (b's mean is ignored).
-cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st);
+// phi = the zero-mean solution of -lap_h phi = b, or phi += it when accumulate.
+cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cudaStream_t st,
+                               bool accumulate = false);
 // Finalise diagnostics: reduce particle partials, accumulator sum, field energy
 // into out[0..7] = {kinetic, px, py, pz, field_energy, acc_sum (as bits), -, -}.
 cudaError_t launch_diag_finalize(const DiagPartials &pd, bool have_particles, FieldBufs &f,
