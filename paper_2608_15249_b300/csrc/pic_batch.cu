@@ -531,7 +531,7 @@ struct BatchGrid {
 
 namespace {
 
-constexpr int B_TILE = PASS_TILE;  // particle tile (the shared pass's tile)
+constexpr int B_TILE = BATCH_TILE;  // particle tile (the shared pass's batch tile)
 constexpr int64_t PAD = 64;      // instance ranges in the particle arena start on multiples of 64
 
 int bitlen_u(uint64_t x)
@@ -765,12 +765,16 @@ ap_pic_status setup_fft(ap_pic_batch *b)
         auto add = [&](int pass, int axis) {
             const int64_t lines = b->cells[i] / c.n[axis];
             const int log2m = g.ax[axis].log2m;
+            // (Bluestein jobs of up to 4096 points; power-of-two jobs of up to 2048, whose
+            // two Stockham buffers then take about as much shared memory)
+            const bool blue = g.ax[axis].bluestein != 0;
+            const int64_t cap = blue ? 4096 : 2048;
             int W = 32;
-            while (W > 1 && (((int64_t)W << log2m) > 4096 || W / 2 >= lines)) W >>= 1;
+            while (W > 1 && (((int64_t)W << log2m) > cap || W / 2 >= lines)) W >>= 1;
             for (int64_t l0 = 0; l0 < lines; l0 += W)
                 jobs[pass].push_back(
                     FftJob{i, axis, l0, (int)(lines - l0 < W ? lines - l0 : W), W});
-            const size_t sm = fft_smem_bytes(W, log2m);
+            const size_t sm = fft_smem_bytes(W, log2m, blue);
             if (sm > b->fft_smem[pass]) b->fft_smem[pass] = sm;
         };
         add(0, 0);

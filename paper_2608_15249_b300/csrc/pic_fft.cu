@@ -626,15 +626,13 @@ int lines_per_cta(int64_t lines, int log2m, int sms, int cap)
     return W;
 }
 
-size_t fft_smem_bytes(int W, int log2m)
+size_t fft_smem_bytes(int W, int log2m, bool bluestein)
 {
-    // radix-2 / Bluestein layout: W padded lines, then m - 1 stage twiddles; Stockham
-    // layout: two buffers of W padded lines
     const size_t m = (size_t)1 << log2m;
-    const size_t ls = m + (log2m >= 5 ? 32 : 0);
-    const size_t radix2 = ((size_t)W * ls + m) * sizeof(float2);
-    const size_t self_sorting = 2 * (size_t)W * (size_t)stockham_ls((int)m) * sizeof(float2);
-    return radix2 > self_sorting ? radix2 : self_sorting;
+    // Bluestein lines (radix-2 stages): W padded lines, then m - 1 stage twiddles
+    if (bluestein) return ((size_t)W * (m + (log2m >= 5 ? 32 : 0)) + m) * sizeof(float2);
+    // power-of-two lines (Stockham passes): two buffers of W padded lines
+    return 2 * (size_t)W * (size_t)stockham_ls((int)m) * sizeof(float2);
 }
 
 cudaError_t fft_configure()
@@ -667,7 +665,8 @@ cudaError_t launch_fft_poisson(const FftPlan &P, const float *b, float *phi, cud
         J.div_n0 = make_fastdiv((uint32_t)P.ax[0].n);
         J.inv_cells = (float)(1.0 / (double)P.cells);
         const int64_t grid = (lines + J.W - 1) / J.W;
-        k_fft_axis<<<(unsigned)grid, FFT_THREADS, fft_smem_bytes(J.W, J.ax.log2m), st>>>(
+        k_fft_axis<<<(unsigned)grid, FFT_THREADS,
+                     fft_smem_bytes(J.W, J.ax.log2m, J.ax.bluestein != 0), st>>>(
             J, P.tw, P.log2M, lines);
         note_launch();
         return cudaGetLastError();

@@ -145,6 +145,9 @@ void make_tile_params(void *dst, const GridParams &g, const float *E, unsigned l
 // 3D (2 per thread: the 3D pass needs more registers per particle).
 constexpr int PASS_TILE = 768;
 constexpr int PASS_TILE_3D = 512;
+// The batch's tiles (one instance each, most of them small): 2 per thread, where the
+// lighter per-thread state lets 5 CTAs share an SM.
+constexpr int BATCH_TILE = 512;
 
 // Number of blocks the particle pass uses for np particles with nv velocity
 // components: one resident wave (the CTAs of the pass that fit an SM, times the
@@ -354,7 +357,7 @@ struct FftJob {
     int nl, W;
 };
 int lines_per_cta(int64_t lines, int log2m, int sms, int cap);
-size_t fft_smem_bytes(int W, int log2m);
+size_t fft_smem_bytes(int W, int log2m, bool bluestein);
 // Runs `jobs` (one pass of a batch's transform: every job in the same mode, except
 // that 1D grids always take the fused forward / scale / inverse form and write their
 // real result to out_1d).

@@ -336,6 +336,7 @@ __device__ __forceinline__ float twice_ke_rel(const float *u, float inv_c2)
 template <int D>
 __host__ __device__ constexpr int tile_of_dim() { return D == 3 ? PASS_TILE_3D : PASS_TILE; }
 constexpr int TILE_MAX = PASS_TILE > PASS_TILE_3D ? PASS_TILE : PASS_TILE_3D;
+static_assert(BATCH_TILE <= TILE_MAX, "the window bound covers every tile size");
 constexpr int WIN_BITS = 11;        // a tile's shared-memory charge window: 2^11 nodes
 constexpr int WIN_CAP = 1 << WIN_BITS;
 constexpr int STAGES = 3;           // tiles in flight per CTA
@@ -421,6 +422,7 @@ struct TileParams {
 // One instance: tiles of `tile` (the pass's tile size) consecutive particles of [0, np).
 struct SingleSrc {
     static constexpr bool PER_TILE_DIAG = false;
+    static constexpr int FIXED_TILE = 0;  // the tile size goes by the dimension
     TileParams tp;
     int64_t np;
     int tile;
@@ -435,6 +437,7 @@ struct SingleSrc {
 // [tiles[t].start, + tiles[t].count) of instance tiles[t].inst.
 struct BatchSrc {
     static constexpr bool PER_TILE_DIAG = true;
+    static constexpr int FIXED_TILE = BATCH_TILE;
     const BatchTile *tiles;
     const TileParams *inst;  // per instance: parameters, field and accumulator
     int64_t nt;
@@ -459,13 +462,19 @@ struct BatchSrc {
 // Src supplies the tiles: one instance (SingleSrc) or the tiles of many
 // independent instances packed in one particle arena (BatchSrc, whose tiles each
 // carry their instance's parameters, field and charge accumulator).
+template <int D, class Src>
+__host__ __device__ constexpr int pass_tile()
+{
+    return Src::FIXED_TILE ? Src::FIXED_TILE : tile_of_dim<D>();
+}
+
 template <int D, int NV, int MODE, class Src>
-__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
+__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() == 512 ? 5 : 4))
     k_particle_pass(Src src, ParticlesF32 p, double *__restrict__ diag_blocks,
                     int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int TILE = tile_of_dim<D>();
+    constexpr int TILE = pass_tile<D, Src>();
     constexpr int R = TILE / PP_THREADS;
     constexpr int NA_MAX = 1 + D + NV;
     constexpr bool PUSH = (MODE & PASS_PUSH) != 0, MOVE = (MODE & PASS_MOVE) != 0;
@@ -827,10 +836,11 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : 4)
     }
 }
 
-template <int D, int NV>
+template <int D, int NV, class Src>
 constexpr size_t pass_smem_bytes()
 {
-    return (size_t)STAGES * (1 + D + NV) * tile_of_dim<D>() * 4 + STAGES * 8 + WIN_CAP * 4 + 8 * 4;
+    return (size_t)STAGES * (1 + D + NV) * pass_tile<D, Src>() * 4 + STAGES * 8 + WIN_CAP * 4 +
+           8 * 4;
 }
 
 int sm_count()
@@ -851,16 +861,16 @@ int sm_count()
 }
 
 // CTAs of the pass resident per SM, from the occupancy calculator for the fused
-// pass with diagnostics (every mode of a (D, NV) has the same dynamic shared
+// pass with diagnostics (every mode of a (D, NV, Src) has the same dynamic shared
 // memory, and the launch bounds give each at least this many).
-template <int D, int NV>
+template <int D, int NV, class Src = SingleSrc>
 int pass_ctas_per_sm()
 {
     static std::atomic<int> cached{0};
     int c = cached.load(std::memory_order_relaxed);
     if (c) return c;
-    constexpr size_t smem = pass_smem_bytes<D, NV>();
-    auto k = k_particle_pass<D, NV, PASS_PUSH | PASS_MOVE | PASS_DEPOSIT | PASS_DIAG, SingleSrc>;
+    constexpr size_t smem = pass_smem_bytes<D, NV, Src>();
+    auto k = k_particle_pass<D, NV, PASS_PUSH | PASS_MOVE | PASS_DEPOSIT | PASS_DIAG, Src>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k, PP_THREADS, smem) != cudaSuccess ||
@@ -895,7 +905,7 @@ template <int D, int NV, int MODE, class Src>
 static cudaError_t launch_pass_m(const Src &src, ParticlesF32 p, double *diag_blocks, int nblocks,
                                  int *err, cudaStream_t st)
 {
-    constexpr size_t smem = pass_smem_bytes<D, NV>();
+    constexpr size_t smem = pass_smem_bytes<D, NV, Src>();
     static std::atomic<unsigned long long> configured{0};
     cudaError_t e = once_per_device(configured, [] {
         return cudaFuncSetAttribute(k_particle_pass<D, NV, MODE, Src>,
@@ -984,7 +994,8 @@ cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
     src.nt = ntiles;
     // at most one resident wave, whatever the tuning asks for
     const int64_t wave = (int64_t)sm_count() *
-                         (ndim == 1 ? pass_ctas_per_sm<1, 2>() : pass_ctas_per_sm<2, 2>());
+                         (ndim == 1 ? pass_ctas_per_sm<1, 2, BatchSrc>()
+                                    : pass_ctas_per_sm<2, 2, BatchSrc>());
     int64_t nb64 = nblocks < ntiles ? nblocks : ntiles;
     nb64 = nb64 < wave ? nb64 : wave;
     const int nb = (int)(nb64 < 1 ? 1 : nb64);
