@@ -302,6 +302,13 @@ __device__ __forceinline__ void hc_push(float *u, const float *e, const GridPara
     float um[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) um[a] = u[a] + g.qmh2 * e[a];
+    if (!g.magnetised) {
+        // tau = 0: the rotation is the identity (s = 1, t = 0), so u = u- + eps E; the
+        // same numbers the general form gives, without its square roots and division
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = um[a] + g.qmh2 * e[a];
+        return;
+    }
     const float tau2 = g.t[0] * g.t[0] + g.t[1] * g.t[1] + g.t[2] * g.t[2];
     const float um2 = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
     const float ustar = um[0] * g.t[0] + um[1] * g.t[1] + um[2] * g.t[2];
