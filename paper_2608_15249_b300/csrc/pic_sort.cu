@@ -145,12 +145,30 @@ __global__ void __launch_bounds__(ST_THREADS)
 
 // ---- stable scatter --------------------------------------------------------------------------
 
+// The lanes whose digit equals this lane's (NO_DIGIT lanes form their own group), from
+// one ballot per digit bit: cheaper on this GPU than a lane match over many distinct
+// values.
+template <int RADIX>
+__device__ __forceinline__ unsigned peer_mask(int d)
+{
+    const bool valid = d != NO_DIGIT;
+    const unsigned vb = __ballot_sync(0xffffffffu, valid);
+    unsigned m = valid ? vb : ~vb;
+#pragma unroll
+    for (int b = 0; (1 << b) < RADIX; ++b) {
+        const bool bit = (d >> b) & 1;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 // Warp w of a tile owns the contiguous items [w*512, (w+1)*512) of the tile and
 // walks them in 16 rounds of 32, so (warp, round, lane) order is input order.  A
 // round whose 32 digits are all equal (the usual case for the near-sorted keys of
 // a re-sort) ranks by lane, against a running count of that digit kept in a
-// register; other rounds rank with a match over the lanes against the warp's
-// shared per-digit counts.
+// register; other rounds rank against the warp's shared per-digit counts within
+// groups of equal digits (peer_mask).
 template <int RADIX>
 __global__ void __launch_bounds__(ST_THREADS, 3)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
@@ -192,7 +210,7 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
             if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
             cd = NO_DIGIT;
             __syncwarp();
-            const unsigned m = __match_any_sync(0xffffffffu, d);
+            const unsigned m = peer_mask<RADIX>(d);
             uint32_t before = 0;
             if (d != NO_DIGIT) before = wcount(w, d);
             rank[r] = before + (uint32_t)__popc(m & lt);
