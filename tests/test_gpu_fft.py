@@ -125,3 +125,27 @@ def test_step_graph_replay_equals_direct_launches(pk):
         np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(a[3], b[3])
     assert a[4]["step"] == b[4]["step"] == 9 and a[4]["kinetic"] == b[4]["kinetic"]
+
+
+@pytest.mark.parametrize("n", [4096, 4095])
+def test_fft_longest_axes(pk, n):
+    """The longest axes: 4096 (the largest power-of-two line: four radix-8 passes and a
+    radix-2 pass in the largest shared-memory layout) and 4095 (Bluestein on 8192
+    points), on a displaced lattice, 4 per cell.  (Uniform random positions on a line
+    this long give a potential thousands of times larger than E, whose FP32 storage
+    alone then costs E about 1e-5; a displaced lattice keeps the potential within about
+    sqrt(n) of E and the comparison at the transform's own accuracy.)"""
+    rng = np.random.default_rng(59)
+    ppc = 4
+    npart = ppc * n
+    x = (np.arange(npart) + 0.5) / ppc + rng.uniform(-0.3, 0.3, npart) / ppc
+    x = np.mod(x, float(n))[:, None]
+    v = rng.normal(0.0, 1.0, (npart, 1))
+    cfg = pk.make_config(1, (n,), dt=0.1, nv=1, weight=1.0 / ppc, solver=pk.AP_PIC_SOLVER_FFT)
+    g = pk.Pic(cfg).load(x, v, half_push=False)
+    sim = oracle.Simulation(1, (n,), (1.0,), 0.1, weight=1.0 / ppc, rtol=1e-12).load(
+        x, v, half_push=False)
+    phi_o = sim.phi - sim.phi.mean()
+    assert rel(g.get_phi(), phi_o, np.abs(phi_o).max()) <= TOL
+    assert rel(g.get_E(), sim.E, np.abs(sim.E).max()) <= TOL
+    g.close()
