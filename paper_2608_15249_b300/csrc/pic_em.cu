@@ -102,9 +102,10 @@ __device__ __forceinline__ void em_boris(const float *v, const float *e, const f
         t[a] = g.qmh2 * b[a];
         tt += t[a] * t[a];
     }
+    const float s_over_t = 2.0f / (1.0f + tt);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        s[a] = 2.0f * t[a] / (1.0f + tt);
+        s[a] = t[a] * s_over_t;
         vm[a] = v[a] + g.qmh2 * e[a];
     }
     const float w0 = vm[0] + (vm[1] * t[2] - vm[2] * t[1]);
@@ -146,12 +147,15 @@ __device__ __forceinline__ bool em_move_axis(float f, float vdtdx, int *sh, int 
     return ok;
 }
 
-// Jz weight of lattice node (aq, bq) of the stencil (Esirkepov's W_z in 2D).
+// Jz weight of lattice node (aq, bq) of the stencil, Esirkepov's 2D
+//   W_z = S0x S0y + DSx S0y / 2 + S0x DSy / 2 + DSx DSy / 3,
+// grouped as S0x (S0y + DSy / 2) + DSx (S0y / 2 + DSy / 3): the bracket of the first
+// term is the Jx factor of the same row, and both brackets are shared along it.
 __device__ __forceinline__ float esirkepov_wz(const float (&S0)[2][3], const float (&DS)[2][3],
                                               int aq, int bq)
 {
-    return S0[0][aq] * S0[1][bq] + 0.5f * DS[0][aq] * S0[1][bq] + 0.5f * S0[0][aq] * DS[1][bq] +
-           DS[0][aq] * DS[1][bq] * (1.0f / 3.0f);
+    return fmaf(S0[0][aq], S0[1][bq] + 0.5f * DS[1][bq],
+                DS[0][aq] * (0.5f * S0[1][bq] + DS[1][bq] * (1.0f / 3.0f)));
 }
 
 // One particle through the whole particle part of the step, reading the fields and
@@ -477,11 +481,12 @@ __global__ void __launch_bounds__(EM_THREADS)
                         if (q) atomicAdd(col + bq * W0, q);
                     }
                 }
+                const float vz_scaled = vn[2] * J_SCALE;  // exact: a power-of-two scale
 #pragma unroll
                 for (int bq = 0; bq < 3; ++bq)
 #pragma unroll
                     for (int aq = 0; aq < 3; ++aq) {
-                        const float y = vn[2] * esirkepov_wz(S0, DS, aq, bq) * J_SCALE;
+                        const float y = vz_scaled * esirkepov_wz(S0, DS, aq, bq);
                         const int l = (B1i + bq) * W0 + B0i + aq;
                         if (fabsf(y) < J_SCALE) {
                             const int q = __float_as_int(y + RND_MAGIC_F) - RND_MAGIC_I;
