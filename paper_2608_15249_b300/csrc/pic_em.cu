@@ -70,12 +70,6 @@ __device__ __forceinline__ float lattice_cic(const float *__restrict__ F, int n0
            fy * ((1.0f - fx) * __ldg(F + i0 + n0 * j1) + fx * __ldg(F + i1 + n0 * j1));
 }
 
-__device__ __forceinline__ float shape1(float d)
-{
-    const float a = fabsf(d);
-    return a < 1.0f ? 1.0f - a : 0.0f;
-}
-
 // |v| <= 1: round(v 2^22) by the FMA magic number
 __device__ __forceinline__ void add_fx_unit(unsigned long long *acc, float v)
 {
@@ -137,13 +131,17 @@ __device__ __forceinline__ bool em_move_axis(float f, float vdtdx, int *sh, int 
     *fr = r;
     const int mm = s < 0 ? -1 : 0;
     *m = mm;
-    // positions relative to node c + m: old f - m, new fr + sh - m (both in [0, 2))
-    const float u0 = f - (float)mm, u1 = r + (float)(s - mm);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        S0[k] = shape1(u0 - (float)k);
-        DS[k] = shape1(u1 - (float)k) - S0[k];
-    }
+    // Relative to node c + m the old position is f - m and the new one fr + sh - m,
+    // both in [0, 2): the CIC weights (1 - x, x) sit on nodes 0, 1 when the position
+    // is below 1, else on nodes 1, 2.
+    const bool old_low = mm == 0, new_low = s == mm;
+    const float g0 = 1.0f - f, g1 = 1.0f - r;
+    S0[0] = old_low ? g0 : 0.0f;
+    S0[1] = old_low ? f : g0;
+    S0[2] = old_low ? 0.0f : f;
+    DS[0] = (new_low ? g1 : 0.0f) - S0[0];
+    DS[1] = (new_low ? r : g1) - S0[1];
+    DS[2] = (new_low ? 0.0f : r) - S0[2];
     return ok;
 }
 
