@@ -94,9 +94,11 @@ def test_fft_agrees_with_cg(pk):
     b.close()
 
 
-@pytest.mark.parametrize("n", [(256, 128), (300, 211), (1000,)])
+@pytest.mark.parametrize("n", [(256, 128), (300, 211), (1000,), (64, 601)])
 def test_fft_larger_grids(pk, n):
-    """Grids of many lines and CTAs (a prime length included) against the oracle."""
+    """Grids of many lines and CTAs (a prime length included) against the oracle;
+    (64, 601) puts two power-of-two lines in a CTA with an odd line count, so the
+    last CTA holds one."""
     w = plasma.sparse_box(len(n), n, 4 * int(np.prod(n)), nv=len(n), seed=58)
     g = pk.from_workload(w, solver=pk.AP_PIC_SOLVER_FFT).load(w.x, w.v, half_push=False)
     sim = _sim(w).load(w.x, w.v, half_push=False)
