@@ -322,6 +322,7 @@ def bench_ours(args):
     collisions = None if (f64 or args.no_collisions) else bench_collisions(
         args, pk, torch, stream, peak, peak_kind)
     em = None if (f64 or args.no_em) else bench_em(args, pk, torch, stream, peak, peak_kind)
+    cpml = None if (f64 or args.no_em) else bench_cpml(args, pk, torch, stream, peak, peak_kind)
     e2e = None
     if not args.no_e2e:
         solver = "cg" if f64 else args.e2e_solver
@@ -361,6 +362,7 @@ def bench_ours(args):
             "higuera_cary": hc,
             "collisions": collisions,
             "electromagnetic": em,
+            "cpml_fields": cpml,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -518,6 +520,51 @@ def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
         out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": sample * 2 / secs,
                          "sample": f"{sample} of {w.np_} particles on the full grid, 2 full "
                                    f"electromagnetic steps ({secs:.1f} s)"}
+    return out
+
+
+def bench_cpml(args, pk, torch, stream, peak, peak_kind, n=2048, npml=16, steps=50):
+    """The field-only electromagnetic step on a non-periodic n x n grid with a
+    convolutional PML of npml cells on every side (c = 1, dt = 0.5, a prescribed
+    current at the centre): CUDA-event time per step and its roofline.  Algorithmic
+    bytes per node: the current conversion (24 B int64 read and cleared, 12 B prescribed
+    current read, 12 B FP32 current written), two B half steps (12 B E read, 24 B B read
+    and written, each) and the E step (12 B B, 12 B J read, 24 B E read and written),
+    204 B; plus, in the layers, the eight psi arrays read and written (64 B).  Beside
+    it, the oracle's CpmlField step on a 512 x 512 grid."""
+    import oracle
+
+    cfg = pk.make_config(2, (n, n), dt=0.5, nv=3, em=1, c_light=1.0, em_boundary=1,
+                         pml_cells=npml, sort_every=0, diag_every=1 << 20)
+    g = pk.Pic(cfg).load(np.zeros((0, 2)), np.zeros((0, 3)))
+    J = np.zeros((3, n * n))
+    J[2, n // 2 + n * (n // 2)] = 1.0
+    g.set_current(J)
+    g.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    g.close()
+    nodes = n * n
+    layer_nodes = nodes - (n - 2 * npml) ** 2
+    out = {"ms_per_step": ms, "nodes": nodes, "node_steps_per_s": nodes / (ms * 1e-3),
+           "roofline": _roofline(nodes * 204 + layer_nodes * 64, ms,
+                                 "CPML field step (k_em_j_convert, k_cpml_b x 2, k_cpml_e)",
+                                 peak, peak_kind),
+           "workload": f"non-periodic {n}x{n} grid, {npml}-cell CPML, c = 1, dt = 0.5, "
+                       "prescribed current, fields only"}
+    if not args.no_row_oracles:
+        m = 512
+        f = oracle.CpmlField((m, m), (1.0, 1.0), 0.5, 1.0, npml)
+        Jo = np.zeros((3, m * m))
+        Jo[2, m // 2 + m * (m // 2)] = 1.0
+        _, secs = _timed(lambda: f.step(Jo, nsteps=16))
+        out["oracle"] = {"kind": "oracle", "cores": 1, "node_steps_per_s": m * m * 16 / secs,
+                         "sample": f"{m}x{m} grid, 16 steps ({secs:.2f} s)"}
     return out
 
 

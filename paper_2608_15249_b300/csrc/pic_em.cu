@@ -625,19 +625,36 @@ __global__ void __launch_bounds__(EM_THREADS)
     }
 }
 
+// An int64 as FP32 with no conversion instruction (those issue on this GPU's slow FP64
+// pipe): the magnitude (below 2^62) in three 22-bit parts, each of which becomes a
+// float exactly by the magic-number trick (bits of 1.5 * 2^23 plus the integer, less
+// 1.5 * 2^23, exact below 2^22); the parts, all of one sign, are summed with two
+// roundings, then the sign is applied.
+__device__ __forceinline__ float i64_to_f32(long long a)
+{
+    const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    const int lo = (int)(m & 0x3FFFFF), mid = (int)((m >> 22) & 0x3FFFFF), hi = (int)(m >> 44);
+    const float flo = __int_as_float(RND_MAGIC_I + lo) - RND_MAGIC_F;
+    const float fmid = __int_as_float(RND_MAGIC_I + mid) - RND_MAGIC_F;
+    const float fhi = __int_as_float(RND_MAGIC_I + hi) - RND_MAGIC_F;
+    const float v = fmaf(fhi, 17592186044416.0f, fmaf(fmid, 4194304.0f, flo));  // 2^44, 2^22
+    return a < 0 ? -v : v;
+}
+
 // J = the fixed-point weights times their factors: Jx -(qw / (dy dt)), Jy
-// -(qw / (dx dt)), Jz qw / (dx dy); the accumulator is cleared for the next step.
+// -(qw / (dx dt)), Jz qw / (dx dy), each divided by the fixed-point scale; the
+// accumulator is cleared for the next step.
 __global__ void __launch_bounds__(EM_THREADS)
     k_em_j_convert(int64_t cells, unsigned long long *__restrict__ Jacc, float *__restrict__ J,
-                   const float *__restrict__ Jext, double fx, double fy, double fz)
+                   const float *__restrict__ Jext, float fx, float fy, float fz)
 {
-    const double f[3] = {fx, fy, fz};
+    const float f[3] = {fx, fy, fz};
     for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
          id += (int64_t)gridDim.x * EM_THREADS)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const long long a = (long long)Jacc[k * cells + id];
-            float j = (float)(f[k] * (double)a / (double)J_SCALE);
+            float j = f[k] * i64_to_f32(a);
             if (Jext) j += Jext[k * cells + id];
             J[k * cells + id] = j;
             Jacc[k * cells + id] = 0ull;
@@ -669,14 +686,21 @@ __global__ void __launch_bounds__(EM_THREADS)
         const float dxEz = (at_or_zero(Ez, n0, n1, i + 1, j) - Ez[id]) * idx;
         const float dxEy = (at_or_zero(Ey, n0, n1, i + 1, j) - Ey[id]) * idx;
         const float dyEx = (at_or_zero(Ex, n0, n1, i, j + 1) - Ex[id]) * idy;
-        const float p0 = em.pb[3][j] * em.psib[0][id] + em.pb[4][j] * dyEz;
-        const float p1 = em.pb[0][i] * em.psib[1][id] + em.pb[1][i] * dxEz;
-        const float p2 = em.pb[0][i] * em.psib[2][id] + em.pb[1][i] * dxEy;
-        const float p3 = em.pb[3][j] * em.psib[3][id] + em.pb[4][j] * dyEx;
-        em.psib[0][id] = p0;
-        em.psib[1][id] = p1;
-        em.psib[2][id] = p2;
-        em.psib[3][id] = p3;
+        // outside the layer along an axis (b = 1, c = 0) psi stays zero: it is neither
+        // read nor written there
+        float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+        if (em.pb[4][j] != 0.0f || em.pb[3][j] != 1.0f) {
+            p0 = em.pb[3][j] * em.psib[0][id] + em.pb[4][j] * dyEz;
+            p3 = em.pb[3][j] * em.psib[3][id] + em.pb[4][j] * dyEx;
+            em.psib[0][id] = p0;
+            em.psib[3][id] = p3;
+        }
+        if (em.pb[1][i] != 0.0f || em.pb[0][i] != 1.0f) {
+            p1 = em.pb[0][i] * em.psib[1][id] + em.pb[1][i] * dxEz;
+            p2 = em.pb[0][i] * em.psib[2][id] + em.pb[1][i] * dxEy;
+            em.psib[1][id] = p1;
+            em.psib[2][id] = p2;
+        }
         Bx[id] -= h * (em.pb[5][j] * dyEz + p0);
         By[id] += h * (em.pb[2][i] * dxEz + p1);
         Bz[id] -= h * ((em.pb[2][i] * dxEy + p2) - (em.pb[5][j] * dyEx + p3));
@@ -699,14 +723,19 @@ __global__ void __launch_bounds__(EM_THREADS)
         const float dxBz = (Bz[id] - at_or_zero(Bz, n0, n1, i - 1, j)) * idx;
         const float dxBy = (By[id] - at_or_zero(By, n0, n1, i - 1, j)) * idx;
         const float dyBx = (Bx[id] - at_or_zero(Bx, n0, n1, i, j - 1)) * idy;
-        const float p0 = em.pe[3][j] * em.psie[0][id] + em.pe[4][j] * dyBz;
-        const float p1 = em.pe[0][i] * em.psie[1][id] + em.pe[1][i] * dxBz;
-        const float p2 = em.pe[0][i] * em.psie[2][id] + em.pe[1][i] * dxBy;
-        const float p3 = em.pe[3][j] * em.psie[3][id] + em.pe[4][j] * dyBx;
-        em.psie[0][id] = p0;
-        em.psie[1][id] = p1;
-        em.psie[2][id] = p2;
-        em.psie[3][id] = p3;
+        float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // zero outside the layer
+        if (em.pe[4][j] != 0.0f || em.pe[3][j] != 1.0f) {
+            p0 = em.pe[3][j] * em.psie[0][id] + em.pe[4][j] * dyBz;
+            p3 = em.pe[3][j] * em.psie[3][id] + em.pe[4][j] * dyBx;
+            em.psie[0][id] = p0;
+            em.psie[3][id] = p3;
+        }
+        if (em.pe[1][i] != 0.0f || em.pe[0][i] != 1.0f) {
+            p1 = em.pe[0][i] * em.psie[1][id] + em.pe[1][i] * dxBz;
+            p2 = em.pe[0][i] * em.psie[2][id] + em.pe[1][i] * dxBy;
+            em.psie[1][id] = p1;
+            em.psie[2][id] = p2;
+        }
         const bool xb = i == 0 || i == n0 - 1, yb = j == 0 || j == n1 - 1;
         const float ex = Ex[id] + dt * (c2 * (em.pe[5][j] * dyBz + p0) - J[id]);
         const float ey = Ey[id] + dt * (-c2 * (em.pe[2][i] * dxBz + p1) - J[cells + id]);
@@ -826,8 +855,9 @@ cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, d
 {
     const int64_t cells = (int64_t)g.n[0] * g.n[1];
     const int nb = em_blocks(cells);
-    k_em_j_convert<<<nb, EM_THREADS, 0, st>>>(cells, em.J, em.Jf, em.Jext, -qw / (dy * dt),
-                                              -qw / (dx * dt), qw / (dx * dy));
+    k_em_j_convert<<<nb, EM_THREADS, 0, st>>>(
+        cells, em.J, em.Jf, em.Jext, (float)(-qw / (dy * dt) / J_SCALE),
+        (float)(-qw / (dx * dt) / J_SCALE), (float)(qw / (dx * dy) / J_SCALE));
     if (em.pb[0]) {
         // non-periodic grid with the absorbing layer
         const float idx = (float)(1.0 / dx), idy = (float)(1.0 / dy);
