@@ -795,13 +795,7 @@ __global__ void __launch_bounds__(EM_THREADS)
 
 int em_blocks(int64_t n)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
+    const int sms = sm_count();
     const int64_t need = (n + EM_THREADS - 1) / EM_THREADS;
     const int64_t cap = (int64_t)sms * 8;
     const int64_t b = need < cap ? need : cap;

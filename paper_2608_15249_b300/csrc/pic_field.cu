@@ -23,13 +23,7 @@ enum : int { SC_BNORM = 0, SC_RZ0 = 1, SC_RZ1 = 2, SC_RELRES = 3, SC_NSCAL = 8 }
 
 int field_blocks(int64_t cells)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
+    const int sms = sm_count();
     int64_t need = (cells + FT - 1) / FT;
     int64_t cap = (int64_t)sms * 4;
     int64_t b = need < cap ? need : cap;

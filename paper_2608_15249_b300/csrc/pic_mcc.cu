@@ -170,13 +170,7 @@ __global__ void __launch_bounds__(MCC_THREADS) k_iota(uint32_t *__restrict__ id,
 
 int mcc_blocks(int64_t np)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
+    const int sms = sm_count();
     const int64_t need = (np + (int64_t)MCC_CHUNK * (MCC_THREADS / 32) - 1) /
                          ((int64_t)MCC_CHUNK * (MCC_THREADS / 32));
     const int64_t cap = (int64_t)sms * 8;
