@@ -89,6 +89,18 @@ def _declare(L):
     L.orc_cpml_b.restype = None
     L.orc_cpml_e.argtypes = [_I32, _D, _D, _D, d, d, _D, PP, PP]
     L.orc_cpml_e.restype = None
+    L.orc_yee3_b.argtypes = [_I32, _D, _D, _D, d]
+    L.orc_yee3_b.restype = None
+    L.orc_yee3_e.argtypes = [_I32, _D, _D, _D, d, d, _D]
+    L.orc_yee3_e.restype = None
+    L.orc_yee3_div_e.argtypes = [_I32, _D, _D, _D]
+    L.orc_yee3_div_e.restype = None
+    L.orc_yee3_div_b.argtypes = [_I32, _D, _D, _D]
+    L.orc_yee3_div_b.restype = None
+    L.orc_em3_gather.argtypes = [_I32, _D, i64, _D, _D, _D, _D]
+    L.orc_em3_gather.restype = None
+    L.orc_esirkepov3.argtypes = [_I32, _D, i64, _D, _D, d, d, _D]
+    L.orc_esirkepov3.restype = None
     L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
     L.orc_hc.restype = None
     L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
@@ -555,6 +567,120 @@ class EmSimulation:
 
     def gauss_residual(self):
         return yee_div_e(self.n, self.dx, self.E) - self.rho
+
+
+# ---- electromagnetic step in 3D (E_Maxwell, Sec. 2.2): periodic Yee lattice --------------------
+# Ex (1/2,0,0), Ey (0,1/2,0), Ez (0,0,1/2); Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0);
+# arrays [3][cells] with x fastest.
+
+def _cells3(n):
+    return int(n[0]) * int(n[1]) * int(n[2])
+
+
+def yee3_b(n, dx, E, B, h):
+    """In-place B -= h curl E on the 3D Yee lattice."""
+    assert B.dtype == np.float64 and B.flags.c_contiguous
+    lib().orc_yee3_b(_n3(n), _dx3(dx), _dp(_f(E)), _dp(B), float(h))
+    return B
+
+
+def yee3_e(n, dx, B, J, c, dt, E):
+    """In-place E += dt (c^2 curl B - J) on the 3D Yee lattice."""
+    assert E.dtype == np.float64 and E.flags.c_contiguous
+    lib().orc_yee3_e(_n3(n), _dx3(dx), _dp(_f(B)), _dp(_f(J)), float(c) ** 2, float(dt), _dp(E))
+    return E
+
+
+def yee3_div_e(n, dx, E):
+    out = np.empty(_cells3(n))
+    lib().orc_yee3_div_e(_n3(n), _dx3(dx), _dp(_f(E)), _dp(out))
+    return out
+
+
+def yee3_div_b(n, dx, B):
+    out = np.empty(_cells3(n))
+    lib().orc_yee3_div_b(_n3(n), _dx3(dx), _dp(_f(B)), _dp(out))
+    return out
+
+
+def em3_gather(n, dx, x, E, B):
+    """E and B at the particles (np x 6), trilinear CIC on each staggered lattice."""
+    x = _f(x)
+    out = np.empty((x.shape[0], 6))
+    lib().orc_em3_gather(_n3(n), _dx3(dx), x.shape[0], _dp(x), _dp(_f(E)), _dp(_f(B)), _dp(out))
+    return out
+
+
+def esirkepov3(n, dx, x0, x1, qw, dt, J):
+    """Add the charge-conserving 3D current of the moves x0 -> x1 into J ([3][cells])."""
+    assert J.dtype == np.float64 and J.flags.c_contiguous
+    x0, x1 = _f(x0), _f(x1)
+    lib().orc_esirkepov3(_n3(n), _dx3(dx), x0.shape[0], _dp(x0), _dp(x1), float(qw), float(dt),
+                         _dp(J))
+    return J
+
+
+class EmSimulation3:
+    """The electromagnetic PIC cycle on a periodic 3D Yee lattice, FP64: the 3D form of
+    EmSimulation.  Each step: gather E^n, B^n (+ uniform B0) -> Boris -> move ->
+    Esirkepov current J^(n+1/2) -> B -= (dt/2) curl E -> E += dt (c^2 curl B - J) ->
+    B -= (dt/2) curl E.  Loading solves the Poisson equation of the loaded charge for
+    the initial E (forward differences of phi onto the staggered points, so that
+    div E = rho exactly), B = 0, then the backward half push."""
+
+    def __init__(self, n, dx, dt, c, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0), rtol=1e-12):
+        self.n = tuple(int(k) for k in n[:3])
+        self.dx = tuple(float(h) for h in dx[:3])
+        self.dt, self.c, self.q, self.m, self.w = float(dt), float(c), float(q), float(m), float(weight)
+        self.B0 = np.array(list(B0) + [0.0] * (3 - len(B0)))[:3]
+        self.rtol = rtol
+        self.cells = _cells3(self.n)
+        self.dV = self.dx[0] * self.dx[1] * self.dx[2]
+        self.V = self.dV * self.cells
+        self.step_count = 0
+
+    def _rho(self):
+        rho_e = deposit(3, self.n, self.dx, self.x, self.q * self.w)
+        return rho_e + (-self.q * self.w * self.x.shape[0] / self.V)
+
+    def load(self, x, v, half_push=True):
+        self.x = np.array(x, dtype=np.float64, order="C")
+        self.v = np.array(v, dtype=np.float64, order="C")
+        assert self.x.shape[1] == 3 and self.v.shape[1] == 3
+        rho = self._rho()
+        phi, _, _ = poisson(3, self.n, self.dx, rho, self.rtol, 200000)
+        ph = phi.reshape(self.n[2], self.n[1], self.n[0])
+        self.E = np.zeros((3, self.cells))
+        for a, axis in ((0, 2), (1, 1), (2, 0)):  # numpy axis of x, y, z
+            self.E[a] = (-(np.roll(ph, -1, axis=axis) - ph) / self.dx[a]).ravel()
+        self.B = np.zeros((3, self.cells))
+        self.J = np.zeros((3, self.cells))
+        self.rho = rho
+        if half_push:
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, -0.5 * self.dt)
+        return self
+
+    def _fields_at(self, x):
+        EB = em3_gather(self.n, self.dx, x, self.E, self.B)
+        EB[:, 3:] += self.B0
+        return EB
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, self.dt)
+            x0 = self.x.copy()
+            move(3, self.n, self.dx, self.x, self.v, self.dt)
+            self.J = np.zeros((3, self.cells))
+            esirkepov3(self.n, self.dx, x0, self.x, self.q * self.w, self.dt, self.J)
+            yee3_b(self.n, self.dx, self.E, self.B, 0.5 * self.dt)
+            yee3_e(self.n, self.dx, self.B, self.J, self.c, self.dt, self.E)
+            yee3_b(self.n, self.dx, self.E, self.B, 0.5 * self.dt)
+            self.rho = self._rho()
+            self.step_count += 1
+        return self
+
+    def gauss_residual(self):
+        return yee3_div_e(self.n, self.dx, self.E) - self.rho
 
 
 # ---- convolutional PML (E_Maxwell, Sec. 2.2; Roden and Gedney 2000) ---------------------------

@@ -688,6 +688,176 @@ void orc_esirkepov(const int *n, const double *dx, int64_t np, const double *x0,
     }
 }
 
+/* ---- electromagnetic step in 3D (E_Maxwell, Sec. 2.2: FDTD on the Yee lattice) --------------
+ * Periodic grid of n0 x n1 x n2 nodes, component-major [3][cells] arrays, element
+ * (i, j, k) of a component at ((i + sx) dx, (j + sy) dy, (k + sz) dz) with the Yee
+ * offsets
+ *   Ex (1/2, 0, 0), Ey (0, 1/2, 0), Ez (0, 0, 1/2);
+ *   Bx (0, 1/2, 1/2), By (1/2, 0, 1/2), Bz (1/2, 1/2, 0);
+ * J staggered like E.  A field that does not depend on z is the 2D3V lattice above
+ * (there Ez and Bz sit at the 2D positions (0, 0) and (1/2, 1/2)). */
+static const double EM3_S[6][3] = {{0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},
+                                   {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0}};
+
+static int64_t at3(const int *n, int i, int j, int k)
+{
+    i %= n[0];
+    if (i < 0) i += n[0];
+    j %= n[1];
+    if (j < 0) j += n[1];
+    k %= n[2];
+    if (k < 0) k += n[2];
+    return (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
+}
+
+/* Faraday: B -= h curl E, each component of curl E by centred differences of E at
+ * the B component's own position. */
+void orc_yee3_b(const int *n, const double *dx, const double *E, double *B, double h)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    const double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int64_t c = at3(n, i, j, k);
+                const double curl_x = (Ez[at3(n, i, j + 1, k)] - Ez[c]) / dx[1] -
+                                      (Ey[at3(n, i, j, k + 1)] - Ey[c]) / dx[2];
+                const double curl_y = (Ex[at3(n, i, j, k + 1)] - Ex[c]) / dx[2] -
+                                      (Ez[at3(n, i + 1, j, k)] - Ez[c]) / dx[0];
+                const double curl_z = (Ey[at3(n, i + 1, j, k)] - Ey[c]) / dx[0] -
+                                      (Ex[at3(n, i, j + 1, k)] - Ex[c]) / dx[1];
+                Bx[c] -= h * curl_x;
+                By[c] -= h * curl_y;
+                Bz[c] -= h * curl_z;
+            }
+}
+
+/* Ampere: E += dt (c^2 curl B - J), curl B by centred differences at the E positions. */
+void orc_yee3_e(const int *n, const double *dx, const double *B, const double *J, double c2,
+                double dt, double *E)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    const double *Bx = B, *By = B + cells, *Bz = B + 2 * cells;
+    double *Ex = E, *Ey = E + cells, *Ez = E + 2 * cells;
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int64_t c = at3(n, i, j, k);
+                const double cx = (Bz[c] - Bz[at3(n, i, j - 1, k)]) / dx[1] -
+                                  (By[c] - By[at3(n, i, j, k - 1)]) / dx[2];
+                const double cy = (Bx[c] - Bx[at3(n, i, j, k - 1)]) / dx[2] -
+                                  (Bz[c] - Bz[at3(n, i - 1, j, k)]) / dx[0];
+                const double cz = (By[c] - By[at3(n, i - 1, j, k)]) / dx[0] -
+                                  (Bx[c] - Bx[at3(n, i, j - 1, k)]) / dx[1];
+                Ex[c] += dt * (c2 * cx - J[c]);
+                Ey[c] += dt * (c2 * cy - J[cells + c]);
+                Ez[c] += dt * (c2 * cz - J[2 * cells + c]);
+            }
+}
+
+/* div E at the nodes and div B at the cell centres (i+1/2, j+1/2, k+1/2). */
+void orc_yee3_div_e(const int *n, const double *dx, const double *E, double *div)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int64_t c = at3(n, i, j, k);
+                div[c] = (E[c] - E[at3(n, i - 1, j, k)]) / dx[0] +
+                         (E[cells + c] - E[cells + at3(n, i, j - 1, k)]) / dx[1] +
+                         (E[2 * cells + c] - E[2 * cells + at3(n, i, j, k - 1)]) / dx[2];
+            }
+}
+
+void orc_yee3_div_b(const int *n, const double *dx, const double *B, double *div)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int64_t c = at3(n, i, j, k);
+                div[c] = (B[at3(n, i + 1, j, k)] - B[c]) / dx[0] +
+                         (B[cells + at3(n, i, j + 1, k)] - B[cells + c]) / dx[1] +
+                         (B[2 * cells + at3(n, i, j, k + 1)] - B[2 * cells + c]) / dx[2];
+            }
+}
+
+/* E and B at the particles (np x 6: Ex Ey Ez Bx By Bz), trilinear CIC on each
+ * component's own staggered lattice; x is np x 3. */
+void orc_em3_gather(const int *n, const double *dx, int64_t np, const double *x, const double *E,
+                    const double *B, double *out)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    for (int64_t p = 0; p < np; ++p)
+        for (int q = 0; q < 6; ++q) {
+            const double *F = (q < 3 ? E : B) + (int64_t)(q % 3) * cells;
+            int i0[3];
+            double f[3];
+            for (int a = 0; a < 3; ++a) {
+                const double u = x[3 * p + a] / dx[a] - EM3_S[q][a];
+                const double iu = floor(u);
+                i0[a] = (int)iu;
+                f[a] = u - iu;
+            }
+            double s = 0.0;
+            for (int corner = 0; corner < 8; ++corner) {
+                const int b0 = corner & 1, b1 = (corner >> 1) & 1, b2 = corner >> 2;
+                const double w = (b0 ? f[0] : 1.0 - f[0]) * (b1 ? f[1] : 1.0 - f[1]) *
+                                 (b2 ? f[2] : 1.0 - f[2]);
+                s += w * F[at3(n, i0[0] + b0, i0[1] + b1, i0[2] + b2)];
+            }
+            out[6 * p + q] = s;
+        }
+}
+
+/* Charge-conserving current of particles moving from x0 to x1 in one step (Esirkepov
+ * 2001, 3D, CIC shapes); every displacement under one cell per axis, taken modulo the
+ * box.  With S0, S1 the node shapes before and after per axis and DS = S1 - S0,
+ *   Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3), and cyclically,
+ *   Jx(i+1/2, j, k) = -(qw / (dy dz dt)) sum_{i' <= i} Wx(i', j, k), and cyclically,
+ * added into J ([3][cells], staggered like E), so that rho1 - rho0 + dt div J = 0. */
+void orc_esirkepov3(const int *n, const double *dx, int64_t np, const double *x0,
+                    const double *x1, double qw, double dt, double *J)
+{
+    const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+    const double L[3] = {n[0] * dx[0], n[1] * dx[1], n[2] * dx[2]};
+    for (int64_t p = 0; p < np; ++p) {
+        double S0[3][4], DS[3][4];
+        int base[3];
+        for (int a = 0; a < 3; ++a) {
+            double d = x1[3 * p + a] - x0[3 * p + a];
+            d -= L[a] * floor(d / L[a] + 0.5);
+            const double u0 = x0[3 * p + a] / dx[a], u1 = u0 + d / dx[a];
+            base[a] = (int)floor(u0) - 1;
+            for (int k = 0; k < 4; ++k) {
+                S0[a][k] = cic1(u0 - (base[a] + k));
+                DS[a][k] = cic1(u1 - (base[a] + k)) - S0[a][k];
+            }
+        }
+        /* axis a's current: prefix sums along a of W_a, for each node of the other two */
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3, c = (a + 2) % 3;
+            const double fa = -qw / (dx[b] * dx[c] * dt);
+            for (int kb = 0; kb < 4; ++kb)
+                for (int kc = 0; kc < 4; ++kc) {
+                    const double perp = S0[b][kb] * S0[c][kc] + 0.5 * DS[b][kb] * S0[c][kc] +
+                                        0.5 * S0[b][kb] * DS[c][kc] +
+                                        DS[b][kb] * DS[c][kc] / 3.0;
+                    double run = 0.0;
+                    for (int ka = 0; ka < 4; ++ka) {
+                        run += DS[a][ka] * perp;
+                        int idx[3];
+                        idx[a] = base[a] + ka;
+                        idx[b] = base[b] + kb;
+                        idx[c] = base[c] + kc;
+                        J[(int64_t)a * cells + at3(n, idx[0], idx[1], idx[2])] += fa * run;
+                    }
+                }
+        }
+    }
+}
+
 /* ---- convolutional PML (E_Maxwell, Sec. 2.2, the CPML the paper cites: Roden and
  * Gedney 2000) on a 2D Yee grid with a perfectly conducting wall behind it -------------- */
 /* Non-periodic grid of n0 x n1 nodes; the Yee offsets as above; the tangential E on the
