@@ -101,6 +101,12 @@ def _declare(L):
     L.orc_em3_gather.restype = None
     L.orc_esirkepov3.argtypes = [_I32, _D, i64, _D, _D, d, d, _D]
     L.orc_esirkepov3.restype = None
+    L.orc_em_gather_np.argtypes = [_I32, _D, i64, _D, _D, _D, _D]
+    L.orc_em_gather_np.restype = None
+    L.orc_esirkepov_np.argtypes = [_I32, _D, i64, _D, _D, _D, d, d, _D]
+    L.orc_esirkepov_np.restype = None
+    L.orc_deposit_np.argtypes = [_I32, _D, i64, _D, d, _D]
+    L.orc_deposit_np.restype = None
     L.orc_hc.argtypes = [i, i, i64, _D, _D, _D, _D, d, d, d]
     L.orc_hc.restype = None
     L.orc_kinetic_rel.argtypes = [i, i64, _D, d, d]
@@ -752,3 +758,79 @@ class CpmlField:
     def energy(self):
         return 0.5 * float(np.sum(self.E ** 2) + self.c ** 2 * np.sum(self.B ** 2)) * \
             self.dx[0] * self.dx[1]
+
+
+# ---- particles in the CPML mode (non-periodic 2D3V grid, absorbing particle walls) -----------
+
+class CpmlPlasma(CpmlField):
+    """Particles on the non-periodic grid of CpmlField: the electromagnetic cycle of
+    EmSimulation with the CPML field update, gathers and currents that leave out the
+    nodes outside the grid, and absorbing particle walls.  Particles live in the box
+    [0, (n0 - 1) dx) x [0, (n1 - 1) dy); one that leaves it during a move deposits the
+    current of its whole move (what falls outside the grid is dropped) and is then
+    removed.  Fields start at zero (E = B = 0): the load solves no Poisson equation, so
+    div E - rho starts at -rho and, by charge conservation, keeps its value at every
+    node where neither the layer nor the wall modifies the update."""
+
+    def __init__(self, n, dx, dt, c, npml, q=-1.0, m=1.0, weight=1.0, B0=(0, 0, 0), **kw):
+        super().__init__(n, dx, dt, c, npml, **kw)
+        self.q, self.m, self.w = float(q), float(m), float(weight)
+        self.B0 = np.array(list(B0) + [0.0] * (3 - len(B0)))[:3]
+        self.box = np.array([(self.n[0] - 1) * self.dx[0], (self.n[1] - 1) * self.dx[1]])
+        self.absorbed = 0
+        self.step_count = 0
+
+    def _inside(self, x):
+        return np.all((x >= 0.0) & (x < self.box), axis=1)
+
+    def rho_e(self):
+        rho = np.empty(self.n[0] * self.n[1])
+        lib().orc_deposit_np(_n2(self.n), _dx2(self.dx), self.x.shape[0], _dp(self.x),
+                             self.q * self.w, _dp(rho))
+        return rho
+
+    def _fields_at(self, x):
+        out = np.empty((x.shape[0], 6))
+        lib().orc_em_gather_np(_n2(self.n), _dx2(self.dx), x.shape[0], _dp(_f(x)), _dp(self.E),
+                               _dp(self.B), _dp(out))
+        out[:, 3:] += self.B0
+        return out
+
+    def load(self, x, v, half_push=True):
+        self.x = np.array(x, dtype=np.float64, order="C")
+        self.v = np.array(v, dtype=np.float64, order="C")
+        assert self.x.shape[1] == 2 and self.v.shape[1] == 3
+        assert np.all(self._inside(self.x)), "particles must start inside the walls"
+        if half_push:
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, -0.5 * self.dt)
+        self.rho = self.rho_e()
+        return self
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            boris_eb(self.v, self._fields_at(self.x), self.q / self.m, self.dt)
+            x0 = self.x.copy()
+            self.x += self.v[:, :2] * self.dt
+            J = np.zeros((3, self.n[0] * self.n[1]))
+            lib().orc_esirkepov_np(_n2(self.n), _dx2(self.dx), x0.shape[0], _dp(x0),
+                                   _dp(self.x), _dp(np.ascontiguousarray(self.v[:, 2])),
+                                   self.q * self.w, self.dt, _dp(J))
+            CpmlField.step(self, J)
+            keep = self._inside(self.x)
+            self.absorbed += int(np.count_nonzero(~keep))
+            self.x = np.ascontiguousarray(self.x[keep])
+            self.v = np.ascontiguousarray(self.v[keep])
+            self.rho = self.rho_e()
+            self.step_count += 1
+        return self
+
+    def div_e(self):
+        """Discrete div E at the nodes, E outside the grid counting as zero."""
+        ex = self.E[0].reshape(self.n[1], self.n[0])
+        ey = self.E[1].reshape(self.n[1], self.n[0])
+        dx = ex - np.pad(ex, ((0, 0), (1, 0)))[:, :-1]
+        dy = ey - np.pad(ey, ((1, 0), (0, 0)))[:-1, :]
+        return (dx / self.dx[0] + dy / self.dx[1]).ravel()
+
+    def gauss_residual(self):
+        return self.div_e() - self.rho

@@ -933,3 +933,92 @@ void orc_cpml_e(const int *n, const double *dx, const double *B, const double *J
             if (xb || j == n[1] - 1) Ey[c] = 0.0;
         }
 }
+
+/* ---- particles on the non-periodic grid (the CPML mode) ---------------------------------
+ * Particles live in the box [0, (n0 - 1) dx) x [0, (n1 - 1) dy) between the walls.  The
+ * gather, the current and the charge use the periodic forms above with every node
+ * outside the grid left out (a field value there counts as zero, a contribution to it
+ * is dropped).  A particle whose move leaves the box deposits the current of its whole
+ * move (what falls outside the grid is dropped) and is then absorbed by the caller. */
+void orc_em_gather_np(const int *n, const double *dx, int64_t np, const double *x,
+                      const double *E, const double *B, double *out)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int64_t p = 0; p < np; ++p)
+        for (int k = 0; k < 6; ++k) {
+            const double *F = (k < 3 ? E : B) + (int64_t)(k % 3) * cells;
+            const double u = x[2 * p] / dx[0] - EM_SX[k], w = x[2 * p + 1] / dx[1] - EM_SY[k];
+            const double iu = floor(u), iw = floor(w);
+            const double fu = u - iu, fw = w - iw;
+            const int i0 = (int)iu, j0 = (int)iw;
+            out[6 * p + k] = (1.0 - fw) * ((1.0 - fu) * pec_get(F, n, i0, j0) +
+                                           fu * pec_get(F, n, i0 + 1, j0)) +
+                             fw * ((1.0 - fu) * pec_get(F, n, i0, j0 + 1) +
+                                   fu * pec_get(F, n, i0 + 1, j0 + 1));
+        }
+}
+
+static void add_np(double *F, const int *n, int i, int j, double v)
+{
+    if (i < 0 || j < 0 || i >= n[0] || j >= n[1]) return;
+    F[(int64_t)i + (int64_t)n[0] * j] += v;
+}
+
+void orc_esirkepov_np(const int *n, const double *dx, int64_t np, const double *x0,
+                      const double *x1, const double *vz, double qw, double dt, double *J)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int64_t p = 0; p < np; ++p) {
+        double S0[2][4], DS[2][4];
+        int base[2];
+        for (int a = 0; a < 2; ++a) {
+            const double u0 = x0[2 * p + a] / dx[a], u1 = x1[2 * p + a] / dx[a];
+            base[a] = (int)floor(u0) - 1;
+            for (int k = 0; k < 4; ++k) {
+                S0[a][k] = cic1(u0 - (base[a] + k));
+                DS[a][k] = cic1(u1 - (base[a] + k)) - S0[a][k];
+            }
+        }
+        const double fx = -qw / (dx[1] * dt), fy = -qw / (dx[0] * dt);
+        const double fz = qw * vz[p] / (dx[0] * dx[1]);
+        for (int b = 0; b < 4; ++b) {
+            double run = 0.0;
+            for (int a = 0; a < 4; ++a) {
+                run += DS[0][a] * (S0[1][b] + 0.5 * DS[1][b]);
+                add_np(J, n, base[0] + a, base[1] + b, fx * run);
+            }
+        }
+        for (int a = 0; a < 4; ++a) {
+            double run = 0.0;
+            for (int b = 0; b < 4; ++b) {
+                run += DS[1][b] * (S0[0][a] + 0.5 * DS[0][a]);
+                add_np(J + cells, n, base[0] + a, base[1] + b, fy * run);
+            }
+        }
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const double wz = S0[0][a] * S0[1][b] + 0.5 * DS[0][a] * S0[1][b] +
+                                  0.5 * S0[0][a] * DS[1][b] + DS[0][a] * DS[1][b] / 3.0;
+                add_np(J + 2 * cells, n, base[0] + a, base[1] + b, fz * wz);
+            }
+    }
+}
+
+/* CIC charge density (qw / (dx dy) per particle) on the nodes of the non-periodic grid. */
+void orc_deposit_np(const int *n, const double *dx, int64_t np, const double *x, double qw,
+                    double *rho)
+{
+    const int64_t cells = (int64_t)n[0] * n[1];
+    for (int64_t c = 0; c < cells; ++c) rho[c] = 0.0;
+    const double s = qw / (dx[0] * dx[1]);
+    for (int64_t p = 0; p < np; ++p) {
+        const double u = x[2 * p] / dx[0], w = x[2 * p + 1] / dx[1];
+        const double iu = floor(u), iw = floor(w);
+        const double fu = u - iu, fw = w - iw;
+        const int i0 = (int)iu, j0 = (int)iw;
+        add_np(rho, n, i0, j0, s * (1.0 - fu) * (1.0 - fw));
+        add_np(rho, n, i0 + 1, j0, s * fu * (1.0 - fw));
+        add_np(rho, n, i0, j0 + 1, s * (1.0 - fu) * fw);
+        add_np(rho, n, i0 + 1, j0 + 1, s * fu * fw);
+    }
+}
