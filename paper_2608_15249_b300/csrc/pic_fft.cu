@@ -12,13 +12,14 @@
 // takes W lines (consecutive rows for the x axis, W adjacent columns otherwise, so
 // that global accesses are W-wide segments), holds them in shared memory and
 // transforms them there:
-//   - power-of-two lengths: radix-2 decimation in time (input scattered to
-//     bit-reversed positions, natural-order output) for the forward transform and
-//     decimation in frequency (natural input, bit-reversed output) for the inverse,
-//     so no separate reordering pass is needed;
+//   - power-of-two lengths: self-sorting (Stockham) mixed-radix passes, radix 8 and
+//     a last radix 4 or 2, natural order in and out (see stockham below);
 //   - other lengths: Bluestein's chirp-z form, X_k = w_k sum_j (x_j w_j) conj(w_{k-j})
 //     with w_j = exp(-i pi j^2 / n), a cyclic convolution of power-of-two length
-//     m >= 2n - 1 done with the same two transforms and a precomputed filter.
+//     m >= 2n - 1 done with radix-2 stages: decimation in time (input scattered to
+//     bit-reversed positions, natural-order output) for the forward transform and
+//     decimation in frequency (natural input, bit-reversed output) for the inverse,
+//     so no separate reordering pass is needed, and a precomputed filter.
 // The last axis does forward transform, scaling by 1 / (N K^2) and inverse in one
 // kernel; 1D is a single kernel, 2D three, 3D five.
 #include <cuda_runtime.h>
