@@ -160,3 +160,31 @@ def test_em3_cycle_keeps_gauss_law():
     sim.step(8)
     assert np.abs(sim.gauss_residual()).max() <= 1e-9 * scale
     assert np.abs(oracle.yee3_div_b(n, dx, sim.B)).max() <= 1e-12 * max(np.abs(sim.B).max(), 1e-30)
+
+
+def test_em3_cold_plasma_oscillates_at_the_plasma_frequency():
+    """A cold electron lattice displaced by a small sine along x (weight such that
+    omega_p = 1) oscillates longitudinally in the full 3D electromagnetic cycle: the
+    mode's Ex changes sign at a rate within 1 % of omega_p (the coupling's signs and
+    magnitudes in 3D)."""
+    n, dx, dt = (32, 4, 4), (0.5, 0.5, 0.5), 0.05
+    L = np.array([n[a] * dx[a] for a in range(3)])
+    gx = np.arange(2 * n[0]) / (2 * n[0]) * L[0]
+    gy, gz = (np.arange(n[1]) + 0.5) * dx[1], (np.arange(n[2]) + 0.5) * dx[2]
+    X, Y, Z = np.meshgrid(gx, gy, gz, indexing="ij")
+    x = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    k = 2 * np.pi / L[0]
+    x[:, 0] = np.mod(x[:, 0] + 0.01 * np.sin(k * x[:, 0]), L[0])
+    sim = oracle.EmSimulation3(n, dx, dt, c=5.0, weight=float(np.prod(L)) / x.shape[0])
+    sim.load(x, np.zeros_like(x))
+    W = np.broadcast_to(np.sin(k * (np.arange(n[0]) + 0.5) * dx[0]), (n[2], n[1], n[0])).ravel()
+    sig = []
+    for _ in range(300):
+        sim.step(1)
+        sig.append(float(np.sum(sim.E[0] * W)))
+    sig = np.array(sig)
+    t = [(i - 1) + sig[i - 1] / (sig[i - 1] - sig[i]) for i in range(1, len(sig))
+         if sig[i - 1] * sig[i] < 0]
+    assert len(t) >= 4
+    omega = np.pi / (np.mean(np.diff(t)) * dt)
+    assert abs(omega - 1.0) < 0.01, omega
