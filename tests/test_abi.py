@@ -109,3 +109,32 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
+
+
+def test_electromagnetic_configuration_is_validated_on_the_host(libpath):
+    """The electromagnetic step's configuration is checked before any device work: the
+    2D3V FP32 form with Boris, c > 0 and a Courant number below 1; the absorbing layer
+    only with em = 1 and with layers thinner than half the grid on each axis."""
+    import paper_2608_15249_b300 as pk
+    base = dict(ndim=2, n=(32, 32), dt=0.1, nv=3, em=1, c_light=2.0)
+    cases = (
+        (dict(em=2), -1),
+        (dict(ndim=3, n=(8, 8, 8)), -2),
+        (dict(nv=2), -2),
+        (dict(precision=pk.AP_PIC_FP64_PLAIN), -2),
+        (dict(pusher=pk.AP_PIC_PUSHER_HIGUERA_CARY), -2),
+        (dict(c_light=0.0), -1),
+        (dict(c_light=10.0), -1),  # c dt sqrt(2) = 1.41: past the Courant limit
+        (dict(em_boundary=2), -1),
+        (dict(em=0, em_boundary=1), -1),
+        (dict(em_boundary=1, pml_cells=16), -1),  # 2 * 16 = n: no interior left
+    )
+    for bad, want in cases:
+        kw = dict(base)
+        kw.update(bad)
+        cfg = pk.make_config(**kw)
+        h = ctypes.c_void_p()
+        st = pk.lib().ap_pic_create(ctypes.byref(cfg), None, None, ctypes.byref(h))
+        assert st == want, (bad, st)
+        assert pk.lib().ap_pic_last_error(h)
+        pk.lib().ap_pic_destroy(h)
