@@ -115,16 +115,21 @@ def test_cold_two_stream_growth_1d(orc):
 @pytest.mark.slow
 def test_paper_two_stream_growth_and_energy(orc):
     """The paper's worked example run by the oracle from a quiet start: growth rate of
-    2|E_par(2,1)| fitted on 10 <= t <= 19 within 8 % of gamma_th (one realisation;
-    the seeded density perturbation also excites the oscillating roots, which
-    modulate the amplitude inside the fit window; the paper's own run lands within
-    0.5 %), the mode peaks in the twenties, and the total energy error stays below
-    0.05 % of W0 (the paper reports 0.0183 %)."""
+    2|E_par(2,1)| fitted on 10 <= t <= 19 within 5 % of gamma_th, the mode peaks in
+    the twenties, and the total energy error stays below 0.05 % of W0 (the paper
+    reports 0.0183 %).
+
+    One realisation cannot reach the paper's 0.5 %: the displacement seed of Eq. 1
+    also excites the stable roots of Eqs. 5-6, which have not died out by t = 10,
+    and the random thermal velocities seed other modes.  Over velocity seeds 1-9
+    the fitted rate ranged over 0.2599-0.2797 (mean 0.2695, +3.0 %); seed 7 gives
+    0.2694.  The eigenmode-loaded run of the same wave vector (test of the
+    diagnostics module) excites the growing root alone and pins gamma to 0.5 %."""
     pv = _paper_values()
     w = workloads.paper_two_stream()
     sim, t, amp, WE, KE = _run_energy_and_mode(orc, w)
     gamma, r2 = physics.fit_growth(t, amp, pv["fit_t_lo"], pv["fit_t_hi"])
-    assert abs(gamma - pv["gamma_th"]) < 0.08 * pv["gamma_th"], gamma
+    assert abs(gamma - pv["gamma_th"]) < 0.05 * pv["gamma_th"], gamma
     assert r2 > 0.9
     t_peak = t[np.argmax(amp)]
     assert 20.0 <= t_peak <= 30.0, t_peak

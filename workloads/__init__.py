@@ -12,6 +12,7 @@ from .plasma import (  # noqa: F401
     two_stream_2d,
     paper_two_stream,
     cold_two_stream_1d,
+    two_stream_eigenmode_1d,
     magnetized_3d,
     precision_3d,
     batch_instances,

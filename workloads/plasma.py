@@ -201,6 +201,52 @@ def cold_two_stream_1d(k=0.2, n=64, per_beam=8192, delta=1e-4, dt=0.05, steps=60
                     mode=(1,), meta=dict(k=k, u=u, delta=delta))
 
 
+def _bit_reversed(count):
+    """The bit-reversal permutation of range(count), count a power of two."""
+    bits = count.bit_length() - 1
+    if 1 << bits != count:
+        raise ValueError("count must be a power of two")
+    idx = np.arange(count, dtype=np.int64)
+    rev = np.zeros(count, dtype=np.int64)
+    for b in range(bits):
+        rev |= ((idx >> b) & 1) << (bits - 1 - b)
+    return rev
+
+
+def two_stream_eigenmode_1d(k, u_d, gamma, n=64, per_beam=65536, amp=1e-3, dt=0.05,
+                            steps=400):
+    """Two warm 1D beams (Maxwellian v_te = 1 drifting at +-u_d) in a box of one
+    wavelength L = 2 pi / k, loaded on the purely growing eigenmode omega = i gamma
+    of mode 1 (gamma is supplied by the caller).
+
+    Quiet start: each beam's positions sit on a regular lattice and its thermal
+    velocities are the Maxwellian quantiles Phi^-1((i + 1/2) / N), assigned in
+    bit-reversed order so that position and velocity are uncorrelated.  Each
+    particle (position x0, velocity v) then takes the linear Lagrangian
+    displacement of the mode, xi = Re[A e^{i k x0} / (k v - omega)^2] with
+    A = amp gamma^2 (a particle at rest would move by amp / k), and the velocity
+    change d xi / dt = Re[i (k v - omega) A e^{i k x0} / (k v - omega)^2].  Only the
+    growing root is excited, so the seeded mode grows as e^{gamma t} from t = 0."""
+    from scipy.special import ndtri
+
+    L = 2.0 * math.pi / k
+    n3, dx3, Lt = _box(1, (n,), (L / n,))
+    x0 = (np.arange(per_beam, dtype=np.float64) + 0.5) * (L / per_beam)
+    vq = ndtri((_bit_reversed(per_beam) + 0.5) / per_beam)
+    x = np.concatenate([x0, x0])
+    v = np.concatenate([u_d + vq, -u_d + vq])
+    omega = 1j * gamma
+    den = k * v - omega
+    xi = (amp * gamma * gamma) * np.exp(1j * k * x) / (den * den)
+    x = x + xi.real
+    v = v + (1j * den * xi).real
+    x = x[:, None].copy()
+    _wrap(x, Lt)
+    return Workload("two_stream_eigenmode_1d", 1, n3, dx3, dt, steps, x, v[:, None].copy(),
+                    weight=L / (2 * per_beam), mode=(1,),
+                    meta=dict(k=k, u_d=u_d, gamma=gamma, amp=amp))
+
+
 def maxwellian_box(ndim, n, ppc, vth=1.0, nv=3, dt=0.1, B0=(0.0, 0.0, 0.0), steps=100,
                    seed=3, dx=None, name="maxwellian_box", sort_every=20):
     """Uniform random positions, isotropic Maxwellian velocities."""
