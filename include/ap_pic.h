@@ -260,7 +260,10 @@ ap_pic_status ap_pic_sort(ap_pic *h);
  * Scratch is one fixed array of ~17 MiB in device global memory, held by
  * every GPU that loads the library until the process exits.  The first call
  * on a device (with that device current) looks up the array's device address
- * and keeps it.  All calls share the array and each overwrites it: calls that
+ * and keeps it for the life of the process, so it must come before any stream
+ * capture, and the entry point must not be called on a device again after
+ * cudaDeviceReset there (the reset unloads the array; the kept address would
+ * be stale).  All calls share the array and each overwrites it: calls that
  * overlap on the GPU race, so the caller must order them (one stream per
  * device, or explicit synchronisation). */
 ap_pic_status ap_pic_sort_perm_noalloc(int ndim, const int n[3], const int brick[3], int64_t np,

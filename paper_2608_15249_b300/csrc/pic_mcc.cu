@@ -54,8 +54,14 @@ __device__ __forceinline__ int collide_one(ParticlesF32 p, int64_t i, uint32_t i
     const float nu_exc = energy >= c.eps_exc ? c.ng_sig_exc * speed : 0.0f;
     *over = nu_el + nu_exc > c.nu_max;
     const float u1 = (float)draw24(c.seed, step, id, 1) * inv24;
-    const float u2 = ((float)draw24(c.seed, step, id, 2) + 0.5f) * inv24;
-    const float cchi = 1.0f - 2.0f * u2;
+    // cos chi = 1 - 2 u2, u2 = (r2 + 1/2) / 2^24.  With t the smaller of u2 and 1 - u2
+    // (both (k + 1/2) / 2^24 with k < 2^23, exact in FP32), cos chi = +-(1 - 2 t) and
+    // sin chi = 2 sqrt(t (1 - t)): near-forward and near-backward scattering keep
+    // their small sin chi, which 1 - cos^2 chi in FP32 would round away.
+    const uint32_t r2 = draw24(c.seed, step, id, 2);
+    const bool fwd = r2 < (1u << 23);
+    const float t2 = ((float)(fwd ? r2 : 16777215u - r2) + 0.5f) * inv24;
+    const float cchi = fwd ? 1.0f - 2.0f * t2 : 2.0f * t2 - 1.0f;
     float snew;
     int kind;
     if (u1 < nu_el / c.nu_max) {
@@ -72,7 +78,7 @@ __device__ __forceinline__ int collide_one(ParticlesF32 p, int64_t i, uint32_t i
     const float u3 = (float)draw24(c.seed, step, id, 3) * inv24;
     float sp, cp;
     sincospif(2.0f * u3, &sp, &cp);
-    const float schi = sqrtf(fmaxf(1.0f - cchi * cchi, 0.0f));
+    const float schi = 2.0f * sqrtf(t2 * (1.0f - t2));
     float n[3] = {1.0f, 0.0f, 0.0f};
     if (speed > 0.0f) {
         const float is = 1.0f / speed;

@@ -13,7 +13,11 @@
 //
 // Host code cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the first call on each device, with that
-// device current, looks the address up with cudaGetSymbolAddress and keeps it.
+// device current, looks the address up with cudaGetSymbolAddress and keeps it
+// for the life of the process.  That first call must therefore come before any
+// stream capture, and a caller that resets the device (cudaDeviceReset, which
+// unloads this library's module and its array) must not call the entry point on
+// that device again: the kept address would be stale.
 // Every call shares the array: calls whose work overlaps on the GPU (different
 // streams, or different host threads on the same device) race on it and must
 // be ordered by the caller.  No word of the scratch needs to start at zero:

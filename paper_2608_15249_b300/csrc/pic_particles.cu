@@ -154,62 +154,6 @@ __device__ __forceinline__ void corner_nodes(const int *c, const int *n, int *no
     }
 }
 
-// Warp-cooperative deposit of R particles per lane.  For each r, lanes hold
-// consecutive particles of the sorted array, so runs of lanes share a cell
-// (key).  A segmented inclusive scan over the lanes (five shuffle steps, fixed
-// cost whatever the data) sums the first 2^d - 1 corner quanta of each run; the
-// run's last corner is its particle count times 2^S minus those sums (the
-// per-particle remainder rule, summed).  The last lane of each run hands each
-// corner's total to emit(r, corner, value).  The R scans are interleaved step by
-// step so their shuffles overlap.  Lanes with key < 0 deposit nothing.  Integer
-// sums make the result independent of how lanes group and of the order in
-// which totals are added.  All 32 lanes must call it.
-template <int D, int R, class Emit>
-__device__ __forceinline__ void warp_deposit(const int (&key)[R], const int (&q)[R][1 << D],
-                                             int one, Emit emit)
-{
-    constexpr int NC = 1 << D;
-    const int lane = threadIdx.x & 31;
-    const unsigned le = 0xffffffffu >> (31 - lane);
-    int seg[R];
-    unsigned heads[R];
-    int s[R][NC - 1];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int kprev = __shfl_up_sync(0xffffffffu, key[r], 1);
-        heads[r] = __ballot_sync(0xffffffffu, lane == 0 || kprev != key[r]);
-        // first lane of this lane's run: the highest head at or below this lane
-        seg[r] = 31 - __clz(heads[r] & le);
-#pragma unroll
-        for (int k = 0; k < NC - 1; ++k) s[r][k] = q[r][k];
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const bool take = lane - d >= seg[r];
-#pragma unroll
-            for (int k = 0; k < NC - 1; ++k) {
-                const int y = __shfl_up_sync(0xffffffffu, s[r][k], d);
-                if (take) s[r][k] += y;
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const bool tail = lane == 31 || ((heads[r] >> (lane + 1)) & 1u);
-        if (tail && key[r] >= 0) {
-            int rest = (lane - seg[r] + 1) * one;
-#pragma unroll
-            for (int k = 0; k < NC - 1; ++k) {
-                rest -= s[r][k];
-                emit(r, k, s[r][k]);
-            }
-            emit(r, NC - 1, rest);
-        }
-    }
-}
-
 // Boris velocity advance in FP32 (A_Pusher, Sec. 2.2):
 //   v- = v + qmh2 E;  w = v- + v- x t;  v+ = v- + w x s;  v = v+ + qmh2 E.
 __device__ __forceinline__ void boris(float *v, const float *e, const GridParams &g)
@@ -461,10 +405,11 @@ struct BatchSrc {
 // bulk copies, STAGES - 1 tiles ahead of the one being computed; the updated
 // record is written back into the same stage and returned to global memory by
 // TMA bulk stores, so no thread waits on its own loads or stores.  Each thread
-// owns R = TILE / 256 particles of a tile (lane i of warp w: particles
-// r * 256 + w * 32 + i, so a warp's lanes hold consecutive sorted particles for
-// the warp-cooperative deposit) and takes all R through each phase together:
-// the field gathers are issued together and the R deposit scans interleave.
+// owns R = TILE / 256 particles of a tile and takes all R through each phase
+// together (the field gathers are issued together).  The lanes of a warp hold
+// particles spread over the whole tile (particle_of): sorted neighbours share a
+// cell, and 32 lanes in one or two cells would serialise on the same few window
+// words in every shared-memory atomic of the deposit.
 // MODE (PASS_* bits) is a compile-time choice so each use carries only its work.
 // Src supplies the tiles: one instance (SingleSrc) or the tiles of many
 // independent instances packed in one particle arena (BatchSrc, whose tiles each
@@ -473,6 +418,18 @@ template <int D, class Src>
 __host__ __device__ constexpr int pass_tile()
 {
     return Src::FIXED_TILE ? Src::FIXED_TILE : tile_of_dim<D>();
+}
+
+// Particle (index within the tile) of slot r of thread `tid`, for tiles of
+// R * 256 particles seen as 8 R rows of 32: lane i of warp w takes column i of row
+// (w R + r + i) mod 8 R.  Each (w, r) visits every row once across its 32 lanes, so
+// a warp's lanes are spread over the tile, while every shared-memory access of the
+// record (one column per lane) stays free of bank conflicts.
+template <int R>
+__device__ __forceinline__ int particle_of(int r, int tid)
+{
+    const int lane = tid & 31;
+    return 32 * (((tid >> 5) * R + r + lane) % (8 * R)) + lane;
 }
 
 template <int D, int NV, int MODE, class Src>
@@ -605,7 +562,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         bool valid[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int j = r * PP_THREADS + tid;
+            const int j = particle_of<R>(r, tid);
             valid[r] = j < cnt;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -629,7 +586,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!valid[r]) continue;
-            const int j = r * PP_THREADS + tid;
+            const int j = particle_of<R>(r, tid);
             bool finite = true;
             if (PUSH) {
 #pragma unroll
@@ -685,9 +642,9 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         // phase C: deposit at the (new) positions.  The tile's particles occupy a small
         // box of cells (they were sorted); when its nodes fit the shared-memory
         // window, every corner is added there and each touched node goes to the
-        // global accumulator once; otherwise warp-summed runs go to global memory.
+        // global accumulator once; otherwise the corners go to global memory.
         if (DEPOSIT) {
-            int q[R][1 << D], key[R], dd[R][3];
+            int q[R][1 << D], dd[R][3];
             int lo[3], hi[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -697,7 +654,6 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 cic_quanta<D>(f[r], scale, one, q[r]);
-                key[r] = valid[r] ? encode_cell<D>(c[r], g.n) : -1;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     int d = c[r][a] - ref[a];  // unwrapped to [-n/2, n/2]
@@ -732,32 +688,38 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
                 tot_bits += bits[a];
             }
             const bool use_win = tot_bits <= WIN_BITS && s_box[3] >= s_box[0];
-            auto emit = [&](int r, int kc, int val) {
-                if (use_win) {
-                    int idx = 0;
-#pragma unroll
-                    for (int a = 0; a < D; ++a)
-                        idx += (dd[r][a] + ((kc >> a) & 1) - blo[a]) << sh[a];
-                    atomicAdd(&s_win[idx], (unsigned)val);
-                } else {
-                    int node[1 << D];
-                    corner_nodes<D>(c[r], g.n, node);
-                    atomicAdd(acc + node[kc], (unsigned long long)(long long)val);
-                }
-            };
             if (use_win) {
-                // shared-memory atomics absorb the same-cell contention of sorted
-                // particles cheaply, so each lane adds its own corners
+                // shared-memory atomics into the window: corner k of a particle sits at
+                // its cell's window index plus a per-tile offset
+                int coff[1 << D];
+#pragma unroll
+                for (int kc = 0; kc < (1 << D); ++kc) {
+                    coff[kc] = 0;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) coff[kc] += ((kc >> a) & 1) << sh[a];
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     if (valid[r]) {
+                        int base = 0;
 #pragma unroll
-                        for (int kc = 0; kc < (1 << D); ++kc) emit(r, kc, q[r][kc]);
+                        for (int a = 0; a < D; ++a) base += (dd[r][a] - blo[a]) << sh[a];
+#pragma unroll
+                        for (int kc = 0; kc < (1 << D); ++kc)
+                            atomicAdd(&s_win[base + coff[kc]], (unsigned)q[r][kc]);
                     }
             } else {
-                // box too large for the window (particles far from sorted order): sum
-                // runs of equal cells across the warp first, then global atomics
-                warp_deposit<D, R>(key, q, one, emit);
+                // a box too large for the window (particles far from sorted order,
+                // dilute plasmas): each corner straight to the global accumulator
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (valid[r]) {
+                        int node[1 << D];
+                        corner_nodes<D>(c[r], g.n, node);
+#pragma unroll
+                        for (int kc = 0; kc < (1 << D); ++kc)
+                            atomicAdd(acc + node[kc], (unsigned long long)(long long)q[r][kc]);
+                    }
             }
             __syncthreads();
             if (use_win) {

@@ -364,31 +364,54 @@ cudaError_t launch_plain_rho_convert(FieldBufsF64 &f, double scale, double bg, d
 
 enum : int { PS_BNORM = 0, PS_RZ0 = 1, PS_RELRES = 3 };
 
+// The periodic operator is singular (constants are its null space).  Rounding
+// leaves r with a constant part that CG cannot remove; once the rest has
+// converged, p would turn nearly constant, p.Ap would vanish and alpha blow up
+// (a single-mode right-hand side, converged in one iteration, reaches that state
+// at once).  So, as in the FP32 solve, r is projected onto zero mean at every
+// direction update (its sum comes with the r.r reduction; |r - m|^2 = r.r - N m^2).
 __global__ void __launch_bounds__(PF) k_plain_cg_init(FieldBufsF64 f, LapD L)
 {
-    double rr = 0.0, bb = 0.0;
+    double rr = 0.0, bb = 0.0, rs = 0.0;
     for (int64_t id = (int64_t)blockIdx.x * PF + threadIdx.x; id < f.cells;
          id += (int64_t)gridDim.x * PF) {
         int j[3];
         pcoords(id, f, j);
         const double ri = f.b[id] - pneg_lap(f.phi, id, j, f, L.idx2);
         f.r[id] = ri;
-        f.p[id] = ri * L.inv_diag;
         rr += ri * ri;
+        rs += ri;
         bb += f.b[id] * f.b[id];
     }
     rr = pblock_sum(rr);
+    rs = pblock_sum(rs);
     bb = pblock_sum(bb);
     if (threadIdx.x == 0) {
         f.part[0][blockIdx.x] = rr;
+        f.part[1][blockIdx.x] = rs;
         f.part[2][blockIdx.x] = bb;
+    }
+}
+
+// r -= mean(r);  p = M^-1 r (after the initial residual's sums are reduced).
+__global__ void __launch_bounds__(PF) k_plain_cg_init_dir(FieldBufsF64 f, LapD L)
+{
+    const double m = preduce(f.part[1], f.nblocks) / (double)f.cells;
+    for (int64_t id = (int64_t)blockIdx.x * PF + threadIdx.x; id < f.cells;
+         id += (int64_t)gridDim.x * PF) {
+        const double ri = f.r[id] - m;
+        f.r[id] = ri;
+        f.p[id] = ri * L.inv_diag;
     }
 }
 
 __global__ void __launch_bounds__(PF) k_plain_cg_init_fin(FieldBufsF64 f, LapD L, double rtol)
 {
-    const double rr = preduce(f.part[0], f.nblocks);
+    const double rr0 = preduce(f.part[0], f.nblocks);
+    const double rs = preduce(f.part[1], f.nblocks);
     const double bb = preduce(f.part[2], f.nblocks);
+    const double m = rs / (double)f.cells;
+    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
     if (threadIdx.x == 0) {
         const double bn = sqrt(bb);
         f.scal[PS_BNORM] = bn;
@@ -425,23 +448,30 @@ __global__ void __launch_bounds__(PF) k_plain_cg_update(FieldBufsF64 f, int it)
         if (blockIdx.x == 0 && threadIdx.x == 0) *f.done = 1;
         return;
     }
-    double rr = 0.0;
+    double rr = 0.0, rs = 0.0;
     for (int64_t id = (int64_t)blockIdx.x * PF + threadIdx.x; id < f.cells;
          id += (int64_t)gridDim.x * PF) {
         f.phi[id] += alpha * f.p[id];
         const double ri = f.r[id] - alpha * f.q[id];
         f.r[id] = ri;
         rr += ri * ri;
+        rs += ri;
     }
     rr = pblock_sum(rr);
-    if (threadIdx.x == 0) f.part[1][blockIdx.x] = rr;
+    rs = pblock_sum(rs);
+    if (threadIdx.x == 0) {
+        f.part[1][blockIdx.x] = rr;
+        f.part[2][blockIdx.x] = rs;
+    }
 }
 
 __global__ void __launch_bounds__(PF)
     k_plain_cg_dir(FieldBufsF64 f, LapD L, int it, int maxit, double rtol)
 {
     if (*f.done) return;
-    const double rr = preduce(f.part[1], f.nblocks);
+    const double rr0 = preduce(f.part[1], f.nblocks);
+    const double m = preduce(f.part[2], f.nblocks) / (double)f.cells;
+    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
     const double rz_new = rr * L.inv_diag;
     const double rz = f.scal[PS_RZ0 + (it & 1)];
     const double rel = sqrt(rr) / f.scal[PS_BNORM];
@@ -455,8 +485,11 @@ __global__ void __launch_bounds__(PF)
     if (stop) return;
     const double beta = rz_new / rz;
     for (int64_t id = (int64_t)blockIdx.x * PF + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * PF)
-        f.p[id] = f.r[id] * L.inv_diag + beta * f.p[id];
+         id += (int64_t)gridDim.x * PF) {
+        const double ri = f.r[id] - m;
+        f.r[id] = ri;
+        f.p[id] = ri * L.inv_diag + beta * f.p[id];
+    }
 }
 
 __global__ void k_plain_cg_finish(FieldBufsF64 f, double rtol, int *err)
@@ -468,6 +501,8 @@ cudaError_t launch_plain_cg_init(FieldBufsF64 &f, double rtol, cudaStream_t st)
 {
     const LapD L = make_lapd(f);
     k_plain_cg_init<<<f.nblocks, PF, 0, st>>>(f, L);
+    note_launch();
+    k_plain_cg_init_dir<<<f.nblocks, PF, 0, st>>>(f, L);
     note_launch();
     k_plain_cg_init_fin<<<1, PF, 0, st>>>(f, L, rtol);
     note_launch();

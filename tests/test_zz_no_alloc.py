@@ -61,6 +61,45 @@ def test_noalloc_sort_matches_allocating_sort(env):
         g.close()
 
 
+def _noalloc_vs_sort(pk, torch, w, brick_arg, stream_ptr, steps=3):
+    g = pk.from_workload(w, sort_every=0).load(w.x, w.v)
+    g.step(steps)
+    cell, _, _, _ = g.get_particles(positions=False)
+    g.sort()
+    want = g.get_perm()
+    g.close()
+    d_cell = torch.from_numpy(cell).to("cuda")
+    d_perm = torch.full((w.np_,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    st = _call(pk, w.ndim, w.n, brick_arg, w.np_, d_cell.data_ptr(), d_perm.data_ptr(),
+               stream_ptr)
+    assert st == pk.AP_PIC_OK, st
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d_perm.cpu().numpy().astype(np.int64), want)
+
+
+@pytest.mark.parametrize("case", ["1d_default_brick", "2d_default_brick_stream0",
+                                  "2d_capacity_10bit_digits"])
+def test_noalloc_defaults_capacity_and_default_stream(env, case):
+    """brick (0, 0, 0) takes the library default (ap_pic_sort's, on a handle created
+    with its default brick); a 1D grid; a call on the legacy default stream (NULL);
+    and exactly AP_PIC_NOALLOC_MAX_NP particles on a 1024 x 1024 grid, whose 20-bit
+    keys sort in two 10-bit digit passes, so the per-tile histograms fill the fixed
+    array to its end."""
+    pk, torch = env
+    stream = torch.cuda.current_stream().cuda_stream
+    if case == "1d_default_brick":
+        w = plasma.maxwellian_box(1, (1000,), ppc=40, nv=1, seed=53)
+        _noalloc_vs_sort(pk, torch, w, (0, 0, 0), stream)
+    elif case == "2d_default_brick_stream0":
+        w = plasma.maxwellian_box(2, (70, 50), ppc=12, nv=2, seed=54)
+        _noalloc_vs_sort(pk, torch, w, (0, 0, 0), 0)
+    else:
+        w = plasma.maxwellian_box(2, (1024, 1024), ppc=1, nv=2, seed=55)
+        assert w.np_ == pk.AP_PIC_NOALLOC_MAX_NP
+        _noalloc_vs_sort(pk, torch, w, (0, 0, 0), stream, steps=2)
+
+
 def test_noalloc_rejects_more_than_its_capacity(env):
     pk, torch = env
     st = _call(pk, 2, (8, 8), (0, 0), pk.AP_PIC_NOALLOC_MAX_NP + 1, 0, 0, 0)
