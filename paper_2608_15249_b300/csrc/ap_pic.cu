@@ -111,6 +111,7 @@ struct ap_pic {
     bool use_fft = false;
     FftPlan fft{};
     bool relres_on_device = false;  // last_cg_relres is in f.scal[SCAL_TRUE_REL]
+    bool cg_on_device = false;      // last CG iterations / residual are in f.iters, f.scal
 
     int last_cg_iters = 0;
     double last_cg_relres = 0.0;
@@ -595,6 +596,7 @@ static ap_pic_status create_grid(ap_pic *h)
     TRY(alloc_n(h, &f.phi, c));
     TRY(alloc_n(h, &f.r, c));
     TRY(alloc_n(h, &f.p, c));
+    TRY(alloc_n(h, &f.p2, c));
     TRY(alloc_n(h, &f.q, c));
     TRY(alloc_n(h, &f.x, c));
     TRY(alloc_n(h, &f.E, c * f.Estride));
@@ -603,7 +605,9 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(f.ticket, 0, 4, h->stream));
     TRY(alloc_n(h, &f.scal, 8));
     TRY(alloc_n(h, &f.done, 1));
-    TRY(alloc_n(h, &f.iters, 1));
+    TRY(alloc_n(h, &f.iters, 2));
+    TRY(alloc_n(h, &f.gbar, 2));
+    CU(h, cudaMemsetAsync(f.gbar, 0, 8, h->stream));
     TRY(alloc_n(h, &f.isum_part, (size_t)f.nblocks));
     TRY(alloc_n(h, &f.fe_part, (size_t)f.nblocks));
     TRY(alloc_n(h, &h->d_diag, 8));
@@ -615,7 +619,7 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(f.isum_part, 0, (size_t)f.nblocks * 8, h->stream));
     CU(h, cudaMemsetAsync(f.fe_part, 0, (size_t)f.nblocks * 8, h->stream));
     CU(h, cudaMemsetAsync(f.scal, 0, 64, h->stream));
-    CU(h, cudaMemsetAsync(f.iters, 0, 4, h->stream));
+    CU(h, cudaMemsetAsync(f.iters, 0, 8, h->stream));
     CU(h, cudaMemsetAsync(f.done, 0, 4, h->stream));
     CU(h, cudaMemsetAsync(h->d_diag, 0, 64, h->stream));
     CU(h, cudaMemsetAsync(h->d_err, 0, 4, h->stream));
@@ -904,49 +908,40 @@ static ap_pic_status solve_field_fft(ap_pic *h)
     stage_end(h, mk);
     h->last_cg_iters = 0;
     h->relres_on_device = true;  // the first solve's true residual, read with the diagnostics
+    h->cg_on_device = false;
     return AP_PIC_OK;
 }
 
+// FP32 form: FP32-vector Jacobi-PCG with FP64 dots, warm-started from the previous
+// potential and stopped on its (recursive) relative residual, run as one
+// cooperative launch that tests convergence on the device; then one refinement
+// pass: the true residual rho - mean - A phi in FP64, a short FP32 correction
+// solve A x = r (its cap: what the first solve left of cg_maxit), phi += x.  No
+// host round trip: a solve that stops at its cap latches EF_CG, reported as
+// AP_PIC_ERR_NOT_CONVERGED by the next synchronising call, and the iterations and
+// residual are read with the diagnostics.
 static ap_pic_status solve_field(ap_pic *h)
 {
     if (h->plain) return solve_field_f64(h);
     if (h->use_fft) return solve_field_fft(h);
-    h->relres_on_device = false;
     constexpr double REFINE_RTOL = 1e-2;
     const double rtol = h->cfg.cg_rtol;
     const int maxit = h->cfg.cg_maxit;
     const double mean_total = h->cfg.q * h->cfg.weight * (double)h->np / h->V + bg_density(h);
     FieldBufs &f = h->f;
     const int mk = stage_begin(h, AP_PIC_STAGE_FIELD);
-    CU(h, launch_cg_init(f, rtol, h->stream));
-    TRY(cg_loop(h, f.done, maxit, [&](int it, int n) {
-        return launch_cg_iters(f, it, n, maxit, rtol, h->stream);
-    }));
-    CU(h, launch_cg_finish(f, rtol, h->d_err, h->stream));
-    int k1 = 0, k2 = 0;
-    double rel = 0.0;
-    TRY(read_iters(h, f.iters, &k1));
-    TRY(read_scalar(h, f.scal + 3, &rel));
+    CU(h, launch_cg_solve(f, f.b, f.phi, rtol, maxit, nullptr, f.iters, SCAL_CG_REL, true,
+                          h->d_err, h->stream));
     // refinement pass
-    FieldBufs inner = f;  // the correction solve A x = r: "phi" is x, "b" is r
-    inner.phi = f.x;
     CU(h, launch_residual64(f, mean_total, h->stream));
     CU(h, cudaMemsetAsync(f.x, 0, (size_t)h->cells * 4, h->stream));
-    CU(h, launch_cg_init(inner, REFINE_RTOL, h->stream));
-    const int budget = maxit > k1 ? maxit - k1 : 1;
-    TRY(cg_loop(h, f.done, budget, [&](int it, int n) {
-        return launch_cg_iters(inner, it, n, budget, REFINE_RTOL, h->stream);
-    }));
-    TRY(read_iters(h, f.iters, &k2));
+    CU(h, launch_cg_solve(f, f.b, f.x, REFINE_RTOL, maxit, f.iters, f.iters + 1, SCAL_CG_REL2,
+                          false, h->d_err, h->stream));
     CU(h, launch_add_correction(f, h->stream));
     CU(h, launch_efield(f, h->stream));
     stage_end(h, mk);
-    h->last_cg_iters = k1 + k2;
-    h->last_cg_relres = rel;
-    if (rel > rtol)
-        return fail(h, AP_PIC_ERR_NOT_CONVERGED,
-                    "field solve stopped at %d iterations, relative residual %.3e > %.3e", k1,
-                    rel, rtol);
+    h->relres_on_device = false;
+    h->cg_on_device = true;
     return AP_PIC_OK;
 }
 
@@ -1215,11 +1210,12 @@ extern "C" ap_pic_status ap_pic_collide(ap_pic *h)
 }
 
 // A step can replay a graph when it holds no host decision and no per-step value:
-// the FP32 form with the spectral solve, no collisions (their draws take the step
-// number), not the electromagnetic step, stage timing off.
+// the FP32 form (either solver: the CG tests convergence on the device), no
+// collisions (their draws take the step number), not the electromagnetic step,
+// stage timing off.
 static bool step_graphable(const ap_pic *h)
 {
-    return !h->plain && h->use_fft && !h->mcc_on && !h->em && !h->timing;
+    return !h->plain && !h->mcc_on && !h->em && !h->timing;
 }
 
 // One step through its captured graph (captured on first use of its variant).
@@ -1522,8 +1518,18 @@ extern "C" ap_pic_status ap_pic_get_diag(ap_pic *h, ap_pic_diag *out)
     if (h->relres_on_device)
         CU(h, cudaMemcpyAsync(h->h_diag + 7, h->f.scal + SCAL_TRUE_REL, sizeof(double),
                               cudaMemcpyDeviceToHost, h->stream));
+    if (h->cg_on_device) {
+        CU(h, cudaMemcpyAsync(h->h_diag + 7, h->f.scal + SCAL_CG_REL, sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+        CU(h, cudaMemcpyAsync(h->h_iters, h->f.iters, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
     CU(h, cudaStreamSynchronize(h->stream));
     if (h->relres_on_device) h->last_cg_relres = h->h_diag[7];
+    if (h->cg_on_device) {
+        h->last_cg_relres = h->h_diag[7];
+        h->last_cg_iters = h->h_iters[0] + h->h_iters[1];
+    }
     const double mw = h->cfg.m * h->cfg.weight;
     out->step = h->step;
     out->t = (double)h->step * h->cfg.dt;

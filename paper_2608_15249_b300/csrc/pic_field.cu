@@ -176,163 +176,278 @@ static Lap make_lap(const FieldBufs &f)
 // r.r reduction; |r - m|^2 = r.r - N m^2), and a non-positive or non-finite
 // p.Ap stops the iteration instead of dividing by it.
 
-// r = b - A phi;  p = M^-1 r;  partials of r.r, b.b and sum(r).
-__global__ void __launch_bounds__(FT) k_cg_init(FieldBufs f, Lap L)
+// ---- the whole CG solve in one cooperative launch ----------------------------------------------
+//
+// A CG loop of separate launches (direction, matvec, update: three per
+// iteration) needs the host to read a done flag between blocks of launches.
+// k_cg_coop runs Jacobi-PCG (FP32 vectors, FP64 dots, zero-mean projection of r,
+// breakdown guard) as one cooperative launch of one block per SM: blocks meet at a grid barrier, every
+// block re-reduces the block partials in the same fixed order (so all see
+// bit-identical scalars and take the same decisions), and the convergence test
+// never leaves the device.  The direction update is fused into the matvec: each
+// node recomputes p = (r - mean r) / diag + beta p_old at itself and its
+// neighbours from r and the previous direction (p ping-pongs between two
+// buffers), so an iteration takes two grid barriers.
+constexpr int CG_T = 512;                 // threads per block of the cooperative solve
+constexpr int GRID_WAIT_LIMIT = 1 << 22;  // polls of a grid barrier before giving up
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
-    double rr = 0.0, bb = 0.0, rs = 0.0;
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        int j[3];
-        node_coords(id, f, j);
-        const float bi = f.b[id];
-        const float ri = bi - neg_lap(f.phi, id, j, f, L.idx2);
-        f.r[id] = ri;
-        f.p[id] = ri * L.inv_diag;
-        rr += (double)ri * ri;
-        bb += (double)bi * bi;
-        rs += ri;
-    }
-    rr = block_sum(rr);
-    bb = block_sum(bb);
-    rs = block_sum(rs);
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier across the blocks of a cooperative launch (all co-resident).  *count
+// (zero before the launch) only grows: barrier number g is passed once it reaches
+// g * gridDim.x.  Each block's thread 0 arrives with a release add (its block's
+// writes, ordered by the __syncthreads before it, are released) and polls
+// with acquire loads, with a bound.  Returns false in every thread of the block if
+// the bound ran out.
+__device__ bool grid_barrier(unsigned *count, unsigned &gen)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    ++gen;
     if (threadIdx.x == 0) {
-        f.part[0][blockIdx.x] = rr;
-        f.part[1][blockIdx.x] = rs;
-        f.part[2][blockIdx.x] = bb;
+        int ok = 1;
+        const unsigned target = gen * gridDim.x;
+        red_add_release(count, 1u);
+        int spins = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (++spins > GRID_WAIT_LIMIT) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
     }
+    __syncthreads();
+    return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(FT) k_cg_init_fin(FieldBufs f, Lap L, double rtol)
+// Fixed-order block sums of K values for CG_T threads (one pair of barriers for
+// all K); the totals replace v[] in every thread.  Two calls with the same K must
+// have a block barrier between them (in k_cg_coop, a grid barrier always does).
+template <int K>
+__device__ void cg_block_sums(double (&v)[K])
 {
-    const double rs = reduce_partials(f.part[1], f.nblocks);
-    const double rr0 = reduce_partials(f.part[0], f.nblocks);
-    const double bb = reduce_partials(f.part[2], f.nblocks);
-    const double m = rs / (double)f.cells;
-    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
-    if (threadIdx.x == 0) {
-        const double bn = sqrt(bb);
-        f.scal[SC_BNORM] = bn;
-        f.scal[SC_RZ0] = rr * (double)L.inv_diag;
-        const double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
-        f.scal[SC_RELRES] = rel;
-        *f.iters = 0;
-        *f.done = (bn == 0.0 || rel <= rtol) ? 1 : 0;
+    __shared__ double red[K][CG_T / 32];
+    __shared__ double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double x = warp_sum(v[k]);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
     }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int j = 0; j < CG_T / 32; ++j) t += red[threadIdx.x][j];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = tot[k];
 }
 
-// q = A p;  partial p.q -> part[0].
-__global__ void __launch_bounds__(FT) k_cg_matvec(FieldBufs f, Lap L)
+// Totals of K arrays of per-block partials (L2 loads: written by other blocks of
+// this launch), the same fixed order in every block.
+template <int K>
+__device__ void cg_reduce(double *const (&part)[K], double (&out)[K])
 {
-    if (*f.done) return;
-    double pq = 0.0;
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        int j[3];
-        node_coords(id, f, j);
-        const float qi = neg_lap(f.p, id, j, f, L.idx2);
-        f.q[id] = qi;
-        pq += (double)f.p[id] * qi;
-    }
-    pq = block_sum(pq);
-    if (threadIdx.x == 0) f.part[0][blockIdx.x] = pq;
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = 0.0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += CG_T)
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] += __ldcg(part[k] + j);
+    cg_block_sums<K>(out);
 }
 
-// alpha = rz / p.q;  phi += alpha p;  r -= alpha q;  partials r.r -> part[1],
-// sum(r) -> part[2].
-__global__ void __launch_bounds__(FT) k_cg_update(FieldBufs f, int it)
-{
-    if (*f.done) return;
-    const double pq = reduce_partials(f.part[0], f.nblocks);
-    const double rz = f.scal[SC_RZ0 + (it & 1)];
-    const double a64 = rz / pq;
-    if (!(pq > 0.0) || !isfinite(a64)) {  // breakdown: keep phi as it is and stop
-        if (blockIdx.x == 0 && threadIdx.x == 0) *f.done = 1;
-        return;
-    }
-    const float alpha = (float)a64;
-    double rr = 0.0, rs = 0.0;
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        f.phi[id] += alpha * f.p[id];
-        const float ri = f.r[id] - alpha * f.q[id];
-        f.r[id] = ri;
-        rr += (double)ri * ri;
-        rs += ri;
-    }
-    rr = block_sum(rr);
-    rs = block_sum(rs);
-    if (threadIdx.x == 0) {
-        f.part[1][blockIdx.x] = rr;
-        f.part[2][blockIdx.x] = rs;
-    }
-}
+struct CgCoop {
+    const float *b;      // right-hand side
+    float *x;            // solution, warm start on entry
+    float *pp[2];        // the direction's two buffers
+    int maxit;           // iteration cap
+    const int *it_used;  // iterations already spent (budget = maxit - *it_used), or null
+    int *iters;          // iterations taken (out)
+    int relres_slot;     // scal slot of the final relative residual
+    int latch;           // latch EF_CG when the residual stays above rtol
+};
 
-// beta = rz_new / rz;  p = M^-1 r + beta p;  convergence test.
-__global__ void __launch_bounds__(FT) k_cg_dir(FieldBufs f, Lap L, int it, int maxit, double rtol)
+__global__ void __launch_bounds__(CG_T)
+    k_cg_coop(FieldBufs f, Lap L, CgCoop c, double rtol, unsigned *bar, int *err)
 {
-    if (*f.done) return;
-    const double rs = reduce_partials(f.part[2], f.nblocks);
-    const double rr0 = reduce_partials(f.part[1], f.nblocks);
-    const double m = rs / (double)f.cells;
-    const double rr = fmax(rr0 - (double)f.cells * m * m, 0.0);
-    const float mf = (float)m;
-    const double rz_new = rr * (double)L.inv_diag;
-    const double rz = f.scal[SC_RZ0 + (it & 1)];
-    const double rel = sqrt(rr) / f.scal[SC_BNORM];
-    const bool stop = rel <= rtol || it + 1 >= maxit;
+    unsigned gen = 0u;
+    const int64_t stride = (int64_t)gridDim.x * CG_T;
+    const int64_t first = (int64_t)blockIdx.x * CG_T + threadIdx.x;
+    const double N = (double)f.cells;
+    auto bail = [&]() {
+        if (threadIdx.x == 0) atomicOr(err, EF_TIMEOUT);
+    };
+    // r = b - A x and its sums
+    {
+        double v[3] = {0.0, 0.0, 0.0};  // r.r, sum r, b.b
+        for (int64_t id = first; id < f.cells; id += stride) {
+            int j[3];
+            node_coords(id, f, j);
+            const float bi = c.b[id];
+            const float ri = bi - neg_lap(c.x, id, j, f, L.idx2);
+            f.r[id] = ri;
+            v[0] += (double)ri * ri;
+            v[1] += ri;
+            v[2] += (double)bi * bi;
+        }
+        cg_block_sums<3>(v);
+        if (threadIdx.x == 0) {
+            f.part[0][blockIdx.x] = v[0];
+            f.part[1][blockIdx.x] = v[1];
+            f.part[2][blockIdx.x] = v[2];
+        }
+    }
+    if (!grid_barrier(bar, gen)) return bail();
+    double m, rr, bn;
+    {
+        double *const parts[3] = {f.part[0], f.part[1], f.part[2]};
+        double t[3];
+        cg_reduce<3>(parts, t);
+        m = t[1] / N;
+        rr = fmax(t[0] - N * m * m, 0.0);
+        bn = sqrt(t[2]);
+    }
+    double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+    double rz = rr * (double)L.inv_diag;
+    const int maxit = c.it_used ? max(c.maxit - *c.it_used, 1) : c.maxit;
+    bool done = bn == 0.0 || rel <= rtol || maxit <= 0;
+    double beta = 0.0;
+    int it = 0;
+    while (!done) {
+        const float *po = c.pp[(it + 1) & 1];
+        float *pn = c.pp[it & 1];
+        const float mf = (float)m, bf = (float)beta;
+        // p = (r - m) / diag + beta p_old at each node and its neighbours; q = A p
+        auto dir = [&](int64_t k) {
+            float v = (f.r[k] - mf) * L.inv_diag;
+            if (it > 0) v += bf * po[k];
+            return v;
+        };
+        double pq[1] = {0.0};
+        for (int64_t id = first; id < f.cells; id += stride) {
+            int j[3];
+            node_coords(id, f, j);
+            const float pc = dir(id);
+            float acc = 0.0f;
+            int64_t st = 1;
+            for (int a = 0; a < f.ndim; ++a) {
+                const int na = f.n[a];
+                const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * st : id + st;
+                const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * st : id - st;
+                acc += (2.0f * pc - dir(up) - dir(dn)) * L.idx2[a];
+                st *= na;
+            }
+            pn[id] = pc;
+            f.q[id] = acc;
+            pq[0] += (double)pc * acc;
+        }
+        cg_block_sums<1>(pq);
+        if (threadIdx.x == 0) f.part[0][blockIdx.x] = pq[0];
+        if (!grid_barrier(bar, gen)) return bail();
+        double pqs[1];
+        {
+            double *const parts[1] = {f.part[0]};
+            cg_reduce<1>(parts, pqs);
+        }
+        const double a64 = rz / pqs[0];
+        if (!(pqs[0] > 0.0) || !isfinite(a64)) break;  // breakdown: keep x as it is
+        const float alpha = (float)a64;
+        double v[2] = {0.0, 0.0};  // r.r, sum r
+        for (int64_t id = first; id < f.cells; id += stride) {
+            c.x[id] += alpha * pn[id];
+            const float ri = (f.r[id] - mf) - alpha * f.q[id];
+            f.r[id] = ri;
+            v[0] += (double)ri * ri;
+            v[1] += ri;
+        }
+        cg_block_sums<2>(v);
+        if (threadIdx.x == 0) {
+            f.part[1][blockIdx.x] = v[0];
+            f.part[2][blockIdx.x] = v[1];
+        }
+        if (!grid_barrier(bar, gen)) return bail();
+        {
+            double *const parts[2] = {f.part[1], f.part[2]};
+            double t[2];
+            cg_reduce<2>(parts, t);
+            m = t[1] / N;
+            rr = fmax(t[0] - N * m * m, 0.0);
+        }
+        rel = sqrt(rr) / bn;
+        ++it;
+        const double rz_new = rr * (double)L.inv_diag;
+        beta = rz_new / rz;
+        rz = rz_new;
+        done = rel <= rtol || it >= maxit;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        f.scal[SC_RZ0 + ((it + 1) & 1)] = rz_new;
-        f.scal[SC_RELRES] = rel;
-        *f.iters = it + 1;
-        if (stop) *f.done = 1;
-    }
-    if (stop) return;
-    const float beta = (float)(rz_new / rz);
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        const float ri = f.r[id] - mf;
-        f.r[id] = ri;
-        f.p[id] = ri * L.inv_diag + beta * f.p[id];
+        f.scal[c.relres_slot] = rel;
+        *c.iters = it;
+        if (c.latch && rel > rtol) atomicOr(err, EF_CG);
     }
 }
 
-__global__ void k_cg_finish(FieldBufs f, double rtol, int *err)
+int cg_coop_blocks(int64_t cells)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (f.scal[SC_RELRES] > rtol) atomicOr(err, EF_CG);
+    static std::atomic<int> per_sm{0};
+    int c = per_sm.load(std::memory_order_relaxed);
+    if (!c) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cg_coop, CG_T, 0) != cudaSuccess ||
+            c < 1) {
+            cudaGetLastError();
+            c = 1;
+        }
+        per_sm.store(c, std::memory_order_relaxed);
     }
+    // one block per SM (the barrier's cost grows with the blocks; two per SM measured
+    // slower), never more than the co-resident capacity, the reduction partials
+    // (field_blocks) or the work
+    const int64_t need = (cells + CG_T - 1) / CG_T;
+    int64_t b = (int64_t)sm_count();
+    const int64_t cap = (int64_t)sm_count() * c;
+    const int64_t parts = field_blocks(cells);
+    b = b < cap ? b : cap;
+    b = b < parts ? b : parts;
+    b = b < need ? b : need;
+    return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_cg_init(FieldBufs &f, double rtol, cudaStream_t st)
+cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol, int maxit,
+                            const int *it_used, int *iters, int relres_slot, bool latch,
+                            int *err, cudaStream_t st)
 {
-    const Lap L = make_lap(f);
-    k_cg_init<<<f.nblocks, FT, 0, st>>>(f, L);
+    cudaError_t e = cudaMemsetAsync(f.gbar, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    Lap L = make_lap(f);
+    CgCoop c;
+    c.b = b;
+    c.x = x;
+    c.pp[0] = f.p;
+    c.pp[1] = f.p2;
+    c.maxit = maxit;
+    c.it_used = it_used;
+    c.iters = iters;
+    c.relres_slot = relres_slot;
+    c.latch = latch ? 1 : 0;
+    unsigned *bar = f.gbar;
+    void *args[] = {&f, &L, &c, &rtol, &bar, &err};
+    const int nb = cg_coop_blocks(f.cells);
+    e = cudaLaunchCooperativeKernel((const void *)k_cg_coop, dim3(nb), dim3(CG_T), args, 0, st);
     note_launch();
-    k_cg_init_fin<<<1, FT, 0, st>>>(f, L, rtol);
-    note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cg_iters(FieldBufs &f, int first, int count, int maxit, double rtol,
-                            cudaStream_t st)
-{
-    const Lap L = make_lap(f);
-    for (int it = first; it < first + count && it < maxit; ++it) {
-        k_cg_matvec<<<f.nblocks, FT, 0, st>>>(f, L);
-        note_launch();
-        k_cg_update<<<f.nblocks, FT, 0, st>>>(f, it);
-        note_launch();
-        k_cg_dir<<<f.nblocks, FT, 0, st>>>(f, L, it, maxit, rtol);
-        note_launch();
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err, cudaStream_t st)
-{
-    k_cg_finish<<<1, 32, 0, st>>>(f, rtol, err);
-    note_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 // ---- mixed-precision refinement -----------------------------------------------------------

@@ -235,6 +235,8 @@ struct FieldBufs {
     double *rho;               // total charge density (FP64)
     float *b;                  // rho - mean(rho), FP32
     float *phi, *r, *p, *q;    // CG vectors
+    float *p2;                 // second buffer of the direction (cooperative solve)
+    unsigned *gbar;            // grid barrier of the cooperative solve (count, generation)
     float *x;                  // correction of the refinement step
     float *E;                  // interleaved, stride Estride floats per node
     int Estride;
@@ -253,19 +255,20 @@ int field_blocks(int64_t cells);
 // rho = scale * acc + bg;  b = scale * acc - mean_e;  partial sums of acc.
 cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mean_e,
                                bool zero_acc, cudaStream_t st);
-// CG set-up from the current phi (warm start); returns nothing to the host.
-cudaError_t launch_cg_init(FieldBufs &f, double rtol, cudaStream_t st);
-// `count` CG iterations starting at iteration `first` (device early-exit once
-// converged or at maxit).
-cudaError_t launch_cg_iters(FieldBufs &f, int first, int count, int maxit, double rtol,
-                            cudaStream_t st);
-cudaError_t launch_cg_finish(FieldBufs &f, double rtol, int *err_flags, cudaStream_t st);
+// The whole Jacobi-PCG solve of A x = b (warm start x) as one cooperative launch,
+// convergence tested on the device: iterations to *iters, final relative residual
+// to scal[relres_slot]; the cap is maxit - *it_used when it_used is given; latch:
+// EF_CG when the residual stays above rtol.  A grid barrier that gives up latches
+// EF_TIMEOUT.
+cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol, int maxit,
+                            const int *it_used, int *iters, int relres_slot, bool latch,
+                            int *err_flags, cudaStream_t st);
 // Refinement: b = (float)(rho - mean - A phi) computed in FP64, and its relative norm
 // |rho - mean - A phi| / |rho - mean| into scal[SCAL_TRUE_REL].
 cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st);
 // phi += x
 cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
-enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5 };
+enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5, SCAL_CG_REL = 3, SCAL_CG_REL2 = 6 };
 cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
 
 // ---- electromagnetic step (pic_em.cu) -----------------------------------------------------------
