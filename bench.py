@@ -172,26 +172,58 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_oracle_sample(w, sample_np, steps, warmup):
-    """The oracle's gather + push + move + deposit on `sample_np` particles of the
-    workload (full grid), `warmup` untimed then `steps` timed steps; returns
-    (particle-steps/s, seconds)."""
-    import oracle
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # noqa: BLE001
+        return os.cpu_count() or 1
 
-    sim = oracle.Simulation(w.ndim, w.n, w.dx, w.dt, q=w.q, m=w.m, weight=w.weight, B0=w.B0,
-                            E0=w.E0, rtol=1e-8)
-    sim.load(w.x[:sample_np], w.v[:sample_np])
-    for _ in range(warmup):
-        sim.push()
-        sim.move()
-        oracle.deposit(w.ndim, w.n, w.dx, sim.x, w.q * w.weight)
+
+def _oracle_particle_steps(oracle, ndim, n, dx, dt, x, v, E, q, m, weight, E0, B0, steps):
+    """`steps` of the oracle's gather + Boris push (with the kinetic-energy
+    diagnostic) + move + deposit on x, v in place, in the field E (the timing does
+    not depend on its values); returns the seconds."""
     t0 = time.perf_counter()
     for _ in range(steps):
-        sim.push()
-        sim.move()
-        oracle.deposit(w.ndim, w.n, w.dx, sim.x, w.q * w.weight)
-    dt = time.perf_counter() - t0
+        Ep = oracle.gather(ndim, n, dx, x, E)
+        oracle.boris(ndim, v, Ep, E0, B0, q / m, dt)
+        oracle.kinetic(v, m * weight)
+        oracle.move(ndim, n, dx, x, v, dt)
+        oracle.deposit(ndim, n, dx, x, q * weight)
+    return time.perf_counter() - t0
+
+
+def run_oracle_sample(w, sample_np, steps, warmup, threads=1):
+    """The oracle's gather + push + move + deposit on `sample_np` particles of the
+    workload (full grid, zero field: the field solve is not part of the metric),
+    `warmup` untimed then `steps` timed steps, its particle loops on `threads`
+    threads; returns (particle-steps/s, seconds)."""
+    import oracle
+
+    oracle.set_threads(threads)
+    x = np.ascontiguousarray(w.x[:sample_np], dtype=np.float64)
+    v = np.ascontiguousarray(w.v[:sample_np], dtype=np.float64)
+    E = np.zeros(w.ndim * w.cells)
+    args = (oracle, w.ndim, w.n, w.dx, w.dt, x, v, E, w.q, w.m, w.weight, w.E0, w.B0)
+    _oracle_particle_steps(*args, warmup)
+    dt = _oracle_particle_steps(*args, steps)
+    oracle.set_threads(1)
     return sample_np * steps / dt, dt
+
+
+def cpu_baseline(w, sample_np, steps, warmup=0):
+    """The oracle on all host cores (the baseline) and on one thread, on the same
+    bounded sample of the workload."""
+    cores = host_cores()
+    v1, s1 = run_oracle_sample(w, sample_np, steps, warmup, threads=1)
+    vn, sn = (v1, s1) if cores == 1 else run_oracle_sample(w, sample_np, steps, warmup,
+                                                           threads=cores)
+    what = f"{sample_np} of {w.np_} particles on the full grid, {steps} steps of " \
+           "gather+push+move+deposit"
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what} ({sn:.1f} s on {cores} threads)",
+            "single_thread": {"value": v1, "cores": 1, "seconds": s1}}
 
 
 def bench_reference(args):
@@ -200,16 +232,18 @@ def bench_reference(args):
         return
     w = _workload(args)
     sample = min(w.np_, args.ref_sample)
-    val, secs = run_oracle_sample(w, sample, args.steps, args.warmup)
+    cores = host_cores()
+    val, secs = run_oracle_sample(w, sample, args.steps, args.warmup, threads=cores)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": _config(args, w),
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} of {w.np_} particles on the full grid, "
-                                   f"{args.steps} steps of gather+push+move+deposit"},
+                                   f"{args.steps} steps of gather+push+move+deposit "
+                                   f"on {cores} threads"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -336,11 +370,14 @@ def bench_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = min(w.np_, args.cpu_sample)
-        val, secs = run_oracle_sample(w, sample, args.cpu_steps, 0)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample} of {w.np_} particles on the full grid, {args.cpu_steps} "
-                         f"steps of gather+push+move+deposit ({secs:.1f} s)"}
+        cpu = cpu_baseline(w, min(w.np_, args.cpu_sample), args.cpu_steps)
+
+    # the other single-GPU configurations of the metric: the 3D magnetised plasma and
+    # the batch of uneven instances (with its per-instance FP64 plain comparison)
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs and w.name == "two_stream_2d":
+        configs = {"magnetized_3d": run_config_3d(args, pk, torch, stream),
+                   "batch": run_batch(args, pk, torch, stream, embedded=True)}
 
     if rank == 0:
         line = {
@@ -367,10 +404,65 @@ def bench_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_config_3d(args, pk, torch, stream):
+    """The 3D magnetised configuration (128^3 nodes, 64 ppc, 134,217,728 electrons,
+    Maxwellian v_te = 1, B0 = 2 z, dt = 0.05, sort every 20): particle-steps/s of
+    push + deposit with the sort at its cadence (CUDA events), the pass's roofline
+    from the stage timing, clocks during the timed region, and the oracle on a bounded
+    sample of the same workload."""
+    w = workloads.magnetized_3d(n=(args.n3d,) * 3, ppc=args.ppc3d)
+    g = pk.from_workload(w, stream=stream.cuda_stream, solver=pk.AP_PIC_SOLVER_FFT)
+    t0 = time.perf_counter()
+    g.load(w.x, w.v)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t0
+
+    def hot_step(k):
+        g.push_deposit()
+        if k % w.sort_every == 0:
+            g.sort()
+
+    warm, steps = args.warmup, max(args.steps, w.sort_every)
+    for k in range(1, warm + 1):
+        hot_step(k)
+    torch.cuda.synchronize()
+    g.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pk.kernel_launches()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ev0.record(stream)
+        for k in range(warm + 1, warm + steps + 1):
+            hot_step(k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = pk.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    st = g.get_timing()
+    g.set_timing(False)
+    g.close()
+    peak, peak_kind = _peaks()
+    pd_ms = st["push_deposit"][0] / max(st["push_deposit"][1], 1)
+    alg = w.np_ * _bytes_per_particle(3, 3) + w.cells * _grid_bytes_per_node(3)
+    out = {"metric": METRIC, "value": w.np_ * steps / (ms * 1e-3), "unit": UNIT,
+           "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
+           "config": {"workload": f"magnetized_3d {args.n3d}^3, {args.ppc3d} ppc, {w.np_} "
+                                  f"electrons, B0 = 2 z, dt = {w.dt}, sort every {w.sort_every}",
+                      "particles": w.np_, "load_seconds": load_s,
+                      "l2": "particle state larger than L2 (no flush)"},
+           "stage_ms_per_call": {k: v[0] / max(v[1], 1) for k, v in st.items() if v[1]},
+           "roofline": _roofline(alg, pd_ms, "k_particle_pass (gather+Boris+move+deposit), 3D",
+                                 peak, peak_kind),
+           "gpu_launches": int(launches), "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, min(w.np_, args.cpu_sample_3d), args.cpu_steps_3d)
+    return out
 
 
 _SOLVERS = {"cg": 0, "fft": 1}
@@ -728,6 +820,17 @@ def _per_instance_rate(pk, torch, stream, ws, steps, **over):
 
 
 def bench_batch(args):
+    """The batched serving workload on its own line (see run_batch)."""
+    import torch
+
+    import paper_2608_15249_b300 as pk
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    line = run_batch(args, pk, torch, torch.cuda.current_stream())
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, pk, torch, stream, embedded=False):
     """The batched serving workload: `--instances` independent periodic 1D/2D
     instances (n per axis log-uniform in [32, 1024], 1k-200k electrons log-uniform,
     Maxwellian with a 1 % random mode, dt = 0.1) advanced together.  The value is
@@ -735,16 +838,11 @@ def bench_batch(args):
     particle pass and the charge conversion of every instance, with the sort at the
     tuned cadence); the field solve, the full step, and the same metric run instance
     by instance (FP64 plain and FP32 forms) on an unbiased sample of the instances
-    are reported beside it."""
-    import torch
-
-    import paper_2608_15249_b300 as pk
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    are reported beside it.  Embedded in the default line, the lockstep CG
+    comparison is left out and the oracle runs on a bounded sample of instances."""
     ws = workloads.batch_instances(count=args.instances, seed=5)
     total = sum(w.np_ for w in ws)
     nodes = sum(w.cells for w in ws)
-    stream = torch.cuda.current_stream()
     bt = pk.batch_from_workloads(ws, stream=stream.cuda_stream,
                                  solver=_SOLVERS[args.batch_solver])
     t0 = time.perf_counter()
@@ -800,7 +898,7 @@ def bench_batch(args):
     full_ms = e0.elapsed_time(e1) / args.full_steps
     iters = [bt.get_diag(i)["cg_iters"] for i in range(len(ws))]
     bt.close()
-    if args.batch_solver != "cg" and args.cg_solve_reps > 0:
+    if args.batch_solver != "cg" and args.cg_solve_reps > 0 and not embedded:
         # the lockstep Jacobi-PCG of the same batch, for comparison
         bc = pk.batch_from_workloads(ws, stream=stream.cuda_stream)
         bc.load([w.x for w in ws], [w.v for w in ws])
@@ -848,7 +946,25 @@ def bench_batch(args):
             "fp64_plain": f64_rate, "fp32": f32_rate, "unit": UNIT,
             "batched_over_fp64_plain": value / f64_rate},
     }
-    print(json.dumps(line), flush=True)
+    if not args.no_cpu_baseline:
+        # the oracle on every k-th instance (the same sample), all host cores
+        import oracle
+
+        cores = host_cores()
+        oracle.set_threads(cores)
+        ps, secs = 0, 0.0
+        for w in ws[:: args.plain_stride * 4]:
+            x, v = w.x.copy(), w.v.copy()
+            secs += _oracle_particle_steps(oracle, w.ndim, w.n, w.dx, w.dt, x, v,
+                                           np.zeros(w.ndim * w.cells), w.q, w.m, w.weight,
+                                           w.E0, w.B0, 2)
+            ps += 2 * w.np_
+        oracle.set_threads(1)
+        line["cpu_baseline"] = {
+            "value": ps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {args.plain_stride * 4}th instance, 2 steps of "
+                      f"gather+push+move+deposit each ({secs:.1f} s on {cores} threads)"}
+    return line
 
 
 def main():
@@ -891,6 +1007,12 @@ def main():
     ap.add_argument("--batch-solver", choices=["cg", "fft"], default="fft",
                     help="--workload batch")
     ap.add_argument("--cg-solve-reps", type=int, default=1, help="--workload batch")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the 3D and batch configurations out of the default line")
+    ap.add_argument("--n3d", type=int, default=128, help="3D configuration: nodes per axis")
+    ap.add_argument("--ppc3d", type=int, default=64, help="3D configuration: electrons per cell")
+    ap.add_argument("--cpu-sample-3d", type=int, default=1 << 21)
+    ap.add_argument("--cpu-steps-3d", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

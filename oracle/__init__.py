@@ -43,6 +43,10 @@ _I32 = ctypes.POINTER(ctypes.c_int)
 
 def _declare(L):
     i, i64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.orc_set_threads.argtypes = [i]
+    L.orc_set_threads.restype = None
+    L.orc_get_threads.argtypes = []
+    L.orc_get_threads.restype = i
     L.orc_locate.argtypes = [i, _I32, _D, i64, _D, _I64, _D]
     L.orc_deposit.argtypes = [i, _I32, _D, i64, _D, d, _D]
     L.orc_gather.argtypes = [i, _I32, _D, i64, _D, _D, _D]
@@ -138,6 +142,17 @@ def _cells(ndim, n):
 
 
 # ---- thin functional wrappers -------------------------------------------------------------
+
+def set_threads(n):
+    """Threads of the particle loops (deposit, gather, pushers, move): each takes a
+    contiguous range of particles; the deposit sums per-thread copies of rho in
+    thread order.  1 (the default) is the sequential code."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().orc_get_threads())
+
 
 def locate(ndim, n, dx, x):
     x = np.ascontiguousarray(x, dtype=np.float64)

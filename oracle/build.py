@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
         return LIB
     # -O2 without -ffast-math: plain IEEE FP64, no reassociation of the sums.
     cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-fPIC",
-           "-shared", "-o", LIB + ".tmp", SRC, "-lm"]
+           "-shared", "-o", LIB + ".tmp", SRC, "-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

@@ -29,8 +29,15 @@
  * vector fields are stored component-major (E[a * cells + node]).
  * Particle positions x are row-major (np x ndim), velocities (np x nv).
  * Every loop is a plain sequential loop; nothing is blocked or reordered.
+ * Threading (optional, orc_set_threads): the particle loops of the deposit,
+ * gather, pushers, move and kinetic energy split [0, np) into T contiguous
+ * ranges, one per thread, each running the same sequential loop; the deposit
+ * gives each thread a private rho and sums the copies in thread order, the
+ * kinetic energy adds the per-range sums in range order, so results are
+ * deterministic for a given T (T = 1, the default, is the sequential code).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -45,6 +52,65 @@ static int64_t cells_of(int ndim, const int *n)
 static int64_t node_index(const int *n, const int *j)
 {
     return (int64_t)j[0] + (int64_t)n[0] * ((int64_t)j[1] + (int64_t)n[1] * (int64_t)j[2]);
+}
+
+/* ---- optional threading of the particle loops ----------------------------------------- */
+
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : (n > 1024 ? 1024 : n); }
+int orc_get_threads(void) { return g_threads; }
+
+typedef void (*range_fn)(void *ctx, int64_t p0, int64_t p1, int t);
+
+struct range_job {
+    range_fn fn;
+    void *ctx;
+    int64_t p0, p1;
+    int t;
+};
+
+static void *range_thread(void *arg)
+{
+    struct range_job *j = (struct range_job *)arg;
+    j->fn(j->ctx, j->p0, j->p1, j->t);
+    return NULL;
+}
+
+/* Threads used for np particles: the setting, but at least 1024 particles each. */
+static int threads_for(int64_t np)
+{
+    int64_t t = g_threads;
+    if (t > np / 1024) t = np / 1024;
+    return t < 1 ? 1 : (int)t;
+}
+
+/* fn over [0, np) in T contiguous ranges [t np / T, (t + 1) np / T), range t on
+ * thread t (range 0 on the caller).  A thread that cannot be started runs its
+ * range on the caller after the others were started. */
+static void run_ranges(int64_t np, int T, range_fn fn, void *ctx)
+{
+    if (T <= 1) {
+        fn(ctx, 0, np, 0);
+        return;
+    }
+    pthread_t th[1024];
+    int started[1024];
+    struct range_job jobs[1024];
+    for (int t = 0; t < T; ++t) {
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].p0 = np * t / T;
+        jobs[t].p1 = np * (t + 1) / T;
+        jobs[t].t = t;
+        started[t] = 0;
+    }
+    for (int t = 1; t < T; ++t) started[t] = pthread_create(&th[t], NULL, range_thread, &jobs[t]) == 0;
+    range_thread(&jobs[0]);
+    for (int t = 1; t < T; ++t)
+        if (!started[t]) range_thread(&jobs[t]);
+    for (int t = 1; t < T; ++t)
+        if (started[t]) pthread_join(th[t], NULL);
 }
 
 /* Cell and in-cell offset of one position: c = floor(x / dx), f = x / dx - c.
@@ -99,8 +165,8 @@ static int64_t corner_node(int ndim, const int *n, const int *c, int s)
 /* B_Scatter (Sec. 2.2; module B01 in Sec. 3.1): electron charge density on
  * the nodes, rho_e[j] = (q w / dV) * sum_p W_j(x_p), with W the CIC weights.
  * rho is overwritten. */
-void orc_deposit(int ndim, const int *n, const double *dx, int64_t np, const double *x,
-                 double qw, double *rho)
+static void deposit_serial(int ndim, const int *n, const double *dx, int64_t np,
+                           const double *x, double qw, double *rho)
 {
     int64_t cells = cells_of(ndim, n);
     double dV = 1.0;
@@ -118,8 +184,8 @@ void orc_deposit(int ndim, const int *n, const double *dx, int64_t np, const dou
 
 /* C_Gather (Sec. 2.2; module C01 in Sec. 3.1): field at each particle,
  * Ep[p][a] = sum_j W_j(x_p) E_a[j], with the same weights as the deposit. */
-void orc_gather(int ndim, const int *n, const double *dx, int64_t np, const double *x,
-                const double *E, double *Ep)
+static void gather_serial(int ndim, const int *n, const double *dx, int64_t np,
+                          const double *x, const double *E, double *Ep)
 {
     int64_t cells = cells_of(ndim, n);
     for (int64_t p = 0; p < np; ++p) {
@@ -253,8 +319,8 @@ void orc_efield(int ndim, const int *n, const double *dx, const double *phi, dou
  * uniform external E0; B is the uniform B0.  Velocity components beyond nv
  * enter as zero and are not stored back.  With B = 0 this is the leapfrog
  * kick v += (q/m) E h. */
-void orc_boris(int ndim, int nv, int64_t np, double *v, const double *Ep, const double *E0,
-               const double *B0, double qm, double h)
+static void boris_serial(int ndim, int nv, int64_t np, double *v, const double *Ep,
+                         const double *E0, const double *B0, double qm, double h)
 {
     double t[3], tt = 0.0;
     for (int a = 0; a < 3; ++a) { t[a] = qm * B0[a] * 0.5 * h; tt += t[a] * t[a]; }
@@ -289,8 +355,8 @@ void orc_boris(int ndim, int nv, int64_t np, double *v, const double *Ep, const 
  *   u = u+ + eps E + u+ x t
  * gamma_bar is the Lorentz factor of the mean momentum (u- + u+) / 2, so the
  * rotation is the implicit midpoint one, u+ - u- = (u- + u+) x tau / gamma_bar. */
-void orc_hc(int ndim, int nv, int64_t np, double *u, const double *Ep, const double *E0,
-            const double *B0, double qm, double h, double inv_c2)
+static void hc_serial(int ndim, int nv, int64_t np, double *u, const double *Ep,
+                      const double *E0, const double *B0, double qm, double h, double inv_c2)
 {
     const double eps = 0.5 * qm * h;
     double tau[3], tau2 = 0.0;
@@ -336,8 +402,8 @@ double orc_kinetic_rel(int nv, int64_t np, const double *u, double mw, double in
 /* Position update with periodic boundaries (application code in Sec. 3.1):
  * x_a += v_a dt on the ndim spatial axes, then x_a -= L_a floor(x_a / L_a);
  * a result that rounds to L_a is set to 0. */
-void orc_move(int ndim, const int *n, const double *dx, int nv, int64_t np, double *x,
-              const double *v, double dt)
+static void move_serial(int ndim, const int *n, const double *dx, int nv, int64_t np,
+                        double *x, const double *v, double dt)
 {
     for (int64_t p = 0; p < np; ++p)
         for (int a = 0; a < ndim; ++a) {
@@ -347,6 +413,139 @@ void orc_move(int ndim, const int *n, const double *dx, int nv, int64_t np, doub
             if (xa >= L || xa < 0.0) xa = 0.0;
             x[p * ndim + a] = xa;
         }
+}
+
+/* ---- public particle loops (sequential, or threaded over particle ranges) -------------- */
+
+struct deposit_ctx {
+    int ndim;
+    const int *n;
+    const double *dx, *x;
+    double qw;
+    double **buf;
+};
+
+static void deposit_range(void *c, int64_t p0, int64_t p1, int t)
+{
+    struct deposit_ctx *d = (struct deposit_ctx *)c;
+    deposit_serial(d->ndim, d->n, d->dx, p1 - p0, d->x + p0 * d->ndim, d->qw, d->buf[t]);
+}
+
+/* B_Scatter (Sec. 2.2; module B01 in Sec. 3.1), see deposit_serial.  With T > 1
+ * threads each range deposits into its own copy of rho (at most about 1 GB of
+ * copies: fewer threads on large grids), summed into rho in thread order. */
+void orc_deposit(int ndim, const int *n, const double *dx, int64_t np, const double *x,
+                 double qw, double *rho)
+{
+    int64_t cells = cells_of(ndim, n);
+    int T = threads_for(np);
+    int64_t cap = ((int64_t)1 << 27) / (cells > 0 ? cells : 1);
+    if (T > cap) T = cap < 1 ? 1 : (int)cap;
+    if (T <= 1) {
+        deposit_serial(ndim, n, dx, np, x, qw, rho);
+        return;
+    }
+    double *bufs[1024];
+    bufs[0] = rho;
+    for (int t = 1; t < T; ++t) {
+        bufs[t] = (double *)malloc((size_t)cells * sizeof(double));
+        if (!bufs[t]) {  /* out of memory: the sequential loop */
+            for (int k = 1; k < t; ++k) free(bufs[k]);
+            deposit_serial(ndim, n, dx, np, x, qw, rho);
+            return;
+        }
+    }
+    struct deposit_ctx d = {ndim, n, dx, x, qw, bufs};
+    run_ranges(np, T, deposit_range, &d);
+    for (int64_t j = 0; j < cells; ++j) {
+        double acc = bufs[0][j];
+        for (int t = 1; t < T; ++t) acc += bufs[t][j];
+        rho[j] = acc;
+    }
+    for (int t = 1; t < T; ++t) free(bufs[t]);
+}
+
+struct gather_ctx {
+    int ndim;
+    const int *n;
+    const double *dx, *x, *E;
+    double *Ep;
+};
+
+static void gather_range(void *c, int64_t p0, int64_t p1, int t)
+{
+    struct gather_ctx *g = (struct gather_ctx *)c;
+    (void)t;
+    gather_serial(g->ndim, g->n, g->dx, p1 - p0, g->x + p0 * g->ndim, g->E, g->Ep + p0 * g->ndim);
+}
+
+/* C_Gather (Sec. 2.2; module C01 in Sec. 3.1), see gather_serial. */
+void orc_gather(int ndim, const int *n, const double *dx, int64_t np, const double *x,
+                const double *E, double *Ep)
+{
+    struct gather_ctx g = {ndim, n, dx, x, E, Ep};
+    run_ranges(np, threads_for(np), gather_range, &g);
+}
+
+struct push_ctx {
+    int ndim, nv;
+    double *v;
+    const double *Ep, *E0, *B0;
+    double qm, h, inv_c2;
+    int hc;
+};
+
+static void push_range(void *c, int64_t p0, int64_t p1, int t)
+{
+    struct push_ctx *q = (struct push_ctx *)c;
+    (void)t;
+    const double *Ep = q->Ep ? q->Ep + p0 * q->ndim : NULL;
+    if (q->hc)
+        hc_serial(q->ndim, q->nv, p1 - p0, q->v + p0 * q->nv, Ep, q->E0, q->B0, q->qm, q->h,
+                  q->inv_c2);
+    else
+        boris_serial(q->ndim, q->nv, p1 - p0, q->v + p0 * q->nv, Ep, q->E0, q->B0, q->qm, q->h);
+}
+
+/* A_Pusher (Sec. 2.2): Boris, see boris_serial. */
+void orc_boris(int ndim, int nv, int64_t np, double *v, const double *Ep, const double *E0,
+               const double *B0, double qm, double h)
+{
+    struct push_ctx q = {ndim, nv, v, Ep, E0, B0, qm, h, 0.0, 0};
+    run_ranges(np, threads_for(np), push_range, &q);
+}
+
+/* A_Pusher (Sec. 2.2): Higuera-Cary, see hc_serial. */
+void orc_hc(int ndim, int nv, int64_t np, double *u, const double *Ep, const double *E0,
+            const double *B0, double qm, double h, double inv_c2)
+{
+    struct push_ctx q = {ndim, nv, u, Ep, E0, B0, qm, h, inv_c2, 1};
+    run_ranges(np, threads_for(np), push_range, &q);
+}
+
+struct move_ctx {
+    int ndim, nv;
+    const int *n;
+    const double *dx;
+    double *x;
+    const double *v;
+    double dt;
+};
+
+static void move_range(void *c, int64_t p0, int64_t p1, int t)
+{
+    struct move_ctx *m = (struct move_ctx *)c;
+    (void)t;
+    move_serial(m->ndim, m->n, m->dx, m->nv, p1 - p0, m->x + p0 * m->ndim, m->v + p0 * m->nv,
+                m->dt);
+}
+
+/* Position update with periodic boundaries, see move_serial. */
+void orc_move(int ndim, const int *n, const double *dx, int nv, int64_t np, double *x,
+              const double *v, double dt)
+{
+    struct move_ctx m = {ndim, nv, n, dx, x, v, dt};
+    run_ranges(np, threads_for(np), move_range, &m);
 }
 
 /* Brick-major sort key of a cell: the grid is tiled by bricks of
@@ -393,10 +592,37 @@ int orc_counting_sort(int64_t np, const int64_t *key, int64_t nkeys, int64_t *pe
 
 /* Diagnostics (Sec. 3.2, the energy balance): kinetic energy
  * (1/2) m w sum_p |v_p|^2 over nv components. */
-double orc_kinetic(int nv, int64_t np, const double *v, double mw)
+static double sum_squares(int64_t m, const double *v)
 {
     double s = 0.0;
-    for (int64_t i = 0; i < np * nv; ++i) s += v[i] * v[i];
+    for (int64_t i = 0; i < m; ++i) s += v[i] * v[i];
+    return s;
+}
+
+struct ke_ctx {
+    int nv;
+    const double *v;
+    double part[1024];
+};
+
+static void ke_range(void *c, int64_t p0, int64_t p1, int t)
+{
+    struct ke_ctx *k = (struct ke_ctx *)c;
+    k->part[t] = sum_squares((p1 - p0) * k->nv, k->v + p0 * k->nv);
+}
+
+/* Kinetic energy (1/2) m w sum_p |v_p|^2 (threaded: per-range sums added in range
+ * order). */
+double orc_kinetic(int nv, int64_t np, const double *v, double mw)
+{
+    const int T = threads_for(np);
+    if (T <= 1) return 0.5 * mw * sum_squares(np * nv, v);
+    struct ke_ctx k;
+    k.nv = nv;
+    k.v = v;
+    run_ranges(np, T, ke_range, &k);
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += k.part[t];
     return 0.5 * mw * s;
 }
 
