@@ -362,12 +362,17 @@ ap_pic_status ap_pic_collide(ap_pic *h);
 typedef struct ap_pic_batch ap_pic_batch;
 
 typedef struct {
-    int pass_ctas_per_sm;   /* CTAs per SM of the persistent particle pass (1..8)     */
+    int pass_ctas_per_sm;   /* CTAs per SM of the persistent particle pass (1..16;
+                               at most one resident wave is launched)               */
     int item_cells;         /* nodes per work item of the grid kernels (multiple of
                                256, 256..65536; set before loading)                  */
     int sort_every;         /* steps between sorts (0: never)                         */
     int cg_iters_per_graph; /* CG iterations in each replayed block (1..256)          */
     int use_graph;          /* 1: capture and replay the step front as a CUDA graph   */
+    int pass_threads;       /* threads per CTA of the particle pass: 128, 256 or 512  */
+    int pass_per_thread;    /* particles per thread of the pass (tiles of
+                               threads x per_thread particles): with 128 threads 2
+                               or 4, with 256 threads 1, 2 or 3, with 512 threads 1 */
 } ap_pic_batch_tuning;
 
 void ap_pic_batch_default_tuning(ap_pic_batch_tuning *t);
@@ -407,9 +412,10 @@ ap_pic_status ap_pic_batch_solve_field(ap_pic_batch *b);
 ap_pic_status ap_pic_batch_set_tuning(ap_pic_batch *b, const ap_pic_batch_tuning *t);
 ap_pic_status ap_pic_batch_get_tuning(const ap_pic_batch *b, ap_pic_batch_tuning *t);
 
-/* Picks pass_ctas_per_sm, cg_iters_per_graph and sort_every for this batch by
- * timing `steps_per_trial` steps of each candidate (the batch advances while it
- * is tuned).  With a non-NULL cache_path, a result stored there for the same
+/* Picks the particle pass's shape (pass_threads x pass_per_thread),
+ * pass_ctas_per_sm, cg_iters_per_graph (CG solver only) and sort_every for this
+ * batch by a coordinate search, timing `steps_per_trial` steps of each candidate
+ * (the batch advances while it is tuned).  With a non-NULL cache_path, a result stored there for the same
  * batch shape and GPU is reused, and a new one is written back. */
 ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_trial, const char *cache_path);
 

@@ -105,7 +105,8 @@ class ap_pic_mcc(ctypes.Structure):
 class ap_pic_batch_tuning(ctypes.Structure):
     _fields_ = [("pass_ctas_per_sm", ctypes.c_int), ("item_cells", ctypes.c_int),
                 ("sort_every", ctypes.c_int), ("cg_iters_per_graph", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("pass_threads", ctypes.c_int),
+                ("pass_per_thread", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -531,7 +531,8 @@ struct BatchGrid {
 
 namespace {
 
-constexpr int B_TILE = BATCH_TILE;  // particle tile (the shared pass's batch tile)
+constexpr int B_TILE = BATCH_TILE;  // key tile of the sort (all slots of an instance)
+constexpr int B_MIN_TILE = 256;     // smallest pass tile of the kernel variants
 constexpr int64_t PAD = 64;      // instance ranges in the particle arena start on multiples of 64
 
 int bitlen_u(uint64_t x)
@@ -576,6 +577,9 @@ struct ap_pic_batch {
     ParticlesF32 p{}, p_alt{};
     SortScratch sort{};
     std::vector<BatchTile> tiles1, tiles2, ktiles;  // 1D / 2D pass tiles, key tiles (all slots)
+    int variant = 0;          // pass kernel variant (tune.pass_threads, tune.pass_per_thread)
+    size_t tile_cap1 = 0, tile_cap2 = 0;  // device room for pass tiles (smallest tile size)
+    int ptile = 0;            // particles per pass tile of the current tiles (0: none yet)
     BatchTile *d_tiles1 = nullptr, *d_tiles2 = nullptr, *d_ktiles = nullptr;
     int *d_kinfo = nullptr;
     int64_t *d_pbase = nullptr;
@@ -669,6 +673,43 @@ void bfree_all(ap_pic_batch *b)
         else cudaFree(o.first);
     }
     b->owned.clear();
+}
+
+// Pass tiles of at most `tile` particles, each within one instance, per dimension
+// class; each instance's first tile and tile count go to its BInst.
+void make_pass_tiles(ap_pic_batch *b, int tile)
+{
+    b->tiles1.clear();
+    b->tiles2.clear();
+    for (int i = 0; i < b->count; ++i) {
+        std::vector<BatchTile> &tl = b->cfg[i].ndim == 1 ? b->tiles1 : b->tiles2;
+        b->binst[i].tile0 = (int)tl.size();
+        for (int64_t s = 0; s < b->np[i]; s += tile) {
+            const int cnt = (int)(b->np[i] - s < tile ? b->np[i] - s : tile);
+            tl.push_back(BatchTile{b->pbase[i] + s, cnt, i});
+        }
+        b->binst[i].ntiles = (int)tl.size() - b->binst[i].tile0;
+    }
+    b->ptile = tile;
+}
+
+// The pass tiles (and, once it exists, the device copy of the instance table) to
+// the device; waits for the copies (the host lists may change again right after).
+ap_pic_status upload_pass_tiles(ap_pic_batch *b)
+{
+    if (b->tiles1.size() > b->tile_cap1 || b->tiles2.size() > b->tile_cap2)
+        return bfail(b, AP_PIC_ERR_STATE, "pass tiles exceed their device room");
+    if (!b->tiles1.empty())
+        BCU(b, cudaMemcpyAsync(b->d_tiles1, b->tiles1.data(), b->tiles1.size() * sizeof(BatchTile),
+                               cudaMemcpyHostToDevice, b->stream));
+    if (!b->tiles2.empty())
+        BCU(b, cudaMemcpyAsync(b->d_tiles2, b->tiles2.data(), b->tiles2.size() * sizeof(BatchTile),
+                               cudaMemcpyHostToDevice, b->stream));
+    if (b->G.inst)
+        BCU(b, cudaMemcpyAsync(b->G.inst, b->binst.data(), b->binst.size() * sizeof(BInst),
+                               cudaMemcpyHostToDevice, b->stream));
+    BCU(b, cudaStreamSynchronize(b->stream));
+    return AP_PIC_OK;
 }
 
 void drop_graph(ap_pic_batch *b)
@@ -811,6 +852,8 @@ extern "C" void ap_pic_batch_default_tuning(ap_pic_batch_tuning *t)
     t->sort_every = 20;
     t->cg_iters_per_graph = 16;
     t->use_graph = 1;
+    t->pass_threads = 256;
+    t->pass_per_thread = 2;
 }
 
 extern "C" ap_pic_status ap_pic_batch_create(int count, const ap_pic_config *cfgs,
@@ -901,15 +944,25 @@ extern "C" const char *ap_pic_batch_last_error(const ap_pic_batch *b)
 extern "C" ap_pic_status ap_pic_batch_set_tuning(ap_pic_batch *b, const ap_pic_batch_tuning *t)
 {
     if (!b || !t) return AP_PIC_ERR_ARG;
-    if (t->pass_ctas_per_sm < 1 || t->pass_ctas_per_sm > 8 || t->item_cells < 256 ||
+    if (t->pass_ctas_per_sm < 1 || t->pass_ctas_per_sm > 16 || t->item_cells < 256 ||
         t->item_cells > 65536 || t->item_cells % 256 || t->sort_every < 0 ||
         t->cg_iters_per_graph < 1 || t->cg_iters_per_graph > 256)
         return bfail(b, AP_PIC_ERR_ARG, "tuning out of range");
+    const int variant = batch_variant(t->pass_threads, t->pass_per_thread);
+    if (variant < 0)
+        return bfail(b, AP_PIC_ERR_ARG,
+                     "no particle-pass variant of that (pass_threads, pass_per_thread)");
     const bool relayout = b->loaded && t->item_cells != b->tune.item_cells;
     if (relayout) return bfail(b, AP_PIC_ERR_STATE, "item_cells must be set before loading");
     b->tune = *t;
+    b->variant = variant;
     b->pass_blocks = b->sms * b->tune.pass_ctas_per_sm;
     drop_graph(b);
+    const int tile = t->pass_threads * t->pass_per_thread;
+    if (b->loaded && tile != b->ptile) {
+        make_pass_tiles(b, tile);
+        BTRY(upload_pass_tiles(b));
+    }
     return AP_PIC_OK;
 }
 
@@ -965,11 +1018,13 @@ ap_pic_status batch_sync_check(ap_pic_batch *b)
 ap_pic_status batch_pass(ap_pic_batch *b, bool push, bool mv, bool deposit, bool diag)
 {
     if (!b->tiles1.empty())
-        BCU(b, launch_batch_pass(1, b->d_tiles1, (int64_t)b->tiles1.size(), b->d_tparams, b->p,
+        BCU(b, launch_batch_pass(1, b->variant, b->d_tiles1, (int64_t)b->tiles1.size(),
+                                 b->d_tparams, b->p,
                                  push, mv, deposit, diag ? b->d_tdiag1 : nullptr, b->pass_blocks,
                                  b->d_err, b->stream));
     if (!b->tiles2.empty())
-        BCU(b, launch_batch_pass(2, b->d_tiles2, (int64_t)b->tiles2.size(), b->d_tparams, b->p,
+        BCU(b, launch_batch_pass(2, b->variant, b->d_tiles2, (int64_t)b->tiles2.size(),
+                                 b->d_tparams, b->p,
                                  push, mv, deposit, diag ? b->d_tdiag2 : nullptr, b->pass_blocks,
                                  b->d_err, b->stream));
     return AP_PIC_OK;
@@ -1226,15 +1281,12 @@ ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const 
     b->tiles2.clear();
     b->ktiles.clear();
     std::vector<int> kinfo(8 * n, 0);
+    // pass tiles: capacity for the smallest tile of any variant, then the current one
+    make_pass_tiles(b, B_MIN_TILE);
+    const size_t cap1 = b->tiles1.size(), cap2 = b->tiles2.size();
+    make_pass_tiles(b, b->tune.pass_threads * b->tune.pass_per_thread);
     for (int i = 0; i < n; ++i) {
         const ap_pic_config &c = b->cfg[i];
-        std::vector<BatchTile> &tl = c.ndim == 1 ? b->tiles1 : b->tiles2;
-        b->binst[i].tile0 = (int)tl.size();
-        for (int64_t s = 0; s < np[i]; s += B_TILE) {
-            const int cnt = (int)(np[i] - s < B_TILE ? np[i] - s : B_TILE);
-            tl.push_back(BatchTile{b->pbase[i] + s, cnt, i});
-        }
-        b->binst[i].ntiles = (int)tl.size() - b->binst[i].tile0;
         const int64_t span = (np[i] + PAD - 1) / PAD * PAD;
         for (int64_t s = 0; s < span; s += B_TILE) {
             const int cnt = (int)(span - s < B_TILE ? span - s : B_TILE);
@@ -1257,15 +1309,18 @@ ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const 
                                    cudaMemcpyHostToDevice, b->stream));
         return AP_PIC_OK;
     };
-    BTRY(upload(b->tiles1, &b->d_tiles1));
-    BTRY(upload(b->tiles2, &b->d_tiles2));
+    BTRY(balloc(b, &b->d_tiles1, cap1 > 0 ? cap1 : 1));
+    BTRY(balloc(b, &b->d_tiles2, cap2 > 0 ? cap2 : 1));
+    b->tile_cap1 = cap1;
+    b->tile_cap2 = cap2;
+    BTRY(upload_pass_tiles(b));
     BTRY(upload(b->ktiles, &b->d_ktiles));
     BTRY(upload(kinfo, &b->d_kinfo));
     BTRY(upload(b->pbase, &b->d_pbase));
-    BTRY(balloc(b, &b->d_tdiag1, b->tiles1.size() * 4 + 4));
-    BTRY(balloc(b, &b->d_tdiag2, b->tiles2.size() * 4 + 4));
-    BCU(b, cudaMemsetAsync(b->d_tdiag1, 0, (b->tiles1.size() * 4 + 4) * 8, b->stream));
-    BCU(b, cudaMemsetAsync(b->d_tdiag2, 0, (b->tiles2.size() * 4 + 4) * 8, b->stream));
+    BTRY(balloc(b, &b->d_tdiag1, cap1 * 4 + 4));
+    BTRY(balloc(b, &b->d_tdiag2, cap2 * 4 + 4));
+    BCU(b, cudaMemsetAsync(b->d_tdiag1, 0, (cap1 * 4 + 4) * 8, b->stream));
+    BCU(b, cudaMemsetAsync(b->d_tdiag2, 0, (cap2 * 4 + 4) * 8, b->stream));
     // cell items
     b->items.clear();
     const int ic = b->tune.item_cells;
@@ -1679,13 +1734,16 @@ extern "C" ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_tr
         if (f) {
             char name[256];
             unsigned long long k = 0;
-            int c1, c2, c3;
+            int c1, c2, c3, c4, c5;
             bool hit = false;
-            while (fscanf(f, "%llx %255s %d %d %d", &k, name, &c1, &c2, &c3) == 5) {
+            while (fscanf(f, "%llx %255s %d %d %d %d %d", &k, name, &c1, &c2, &c3, &c4, &c5) ==
+                   7) {
                 if (k == key && gpu == name) {
                     t.pass_ctas_per_sm = c1;
                     t.cg_iters_per_graph = c2;
                     t.sort_every = c3;
+                    t.pass_threads = c4;
+                    t.pass_per_thread = c5;
                     hit = true;
                 }
             }
@@ -1693,8 +1751,10 @@ extern "C" ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_tr
             if (hit) return ap_pic_batch_set_tuning(b, &t);
         }
     }
-    // coordinate search: pass occupancy, then CG block length, then sort cadence
-    const int ctas[] = {2, 3, 4};
+    // Coordinate search: the pass kernel's shape (threads per CTA x particles per
+    // thread), its CTAs per SM, the CG block length (CG solver only: the spectral
+    // solve has no such block), then the sort cadence.
+    const int ctas[] = {2, 3, 4, 6, 8};
     const int iters[] = {8, 16, 32};
     const int sorts[] = {10, 20, 40};
     auto trial = [&](ap_pic_batch_tuning cand, int steps, double *ms) -> ap_pic_status {
@@ -1704,6 +1764,17 @@ extern "C" ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_tr
     };
     double best = 1e300;
     ap_pic_batch_tuning best_t = t;
+    for (int v = 0; v < batch_variant_count(); ++v) {
+        ap_pic_batch_tuning cand = best_t;
+        batch_variant_shape(v, &cand.pass_threads, &cand.pass_per_thread);
+        double ms = 0.0;
+        BTRY(trial(cand, steps_per_trial, &ms));
+        if (ms < best) {
+            best = ms;
+            best_t = cand;
+        }
+    }
+    best = 1e300;
     for (int c : ctas) {
         ap_pic_batch_tuning cand = best_t;
         cand.pass_ctas_per_sm = c;
@@ -1714,15 +1785,17 @@ extern "C" ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_tr
             best_t = cand;
         }
     }
-    best = 1e300;
-    for (int it : iters) {
-        ap_pic_batch_tuning cand = best_t;
-        cand.cg_iters_per_graph = it;
-        double ms = 0.0;
-        BTRY(trial(cand, steps_per_trial, &ms));
-        if (ms < best) {
-            best = ms;
-            best_t = cand;
+    if (!b->use_fft) {
+        best = 1e300;
+        for (int it : iters) {
+            ap_pic_batch_tuning cand = best_t;
+            cand.cg_iters_per_graph = it;
+            double ms = 0.0;
+            BTRY(trial(cand, steps_per_trial, &ms));
+            if (ms < best) {
+                best = ms;
+                best_t = cand;
+            }
         }
     }
     best = 1e300;
@@ -1741,8 +1814,9 @@ extern "C" ap_pic_status ap_pic_batch_autotune(ap_pic_batch *b, int steps_per_tr
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%llx %s %d %d %d\n", (unsigned long long)key, gpu.c_str(),
-                    best_t.pass_ctas_per_sm, best_t.cg_iters_per_graph, best_t.sort_every);
+            fprintf(f, "%llx %s %d %d %d %d %d\n", (unsigned long long)key, gpu.c_str(),
+                    best_t.pass_ctas_per_sm, best_t.cg_iters_per_graph, best_t.sort_every,
+                    best_t.pass_threads, best_t.pass_per_thread);
             fclose(f);
         }
     }

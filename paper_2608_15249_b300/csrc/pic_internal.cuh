@@ -131,12 +131,18 @@ struct BatchTile {
 };
 
 // The particle pass over the tiles of many instances (one dimension class: ndim
-// 1 or 2 with nv = 2).  inst_params: device array of per-instance tile
-// parameters (make_tile_params); diag_tiles: [ntiles][4] per-tile sums or NULL.
-cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
+// 1 or 2 with nv = 2), in kernel variant `variant` (batch_variant: CTA threads and
+// particles per thread; tiles of at most threads * per_thread particles).
+// inst_params: device array of per-instance tile parameters (make_tile_params);
+// diag_tiles: [ntiles][4] per-tile sums or NULL.
+cudaError_t launch_batch_pass(int ndim, int variant, const BatchTile *tiles, int64_t ntiles,
                               const void *inst_params, ParticlesF32 p, bool push, bool mv,
                               bool deposit, double *diag_tiles, int nblocks, int *err,
                               cudaStream_t st);
+// Variant index of (threads per CTA, particles per thread), or -1 if there is none.
+int batch_variant(int threads, int per_thread);
+int batch_variant_count();
+void batch_variant_shape(int variant, int *threads, int *per_thread);
 size_t batch_tile_params_bytes();
 void make_tile_params(void *dst, const GridParams &g, const float *E, unsigned long long *acc);
 

@@ -374,6 +374,7 @@ struct TileParams {
 struct SingleSrc {
     static constexpr bool PER_TILE_DIAG = false;
     static constexpr int FIXED_TILE = 0;  // the tile size goes by the dimension
+    static constexpr int NT = PP_THREADS;  // threads per CTA
     TileParams tp;
     int64_t np;
     int tile;
@@ -385,10 +386,13 @@ struct SingleSrc {
 };
 
 // Many instances packed in one arena: tile t covers particles
-// [tiles[t].start, + tiles[t].count) of instance tiles[t].inst.
-struct BatchSrc {
+// [tiles[t].start, + tiles[t].count) of instance tiles[t].inst; tiles of up to
+// TILE_ particles, CTAs of NT_ threads (the batch's tuning picks the pair).
+template <int TILE_, int NT_>
+struct BatchSrcT {
     static constexpr bool PER_TILE_DIAG = true;
-    static constexpr int FIXED_TILE = BATCH_TILE;
+    static constexpr int FIXED_TILE = TILE_;
+    static constexpr int NT = NT_;
     const BatchTile *tiles;
     const TileParams *inst;  // per instance: parameters, field and accumulator
     int64_t nt;
@@ -411,9 +415,10 @@ struct BatchSrc {
 // cell, and 32 lanes in one or two cells would serialise on the same few window
 // words in every shared-memory atomic of the deposit.
 // MODE (PASS_* bits) is a compile-time choice so each use carries only its work.
-// Src supplies the tiles: one instance (SingleSrc) or the tiles of many
-// independent instances packed in one particle arena (BatchSrc, whose tiles each
-// carry their instance's parameters, field and charge accumulator).
+// Src supplies the tiles and the CTA size: one instance (SingleSrc, 256 threads)
+// or the tiles of many independent instances packed in one particle arena
+// (BatchSrcT, whose tiles each carry their instance's parameters, field and charge
+// accumulator, prefetched one tile ahead by one thread).
 template <int D, class Src>
 __host__ __device__ constexpr int pass_tile()
 {
@@ -421,25 +426,38 @@ __host__ __device__ constexpr int pass_tile()
 }
 
 // Particle (index within the tile) of slot r of thread `tid`, for tiles of
-// R * 256 particles seen as 8 R rows of 32: lane i of warp w takes column i of row
-// (w R + r + i) mod 8 R.  Each (w, r) visits every row once across its 32 lanes, so
-// a warp's lanes are spread over the tile, while every shared-memory access of the
-// record (one column per lane) stays free of bank conflicts.
-template <int R>
+// R * 32 NW particles (NW warps) seen as NW R rows of 32: lane i of warp w takes
+// column i of row (w R + r + i) mod NW R.  For each column the pairs (w, r) cover
+// every row once, so a warp's lanes are spread over the tile, while every
+// shared-memory access of the record (one column per lane) stays free of bank
+// conflicts.
+template <int R, int NW>
 __device__ __forceinline__ int particle_of(int r, int tid)
 {
     const int lane = tid & 31;
-    return 32 * (((tid >> 5) * R + r + lane) % (8 * R)) + lane;
+    return 32 * (((tid >> 5) * R + r + lane) % (NW * R)) + lane;
+}
+
+// Resident CTAs per SM that the launch bounds ask for: a single instance's pass
+// by its tile (3D: 3; 512-particle tiles: 5; 768: 4); a batch variant about 1,280
+// threads per SM (registers kept near 50).
+template <int D, class Src>
+__host__ __device__ constexpr int pass_min_blocks()
+{
+    return Src::PER_TILE_DIAG ? (1280 / Src::NT > 0 ? 1280 / Src::NT : 1)
+                              : (D == 3 ? 3 : (pass_tile<D, Src>() == 512 ? 5 : 4));
 }
 
 template <int D, int NV, int MODE, class Src>
-__global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() == 512 ? 5 : 4))
+__global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
     k_particle_pass(Src src, ParticlesF32 p, double *__restrict__ diag_blocks,
                     int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NT = Src::NT;
     constexpr int TILE = pass_tile<D, Src>();
-    constexpr int R = TILE / PP_THREADS;
+    constexpr int R = TILE / NT;
+    static_assert(R * NT == TILE, "a tile is R particles per thread");
     constexpr int NA_MAX = 1 + D + NV;
     constexpr bool PUSH = (MODE & PASS_PUSH) != 0, MOVE = (MODE & PASS_MOVE) != 0;
     constexpr bool DEPOSIT = (MODE & PASS_DEPOSIT) != 0, DIAG = (MODE & PASS_DIAG) != 0;
@@ -454,11 +472,12 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
     // reference cell, per axis)
     unsigned *s_win = reinterpret_cast<unsigned *>(bars + STAGES);
     int *s_box = reinterpret_cast<int *>(s_win + WIN_CAP);
-    // the current tile's parameters (copied by one thread for a batch), its
-    // reference cell, and per-warp diagnostic partials of a batch tile
-    __shared__ TileParams s_tp;
+    // the current and the next tile's parameters (copied by one thread for a batch,
+    // one tile ahead), the tile's reference cell, and per-warp diagnostic partials
+    // of a batch tile
+    __shared__ TileParams s_tp[2];
     __shared__ int s_ref_cell;
-    __shared__ float s_diag[PP_THREADS / 32][4];
+    __shared__ float s_diag[NT / 32][4];
 
     const int64_t ntiles = src.ntiles();
     const int my_tiles =
@@ -507,9 +526,10 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
     if (tid == 0) {
         for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(&bars[st]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (my_tiles > 0) src.load_params(tile_of(0), &s_tp[0]);
     }
     if (DEPOSIT) {
-        for (int i = tid; i < WIN_CAP; i += PP_THREADS) s_win[i] = 0u;
+        for (int i = tid; i < WIN_CAP; i += NT) s_win[i] = 0u;
         if (tid < 3) {
             s_box[tid] = 0x7fffffff;
             s_box[3 + tid] = -0x7fffffff;
@@ -528,7 +548,9 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         const int st = k % STAGES;
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
         const int64_t t = tile_of(k);
-        if (tid == 0) src.load_params(t, &s_tp);  // the previous tile is finished
+        // the next tile's parameters (its slot was last read by the previous tile,
+        // finished at that tile's closing barrier); this tile's came one tile ago
+        if (tid == 0 && k + 1 < my_tiles) src.load_params(tile_of(k + 1), &s_tp[(k + 1) & 1]);
         const bool ok_wait = mbar_wait_bounded(smem_addr(&bars[st]), parity);
         // the tile's reference cell (its first particle's cell before the move), kept
         // before the barrier so that no thread overwrites it first
@@ -545,7 +567,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
             __syncthreads();
             return;
         }
-        const TileParams &tp = src.params(s_tp);
+        const TileParams &tp = src.params(s_tp[k & 1]);
         const GridParams &g = tp.g;
         const float *__restrict__ E = tp.E;
         unsigned long long *__restrict__ acc = tp.acc;
@@ -562,7 +584,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         bool valid[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int j = particle_of<R>(r, tid);
+            const int j = particle_of<R, NT / 32>(r, tid);
             valid[r] = j < cnt;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -586,7 +608,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!valid[r]) continue;
-            const int j = particle_of<R>(r, tid);
+            const int j = particle_of<R, NT / 32>(r, tid);
             bool finite = true;
             if (PUSH) {
 #pragma unroll
@@ -728,7 +750,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
                 // particle's last corner quantum is at least -2), so its 32 bits
                 // decode unambiguously: WIN_NEG and above are the negative totals.
                 const int total = 1 << tot_bits;
-                for (int i = tid; i < total; i += PP_THREADS) {
+                for (int i = tid; i < total; i += NT) {
                     const unsigned u = s_win[i];
                     if (u == 0u) continue;
                     s_win[i] = 0u;
@@ -771,7 +793,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         __syncthreads();
         if (DIAG && Src::PER_TILE_DIAG && tid < 4) {
             double sum = 0.0;
-            for (int jw = 0; jw < PP_THREADS / 32; ++jw) sum += (double)s_diag[jw][tid];
+            for (int jw = 0; jw < NT / 32; ++jw) sum += (double)s_diag[jw][tid];
             diag_blocks[t * 4 + tid] = sum;
         }
         if (tid == 0) {
@@ -788,7 +810,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
     if (tid == 0 && WRITE) bulk_wait_all();
     if (bad) latch(err, EF_NONFINITE);
     if (DIAG && !Src::PER_TILE_DIAG) {
-        __shared__ double red[4][PP_THREADS / 32];
+        __shared__ double red[4][NT / 32];
         double vals[4] = {ke, mom[0], mom[1], mom[2]};
         const int w = tid >> 5;
 #pragma unroll
@@ -799,7 +821,7 @@ __global__ void __launch_bounds__(PP_THREADS, D == 3 ? 3 : (pass_tile<D, Src>() 
         __syncthreads();
         if (tid < 4) {
             double sum = 0.0;
-            for (int jw = 0; jw < PP_THREADS / 32; ++jw) sum += red[tid][jw];
+            for (int jw = 0; jw < NT / 32; ++jw) sum += red[tid][jw];
             diag_blocks[blockIdx.x * 4 + tid] = sum;
         }
     }
@@ -842,7 +864,7 @@ int pass_ctas_per_sm()
     auto k = k_particle_pass<D, NV, PASS_PUSH | PASS_MOVE | PASS_DEPOSIT | PASS_DIAG, Src>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k, PP_THREADS, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k, Src::NT, smem) != cudaSuccess ||
         c < 1) {
         cudaGetLastError();
         c = 1;
@@ -881,7 +903,7 @@ static cudaError_t launch_pass_m(const Src &src, ParticlesF32 p, double *diag_bl
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (e != cudaSuccess) return e;
-    k_particle_pass<D, NV, MODE, Src><<<nblocks, PP_THREADS, smem, st>>>(src, p, diag_blocks, err);
+    k_particle_pass<D, NV, MODE, Src><<<nblocks, Src::NT, smem, st>>>(src, p, diag_blocks, err);
     note_launch();
     return cudaGetLastError();
 }
@@ -950,27 +972,75 @@ cudaError_t launch_particle_pass(const GridParams &g, ParticlesF32 p, const floa
     }
 }
 
-cudaError_t launch_batch_pass(int ndim, const BatchTile *tiles, int64_t ntiles,
-                              const void *inst_params, ParticlesF32 p, bool push, bool mv,
-                              bool deposit, double *diag_tiles, int nblocks, int *err,
-                              cudaStream_t st)
+// The batch pass's (threads per CTA, particles per thread) variants.
+struct BatchVariant {
+    int threads, per_thread;
+};
+constexpr BatchVariant BATCH_VARIANTS[] = {{256, 2}, {128, 2}, {128, 4}, {256, 1}, {256, 3},
+                                           {512, 1}};
+constexpr int N_BATCH_VARIANTS = (int)(sizeof(BATCH_VARIANTS) / sizeof(BATCH_VARIANTS[0]));
+
+int batch_variant(int threads, int per_thread)
 {
-    if (ntiles == 0) return cudaSuccess;
-    const int mode = pass_mode(push, mv, deposit, diag_tiles != nullptr);
-    BatchSrc src;
+    for (int k = 0; k < N_BATCH_VARIANTS; ++k)
+        if (BATCH_VARIANTS[k].threads == threads && BATCH_VARIANTS[k].per_thread == per_thread)
+            return k;
+    return -1;
+}
+
+int batch_variant_count() { return N_BATCH_VARIANTS; }
+
+void batch_variant_shape(int variant, int *threads, int *per_thread)
+{
+    const BatchVariant v = BATCH_VARIANTS[variant >= 0 && variant < N_BATCH_VARIANTS ? variant : 0];
+    *threads = v.threads;
+    *per_thread = v.per_thread;
+}
+
+template <int NT, int PT>
+static cudaError_t launch_batch_variant(int ndim, const BatchTile *tiles, int64_t ntiles,
+                                        const void *inst_params, ParticlesF32 p, int mode,
+                                        double *diag_tiles, int nblocks, int *err,
+                                        cudaStream_t st)
+{
+    using Src = BatchSrcT<NT * PT, NT>;
+    Src src;
     src.tiles = tiles;
     src.inst = static_cast<const TileParams *>(inst_params);
     src.nt = ntiles;
     // at most one resident wave, whatever the tuning asks for
     const int64_t wave = (int64_t)sm_count() *
-                         (ndim == 1 ? pass_ctas_per_sm<1, 2, BatchSrc>()
-                                    : pass_ctas_per_sm<2, 2, BatchSrc>());
+                         (ndim == 1 ? pass_ctas_per_sm<1, 2, Src>() : pass_ctas_per_sm<2, 2, Src>());
     int64_t nb64 = nblocks < ntiles ? nblocks : ntiles;
     nb64 = nb64 < wave ? nb64 : wave;
     const int nb = (int)(nb64 < 1 ? 1 : nb64);
     switch (ndim * 10 + p.nv) {
     case 12: return launch_pass_t<1, 2>(src, p, mode, diag_tiles, nb, err, st);
     case 22: return launch_pass_t<2, 2>(src, p, mode, diag_tiles, nb, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_pass(int ndim, int variant, const BatchTile *tiles, int64_t ntiles,
+                              const void *inst_params, ParticlesF32 p, bool push, bool mv,
+                              bool deposit, double *diag_tiles, int nblocks, int *err,
+                              cudaStream_t st)
+{
+    if (ntiles == 0) return cudaSuccess;
+    const int mode = pass_mode(push, mv, deposit, diag_tiles != nullptr);
+    switch (variant) {
+    case 0: return launch_batch_variant<256, 2>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
+    case 1: return launch_batch_variant<128, 2>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
+    case 2: return launch_batch_variant<128, 4>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
+    case 3: return launch_batch_variant<256, 1>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
+    case 4: return launch_batch_variant<256, 3>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
+    case 5: return launch_batch_variant<512, 1>(ndim, tiles, ntiles, inst_params, p, mode,
+                                               diag_tiles, nblocks, err, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -116,9 +116,10 @@ def test_batch_autotune_and_cache(pk, tmp_path):
     bt.load([w.x for w in ws], [w.v for w in ws])
     cache = str(tmp_path / "tune.txt")
     t = bt.autotune(steps_per_trial=2, cache_path=cache)
-    assert t["pass_ctas_per_sm"] in (2, 3, 4)
+    assert t["pass_ctas_per_sm"] in (2, 3, 4, 6, 8)
     assert t["cg_iters_per_graph"] in (8, 16, 32)
     assert t["sort_every"] in (10, 20, 40)
+    assert (t["pass_threads"], t["pass_per_thread"]) in PASS_SHAPES
     assert open(cache).read().strip()
     # a second tune of the same shape on this GPU comes from the cache
     t2 = bt.autotune(steps_per_trial=2, cache_path=cache)
@@ -127,6 +128,50 @@ def test_batch_autotune_and_cache(pk, tmp_path):
     for i, w in enumerate(ws):
         d = bt.get_diag(i)
         assert d["charge_fx_sum"] == w.np_ * (1 << d["fx_bits"])
+    bt.close()
+
+
+# (threads per CTA, particles per thread) of the batch pass's kernel variants
+PASS_SHAPES = [(256, 2), (128, 2), (128, 4), (256, 1), (256, 3), (512, 1)]
+
+
+@pytest.mark.parametrize("shape", PASS_SHAPES)
+def test_batch_pass_shapes_match_oracle(pk, shape):
+    """Every shape the autotuner can pick (CTA size x particles per thread, tiles of
+    their product) gives the oracle's state; the shape is switched after loading, so
+    the pass tiles are rebuilt on a loaded batch."""
+    ws = instances()
+    bt = pk.batch_from_workloads(ws, cg_rtol=1e-7, solver=1)
+    bt.set_tuning(sort_every=2)
+    bt.load([w.x for w in ws], [w.v for w in ws])
+    bt.set_tuning(pass_threads=shape[0], pass_per_thread=shape[1])
+    sims = [_oracle(w).load(w.x, w.v) for w in ws]
+    ident = [bt.get_perm(i).copy() for i in range(len(ws))]
+    for k in range(1, 5):
+        bt.step(1)
+        for sim in sims:
+            sim.step(1)
+        if k % 2 == 0:
+            ident = [ident[i][bt.get_perm(i)] for i in range(len(ws))]
+    for i, (w, sim) in enumerate(zip(ws, sims)):
+        _, _, v, x = bt.get_particles(i)
+        L = np.asarray(w.L[: w.ndim])
+        dist = np.abs(x - sim.x[ident[i]])
+        dist = np.minimum(dist, L - dist)
+        assert dist.max() <= TOL, (shape, i, dist.max())
+        assert rel(v, sim.v[ident[i]], np.abs(sim.v).max()) <= TOL, (shape, i)
+        assert rel(bt.get_rho(i), sim.rho, np.abs(sim.rho_e).max()) <= TOL, (shape, i)
+        d = bt.get_diag(i)
+        assert d["charge_fx_sum"] == w.np_ * (1 << d["fx_bits"]), (shape, i)
+        assert abs(d["kinetic"] - sim.ke) <= 1e-5 * sim.ke, (shape, i)
+    bt.close()
+
+
+def test_batch_rejects_unknown_pass_shape(pk):
+    ws = instances()[:2]
+    bt = pk.batch_from_workloads(ws)
+    with pytest.raises(pk.PicError):
+        bt.set_tuning(pass_threads=384, pass_per_thread=2)
     bt.close()
 
 
