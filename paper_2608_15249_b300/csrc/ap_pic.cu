@@ -376,15 +376,16 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
         return fail(h, AP_PIC_ERR_ARG, "unknown solver %d", c->solver);
     if (c->em != 0 && c->em != 1) return fail(h, AP_PIC_ERR_ARG, "em must be 0 or 1");
     if (c->em) {
-        if (c->ndim != 2 || c->nv != 3 || plain)
+        if (c->ndim < 2 || c->nv != 3 || plain)
             return fail(h, AP_PIC_ERR_UNSUPPORTED,
-                        "the electromagnetic step needs ndim = 2, nv = 3 and the FP32 form");
+                        "the electromagnetic step needs ndim = 2 or 3, nv = 3 and the FP32 form");
         if (c->pusher != AP_PIC_PUSHER_BORIS)
             return fail(h, AP_PIC_ERR_UNSUPPORTED, "the electromagnetic step pushes with Boris");
         if (!(c->c_light > 0.0))
             return fail(h, AP_PIC_ERR_ARG, "the electromagnetic step needs c_light > 0");
-        const double courant =
-            c->c_light * c->dt * sqrt(1.0 / (c->dx[0] * c->dx[0]) + 1.0 / (c->dx[1] * c->dx[1]));
+        double idx2 = 0.0;
+        for (int a = 0; a < c->ndim; ++a) idx2 += 1.0 / (c->dx[a] * c->dx[a]);
+        const double courant = c->c_light * c->dt * sqrt(idx2);
         if (!(courant < 1.0))
             return fail(h, AP_PIC_ERR_ARG, "Courant number c dt sqrt(sum 1/dx^2) = %.3f >= 1",
                         courant);
@@ -393,6 +394,8 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
         return fail(h, AP_PIC_ERR_ARG, "em_boundary must be 0 or 1");
     if (c->em_boundary == 1) {
         if (!c->em) return fail(h, AP_PIC_ERR_ARG, "the absorbing layer needs em = 1");
+        if (c->ndim != 2)
+            return fail(h, AP_PIC_ERR_UNSUPPORTED, "the absorbing layer is built for 2D grids");
         if (c->pml_cells == 0) c->pml_cells = 12;
         if (c->pml_cells < 1 || 2 * c->pml_cells >= c->n[0] || 2 * c->pml_cells >= c->n[1])
             return fail(h, AP_PIC_ERR_ARG, "need 1 <= pml_cells and 2 pml_cells < n");
@@ -993,8 +996,12 @@ static ap_pic_status half_push(ap_pic *h)
     }
     const GridParams g = grid_params(h, -0.5 * h->cfg.dt);
     if (h->em) {
-        CU(h, launch_em_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks, h->d_err,
-                             h->stream));
+        if (h->ndim == 3)
+            CU(h, launch_em3_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
+                                  h->d_err, h->stream));
+        else
+            CU(h, launch_em_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
+                                 h->d_err, h->stream));
         return AP_PIC_OK;
     }
     CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, false, false, DiagPartials{},
@@ -1010,7 +1017,10 @@ static ap_pic_status after_load(ap_pic *h, unsigned flags)
     if (h->em) {
         // the electrostatic field of the loaded charge on the Yee lattice, B = 0
         const GridParams g = grid_params(h, h->cfg.dt);
-        CU(h, launch_em_e_from_phi(g, h->f.phi, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->stream));
+        if (h->ndim == 3)
+            CU(h, launch_em3_e_from_phi(g, h->f.phi, h->emb, h->cfg.dx, h->stream));
+        else
+            CU(h, launch_em_e_from_phi(g, h->f.phi, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->stream));
         CU(h, cudaMemsetAsync(h->emb.B, 0, (size_t)h->cells * 12, h->stream));
         CU(h, launch_em_energy(h->emb, h->cells, h->cfg.c_light, h->f.fe_part, h->f.nblocks,
                                h->stream));
@@ -1161,13 +1171,21 @@ static ap_pic_status em_step(ap_pic *h, bool diag)
     CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
     const GridParams g = grid_params(h, h->cfg.dt);
     const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
-    CU(h, launch_em_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
-                         h->dpart.nblocks, h->d_err, h->stream));
+    if (h->ndim == 3)
+        CU(h, launch_em3_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
+                              h->dpart.nblocks, h->d_err, h->stream));
+    else
+        CU(h, launch_em_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
+                             h->dpart.nblocks, h->d_err, h->stream));
     stage_end(h, mk);
     TRY(convert_rho(h));
     const int mf = stage_begin(h, AP_PIC_STAGE_FIELD);
-    CU(h, launch_em_fields(g, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->cfg.dt, h->cfg.c_light,
-                           h->cfg.q * h->cfg.weight, h->stream));
+    if (h->ndim == 3)
+        CU(h, launch_em3_fields(g, h->emb, h->cfg.dx, h->cfg.dt, h->cfg.c_light,
+                                h->cfg.q * h->cfg.weight, h->stream));
+    else
+        CU(h, launch_em_fields(g, h->emb, h->cfg.dx[0], h->cfg.dx[1], h->cfg.dt, h->cfg.c_light,
+                               h->cfg.q * h->cfg.weight, h->stream));
     if (diag)
         CU(h, launch_em_energy(h->emb, h->cells, h->cfg.c_light, h->f.fe_part, h->f.nblocks,
                                h->stream));

@@ -305,6 +305,21 @@ cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em
                            int *err, cudaStream_t st);
 // J from its accumulator (cleared), then B -= (dt/2) curl E; E += dt (c^2 curl B - J);
 // B -= (dt/2) curl E.
+// J (FP32, staggered like E) = the accumulated fixed-point weights of each
+// component times fx, fy, fz (plus the prescribed current); the accumulator is
+// cleared for the next step.
+cudaError_t launch_em_j_convert(int64_t cells, const EmBufs &em, double fx, double fy,
+                                double fz, cudaStream_t st);
+// The 3D electromagnetic step (pic_em3.cu): particles (gather E, B on the 3D Yee
+// lattice, Boris, and with move the move, the 3D Esirkepov current and the charge),
+// the field update, and the load's E from phi.
+cudaError_t launch_em3_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
+                            unsigned long long *rho_acc, double *diag_blocks, int nblocks,
+                            int *err, cudaStream_t st);
+cudaError_t launch_em3_fields(const GridParams &g, const EmBufs &em, const double *dx, double dt,
+                              double c, double qw, cudaStream_t st);
+cudaError_t launch_em3_e_from_phi(const GridParams &g, const float *phi, const EmBufs &em,
+                                  const double *dx, cudaStream_t st);
 cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, double dy,
                              double dt, double c, double qw, cudaStream_t st);
 cudaError_t launch_em_e_from_phi(const GridParams &g, const float *phi, const EmBufs &em,

@@ -113,13 +113,16 @@ def test_binding_structs_match_the_header(tmp_path):
 
 def test_electromagnetic_configuration_is_validated_on_the_host(libpath):
     """The electromagnetic step's configuration is checked before any device work: the
-    2D3V FP32 form with Boris, c > 0 and a Courant number below 1; the absorbing layer
-    only with em = 1 and with layers thinner than half the grid on each axis."""
+    2D3V or 3D FP32 form with Boris, c > 0 and a Courant number below 1; the absorbing
+    layer only with em = 1 on a 2D grid and with layers thinner than half the grid on
+    each axis."""
     import paper_2608_15249_b300 as pk
     base = dict(ndim=2, n=(32, 32), dt=0.1, nv=3, em=1, c_light=2.0)
     cases = (
         (dict(em=2), -1),
-        (dict(ndim=3, n=(8, 8, 8)), -2),
+        (dict(ndim=1, n=(32,)), -2),
+        (dict(ndim=3, n=(8, 8, 8), c_light=6.0), -1),  # 3D: c dt sqrt(3) = 1.04
+        (dict(ndim=3, n=(16, 16, 16), em_boundary=1, pml_cells=4), -2),
         (dict(nv=2), -2),
         (dict(precision=pk.AP_PIC_FP64_PLAIN), -2),
         (dict(pusher=pk.AP_PIC_PUSHER_HIGUERA_CARY), -2),
