@@ -126,24 +126,35 @@ typedef struct {
                               Cary pusher (0: infinite, the non-relativistic limit)
                               and the electromagnetic step (required there)         */
     int em;                /* 0: electrostatic (default); 1: the electromagnetic step
-                              (E_Maxwell, Sec. 2.2): periodic 2D3V Yee grid, E and B
-                              at integer times (B split in two half steps around
-                              the E update), Esirkepov charge-conserving current,
-                              Boris with the gathered B (+ B0).  The load's E is the
-                              Poisson field of the loaded charge, B = 0.  Needs
-                              ndim = 2, nv = 3, the FP32 form, the Boris pusher and
-                              c dt sqrt(1/dx^2 + 1/dy^2) < 1; ap_pic_step advances it
+                              (E_Maxwell, Sec. 2.2): periodic 2D3V or 3D Yee grid, E
+                              and B at integer times (B split in two half steps
+                              around the E update), Esirkepov charge-conserving
+                              current, Boris with the gathered B (+ B0).  The load's E
+                              is the Poisson field of the loaded charge, B = 0.
+                              Needs ndim = 2 or 3, nv = 3, the FP32 form, the Boris
+                              pusher and c dt sqrt(sum_a 1/dx_a^2) < 1 (and moves
+                              under one cell per step); ap_pic_step advances it
                               (the gather_push / deposit / push_deposit /
                               solve_field calls do not apply), ap_pic_get_E then
                               returns the 3 staggered components and ap_pic_get_B
                               the magnetic field                                  */
-    int em_boundary;       /* with em = 1: 0 periodic (default); 1 a convolutional
-                              PML (Roden and Gedney, the CPML of E_Maxwell) of
-                              pml_cells cells on every side, backed by a conducting
-                              wall: a non-periodic field-only grid (no particles;
-                              drive it with ap_pic_set_current).  Graded profiles,
-                              depth d in [0, 1]: sigma = 0.8 (m + 1) c / dx d^3,
-                              kappa = 1, alpha = 0                                 */
+    int em_boundary;       /* with em = 1: 0 periodic (default); 1 (2D only) a
+                              convolutional PML (Roden and Gedney, the CPML of
+                              E_Maxwell) of pml_cells cells on every side, backed by
+                              a conducting wall: a non-periodic grid, with or
+                              without particles (a prescribed current may drive it:
+                              ap_pic_set_current).  Graded profiles, depth d in
+                              [0, 1]: sigma = 0.8 (m + 1) c / dx d^3, kappa = 1,
+                              alpha = 0.  Particles live in [0, (n0 - 1) dx) x
+                              [0, (n1 - 1) dy) (a load outside it is
+                              AP_PIC_ERR_BOUNDS); fields start at zero (no Poisson
+                              solve); gathers, current and charge leave out the
+                              nodes outside the grid; a particle that leaves the box
+                              deposits the current of its whole move and is
+                              absorbed: marked (cell -1) until the next sort, which
+                              drops it (np decreases).  rho's background is
+                              rho_background (NaN: the neutralising density of the
+                              particles present)                                   */
     int pml_cells;         /* PML thickness in cells (0: 12); 2 pml_cells < n[a]    */
 } ap_pic_config;
 

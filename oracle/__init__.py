@@ -816,6 +816,7 @@ class CpmlPlasma(CpmlField):
         self.v = np.array(v, dtype=np.float64, order="C")
         assert self.x.shape[1] == 2 and self.v.shape[1] == 3
         assert np.all(self._inside(self.x)), "particles must start inside the walls"
+        self.ids = np.arange(self.x.shape[0])  # load order of the particles still in the box
         if half_push:
             boris_eb(self.v, self._fields_at(self.x), self.q / self.m, -0.5 * self.dt)
         self.rho = self.rho_e()
@@ -835,6 +836,7 @@ class CpmlPlasma(CpmlField):
             self.absorbed += int(np.count_nonzero(~keep))
             self.x = np.ascontiguousarray(self.x[keep])
             self.v = np.ascontiguousarray(self.v[keep])
+            self.ids = self.ids[keep]
             self.rho = self.rho_e()
             self.step_count += 1
         return self

@@ -99,6 +99,9 @@ struct ap_pic {
 
     // electromagnetic step (cfg.em)
     bool em = false;
+    bool em_np = false;  // particles in the non-periodic mode (absorbing layer, walls)
+    int64_t absorbed_total = 0;  // particles absorbed at the walls and dropped so far
+    unsigned long long *d_absorbed = nullptr;  // particles absorbed since the last sort
     EmBufs emb{};
     float *jext = nullptr;  // storage of the prescribed current
 
@@ -630,6 +633,9 @@ static ap_pic_status create_grid(ap_pic *h)
     CU(h, cudaMemsetAsync(h->d_mcc, 0, 24, h->stream));
     if (h->cfg.em) {
         h->em = true;
+        h->em_np = h->cfg.em_boundary == 1;
+        TRY(alloc_n(h, &h->d_absorbed, 1));
+        CU(h, cudaMemsetAsync(h->d_absorbed, 0, 8, h->stream));
         TRY(alloc_n(h, &h->emb.E, c * 3));
         TRY(alloc_n(h, &h->emb.B, c * 3));
         TRY(alloc_n(h, &h->emb.Jf, c * 3));
@@ -705,7 +711,8 @@ extern "C" ap_pic_status ap_pic_create(const ap_pic_config *cfg, const ap_pic_al
     int64_t nkeys = 1;
     for (int a = 0; a < h->ndim; ++a)
         nkeys *= (int64_t)((h->cfg.n[a] + h->brick[a] - 1) / h->brick[a]) * h->brick[a];
-    h->key_bits = bitlen((uint64_t)(nkeys - 1));
+    // (the non-periodic mode keeps one key past the cells for absorbed particles)
+    h->key_bits = bitlen((uint64_t)(h->cfg.em && h->cfg.em_boundary == 1 ? nkeys : nkeys - 1));
     if (nkeys > (int64_t(1) << 32)) {
         *out = h;
         return fail(h, AP_PIC_ERR_ARG, "sort key range exceeds 32 bits");
@@ -962,6 +969,21 @@ static ap_pic_status sort_particles(ap_pic *h)
     h->p = h->p_alt;
     h->p_alt = t;
     h->perm_slot = slot;
+    if (h->em_np) {
+        // the sort moved the particles absorbed since the last one past the live ones
+        // (their key follows every cell's): drop them
+        unsigned long long gone = 0;
+        CU(h, cudaMemcpyAsync(h->h_accsum + 4, h->d_absorbed, 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CU(h, cudaStreamSynchronize(h->stream));
+        gone = (unsigned long long)h->h_accsum[4];
+        CU(h, cudaMemsetAsync(h->d_absorbed, 0, 8, h->stream));
+        if (gone > (unsigned long long)h->np)
+            return fail(h, AP_PIC_ERR_STATE, "absorbed count exceeds the particles");
+        h->np -= (int64_t)gone;
+        h->absorbed_total += (int64_t)gone;
+        h->p.np = h->p_alt.np = h->np;
+    }
     return AP_PIC_OK;
 }
 
@@ -996,7 +1018,10 @@ static ap_pic_status half_push(ap_pic *h)
     }
     const GridParams g = grid_params(h, -0.5 * h->cfg.dt);
     if (h->em) {
-        if (h->ndim == 3)
+        if (h->em_np)
+            CU(h, launch_em_np_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
+                                    h->d_err, h->d_absorbed, h->stream));
+        else if (h->ndim == 3)
             CU(h, launch_em3_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
                                   h->d_err, h->stream));
         else
@@ -1011,10 +1036,24 @@ static ap_pic_status half_push(ap_pic *h)
 
 static ap_pic_status after_load(ap_pic *h, unsigned flags)
 {
+    if (h->em_np) {
+        const GridParams g = grid_params(h, h->cfg.dt);
+        CU(h, launch_em_np_check(g, h->p, h->d_err, h->stream));
+    }
     TRY(sync_check(h));
     TRY(sort_particles(h));
-    TRY(field_update(h));
-    if (h->em) {
+    if (h->em_np) {
+        // the non-periodic mode starts from zero fields (no Poisson solve): only the
+        // charge of the loaded particles, for the diagnostics
+        TRY(deposit_only(h));
+        CU(h, cudaMemsetAsync(h->emb.E, 0, (size_t)h->cells * 12, h->stream));
+        CU(h, cudaMemsetAsync(h->emb.B, 0, (size_t)h->cells * 12, h->stream));
+        CU(h, launch_em_energy(h->emb, h->cells, h->cfg.c_light, h->f.fe_part, h->f.nblocks,
+                               h->stream));
+    } else {
+        TRY(field_update(h));
+    }
+    if (h->em && !h->em_np) {
         // the electrostatic field of the loaded charge on the Yee lattice, B = 0
         const GridParams g = grid_params(h, h->cfg.dt);
         if (h->ndim == 3)
@@ -1038,8 +1077,6 @@ extern "C" ap_pic_status ap_pic_load(ap_pic *h, int64_t np, const double *x, con
     if (!h) return AP_PIC_ERR_ARG;
     if (np < 0 || np >= (int64_t(1) << 31)) return fail(h, AP_PIC_ERR_ARG, "np out of range");
     if (np > 0 && (!x || !v)) return fail(h, AP_PIC_ERR_ARG, "x and v are required");
-    if (np > 0 && h->cfg.em_boundary == 1)
-        return fail(h, AP_PIC_ERR_UNSUPPORTED, "the absorbing layer runs fields only (np = 0)");
     TRY(alloc_particles(h, np));
     const int64_t chunk = np < LOAD_CHUNK ? (np > 0 ? np : 1) : LOAD_CHUNK;
     double *dx_buf = nullptr, *dv_buf = nullptr;
@@ -1171,7 +1208,10 @@ static ap_pic_status em_step(ap_pic *h, bool diag)
     CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
     const GridParams g = grid_params(h, h->cfg.dt);
     const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
-    if (h->ndim == 3)
+    if (h->em_np)
+        CU(h, launch_em_np_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
+                                h->dpart.nblocks, h->d_err, h->d_absorbed, h->stream));
+    else if (h->ndim == 3)
         CU(h, launch_em3_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
                               h->dpart.nblocks, h->d_err, h->stream));
     else

@@ -602,6 +602,181 @@ __global__ void __launch_bounds__(EM_THREADS)
     }
 }
 
+// ---- particles in the non-periodic mode (absorbing layer and conducting walls) ------------
+// Particles live in cells 0 .. n_a - 2 of each axis, between the walls on the outer
+// nodes.  Gathers, current and charge take the periodic forms with the nodes outside
+// the grid left out: a field there counts as zero and a contribution to it is
+// dropped.  A particle whose move leaves the box deposits the current of its whole
+// move and is then absorbed: its cell becomes -1 (every kernel skips it; the next sort
+// moves it past the live particles, where it is dropped) and it is counted.
+
+// Lower lattice index (possibly -1) and fraction on a non-periodic axis.
+__device__ __forceinline__ void stagger_np(int c, float f, bool half, int *i0, float *fr)
+{
+    if (!half) {
+        *i0 = c;
+        *fr = f;
+    } else if (f >= 0.5f) {
+        *i0 = c;
+        *fr = f - 0.5f;
+    } else {
+        *i0 = c - 1;
+        *fr = f + 0.5f;
+    }
+}
+
+__device__ __forceinline__ float lattice_cic_np(const float *__restrict__ F, int n0, int n1, int i0,
+                                                float fx, int j0, float fy)
+{
+    return (1.0f - fy) * ((1.0f - fx) * at_or_zero(F, n0, n1, i0, j0) +
+                          fx * at_or_zero(F, n0, n1, i0 + 1, j0)) +
+           fy * ((1.0f - fx) * at_or_zero(F, n0, n1, i0, j0 + 1) +
+                 fx * at_or_zero(F, n0, n1, i0 + 1, j0 + 1));
+}
+
+__device__ __forceinline__ bool inside(int n0, int n1, int i, int j)
+{
+    return i >= 0 && j >= 0 && i < n0 && j < n1;
+}
+
+template <bool MOVE>
+__global__ void __launch_bounds__(EM_THREADS)
+    k_em_np_push(GridParams g, ParticlesF32 p, EmBufs em, unsigned long long *__restrict__ rho_acc,
+                 double *__restrict__ diag_blocks, int *__restrict__ err,
+                 unsigned long long *__restrict__ n_absorbed)
+{
+    const int n0 = g.n[0], n1 = g.n[1];
+    const int64_t cells = (int64_t)n0 * n1;
+    const float scale = ldexpf(1.0f, g.fx_bits);
+    const int one = 1 << g.fx_bits;
+    float ke = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
+    bool bad = false;
+    unsigned gone = 0;
+    for (int64_t i = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; i < p.np;
+         i += (int64_t)gridDim.x * EM_THREADS) {
+        const int cell = p.cell[i];
+        if (cell < 0) continue;  // absorbed in an earlier step
+        int c[2];
+        c[1] = (int)fdiv((uint32_t)cell, g.div0);
+        c[0] = cell - c[1] * n0;
+        const float f[2] = {p.off[i], p.off[p.stride + i]};
+        const float v[3] = {p.v[i], p.v[p.stride + i], p.v[2 * p.stride + i]};
+        int ix[2], iy[2];
+        float fx[2], fy[2];
+        stagger_np(c[0], f[0], false, &ix[0], &fx[0]);
+        stagger_np(c[0], f[0], true, &ix[1], &fx[1]);
+        stagger_np(c[1], f[1], false, &iy[0], &fy[0]);
+        stagger_np(c[1], f[1], true, &iy[1], &fy[1]);
+        float e[3], b[3];
+        e[0] = lattice_cic_np(em.E, n0, n1, ix[1], fx[1], iy[0], fy[0]) + g.E0[0];
+        e[1] = lattice_cic_np(em.E + cells, n0, n1, ix[0], fx[0], iy[1], fy[1]) + g.E0[1];
+        e[2] = lattice_cic_np(em.E + 2 * cells, n0, n1, ix[0], fx[0], iy[0], fy[0]) + g.E0[2];
+        b[0] = lattice_cic_np(em.B, n0, n1, ix[0], fx[0], iy[1], fy[1]) + em.B0[0];
+        b[1] = lattice_cic_np(em.B + cells, n0, n1, ix[1], fx[1], iy[0], fy[0]) + em.B0[1];
+        b[2] = lattice_cic_np(em.B + 2 * cells, n0, n1, ix[1], fx[1], iy[1], fy[1]) + em.B0[2];
+        float vn[3];
+        em_boris(v, e, b, g, vn);
+        bool finite = isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]);
+        float o2 = 0.0f, n2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o2 += v[a] * v[a];
+            n2 += vn[a] * vn[a];
+            mom[a] += vn[a];
+            p.v[a * p.stride + i] = vn[a];
+        }
+        ke += 0.5f * (o2 + n2);
+        if constexpr (!MOVE) {
+            if (!finite) bad = true;
+        } else {
+            int sh[2], m[2];
+            float fn[2], S0[2][3], DS[2][3];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                finite &= em_move_axis(f[a], vn[a] * g.dtdx[a], &sh[a], &m[a], &fn[a], S0[a], DS[a]);
+            if (!finite) {
+                bad = true;
+                continue;
+            }
+            const int base[2] = {c[0] + m[0], c[1] + m[1]};
+            // the Esirkepov current of the whole move, nodes outside the grid dropped
+#pragma unroll
+            for (int bq = 0; bq < 3; ++bq) {
+                float run = 0.0f;
+#pragma unroll
+                for (int aq = 0; aq < 2; ++aq) {
+                    run += DS[0][aq] * (S0[1][bq] + 0.5f * DS[1][bq]);
+                    if (inside(n0, n1, base[0] + aq, base[1] + bq))
+                        add_fx_unit(em.J + (base[0] + aq) + (int64_t)n0 * (base[1] + bq), run);
+                }
+            }
+#pragma unroll
+            for (int aq = 0; aq < 3; ++aq) {
+                float run = 0.0f;
+#pragma unroll
+                for (int bq = 0; bq < 2; ++bq) {
+                    run += DS[1][bq] * (S0[0][aq] + 0.5f * DS[0][aq]);
+                    if (inside(n0, n1, base[0] + aq, base[1] + bq))
+                        add_fx_unit(em.J + cells + (base[0] + aq) + (int64_t)n0 * (base[1] + bq),
+                                    run);
+                }
+            }
+#pragma unroll
+            for (int bq = 0; bq < 3; ++bq)
+#pragma unroll
+                for (int aq = 0; aq < 3; ++aq) {
+                    const float wz = esirkepov_wz(S0, DS, aq, bq);
+                    if (wz != 0.0f && inside(n0, n1, base[0] + aq, base[1] + bq))
+                        add_fx(em.J + 2 * cells + (base[0] + aq) + (int64_t)n0 * (base[1] + bq),
+                               vn[2] * wz);
+                }
+            const int cn[2] = {c[0] + sh[0], c[1] + sh[1]};
+            if (cn[0] < 0 || cn[1] < 0 || cn[0] > n0 - 2 || cn[1] > n1 - 2) {
+                // left the box: absorbed (its current is in; no charge)
+                p.cell[i] = -1;
+                ++gone;
+                continue;
+            }
+            // charge at the new position (all four nodes inside the grid)
+            const float wx[2] = {1.0f - fn[0], fn[0]}, wy[2] = {1.0f - fn[1], fn[1]};
+            int qk[4], rest = one;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                qk[k] = __float_as_int(fmaf(wx[k & 1] * wy[k >> 1], scale, RND_MAGIC_F)) -
+                        RND_MAGIC_I;
+                rest -= qk[k];
+            }
+            qk[3] = rest;
+            const int64_t n00 = cn[0] + (int64_t)n0 * cn[1];
+            atomicAdd(rho_acc + n00, (unsigned long long)(long long)qk[0]);
+            atomicAdd(rho_acc + n00 + 1, (unsigned long long)(long long)qk[1]);
+            atomicAdd(rho_acc + n00 + n0, (unsigned long long)(long long)qk[2]);
+            atomicAdd(rho_acc + n00 + n0 + 1, (unsigned long long)(long long)qk[3]);
+            p.cell[i] = (int)n00;
+            p.off[i] = fn[0];
+            p.off[p.stride + i] = fn[1];
+        }
+    }
+    if (bad) atomicOr(err, EF_NONFINITE);
+    gone = __reduce_add_sync(0xffffffffu, gone);
+    if ((threadIdx.x & 31) == 0 && gone) atomicAdd(n_absorbed, (unsigned long long)gone);
+    if (diag_blocks) em_block_diag(ke, mom, diag_blocks, blockIdx.x);
+}
+
+// Loaded positions must lie in the box between the walls: cells 0 .. n_a - 2.
+__global__ void __launch_bounds__(EM_THREADS) k_em_np_check(GridParams g, ParticlesF32 p, int *err)
+{
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; i < p.np;
+         i += (int64_t)gridDim.x * EM_THREADS) {
+        const int cell = p.cell[i];
+        const int c1 = (int)fdiv((uint32_t)cell, g.div0);
+        const int c0 = cell - c1 * g.n[0];
+        bad |= c0 > g.n[0] - 2 || c1 > g.n[1] - 2;
+    }
+    if (bad) atomicOr(err, EF_NONFINITE);
+}
+
 // Initial field of the load: E = -grad phi by forward differences onto the staggered
 // points (so that the discrete div E equals rho), Ez = 0.
 __global__ void __launch_bounds__(EM_THREADS)
@@ -740,6 +915,28 @@ cudaError_t launch_em_e_from_phi(const GridParams &g, const float *phi, const Em
     const int64_t cells = (int64_t)g.n[0] * g.n[1];
     k_em_e_from_phi<<<em_blocks(cells), EM_THREADS, 0, st>>>(g, phi, em.E, (float)(1.0 / dx),
                                                             (float)(1.0 / dy));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_np_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
+                              unsigned long long *rho_acc, double *diag_blocks, int nblocks,
+                              int *err, unsigned long long *n_absorbed, cudaStream_t st)
+{
+    if (p.np == 0) return cudaSuccess;
+    const int nb = nblocks > 0 ? nblocks : 1;  // every diagnostic slot is written
+    if (move)
+        k_em_np_push<true><<<nb, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err, n_absorbed);
+    else
+        k_em_np_push<false><<<nb, EM_THREADS, 0, st>>>(g, p, em, rho_acc, diag_blocks, err, n_absorbed);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_np_check(const GridParams &g, ParticlesF32 p, int *err, cudaStream_t st)
+{
+    if (p.np == 0) return cudaSuccess;
+    k_em_np_check<<<em_blocks(p.np), EM_THREADS, 0, st>>>(g, p, err);
     note_launch();
     return cudaGetLastError();
 }

@@ -310,6 +310,15 @@ cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em
 // cleared for the next step.
 cudaError_t launch_em_j_convert(int64_t cells, const EmBufs &em, double fx, double fy,
                                 double fz, cudaStream_t st);
+// Particles in the non-periodic mode (absorbing layer, conducting walls): gather
+// with fields outside the grid zero, Boris, and with move the move, the Esirkepov
+// current (contributions outside the grid dropped), the charge of the particles
+// still in the box; a particle that leaves the box gets cell -1 and is counted in
+// *n_absorbed.  The check latches EF_NONFINITE for a loaded particle outside the box.
+cudaError_t launch_em_np_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
+                              unsigned long long *rho_acc, double *diag_blocks, int nblocks,
+                              int *err, unsigned long long *n_absorbed, cudaStream_t st);
+cudaError_t launch_em_np_check(const GridParams &g, ParticlesF32 p, int *err, cudaStream_t st);
 // The 3D electromagnetic step (pic_em3.cu): particles (gather E, B on the 3D Yee
 // lattice, Boris, and with move the move, the 3D Esirkepov current and the charge),
 // the field update, and the load's E from phi.

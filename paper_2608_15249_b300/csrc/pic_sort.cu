@@ -39,11 +39,14 @@ size_t sort_hist_len(int64_t np) { return (size_t)MAX_RADIX * (size_t)tiles_of(n
 struct KeyParams {
     FastDiv dn0, dn1, db0, db1, db2;
     uint32_t nb0, nb1;
+    uint32_t absorbed;  // key of a particle marked absorbed (negative cell): one past the
+                        // last cell key, so the sort moves such particles to the end
 };
 
 template <int D>
 __device__ __forceinline__ uint32_t brick_key(uint32_t c, const KeyParams &k)
 {
+    if ((int32_t)c < 0) return k.absorbed;
     uint32_t c0, c1 = 0, c2 = 0;
     if (D == 1) {
         c0 = c;
@@ -369,6 +372,12 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
     kp.db2 = make_fastdiv((uint32_t)b2);
     kp.nb0 = (uint32_t)((g.n[0] + b0 - 1) / b0);
     kp.nb1 = g.ndim >= 2 ? (uint32_t)((g.n[1] + b1 - 1) / b1) : 1u;
+    {
+        uint64_t nk = (uint64_t)kp.nb0 * b0;
+        if (g.ndim >= 2) nk *= (uint64_t)kp.nb1 * b1;
+        if (g.ndim >= 3) nk *= (uint64_t)((g.n[2] + b2 - 1) / b2) * b2;
+        kp.absorbed = (uint32_t)nk;  // needs key_bits > bitlen(nk - 1) where it occurs
+    }
     // a persistent grid of 8 CTAs per SM (fewer for small np)
     int64_t kb = (np / 4 + 255) / 256;
     const int64_t cap = (int64_t)sm_count() * 8;

@@ -54,13 +54,8 @@ def test_cpml_pulse_matches_oracle(pk, n, dx):
     g.close()
 
 
-def test_cpml_rejects_particles_and_bad_thickness(pk):
-    cfg = pk.make_config(2, (40, 40), dt=0.5, nv=3, em=1, c_light=1.0, em_boundary=1,
-                         pml_cells=8)
-    g = pk.Pic(cfg)
-    with pytest.raises(pk.PicError):
-        g.load(np.array([[3.0, 4.0]]), np.zeros((1, 3)))
-    g.close()
+def test_cpml_rejects_bad_thickness(pk):
+    """(Particles in this mode are covered by test_gpu_cpml_particles.py.)"""
     with pytest.raises(pk.PicError):
         pk.Pic(pk.make_config(2, (20, 20), dt=0.5, nv=3, em=1, c_light=1.0, em_boundary=1,
                               pml_cells=10))
