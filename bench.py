@@ -356,6 +356,7 @@ def bench_ours(args):
     collisions = None if (f64 or args.no_collisions) else bench_collisions(
         args, pk, torch, stream, peak, peak_kind)
     em = None if (f64 or args.no_em) else bench_em(args, pk, torch, stream, peak, peak_kind)
+    em3 = None if (f64 or args.no_em) else bench_em3(args, pk, torch, stream, peak, peak_kind)
     cpml = None if (f64 or args.no_em) else bench_cpml(args, pk, torch, stream, peak, peak_kind)
     e2e = None
     if not args.no_e2e:
@@ -399,6 +400,7 @@ def bench_ours(args):
             "higuera_cary": hc,
             "collisions": collisions,
             "electromagnetic": em,
+            "electromagnetic_3d": em3,
             "cpml_fields": cpml,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -612,6 +614,51 @@ def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
         out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": sample * 2 / secs,
                          "sample": f"{sample} of {w.np_} particles on the full grid, 2 full "
                                    f"electromagnetic steps ({secs:.1f} s)"}
+    return out
+
+
+def bench_em3(args, pk, torch, stream, peak, peak_kind, n=128, ppc=8, steps=10):
+    """CUDA-event time of full 3D electromagnetic steps (periodic 3D Yee lattice,
+    particles with the 3D Esirkepov current, sort every 20 steps) on a 3D Maxwellian of
+    16.8M electrons (128^3 x 8 ppc), c = 3 v_te, dt = 0.1 (Courant number 0.52); the
+    roofline of its particle kernel (56 B of record read and written per particle; E
+    and B read, the int64 current and charge written: 56 B per node); the oracle's
+    EmSimulation3 step on a sample of the particles on the same grid."""
+    import oracle
+
+    w = workloads.maxwellian_box(3, (n, n, n), ppc=ppc, nv=3, dt=0.1, seed=9)
+    g = pk.from_workload(w, stream=stream.cuda_stream, em=1, c_light=3.0, sort_every=20)
+    g.load(w.x, w.v)
+    g.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    g.set_timing(True)
+    g.step(steps)
+    st = g.get_timing()
+    g.set_timing(False)
+    g.close()
+    push_ms = st["push_deposit"][0] / max(st["push_deposit"][1], 1)
+    field_ms = st["field"][0] / max(st["field"][1], 1)
+    out = {"ms_per_step": ms, "particles": w.np_, "particle_steps_per_s": w.np_ / (ms * 1e-3),
+           "stage_ms": {"em_particles": push_ms, "yee_fields": field_ms},
+           "roofline": _roofline(w.np_ * 56 + w.cells * 56, push_ms,
+                                 "k_em3_push (gather E, B + Boris + move + 3D Esirkepov current)",
+                                 peak, peak_kind),
+           "workload": f"maxwellian 3D {n}^3, {ppc} ppc, c = 3, dt = 0.1, full 3D "
+                       "electromagnetic step"}
+    if not args.no_row_oracles:
+        sample = min(w.np_, 1 << 18)
+        sim = oracle.EmSimulation3(w.n, w.dx, w.dt, 3.0, weight=w.weight, rtol=1e-6)
+        sim.load(w.x[:sample], w.v[:sample])
+        _, secs = _timed(lambda: sim.step(1))
+        out["oracle"] = {"kind": "oracle", "cores": 1, "particle_steps_per_s": sample / secs,
+                         "sample": f"{sample} of {w.np_} particles on the full grid, 1 full 3D "
+                                   f"electromagnetic step ({secs:.1f} s)"}
     return out
 
 

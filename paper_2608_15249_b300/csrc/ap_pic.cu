@@ -593,7 +593,7 @@ static ap_pic_status create_grid(ap_pic *h)
     }
     f.div0 = make_fastdiv((uint32_t)f.n[0]);
     f.div1 = make_fastdiv((uint32_t)f.n[1]);
-    f.Estride = h->ndim == 3 ? 4 : h->ndim;
+    f.Estride = h->ndim == 3 ? 4 : 2 * h->ndim;
     f.nblocks = field_blocks(h->cells);
     const size_t c = (size_t)h->cells;
     TRY(alloc_n(h, &f.acc, c));

@@ -562,10 +562,16 @@ __global__ void __launch_bounds__(FT) k_efield(FieldBufs f, float h0, float h1, 
             fe += (double)e[a] * e[a];
             stride *= na;
         }
-        if (f.Estride == 1) {
-            f.E[id] = e[0];
-        } else if (f.Estride == 2) {
-            reinterpret_cast<float2 *>(f.E)[id] = make_float2(e[0], e[1]);
+        // 1D and 2D: pairs (node x holds its own field and that of x + 1), so a node's
+        // field goes to its own first half and to its lower x-neighbour's second half
+        if (f.ndim == 1) {
+            const int64_t left = j[0] == 0 ? id + f.n[0] - 1 : id - 1;
+            f.E[2 * id] = e[0];
+            f.E[2 * left + 1] = e[0];
+        } else if (f.ndim == 2) {
+            const int64_t left = j[0] == 0 ? id + f.n[0] - 1 : id - 1;
+            reinterpret_cast<float2 *>(f.E)[2 * id] = make_float2(e[0], e[1]);
+            reinterpret_cast<float2 *>(f.E)[2 * left + 1] = make_float2(e[0], e[1]);
         } else {
             reinterpret_cast<float4 *>(f.E)[id] = make_float4(e[0], e[1], e[2], 0.0f);
         }

@@ -244,7 +244,9 @@ struct FieldBufs {
     float *p2;                 // second buffer of the direction (cooperative solve)
     unsigned *gbar;            // grid barrier of the cooperative solve (count, generation)
     float *x;                  // correction of the refinement step
-    float *E;                  // interleaved, stride Estride floats per node
+    float *E;                  // interleaved, Estride floats per node: 1D and 2D the
+                               // node's field and its upper x-neighbour's (2, 4),
+                               // 3D (Ex, Ey, Ez, 0)
     int Estride;
     double *part[3];           // reduction partials (ping-pong + spare), nblocks each
     int nblocks;

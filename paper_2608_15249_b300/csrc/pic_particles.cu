@@ -4,9 +4,11 @@
 // (B01) -- the order of the paper's worked example (Sec. 3.1, Listing 1).
 //
 // Storage: int32 linear cell index, FP32 offsets in [0, 1) per axis (SoA,
-// one array per axis), FP32 velocities (SoA).  E is stored interleaved per
-// node (float, float2 or float4 for 1, 2, 3 dimensions) so a corner's field
-// is one vector load.  Charge goes to an int64 fixed-point accumulator: each
+// one array per axis), FP32 velocities (SoA).  E is stored per node so that a
+// gather takes few vector loads: in 1D and 2D each node holds its own field and
+// its upper x-neighbour's (the periodic wrap already applied), so a row of two
+// corners is one load (float2 in 1D, float4 in 2D); in 3D one float4 per node.
+// (A batch's instances keep one field per node: its pass reads E without pairs.)  Charge goes to an int64 fixed-point accumulator: each
 // particle deposits exactly 2^S split over its 2^d corners (the last corner
 // takes the remainder), so totals are exact and the sum is independent of
 // the order of the atomics.
@@ -51,10 +53,26 @@ __device__ __forceinline__ int encode_cell(const int *c, const int *n)
 // Upper neighbour on a periodic axis.
 __device__ __forceinline__ int up(int c, int n) { return (c + 1 == n) ? 0 : c + 1; }
 
-template <int D>
+// CIC gather of E at a particle in cell c, offsets f.  PAIRS: the 1D / 2D pair
+// layout (node x holds E(x) and E(x + 1)); otherwise one field per node.
+template <int D, bool PAIRS = false>
 __device__ __forceinline__ void gather_E(const float *__restrict__ E, const int *c, const float *f,
                                          const int *n, float *e)
 {
+    if (PAIRS && D == 1) {
+        const float2 pr = __ldg(reinterpret_cast<const float2 *>(E) + c[0]);
+        e[0] = (1.0f - f[0]) * pr.x + f[0] * pr.y;
+        return;
+    }
+    if (PAIRS && D == 2) {
+        const float4 *P = reinterpret_cast<const float4 *>(E);
+        const int y0 = c[1] * n[0], y1 = up(c[1], n[1]) * n[0];
+        const float4 r0 = __ldg(P + c[0] + y0), r1 = __ldg(P + c[0] + y1);
+        const float wx0 = 1.0f - f[0], wx1 = f[0], wy0 = 1.0f - f[1], wy1 = f[1];
+        e[0] = wy0 * (wx0 * r0.x + wx1 * r0.z) + wy1 * (wx0 * r1.x + wx1 * r1.z);
+        e[1] = wy0 * (wx0 * r0.y + wx1 * r0.w) + wy1 * (wx0 * r1.y + wx1 * r1.w);
+        return;
+    }
     if (D == 1) {
         const float w0 = 1.0f - f[0], w1 = f[0];
         e[0] = w0 * __ldg(E + c[0]) + w1 * __ldg(E + up(c[0], n[0]));
@@ -601,7 +619,7 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
 #pragma unroll
                     for (int a = 0; a < NV; ++a) v[r][a] = stage_arr(st, 1 + D + a)[j];
                 }
-                if (PUSH) gather_E<D>(E, c[r], f[r], g.n, e[r]);
+                if (PUSH) gather_E<D, !Src::PER_TILE_DIAG>(E, c[r], f[r], g.n, e[r]);
             }
         }
         // phase B: push, move, write the record back into the stage
