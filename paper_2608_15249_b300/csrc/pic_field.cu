@@ -181,10 +181,10 @@ static Lap make_lap(const FieldBufs &f)
 // A CG loop of separate launches (direction, matvec, update: three per
 // iteration) needs the host to read a done flag between blocks of launches.
 // k_cg_coop runs Jacobi-PCG (FP32 vectors, FP64 dots, zero-mean projection of r,
-// breakdown guard) as one cooperative launch of one block per SM: blocks meet at a grid barrier, every
-// block re-reduces the block partials in the same fixed order (so all see
-// bit-identical scalars and take the same decisions), and the convergence test
-// never leaves the device.  The direction update is fused into the matvec: each
+// breakdown guard) as one cooperative launch of one block per SM: blocks meet at
+// a grid barrier, every block re-reduces the block partials in the same fixed
+// order (so all see bit-identical scalars and take the same decisions), and the
+// convergence test never leaves the device.  The direction update is fused into the matvec: each
 // node recomputes p = (r - mean r) / diag + beta p_old at itself and its
 // neighbours from r and the previous direction (p ping-pongs between two
 // buffers), so an iteration takes two grid barriers.

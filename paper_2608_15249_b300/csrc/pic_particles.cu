@@ -8,10 +8,11 @@
 // gather takes few vector loads: in 1D and 2D each node holds its own field and
 // its upper x-neighbour's (the periodic wrap already applied), so a row of two
 // corners is one load (float2 in 1D, float4 in 2D); in 3D one float4 per node.
-// (A batch's instances keep one field per node: its pass reads E without pairs.)  Charge goes to an int64 fixed-point accumulator: each
-// particle deposits exactly 2^S split over its 2^d corners (the last corner
-// takes the remainder), so totals are exact and the sum is independent of
-// the order of the atomics.
+// (A batch's instances keep one field per node: its pass reads E without
+// pairs.)  Charge goes to an int64 fixed-point accumulator: each particle
+// deposits exactly 2^S split over its 2^d corners (the last corner takes the
+// remainder), so totals are exact and the sum is independent of the order of
+// the atomics.
 #include <math.h>
 
 #include <type_traits>
