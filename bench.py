@@ -617,17 +617,19 @@ def bench_em(args, pk, torch, stream, peak, peak_kind, steps=20):
     return out
 
 
-def bench_em3(args, pk, torch, stream, peak, peak_kind, n=128, ppc=8, steps=10):
+def bench_em3(args, pk, torch, stream, peak, peak_kind, n=128, ppc=8, steps=10, sort_every=5):
     """CUDA-event time of full 3D electromagnetic steps (periodic 3D Yee lattice,
-    particles with the 3D Esirkepov current, sort every 20 steps) on a 3D Maxwellian of
-    16.8M electrons (128^3 x 8 ppc), c = 3 v_te, dt = 0.1 (Courant number 0.52); the
+    particles with the 3D Esirkepov current, sorted every 5 steps into the step's
+    default 4 x 4 x 4 bricks: the cadence with the shortest full step, as the particle
+    kernel's fixed deposit windows hold more particles soon after a sort) on a 3D
+    Maxwellian of 16.8M electrons (128^3 x 8 ppc), c = 3 v_te, dt = 0.1 (Courant number 0.52); the
     roofline of its particle kernel (56 B of record read and written per particle; E
     and B read, the int64 current and charge written: 56 B per node); the oracle's
     EmSimulation3 step on a sample of the particles on the same grid."""
     import oracle
 
     w = workloads.maxwellian_box(3, (n, n, n), ppc=ppc, nv=3, dt=0.1, seed=9)
-    g = pk.from_workload(w, stream=stream.cuda_stream, em=1, c_light=3.0, sort_every=20)
+    g = pk.from_workload(w, stream=stream.cuda_stream, em=1, c_light=3.0, sort_every=sort_every)
     g.load(w.x, w.v)
     g.step(3)
     torch.cuda.synchronize()
@@ -649,8 +651,8 @@ def bench_em3(args, pk, torch, stream, peak, peak_kind, n=128, ppc=8, steps=10):
            "roofline": _roofline(w.np_ * 56 + w.cells * 56, push_ms,
                                  "k_em3_push (gather E, B + Boris + move + 3D Esirkepov current)",
                                  peak, peak_kind),
-           "workload": f"maxwellian 3D {n}^3, {ppc} ppc, c = 3, dt = 0.1, full 3D "
-                       "electromagnetic step"}
+           "workload": f"maxwellian 3D {n}^3, {ppc} ppc, c = 3, dt = 0.1, sort every "
+                       f"{sort_every}, full 3D electromagnetic step"}
     if not args.no_row_oracles:
         sample = min(w.np_, 1 << 18)
         sim = oracle.EmSimulation3(w.n, w.dx, w.dt, 3.0, weight=w.weight, rtol=1e-6)

@@ -412,13 +412,15 @@ static ap_pic_status validate(ap_pic *h, ap_pic_config *c)
                             FFT_MAX_N);
     }
     if (c->diag_every == 0) c->diag_every = 1;
-    // default sort brick: 64 cells in 1D, 8 x 8 in 2D, 8 x 8 x 8 in 3D (capped by n)
+    // default sort brick: 64 cells in 1D, 8 x 8 in 2D, 8 x 8 x 8 in 3D, 4 x 4 x 4 in
+    // the 3D electromagnetic step (its tiles of 256 particles then span few cells per
+    // axis, which its fixed deposit window needs at low densities); capped by n
     for (int a = 0; a < 3; ++a) {
         if (a >= c->ndim) {
             c->brick[a] = 1;
             continue;
         }
-        if (c->brick[a] == 0) c->brick[a] = c->ndim == 1 ? 64 : 8;
+        if (c->brick[a] == 0) c->brick[a] = c->ndim == 1 ? 64 : (c->ndim == 3 && c->em ? 4 : 8);
         if (c->brick[a] < 1) return fail(h, AP_PIC_ERR_ARG, "brick[%d] must be >= 1", a);
         if (c->brick[a] > c->n[a]) c->brick[a] = c->n[a];
     }
@@ -671,6 +673,7 @@ static void free_particles(ap_pic *h)
     dev_free(h, h->dpart.blocks);
     dev_free(h, h->emb.tile_flag);
     h->emb.tile_flag = nullptr;
+    h->emb.tile_spill = nullptr;
     h->p = ParticlesF32{};
     h->p_alt = ParticlesF32{};
     h->sort = SortScratch{};
@@ -761,14 +764,17 @@ static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
     const int cap = 62 - bitlen((uint64_t)(np > 0 ? np : 1));
     h->fx_bits = h->cfg.fx_bits < cap ? h->cfg.fx_bits : cap;
     h->dpart.nblocks = h->plain ? plain_pass_blocks(np > 0 ? np : 1, h->ndim)
-                       : h->em  ? 2 * em_particle_blocks(np > 0 ? np : 1)
+                       : h->em  ? 2 * (h->ndim == 3 ? em3_particle_blocks(np > 0 ? np : 1)
+                                                     : em_particle_blocks(np > 0 ? np : 1))
                                 : particle_pass_blocks(np > 0 ? np : 1, h->ndim, h->nv);
     TRY(alloc_n(h, &h->dpart.blocks, (size_t)h->dpart.nblocks * 4));
     CU(h, cudaMemsetAsync(h->dpart.blocks, 0, (size_t)h->dpart.nblocks * 32, h->stream));
     if (h->em) {
+        // a flag (2D) or a 16-bit count (3D) per particle tile
         const size_t tiles = (size_t)((np + EM_PASS_TILE - 1) / EM_PASS_TILE) + 1;
-        TRY(alloc_n(h, &h->emb.tile_flag, tiles));
-        CU(h, cudaMemsetAsync(h->emb.tile_flag, 0, tiles, h->stream));
+        TRY(alloc_n(h, &h->emb.tile_flag, 2 * tiles));
+        CU(h, cudaMemsetAsync(h->emb.tile_flag, 0, 2 * tiles, h->stream));
+        h->emb.tile_spill = reinterpret_cast<unsigned short *>(h->emb.tile_flag);
     }
     if (h->plain) {
         TRY(alloc_n(h, &h->p64.x, n * h->ndim));
@@ -1023,7 +1029,7 @@ static ap_pic_status half_push(ap_pic *h)
                                     h->d_err, h->d_absorbed, h->stream));
         else if (h->ndim == 3)
             CU(h, launch_em3_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
-                                  h->d_err, h->stream));
+                                  h->d_err, nullptr, h->stream));
         else
             CU(h, launch_em_push(g, h->p, h->emb, false, nullptr, nullptr, h->dpart.nblocks,
                                  h->d_err, h->stream));
@@ -1212,8 +1218,10 @@ static ap_pic_status em_step(ap_pic *h, bool diag)
         CU(h, launch_em_np_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
                                 h->dpart.nblocks, h->d_err, h->d_absorbed, h->stream));
     else if (h->ndim == 3)
+        // the sort's destination buffer is free between sorts: its cell array holds
+        // the list of particles the tiled kernel leaves to the global-memory kernel
         CU(h, launch_em3_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
-                              h->dpart.nblocks, h->d_err, h->stream));
+                              h->dpart.nblocks, h->d_err, h->p_alt.cell, h->stream));
     else
         CU(h, launch_em_push(g, h->p, h->emb, true, h->f.acc, diag ? h->dpart.blocks : nullptr,
                              h->dpart.nblocks, h->d_err, h->stream));

@@ -294,6 +294,9 @@ struct EmBufs {
     // per particle tile of the step kernel: 1 when its particles were too spread out
     // for the shared-memory windows (handled particle by particle), else 0
     unsigned char *tile_flag;
+    // 3D: per particle tile, the number of its particles left to the global-memory
+    // kernel (the same allocation as tile_flag, two bytes per tile)
+    unsigned short *tile_spill;
 };
 // Particles per tile of the electromagnetic step kernel (one per thread).
 constexpr int EM_PASS_TILE = 256;
@@ -324,9 +327,14 @@ cudaError_t launch_em_np_check(const GridParams &g, ParticlesF32 p, int *err, cu
 // The 3D electromagnetic step (pic_em3.cu): particles (gather E, B on the 3D Yee
 // lattice, Boris, and with move the move, the 3D Esirkepov current and the charge),
 // the field update, and the load's E from phi.
+// Blocks of one resident wave of the 3D tiled particle kernel; the handle keeps twice
+// as many diagnostic slots (the tiled kernel's and the listed particles' kernel's).
+int em3_particle_blocks(int64_t np);
+// spill_list: np int32 slots of scratch (free between sorts), for the particles the
+// tiled kernel leaves to the global-memory kernel.
 cudaError_t launch_em3_push(const GridParams &g, ParticlesF32 p, const EmBufs &em, bool move,
                             unsigned long long *rho_acc, double *diag_blocks, int nblocks,
-                            int *err, cudaStream_t st);
+                            int *err, int32_t *spill_list, cudaStream_t st);
 cudaError_t launch_em3_fields(const GridParams &g, const EmBufs &em, const double *dx, double dt,
                               double c, double qw, cudaStream_t st);
 cudaError_t launch_em3_e_from_phi(const GridParams &g, const float *phi, const EmBufs &em,
