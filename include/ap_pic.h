@@ -117,7 +117,10 @@ typedef struct {
                               int64 sum cannot overflow                            */
     double cg_rtol;        /* field-solve relative residual target (0: 1e-6)      */
     int cg_maxit;          /* field-solve iteration cap (0: 20000)                 */
-    int brick[3];          /* sort brick in cells per axis (0: library default)    */
+    int brick[3];          /* sort brick in cells per axis (0: library default:
+                              64 in 1D, 8 per axis in 2D and 3D, 4 per axis in the 3D
+                              electromagnetic step, whose particle kernel's fixed
+                              deposit windows need compact tiles)                     */
     int diag_every;        /* diagnostics every this many steps (0: every step)    */
     int solver;            /* AP_PIC_SOLVER_CG (default) or AP_PIC_SOLVER_FFT; both
                               end with one FP64-residual refinement pass           */
@@ -261,7 +264,7 @@ ap_pic_status ap_pic_sort(ap_pic *h);
  * Computes the same stable brick-major permutation as ap_pic_sort: perm[r] =
  * index in `cell` of the particle of rank r (ties keep input order).
  *   ndim, n[3], brick[3]: grid and sort brick as in ap_pic_config (brick 0:
- *       the library default; bricks are capped by n);
+ *       the library default of an electrostatic handle; bricks are capped by n);
  *   np: particles, 0 <= np <= AP_PIC_NOALLOC_MAX_NP, else AP_PIC_ERR_TOO_LARGE
  *       with no device work;
  *   cell: device, np int32 linear cell indices in [0, cells);
