@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(EM_THREADS)
     const int64_t ntiles = (p.np + EMT_TILE - 1) / EMT_TILE;
     int par = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, par ^= 1) {
-        const int64_t i = t * EMT_TILE + tid;
+        // a warp's lanes take four rows of 32 of the tile (lane i: column i of row
+        // (w + i mod 4) mod 8), so its window atomics spread over more nodes; lanes
+        // of one row share cells, whose window reads are broadcasts
+        const int64_t i = t * EMT_TILE + 32 * (((tid >> 5) + (lane & 3)) & 7) + lane;
         const bool valid = i < p.np;
         // reference cell: the tile's first particle's; d = old cell - reference,
         // unwrapped to [-n/2, n/2] per axis

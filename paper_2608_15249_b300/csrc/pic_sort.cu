@@ -146,6 +146,17 @@ __global__ void __launch_bounds__(ST_THREADS)
         hist[(int64_t)j * ntiles + blockIdx.x] = h[j];
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
 // ---- stable scatter --------------------------------------------------------------------------
 
 // The lanes whose digit equals this lane's (NO_DIGIT lanes form their own group), from
@@ -171,19 +182,37 @@ __device__ __forceinline__ unsigned peer_mask(int d)
 // round whose 32 digits are all equal (the usual case for the near-sorted keys of
 // a re-sort) ranks by lane, against a running count of that digit kept in a
 // register; other rounds rank against the warp's shared per-digit counts within
-// groups of equal digits (peer_mask).
+// groups of equal digits (peer_mask).  The ranked items are then placed in shared
+// memory in the tile's own sorted order (digit runs one after another) and written
+// out from there: consecutive threads write consecutive positions of each digit's
+// run, so the global writes come in whole sectors instead of scattered words.
+template <int RADIX>
+constexpr size_t scatter_smem_bytes()
+{
+    // per-warp digit counts, the tile's staged keys and indices, per-digit local
+    // starts and global deltas
+    return ((size_t)ST_WARPS * RADIX + 2 * (size_t)ST_TILE + 2 * (size_t)RADIX) * 4;
+}
+
 template <int RADIX>
 __global__ void __launch_bounds__(ST_THREADS, 3)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
               int shift, const uint32_t *__restrict__ offs, int64_t ntiles,
               uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
 {
-    extern __shared__ uint32_t wcount_flat[];  // [ST_WARPS][RADIX]
+    extern __shared__ uint32_t sm_flat[];
+    uint32_t *wcount_flat = sm_flat;                       // [ST_WARPS][RADIX]
+    uint32_t *s_key = wcount_flat + ST_WARPS * RADIX;     // [ST_TILE], tile order
+    uint32_t *s_idx = s_key + ST_TILE;                    // [ST_TILE]
+    uint32_t *s_lstart = s_idx + ST_TILE;                 // [RADIX] digit run starts in the tile
+    uint32_t *s_gdelta = s_lstart + RADIX;                // [RADIX] global start - local start
     auto wcount = [&](int w, int d) -> uint32_t & { return wcount_flat[w * RADIX + d]; };
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < ST_WARPS * RADIX; j += ST_THREADS) wcount_flat[j] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * ST_TILE + (int64_t)w * (ST_ITEMS * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * ST_TILE;
+    const int64_t base = tile0 + (int64_t)w * (ST_ITEMS * 32);
+    const int count = np - tile0 < ST_TILE ? (int)(np - tile0) : ST_TILE;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[ST_ITEMS], rank[ST_ITEMS];
 #pragma unroll
@@ -224,23 +253,64 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
     }
     if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
     __syncthreads();
+    // per digit: each warp's offset within the tile's run of that digit, and the run
+    // length (kept in s_lstart until the scan below)
     for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
-        uint32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
+        uint32_t run = 0;
         for (int ww = 0; ww < ST_WARPS; ++ww) {
             const uint32_t t = wcount(ww, d);
             wcount(ww, d) = run;
             run += t;
         }
+        s_lstart[d] = run;
     }
     __syncthreads();
+    // exclusive scan of the run lengths over the digits: RADIX / ST_THREADS (or one)
+    // consecutive digits per thread, then a warp scan and the warps' totals
+    {
+        constexpr int PER = RADIX >= ST_THREADS ? RADIX / ST_THREADS : 1;
+        const int d0 = threadIdx.x * PER;
+        uint32_t v[PER], run = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            v[k] = d0 + k < RADIX ? s_lstart[d0 + k] : 0u;
+            const uint32_t t = v[k];
+            v[k] = run;
+            run += t;
+        }
+        const uint32_t incl = warp_incl_scan(run);
+        __shared__ uint32_t s_wsum[ST_WARPS];
+        if (lane == 31) s_wsum[w] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int j = 0; j < w; ++j) wbase += s_wsum[j];
+        const uint32_t excl = wbase + incl - run;
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (d0 + k < RADIX) {
+                const uint32_t ls = v[k] + excl;
+                s_lstart[d0 + k] = ls;
+                s_gdelta[d0 + k] = offs[(int64_t)(d0 + k) * ntiles + blockIdx.x] - ls;
+            }
+    }
+    __syncthreads();
+    // the tile's items in its own sorted order
 #pragma unroll
     for (int r = 0; r < ST_ITEMS; ++r) {
         const int d = digit(r);
         if (d == NO_DIGIT) continue;
         const int64_t i = base + r * 32 + lane;
-        const uint32_t pos = wcount(w, d) + rank[r];
-        if (keys_out) keys_out[pos] = key[r];
-        idx_out[pos] = idx_in ? idx_in[i] : (uint32_t)i;
+        const uint32_t lp = s_lstart[d] + wcount(w, d) + rank[r];
+        s_key[lp] = key[r];
+        s_idx[lp] = idx_in ? idx_in[i] : (uint32_t)i;
+    }
+    __syncthreads();
+    // out in runs: local position q of digit d goes to global position gdelta[d] + q
+    for (int q = threadIdx.x; q < count; q += ST_THREADS) {
+        const uint32_t k = s_key[q];
+        const uint32_t pos = s_gdelta[(k >> shift) & (RADIX - 1)] + (uint32_t)q;
+        if (keys_out) keys_out[pos] = k;
+        idx_out[pos] = s_idx[q];
     }
 }
 
@@ -258,17 +328,6 @@ size_t sort_scan_tmp_len(size_t n)
         total += n;
     }
     return total + 1;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
 }
 
 // Exclusive scan of one tile held 16 consecutive items per thread; returns the
@@ -416,7 +475,7 @@ cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm
             note_launch();
             cudaError_t e2 = launch_exclusive_scan_u32(s.hist, s.hist, hist_len, s.scan_tmp, st);
             if (e2 != cudaSuccess) return e2;
-            const size_t smem = (size_t)ST_WARPS * RADIX * 4;
+            const size_t smem = scatter_smem_bytes<RADIX>();
             static std::atomic<unsigned long long> configured{0};
             e2 = once_per_device(configured, [smem] {
                 return cudaFuncSetAttribute(k_scatter<RADIX>,
