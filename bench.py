@@ -929,8 +929,10 @@ def run_batch(args, pk, torch, stream, embedded=False):
     e1.record(stream)
     torch.cuda.synchronize()
     pd_ms = e0.elapsed_time(e1) / 10
+    # per node: E read (4 B per axis), the int64 accumulator cleared and read back by
+    # the conversion (16 B), the FP32 right-hand side written (4 B)
     alg_bytes = sum(w.np_ * _bytes_per_particle(w.ndim, 2)
-                    + w.cells * (4 * w.ndim + 8 + 8 + 12) for w in ws)
+                    + w.cells * (4 * w.ndim + 8 + 8 + 4) for w in ws)
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (pd_ms * 1e-3) / 1e9
     # the field solve of every instance, and the full step

@@ -599,7 +599,6 @@ static ap_pic_status create_grid(ap_pic *h)
     f.nblocks = field_blocks(h->cells);
     const size_t c = (size_t)h->cells;
     TRY(alloc_n(h, &f.acc, c));
-    TRY(alloc_n(h, &f.rho, c));
     TRY(alloc_n(h, &f.b, c));
     TRY(alloc_n(h, &f.phi, c));
     TRY(alloc_n(h, &f.r, c));
@@ -818,17 +817,29 @@ static double bg_density(const ap_pic *h)
     return isnan(c) ? -h->cfg.q * h->cfg.weight * (double)h->np / h->V : c;
 }
 
+// rho_e = q w / dV * acc / 2^S: the charge density per unit of the accumulator.
+static double rho_scale(const ap_pic *h)
+{
+    return h->cfg.q * h->cfg.weight / h->dV * ldexp(1.0, -h->fx_bits);
+}
+
 // rho from the accumulator: rho_e = q w / dV * acc / 2^S;  b = rho_e - mean(rho_e)
 // (mean exact: every particle deposits 2^S, so mean(rho_e) = q w np / V).
 static ap_pic_status convert_rho(ap_pic *h)
 {
-    const double scale = h->cfg.q * h->cfg.weight / h->dV * ldexp(1.0, -h->fx_bits);
+    const double scale = rho_scale(h);
     const double mean_e = h->cfg.q * h->cfg.weight * (double)h->np / h->V;
     const int mk = stage_begin(h, AP_PIC_STAGE_RHO);
-    if (h->plain)
+    if (h->plain) {
         CU(h, launch_plain_rho_convert(h->f64, scale, bg_density(h), mean_e, h->stream));
-    else
-        CU(h, launch_rho_convert(h->f, scale, bg_density(h), mean_e, false, h->stream));
+    } else {
+        // the accumulator's mean, np 2^S / cells, as an integer part and a fraction
+        const unsigned long long M = (unsigned long long)h->np << h->fx_bits;  // < 2^62
+        const unsigned long long C = (unsigned long long)h->cells;
+        const unsigned long long q = M / C;
+        CU(h, launch_rho_convert(h->f, (long long)q, (float)((double)(M - q * C) / (double)C),
+                                 (float)scale, h->stream));
+    }
     stage_end(h, mk);
     return AP_PIC_OK;
 }
@@ -918,7 +929,7 @@ static ap_pic_status solve_field_fft(ap_pic *h)
     CU(h, launch_fft_poisson(h->fft, f.b, f.phi, h->stream));
     // refinement pass: the FP64 residual of the FP32 solve, solved again and added to
     // phi by the transform's last pass
-    CU(h, launch_residual64(f, mean_total, h->stream));
+    CU(h, launch_residual64(f, rho_scale(h), bg_density(h), mean_total, h->stream));
     CU(h, launch_fft_poisson(h->fft, f.b, f.phi, h->stream, true));
     CU(h, launch_efield(f, h->stream));
     stage_end(h, mk);
@@ -949,7 +960,7 @@ static ap_pic_status solve_field(ap_pic *h)
     CU(h, launch_cg_solve(f, f.b, f.phi, rtol, maxit, nullptr, f.iters, SCAL_CG_REL, true,
                           h->d_err, h->stream));
     // refinement pass
-    CU(h, launch_residual64(f, mean_total, h->stream));
+    CU(h, launch_residual64(f, rho_scale(h), bg_density(h), mean_total, h->stream));
     CU(h, cudaMemsetAsync(f.x, 0, (size_t)h->cells * 4, h->stream));
     CU(h, launch_cg_solve(f, f.b, f.x, REFINE_RTOL, maxit, f.iters, f.iters + 1, SCAL_CG_REL2,
                           false, h->d_err, h->stream));
@@ -1373,9 +1384,24 @@ extern "C" ap_pic_status ap_pic_step(ap_pic *h, int nsteps)
 extern "C" ap_pic_status ap_pic_get_rho(ap_pic *h, double *out)
 {
     if (!h || !out) return AP_PIC_ERR_ARG;
-    CU(h, cudaMemcpyAsync(out, h->plain ? h->f64.rho : h->f.rho, (size_t)h->cells * 8,
-                          cudaMemcpyDeviceToHost, h->stream));
-    return sync_check(h);
+    if (h->plain) {
+        CU(h, cudaMemcpyAsync(out, h->f64.rho, (size_t)h->cells * 8, cudaMemcpyDeviceToHost,
+                              h->stream));
+        return sync_check(h);
+    }
+    // the FP32 form keeps the charge as the int64 accumulator: rho = scale acc + bg,
+    // formed here in place (the same FP64 arithmetic as the device's residual)
+    CU(h, cudaMemcpyAsync(out, h->f.acc, (size_t)h->cells * 8, cudaMemcpyDeviceToHost,
+                          h->stream));
+    const ap_pic_status st = sync_check(h);
+    if (st != AP_PIC_OK) return st;
+    const double scale = rho_scale(h), bg = bg_density(h);
+    for (int64_t j = 0; j < h->cells; ++j) {
+        int64_t a;
+        memcpy(&a, &out[j], 8);
+        out[j] = scale * (double)a + bg;
+    }
+    return AP_PIC_OK;
 }
 
 extern "C" ap_pic_status ap_pic_get_rho_fx(ap_pic *h, int64_t *out)

@@ -49,6 +49,9 @@ struct BInst {
     double scale;       // q w / dV / 2^S
     double bg;          // background density
     double mean_e;      // mean electron density (exact)
+    long long mean_q;   // the accumulator's mean, np 2^S / cells: integer part
+    float mean_r;       // and fraction
+    float scale_f;      // scale in FP32
     int item0, nitems;  // this instance's cell items
     int tile0, ntiles;  // this instance's particle tiles (in its dimension class list)
     double dV;
@@ -61,8 +64,7 @@ struct CellItem {
 };
 
 struct BArena {
-    unsigned long long *acc;
-    double *rho;
+    unsigned long long *acc;  // charge (int64 fixed point); rho = scale acc + bg where read
     float *b, *phi, *r, *p, *q, *x;
     float2 *E;
 };
@@ -174,25 +176,20 @@ struct BCG {
     for (int k_ = blockIdx.x, it_ = 0; k_ < nact && ((it_ = act ? act[k_] : k_), true);      \
          k_ += gridDim.x)
 
+// b = scale (acc - mean(acc)) in FP32 per node, with no FP64 arithmetic (the exact
+// mean split into an integer part and a fraction; see launch_rho_convert).
 __global__ void __launch_bounds__(BT)
     k_b_convert(const CellItem *__restrict__ items, int nitems, const BInst *__restrict__ inst,
-                BArena A, double *__restrict__ ipart)
+                BArena A)
 {
     ITEM_LOOP
     {
         const CellItem ci = items[it_];
         const BInst in = inst[ci.inst];
-        double isum = 0.0;
         for (int k = threadIdx.x; k < ci.count; k += BT) {
             const int64_t a = ci.start + k;
-            const long long v = (long long)A.acc[a];
-            isum += (double)v;
-            const double re = in.scale * (double)v;
-            A.rho[a] = re + in.bg;
-            A.b[a] = (float)(re - in.mean_e);
+            A.b[a] = in.scale_f * (i64_to_f32((long long)A.acc[a] - in.mean_q) - in.mean_r);
         }
-        isum = bblock_sum(isum);
-        if (threadIdx.x == 0) ipart[it_] = isum;
     }
 }
 
@@ -362,7 +359,8 @@ __global__ void __launch_bounds__(BT)
             const int64_t a = ci.start + k;
             int j[2];
             bcoords(a - in.node0, in, j);
-            A.b[a] = (float)((A.rho[a] - mean_total) - bneg_lap64(A.phi, in, a, j));
+            const double rho = in.scale * (double)(long long)A.acc[a] + in.bg;
+            A.b[a] = (float)((rho - mean_total) - bneg_lap64(A.phi, in, a, j));
         }
     }
 }
@@ -516,7 +514,6 @@ struct BatchGrid {
     BArena A;
     BCG cg;
     double *fepart;
-    double *ipart;
     long long *ipart_ll;
     int nblocks;
     const int *act;  // items the CG iterations walk (null: all), nact of them
@@ -1039,7 +1036,7 @@ int grid_blocks(const ap_pic_batch *b)
 ap_pic_status batch_convert(ap_pic_batch *b)
 {
     BatchGrid &G = b->G;
-    k_b_convert<<<grid_blocks(b), BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A, G.ipart);
+    k_b_convert<<<grid_blocks(b), BT, 0, b->stream>>>(G.items, G.nitems, G.inst, G.A);
     note_launch();
     BCU(b, cudaGetLastError());
     return AP_PIC_OK;
@@ -1359,6 +1356,11 @@ ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const 
         in.scale = c.q * c.weight / dV * ldexp(1.0, -b->fx_bits[i]);
         in.mean_e = c.q * c.weight * (double)np[i] / V;
         in.bg = isnan(c.rho_background) ? -in.mean_e : c.rho_background;
+        const unsigned long long M = (unsigned long long)np[i] << b->fx_bits[i];  // < 2^62
+        const unsigned long long C = (unsigned long long)in.cells;
+        in.mean_q = (long long)(M / C);
+        in.mean_r = (float)((double)(M - (M / C) * C) / (double)C);
+        in.scale_f = (float)in.scale;
     }
     BatchGrid &G = b->G;
     G.nitems = (int)b->items.size();
@@ -1367,7 +1369,6 @@ ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const 
     BTRY(upload(b->binst, &G.inst));
     const size_t nn = (size_t)(nodes > 0 ? nodes : 1);
     BTRY(balloc(b, &G.A.acc, nn));
-    BTRY(balloc(b, &G.A.rho, nn));
     BTRY(balloc(b, &G.A.b, nn));
     BTRY(balloc(b, &G.A.phi, nn));
     BTRY(balloc(b, &G.A.r, nn));
@@ -1392,7 +1393,6 @@ ap_pic_status load_body(ap_pic_batch *b, const int64_t *np, const double *const 
     G.act = nullptr;
     G.nact = G.nitems;
     BTRY(balloc(b, &G.fepart, (size_t)G.nitems + 1));
-    BTRY(balloc(b, &G.ipart, (size_t)G.nitems + 1));
     BTRY(balloc(b, &G.ipart_ll, (size_t)G.nitems + 1));
     BTRY(balloc(b, &b->d_diag, (size_t)n * 8));
     BTRY(balloc(b, &b->d_isum, (size_t)n));
@@ -1559,9 +1559,18 @@ extern "C" ap_pic_status ap_pic_batch_get_rho(ap_pic_batch *b, int i, double *ou
 {
     BTRY(need_loaded(b, i));
     if (!out) return bfail(b, AP_PIC_ERR_ARG, "out is NULL");
-    BCU(b, cudaMemcpyAsync(out, b->G.A.rho + b->node0[i], (size_t)b->cells[i] * 8,
+    // rho = scale acc + bg, formed here in place from the int64 accumulator
+    BCU(b, cudaMemcpyAsync(out, b->G.A.acc + b->node0[i], (size_t)b->cells[i] * 8,
                            cudaMemcpyDeviceToHost, b->stream));
-    return batch_sync_check(b);
+    const ap_pic_status st = batch_sync_check(b);
+    if (st != AP_PIC_OK) return st;
+    const BInst &in = b->binst[i];
+    for (int64_t j = 0; j < b->cells[i]; ++j) {
+        int64_t a;
+        memcpy(&a, &out[j], 8);
+        out[j] = in.scale * (double)a + in.bg;
+    }
+    return AP_PIC_OK;
 }
 
 extern "C" ap_pic_status ap_pic_batch_get_E(ap_pic_batch *b, int i, double *out)

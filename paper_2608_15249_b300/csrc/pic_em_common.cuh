@@ -142,20 +142,4 @@ __device__ __forceinline__ void em_block_diag(float ke, const float *mom, double
     }
 }
 
-// An int64 as FP32 with no conversion instruction (those issue on this GPU's slow FP64
-// pipe): the magnitude (below 2^62) in three 22-bit parts, each of which becomes a
-// float exactly by the magic-number trick (bits of 1.5 * 2^23 plus the integer, less
-// 1.5 * 2^23, exact below 2^22); the parts, all of one sign, are summed with two
-// roundings, then the sign is applied.
-__device__ __forceinline__ float i64_to_f32(long long a)
-{
-    const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
-    const int lo = (int)(m & 0x3FFFFF), mid = (int)((m >> 22) & 0x3FFFFF), hi = (int)(m >> 44);
-    const float flo = __int_as_float(RND_MAGIC_I + lo) - RND_MAGIC_F;
-    const float fmid = __int_as_float(RND_MAGIC_I + mid) - RND_MAGIC_F;
-    const float fhi = __int_as_float(RND_MAGIC_I + hi) - RND_MAGIC_F;
-    const float v = fmaf(fhi, 17592186044416.0f, fmaf(fmid, 4194304.0f, flo));  // 2^44, 2^22
-    return a < 0 ? -v : v;
-}
-
 }  // namespace apk

@@ -127,25 +127,25 @@ __device__ __forceinline__ float neg_lap(const float *__restrict__ u, int64_t id
 // ---- charge conversion ----------------------------------------------------------------------
 
 __global__ void __launch_bounds__(FT)
-    k_rho_convert(FieldBufs f, double scale, double bg, double mean_e)
+    k_rho_convert(FieldBufs f, long long mean_q, float mean_r, float scale)
 {
     long long isum = 0;
     for (int64_t j = (int64_t)blockIdx.x * FT + threadIdx.x; j < f.cells;
          j += (int64_t)gridDim.x * FT) {
         const long long a = (long long)f.acc[j];
         isum += a;
-        const double re = scale * (double)a;
-        f.rho[j] = re + bg;
-        f.b[j] = (float)(re - mean_e);
+        // acc - mean: the integer difference is exact, its float rounds once, then the
+        // fraction of the mean and the scale (no cancellation of large terms)
+        f.b[j] = scale * (i64_to_f32(a - mean_q) - mean_r);
     }
     const long long t = block_sum_ll(isum);
     if (threadIdx.x == 0) f.isum_part[blockIdx.x] = t;
 }
 
-cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mean_e, bool,
+cudaError_t launch_rho_convert(FieldBufs &f, long long mean_q, float mean_r, float scale,
                                cudaStream_t st)
 {
-    k_rho_convert<<<f.nblocks, FT, 0, st>>>(f, scale, bg, mean_e);
+    k_rho_convert<<<f.nblocks, FT, 0, st>>>(f, mean_q, mean_r, scale);
     note_launch();
     return cudaGetLastError();
 }
@@ -475,7 +475,8 @@ __device__ __forceinline__ double neg_lap64(const float *__restrict__ u, int64_t
 }
 
 __global__ void __launch_bounds__(FT)
-    k_residual64(FieldBufs f, double i0, double i1, double i2, double mean_total)
+    k_residual64(FieldBufs f, double i0, double i1, double i2, double scale, double bg,
+                 double mean_total)
 {
     const double idx2[3] = {i0, i1, i2};
     double rr = 0.0, bb = 0.0;
@@ -483,7 +484,8 @@ __global__ void __launch_bounds__(FT)
          id += (int64_t)gridDim.x * FT) {
         int j[3];
         node_coords(id, f, j);
-        const double bj = f.rho[id] - mean_total;
+        const double rho = scale * (double)(long long)f.acc[id] + bg;
+        const double bj = rho - mean_total;
         const double rj = bj - neg_lap64(f.phi, id, j, f, idx2);
         f.b[id] = (float)rj;
         rr += rj * rj;
@@ -519,11 +521,12 @@ __global__ void __launch_bounds__(FT)
     }
 }
 
-cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st)
+cudaError_t launch_residual64(FieldBufs &f, double scale, double bg, double mean_total,
+                              cudaStream_t st)
 {
     double i2[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < f.ndim; ++a) i2[a] = 1.0 / (f.dx[a] * f.dx[a]);
-    k_residual64<<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], mean_total);
+    k_residual64<<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], scale, bg, mean_total);
     note_launch();
     return cudaGetLastError();
 }

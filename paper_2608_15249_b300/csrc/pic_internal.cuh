@@ -98,6 +98,22 @@ struct ParticlesF32 {
     uint32_t *id;      // [stride] particle ids (load order), only with collisions; else null
 };
 
+// An int64 as FP32 with no conversion instruction (those issue on this GPU's slow FP64
+// pipe): the magnitude (below 2^62) in three 22-bit parts, each of which becomes a
+// float exactly by the magic-number trick (bits of 1.5 * 2^23 plus the integer, less
+// 1.5 * 2^23, exact below 2^22); the parts, all of one sign, are summed with two
+// roundings, then the sign is applied.
+__device__ __forceinline__ float i64_to_f32(long long a)
+{
+    const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    const int lo = (int)(m & 0x3FFFFF), mid = (int)((m >> 22) & 0x3FFFFF), hi = (int)(m >> 44);
+    const float flo = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+    const float fmid = __int_as_float(0x4B400000 + mid) - 12582912.0f;
+    const float fhi = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+    const float v = fmaf(fhi, 17592186044416.0f, fmaf(fmid, 4194304.0f, flo));  // 2^44, 2^22
+    return a < 0 ? -v : v;
+}
+
 // Component stride for np particles.
 inline int64_t soa_stride(int64_t np) { return ((np > 0 ? np : 1) + 63) / 64 * 64; }
 
@@ -238,8 +254,8 @@ struct FieldBufs {
     int64_t cells;
     double dx[3];
     unsigned long long *acc;   // int64 fixed point
-    double *rho;               // total charge density (FP64)
-    float *b;                  // rho - mean(rho), FP32
+    float *b;                  // rho - mean(rho), FP32 (rho itself, in FP64, is formed
+                               // from acc where it is read)
     float *phi, *r, *p, *q;    // CG vectors
     float *p2;                 // second buffer of the direction (cooperative solve)
     unsigned *gbar;            // grid barrier of the cooperative solve (count, generation)
@@ -260,9 +276,13 @@ struct FieldBufs {
 
 int field_blocks(int64_t cells);
 
-// rho = scale * acc + bg;  b = scale * acc - mean_e;  partial sums of acc.
-cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mean_e,
-                               bool zero_acc, cudaStream_t st);
+// b = scale (acc - mean(acc)) in FP32, with mean(acc) = mean_q + mean_r (its integer
+// part and fraction: every particle deposits exactly 2^S, so the mean is known before
+// the deposit), formed without FP64 arithmetic; partial sums of acc.  rho itself,
+// scale acc + bg in FP64, is formed where it is read (the refinement's residual, the
+// read-back).
+cudaError_t launch_rho_convert(FieldBufs &f, long long mean_q, float mean_r, float scale,
+                               cudaStream_t st);
 // The whole Jacobi-PCG solve of A x = b (warm start x) as one cooperative launch,
 // convergence tested on the device: iterations to *iters, final relative residual
 // to scal[relres_slot]; the cap is maxit - *it_used when it_used is given; latch:
@@ -271,9 +291,10 @@ cudaError_t launch_rho_convert(FieldBufs &f, double scale, double bg, double mea
 cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol, int maxit,
                             const int *it_used, int *iters, int relres_slot, bool latch,
                             int *err_flags, cudaStream_t st);
-// Refinement: b = (float)(rho - mean - A phi) computed in FP64, and its relative norm
-// |rho - mean - A phi| / |rho - mean| into scal[SCAL_TRUE_REL].
-cudaError_t launch_residual64(FieldBufs &f, double mean_total, cudaStream_t st);
+// Refinement: b = (float)(rho - mean - A phi) computed in FP64 with rho = scale acc +
+// bg, and its relative norm |rho - mean - A phi| / |rho - mean| into scal[SCAL_TRUE_REL].
+cudaError_t launch_residual64(FieldBufs &f, double scale, double bg, double mean_total,
+                              cudaStream_t st);
 // phi += x
 cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st);
 enum : int { SCAL_TRUE_REL = 4, SCAL_BNORM64 = 5, SCAL_CG_REL = 3, SCAL_CG_REL2 = 6 };
