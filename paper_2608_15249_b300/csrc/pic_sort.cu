@@ -186,15 +186,16 @@ __device__ __forceinline__ unsigned peer_mask(int d)
 // memory in the tile's own sorted order (digit runs one after another) and written
 // out from there: consecutive threads write consecutive positions of each digit's
 // run, so the global writes come in whole sectors instead of scattered words.
-template <int RADIX>
+template <int RADIX, bool STAGED>
 constexpr size_t scatter_smem_bytes()
 {
-    // per-warp digit counts, the tile's staged keys and indices, per-digit local
+    // per-warp digit counts; staged: the tile's keys and indices, per-digit local
     // starts and global deltas
-    return ((size_t)ST_WARPS * RADIX + 2 * (size_t)ST_TILE + 2 * (size_t)RADIX) * 4;
+    return STAGED ? ((size_t)ST_WARPS * RADIX + 2 * (size_t)ST_TILE + 2 * (size_t)RADIX) * 4
+                  : (size_t)ST_WARPS * RADIX * 4;
 }
 
-template <int RADIX>
+template <int RADIX, bool STAGED>
 __global__ void __launch_bounds__(ST_THREADS, 3)
     k_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t np,
               int shift, const uint32_t *__restrict__ offs, int64_t ntiles,
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
 {
     extern __shared__ uint32_t sm_flat[];
     uint32_t *wcount_flat = sm_flat;                       // [ST_WARPS][RADIX]
-    uint32_t *s_key = wcount_flat + ST_WARPS * RADIX;     // [ST_TILE], tile order
+    uint32_t *s_key = wcount_flat + ST_WARPS * RADIX;     // [ST_TILE], tile order (staged)
     uint32_t *s_idx = s_key + ST_TILE;                    // [ST_TILE]
     uint32_t *s_lstart = s_idx + ST_TILE;                 // [RADIX] digit run starts in the tile
     uint32_t *s_gdelta = s_lstart + RADIX;                // [RADIX] global start - local start
@@ -253,64 +254,87 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
     }
     if (cd != NO_DIGIT && lane == 0) wcount(w, cd) = cc;
     __syncthreads();
-    // per digit: each warp's offset within the tile's run of that digit, and the run
-    // length (kept in s_lstart until the scan below)
-    for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
-        uint32_t run = 0;
-        for (int ww = 0; ww < ST_WARPS; ++ww) {
-            const uint32_t t = wcount(ww, d);
-            wcount(ww, d) = run;
-            run += t;
-        }
-        s_lstart[d] = run;
-    }
-    __syncthreads();
-    // exclusive scan of the run lengths over the digits: RADIX / ST_THREADS (or one)
-    // consecutive digits per thread, then a warp scan and the warps' totals
-    {
-        constexpr int PER = RADIX >= ST_THREADS ? RADIX / ST_THREADS : 1;
-        const int d0 = threadIdx.x * PER;
-        uint32_t v[PER], run = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            v[k] = d0 + k < RADIX ? s_lstart[d0 + k] : 0u;
-            const uint32_t t = v[k];
-            v[k] = run;
-            run += t;
-        }
-        const uint32_t incl = warp_incl_scan(run);
-        __shared__ uint32_t s_wsum[ST_WARPS];
-        if (lane == 31) s_wsum[w] = incl;
-        __syncthreads();
-        uint32_t wbase = 0;
-        for (int j = 0; j < w; ++j) wbase += s_wsum[j];
-        const uint32_t excl = wbase + incl - run;
-#pragma unroll
-        for (int k = 0; k < PER; ++k)
-            if (d0 + k < RADIX) {
-                const uint32_t ls = v[k] + excl;
-                s_lstart[d0 + k] = ls;
-                s_gdelta[d0 + k] = offs[(int64_t)(d0 + k) * ntiles + blockIdx.x] - ls;
+    if constexpr (!STAGED) {
+        // each item straight to its global position (the digit runs of a pass whose
+        // rounds are mostly uniform already come in long runs)
+        for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
+            uint32_t run = offs[(int64_t)d * ntiles + blockIdx.x];
+            for (int ww = 0; ww < ST_WARPS; ++ww) {
+                const uint32_t t = wcount(ww, d);
+                wcount(ww, d) = run;
+                run += t;
             }
-    }
-    __syncthreads();
-    // the tile's items in its own sorted order
+        }
+        __syncthreads();
 #pragma unroll
-    for (int r = 0; r < ST_ITEMS; ++r) {
-        const int d = digit(r);
-        if (d == NO_DIGIT) continue;
-        const int64_t i = base + r * 32 + lane;
-        const uint32_t lp = s_lstart[d] + wcount(w, d) + rank[r];
-        s_key[lp] = key[r];
-        s_idx[lp] = idx_in ? idx_in[i] : (uint32_t)i;
-    }
-    __syncthreads();
-    // out in runs: local position q of digit d goes to global position gdelta[d] + q
-    for (int q = threadIdx.x; q < count; q += ST_THREADS) {
-        const uint32_t k = s_key[q];
-        const uint32_t pos = s_gdelta[(k >> shift) & (RADIX - 1)] + (uint32_t)q;
-        if (keys_out) keys_out[pos] = k;
-        idx_out[pos] = s_idx[q];
+        for (int r = 0; r < ST_ITEMS; ++r) {
+            const int d = digit(r);
+            if (d == NO_DIGIT) continue;
+            const int64_t i = base + r * 32 + lane;
+            const uint32_t pos = wcount(w, d) + rank[r];
+            if (keys_out) keys_out[pos] = key[r];
+            idx_out[pos] = idx_in ? idx_in[i] : (uint32_t)i;
+        }
+    } else {
+        // per digit: each warp's offset within the tile's run of that digit, and the run
+        // length (kept in s_lstart until the scan below)
+        for (int d = threadIdx.x; d < RADIX; d += ST_THREADS) {
+            uint32_t run = 0;
+            for (int ww = 0; ww < ST_WARPS; ++ww) {
+                const uint32_t t = wcount(ww, d);
+                wcount(ww, d) = run;
+                run += t;
+            }
+            s_lstart[d] = run;
+        }
+        __syncthreads();
+        // exclusive scan of the run lengths over the digits: RADIX / ST_THREADS (or one)
+        // consecutive digits per thread, then a warp scan and the warps' totals
+        {
+            constexpr int PER = RADIX >= ST_THREADS ? RADIX / ST_THREADS : 1;
+            const int d0 = threadIdx.x * PER;
+            uint32_t v[PER], run = 0;
+    #pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                v[k] = d0 + k < RADIX ? s_lstart[d0 + k] : 0u;
+                const uint32_t t = v[k];
+                v[k] = run;
+                run += t;
+            }
+            const uint32_t incl = warp_incl_scan(run);
+            __shared__ uint32_t s_wsum[ST_WARPS];
+            if (lane == 31) s_wsum[w] = incl;
+            __syncthreads();
+            uint32_t wbase = 0;
+            for (int j = 0; j < w; ++j) wbase += s_wsum[j];
+            const uint32_t excl = wbase + incl - run;
+    #pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (d0 + k < RADIX) {
+                    const uint32_t ls = v[k] + excl;
+                    s_lstart[d0 + k] = ls;
+                    s_gdelta[d0 + k] = offs[(int64_t)(d0 + k) * ntiles + blockIdx.x] - ls;
+                }
+        }
+        __syncthreads();
+        // the tile's items in its own sorted order
+    #pragma unroll
+        for (int r = 0; r < ST_ITEMS; ++r) {
+            const int d = digit(r);
+            if (d == NO_DIGIT) continue;
+            const int64_t i = base + r * 32 + lane;
+            const uint32_t lp = s_lstart[d] + wcount(w, d) + rank[r];
+            s_key[lp] = key[r];
+            s_idx[lp] = idx_in ? idx_in[i] : (uint32_t)i;
+        }
+        __syncthreads();
+        // out in runs: local position q of digit d goes to global position gdelta[d] + q
+        for (int q = threadIdx.x; q < count; q += ST_THREADS) {
+            const uint32_t k = s_key[q];
+            const uint32_t pos = s_gdelta[(k >> shift) & (RADIX - 1)] + (uint32_t)q;
+            if (keys_out) keys_out[pos] = k;
+            idx_out[pos] = s_idx[q];
+        }
     }
 }
 
@@ -450,6 +474,23 @@ cudaError_t launch_sort_perm(const GridParams &g, const int brick[3], int key_bi
     return launch_sort_keys(key_bits, np, s, perm_slot, st);
 }
 
+template <int RADIX, bool STAGED>
+static cudaError_t launch_scatter(const uint32_t *keys_in, const uint32_t *idx_in, int64_t np,
+                                  int shift, const uint32_t *offs, int64_t ntiles,
+                                  uint32_t *keys_out, uint32_t *idx_out, cudaStream_t st)
+{
+    constexpr size_t smem = scatter_smem_bytes<RADIX, STAGED>();
+    static std::atomic<unsigned long long> configured{0};
+    const cudaError_t e = once_per_device(configured, [] {
+        return cudaFuncSetAttribute(k_scatter<RADIX, STAGED>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    k_scatter<RADIX, STAGED><<<(unsigned)ntiles, ST_THREADS, smem, st>>>(
+        keys_in, idx_in, np, shift, offs, ntiles, keys_out, idx_out);
+    return cudaSuccess;
+}
+
 cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm_slot,
                              cudaStream_t st)
 {
@@ -475,15 +516,13 @@ cudaError_t launch_sort_keys(int key_bits, int64_t np, SortScratch &s, int *perm
             note_launch();
             cudaError_t e2 = launch_exclusive_scan_u32(s.hist, s.hist, hist_len, s.scan_tmp, st);
             if (e2 != cudaSuccess) return e2;
-            const size_t smem = scatter_smem_bytes<RADIX>();
-            static std::atomic<unsigned long long> configured{0};
-            e2 = once_per_device(configured, [smem] {
-                return cudaFuncSetAttribute(k_scatter<RADIX>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            });
+            // the last pass (high digits: long runs of equal digits in a re-sort)
+            // writes directly; the others stage their output in shared memory
+            e2 = last ? launch_scatter<RADIX, false>(s.keys[cur], idx_in, np, shift, s.hist,
+                                                     ntiles, keys_out, s.idx[cur ^ 1], st)
+                      : launch_scatter<RADIX, true>(s.keys[cur], idx_in, np, shift, s.hist,
+                                                    ntiles, keys_out, s.idx[cur ^ 1], st);
             if (e2 != cudaSuccess) return e2;
-            k_scatter<RADIX><<<(unsigned)ntiles, ST_THREADS, smem, st>>>(
-                s.keys[cur], idx_in, np, shift, s.hist, ntiles, keys_out, s.idx[cur ^ 1]);
             note_launch();
             return cudaGetLastError();
         };
