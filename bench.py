@@ -668,11 +668,11 @@ def bench_cpml(args, pk, torch, stream, peak, peak_kind, n=2048, npml=16, steps=
     """The field-only electromagnetic step on a non-periodic n x n grid with a
     convolutional PML of npml cells on every side (c = 1, dt = 0.5, a prescribed
     current at the centre): CUDA-event time per step and its roofline.  Algorithmic
-    bytes per node: the current conversion (24 B int64 read and cleared, 12 B prescribed
-    current read, 12 B FP32 current written), two B half steps (12 B E read, 24 B B read
-    and written, each) and the E step (12 B B, 12 B J read, 24 B E read and written),
-    204 B; plus, in the layers, the eight psi arrays read and written (64 B).  Beside
-    it, the oracle's CpmlField step on a 512 x 512 grid."""
+    bytes per node: two B half steps (12 B E read, 24 B B read and written, each) and
+    the E step (12 B B read, 24 B E read and written, the int64 current read and
+    cleared, 24 B each, 12 B prescribed current read), 168 B; plus, in the layers, the eight psi
+    arrays read and written (64 B).  Beside it, the oracle's CpmlField step on a
+    512 x 512 grid."""
     import oracle
 
     cfg = pk.make_config(2, (n, n), dt=0.5, nv=3, em=1, c_light=1.0, em_boundary=1,
@@ -693,8 +693,8 @@ def bench_cpml(args, pk, torch, stream, peak, peak_kind, n=2048, npml=16, steps=
     nodes = n * n
     layer_nodes = nodes - (n - 2 * npml) ** 2
     out = {"ms_per_step": ms, "nodes": nodes, "node_steps_per_s": nodes / (ms * 1e-3),
-           "roofline": _roofline(nodes * 204 + layer_nodes * 64, ms,
-                                 "CPML field step (k_em_j_convert, k_cpml_b x 2, k_cpml_e)",
+           "roofline": _roofline(nodes * 168 + layer_nodes * 64, ms,
+                                 "CPML field step (k_cpml_b x 2, k_cpml_e with the current conversion)",
                                  peak, peak_kind),
            "workload": f"non-periodic {n}x{n} grid, {npml}-cell CPML, c = 1, dt = 0.5, "
                        "prescribed current, fields only"}

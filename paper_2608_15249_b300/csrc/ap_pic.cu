@@ -639,11 +639,9 @@ static ap_pic_status create_grid(ap_pic *h)
         CU(h, cudaMemsetAsync(h->d_absorbed, 0, 8, h->stream));
         TRY(alloc_n(h, &h->emb.E, c * 3));
         TRY(alloc_n(h, &h->emb.B, c * 3));
-        TRY(alloc_n(h, &h->emb.Jf, c * 3));
         TRY(alloc_n(h, &h->emb.J, c * 3));
         CU(h, cudaMemsetAsync(h->emb.E, 0, c * 12, h->stream));
         CU(h, cudaMemsetAsync(h->emb.B, 0, c * 12, h->stream));
-        CU(h, cudaMemsetAsync(h->emb.Jf, 0, c * 12, h->stream));
         CU(h, cudaMemsetAsync(h->emb.J, 0, c * 24, h->stream));
         for (int a = 0; a < 3; ++a) h->emb.B0[a] = (float)h->cfg.B0[a];
         if (h->cfg.em_boundary == 1) TRY(create_cpml(h));

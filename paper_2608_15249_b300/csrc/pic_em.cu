@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(EM_THREADS)
 }
 
 __global__ void __launch_bounds__(EM_THREADS)
-    k_yee_e(GridParams g, const float *__restrict__ B, const float *__restrict__ J,
-            float *__restrict__ E, float c2dtdx, float c2dtdy, float dt)
+    k_yee_e(GridParams g, const float *__restrict__ B, JTake jt, float *__restrict__ E,
+            float c2dtdx, float c2dtdy, float dt)
 {
     const int n0 = g.n[0], n1 = g.n[1];
     const int64_t cells = (int64_t)n0 * n1;
@@ -492,31 +492,14 @@ __global__ void __launch_bounds__(EM_THREADS)
         const int64_t im = (i == 0 ? n0 - 1 : i - 1) + (int64_t)n0 * j;
         const int64_t jm = i + (int64_t)n0 * (j == 0 ? n1 - 1 : j - 1);
         const float bz = B[2 * cells + id];
-        E[id] += c2dtdy * (bz - B[2 * cells + jm]) - dt * J[id];
-        E[cells + id] += -c2dtdx * (bz - B[2 * cells + im]) - dt * J[cells + id];
+        float J[3];
+        get_j(jt, cells, id, J);
+        E[id] += c2dtdy * (bz - B[2 * cells + jm]) - dt * J[0];
+        E[cells + id] += -c2dtdx * (bz - B[2 * cells + im]) - dt * J[1];
         E[2 * cells + id] += c2dtdx * (B[cells + id] - B[cells + im]) -
-                             c2dtdy * (B[id] - B[jm]) - dt * J[2 * cells + id];
+                             c2dtdy * (B[id] - B[jm]) - dt * J[2];
+        clear_j(jt, cells, id);
     }
-}
-
-// J = the fixed-point weights times their factors: Jx -(qw / (dy dt)), Jy
-// -(qw / (dx dt)), Jz qw / (dx dy), each divided by the fixed-point scale; the
-// accumulator is cleared for the next step.
-__global__ void __launch_bounds__(EM_THREADS)
-    k_em_j_convert(int64_t cells, unsigned long long *__restrict__ Jacc, float *__restrict__ J,
-                   const float *__restrict__ Jext, float fx, float fy, float fz)
-{
-    const float f[3] = {fx, fy, fz};
-    for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
-         id += (int64_t)gridDim.x * EM_THREADS)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const long long a = (long long)Jacc[k * cells + id];
-            float j = f[k] * i64_to_f32(a);
-            if (Jext) j += Jext[k * cells + id];
-            J[k * cells + id] = j;
-            Jacc[k * cells + id] = 0ull;
-        }
 }
 
 // ---- convolutional PML on a non-periodic grid (Roden and Gedney) ----------------------------
@@ -566,13 +549,12 @@ __global__ void __launch_bounds__(EM_THREADS)
 }
 
 __global__ void __launch_bounds__(EM_THREADS)
-    k_cpml_e(GridParams g, EmBufs em, float c2, float dt, float idx, float idy)
+    k_cpml_e(GridParams g, EmBufs em, JTake jt, float c2, float dt, float idx, float idy)
 {
     const int n0 = g.n[0], n1 = g.n[1];
     const int64_t cells = (int64_t)n0 * n1;
     const float *Bx = em.B, *By = em.B + cells, *Bz = em.B + 2 * cells;
     float *Ex = em.E, *Ey = em.E + cells, *Ez = em.E + 2 * cells;
-    const float *J = em.Jf;
     for (int64_t id = (int64_t)blockIdx.x * EM_THREADS + threadIdx.x; id < cells;
          id += (int64_t)gridDim.x * EM_THREADS) {
         int i, j;
@@ -595,13 +577,16 @@ __global__ void __launch_bounds__(EM_THREADS)
             em.psie[2][id] = p2;
         }
         const bool xb = i == 0 || i == n0 - 1, yb = j == 0 || j == n1 - 1;
-        const float ex = Ex[id] + dt * (c2 * (em.pe[5][j] * dyBz + p0) - J[id]);
-        const float ey = Ey[id] + dt * (-c2 * (em.pe[2][i] * dxBz + p1) - J[cells + id]);
+        float J[3];
+        get_j(jt, cells, id, J);
+        const float ex = Ex[id] + dt * (c2 * (em.pe[5][j] * dyBz + p0) - J[0]);
+        const float ey = Ey[id] + dt * (-c2 * (em.pe[2][i] * dxBz + p1) - J[1]);
         const float ez = Ez[id] + dt * (c2 * ((em.pe[2][i] * dxBy + p2) - (em.pe[5][j] * dyBx + p3)) -
-                                        J[2 * cells + id]);
+                                        J[2]);
         Ex[id] = (yb || i == n0 - 1) ? 0.0f : ex;
         Ey[id] = (xb || j == n1 - 1) ? 0.0f : ey;
         Ez[id] = (xb || yb) ? 0.0f : ez;
+        clear_j(jt, cells, id);
     }
 }
 
@@ -877,13 +862,15 @@ cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em
     return cudaGetLastError();
 }
 
-cudaError_t launch_em_j_convert(int64_t cells, const EmBufs &em, double fx, double fy,
-                                double fz, cudaStream_t st)
+JTake em_jtake(const EmBufs &em, double fx, double fy, double fz)
 {
-    k_em_j_convert<<<em_blocks(cells), EM_THREADS, 0, st>>>(cells, em.J, em.Jf, em.Jext, (float)fx,
-                                                           (float)fy, (float)fz);
-    note_launch();
-    return cudaGetLastError();
+    JTake t;
+    t.acc = em.J;
+    t.ext = em.Jext;
+    t.f[0] = (float)fx;
+    t.f[1] = (float)fy;
+    t.f[2] = (float)fz;
+    return t;
 }
 
 cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, double dy,
@@ -891,21 +878,22 @@ cudaError_t launch_em_fields(const GridParams &g, const EmBufs &em, double dx, d
 {
     const int64_t cells = (int64_t)g.n[0] * g.n[1];
     const int nb = em_blocks(cells);
-    cudaError_t e = launch_em_j_convert(cells, em, -qw / (dy * dt) / J_SCALE,
-                                        -qw / (dx * dt) / J_SCALE, qw / (dx * dy) / J_SCALE, st);
-    if (e != cudaSuccess) return e;
+    // J: the accumulated weights times -(qw / (dy dt)), -(qw / (dx dt)), qw / (dx dy),
+    // each divided by the fixed-point scale, taken (and cleared) by the E update
+    const JTake jt = em_jtake(em, -qw / (dy * dt) / J_SCALE, -qw / (dx * dt) / J_SCALE,
+                              qw / (dx * dy) / J_SCALE);
     if (em.pb[0]) {
         // non-periodic grid with the absorbing layer
         const float idx = (float)(1.0 / dx), idy = (float)(1.0 / dy);
         k_cpml_b<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(0.5 * dt), idx, idy);
-        k_cpml_e<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(c * c), (float)dt, idx, idy);
+        k_cpml_e<<<nb, EM_THREADS, 0, st>>>(g, em, jt, (float)(c * c), (float)dt, idx, idy);
         k_cpml_b<<<nb, EM_THREADS, 0, st>>>(g, em, (float)(0.5 * dt), idx, idy);
         note_launch(3);
         return cudaGetLastError();
     }
     const float hdx = (float)(0.5 * dt / dx), hdy = (float)(0.5 * dt / dy);
     k_yee_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hdx, hdy);
-    k_yee_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, em.Jf, em.E, (float)(c * c * dt / dx),
+    k_yee_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, jt, em.E, (float)(c * c * dt / dx),
                                        (float)(c * c * dt / dy), (float)dt);
     k_yee_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hdx, hdy);
     note_launch(3);

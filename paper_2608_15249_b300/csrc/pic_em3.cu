@@ -567,8 +567,8 @@ __global__ void __launch_bounds__(EM_THREADS)
 
 // Ampere: E += dt (c^2 curl B - J), curl B by backward differences at the E positions.
 __global__ void __launch_bounds__(EM_THREADS)
-    k_yee3_e(GridParams g, const float *__restrict__ B, const float *__restrict__ J,
-             float *__restrict__ E, float cx, float cy, float cz, float dt)
+    k_yee3_e(GridParams g, const float *__restrict__ B, JTake jt, float *__restrict__ E,
+             float cx, float cy, float cz, float dt)
 {
     const int *n = g.n;
     const int64_t cells = (int64_t)n[0] * n[1] * n[2];
@@ -581,9 +581,12 @@ __global__ void __launch_bounds__(EM_THREADS)
         const int64_t jm = node3(n, c[0], c[1] == 0 ? n[1] - 1 : c[1] - 1, c[2]);
         const int64_t km = node3(n, c[0], c[1], c[2] == 0 ? n[2] - 1 : c[2] - 1);
         const float bx = Bx[id], by = By[id], bz = Bz[id];
-        E[id] += cy * (bz - Bz[jm]) - cz * (by - By[km]) - dt * J[id];
-        E[cells + id] += cz * (bx - Bx[km]) - cx * (bz - Bz[im]) - dt * J[cells + id];
-        E[2 * cells + id] += cx * (by - By[im]) - cy * (bx - Bx[jm]) - dt * J[2 * cells + id];
+        float J[3];
+        get_j(jt, cells, id, J);
+        E[id] += cy * (bz - Bz[jm]) - cz * (by - By[km]) - dt * J[0];
+        E[cells + id] += cz * (bx - Bx[km]) - cx * (bz - Bz[im]) - dt * J[1];
+        E[2 * cells + id] += cx * (by - By[im]) - cy * (bx - Bx[jm]) - dt * J[2];
+        clear_j(jt, cells, id);
     }
 }
 
@@ -675,16 +678,16 @@ cudaError_t launch_em3_fields(const GridParams &g, const EmBufs &em, const doubl
 {
     const int64_t cells = (int64_t)g.n[0] * g.n[1] * g.n[2];
     const int nb = em3_grid_blocks(cells);
-    // J_a = -(q w / (dx_b dx_c dt)) times the accumulated weights / 2^22
-    cudaError_t e = launch_em_j_convert(cells, em, -qw / (dx[1] * dx[2] * dt) / J_SCALE,
-                                        -qw / (dx[2] * dx[0] * dt) / J_SCALE,
-                                        -qw / (dx[0] * dx[1] * dt) / J_SCALE, st);
-    if (e != cudaSuccess) return e;
+    // J_a = -(q w / (dx_b dx_c dt)) times the accumulated weights / 2^22, taken (and
+    // cleared) by the E update
+    const JTake jt = em_jtake(em, -qw / (dx[1] * dx[2] * dt) / J_SCALE,
+                              -qw / (dx[2] * dx[0] * dt) / J_SCALE,
+                              -qw / (dx[0] * dx[1] * dt) / J_SCALE);
     const float hx = (float)(0.5 * dt / dx[0]), hy = (float)(0.5 * dt / dx[1]),
                 hz = (float)(0.5 * dt / dx[2]);
     const double c2dt = c * c * dt;
     k_yee3_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hx, hy, hz);
-    k_yee3_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, em.Jf, em.E, (float)(c2dt / dx[0]),
+    k_yee3_e<<<nb, EM_THREADS, 0, st>>>(g, em.B, jt, em.E, (float)(c2dt / dx[0]),
                                         (float)(c2dt / dx[1]), (float)(c2dt / dx[2]), (float)dt);
     k_yee3_b<<<nb, EM_THREADS, 0, st>>>(g, em.E, em.B, hx, hy, hz);
     note_launch(3);

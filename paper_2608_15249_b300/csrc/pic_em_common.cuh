@@ -119,6 +119,36 @@ __device__ __forceinline__ bool em_move_axis(float f, float vdtdx, int *sh, int 
     return ok;
 }
 
+// The current of the Ampere update, read from its fixed-point accumulator: component
+// k at node id is f[k] times the accumulated weights (as FP32, no conversion
+// instruction), plus the prescribed current when there is one.  The E update reads
+// the three components of a node first and clears them (clear_j) after its own
+// stores, so that no field load waits behind a store to the accumulator.
+struct JTake {
+    unsigned long long *acc;  // [3][cells]
+    const float *ext;         // [3][cells] or null
+    float f[3];
+};
+
+// The current of a step: the accumulator, the prescribed current, the factors.
+JTake em_jtake(const EmBufs &em, double fx, double fy, double fz);
+
+__device__ __forceinline__ void get_j(const JTake &t, int64_t cells, int64_t id, float *j)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t a = k * cells + id;
+        j[k] = t.f[k] * i64_to_f32((long long)t.acc[a]);  // written below: no __ldg
+        if (t.ext) j[k] += __ldg(t.ext + a);
+    }
+}
+
+__device__ __forceinline__ void clear_j(const JTake &t, int64_t cells, int64_t id)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t.acc[k * cells + id] = 0ull;
+}
+
 // The four diagnostic sums of a block (time-centred 2 KE, momentum), in FP64, into
 // diag_blocks[slot * 4 ..].
 __device__ __forceinline__ void em_block_diag(float ke, const float *mom, double *diag_blocks,

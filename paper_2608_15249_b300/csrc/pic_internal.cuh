@@ -303,7 +303,6 @@ cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
 // ---- electromagnetic step (pic_em.cu) -----------------------------------------------------------
 struct EmBufs {
     float *E, *B;              // [3][cells] Yee-staggered fields at integer time
-    float *Jf;                 // [3][cells] current of the last step (staggered like E)
     unsigned long long *J;     // [3][cells] fixed-point current weights (2^30)
     float *Jext;               // [3][cells] prescribed current added each step, or null
     float B0[3];               // uniform external B added to the gathered one
@@ -331,11 +330,6 @@ cudaError_t launch_em_push(const GridParams &g, ParticlesF32 p, const EmBufs &em
                            int *err, cudaStream_t st);
 // J from its accumulator (cleared), then B -= (dt/2) curl E; E += dt (c^2 curl B - J);
 // B -= (dt/2) curl E.
-// J (FP32, staggered like E) = the accumulated fixed-point weights of each
-// component times fx, fy, fz (plus the prescribed current); the accumulator is
-// cleared for the next step.
-cudaError_t launch_em_j_convert(int64_t cells, const EmBufs &em, double fx, double fy,
-                                double fz, cudaStream_t st);
 // Particles in the non-periodic mode (absorbing layer, conducting walls): gather
 // with fields outside the grid zero, Boris, and with move the move, the Esirkepov
 // current (contributions outside the grid dropped), the charge of the particles
