@@ -303,7 +303,7 @@ cudaError_t launch_efield(FieldBufs &f, cudaStream_t st);
 // ---- electromagnetic step (pic_em.cu) -----------------------------------------------------------
 struct EmBufs {
     float *E, *B;              // [3][cells] Yee-staggered fields at integer time
-    unsigned long long *J;     // [3][cells] fixed-point current weights (2^30)
+    unsigned long long *J;     // [3][cells] fixed-point current weights (2^22 per unit)
     float *Jext;               // [3][cells] prescribed current added each step, or null
     float B0[3];               // uniform external B added to the gathered one
     // convolutional PML (non-periodic grid), null when periodic:
