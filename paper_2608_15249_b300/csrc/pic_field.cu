@@ -107,6 +107,53 @@ __device__ __forceinline__ void node_coords(int64_t id, const FieldBufs &f, int 
     }
 }
 
+// The periodic neighbours of node id along each of the D axes, as 32-bit node
+// indices (cells < 2^31), for stencils whose axis loop is unrolled at compile time.
+template <int D>
+struct Nbrs {
+    int up[D], dn[D];
+};
+
+template <int D>
+__device__ __forceinline__ Nbrs<D> neighbours(int id, const FieldBufs &f)
+{
+    int j[3] = {id, 0, 0};
+    if (D >= 2) {
+        const uint32_t u = (uint32_t)id;
+        const uint32_t r = fdiv(u, f.div0);
+        j[0] = (int)(u - r * (uint32_t)f.n[0]);
+        if (D == 2) {
+            j[1] = (int)r;
+        } else {
+            const uint32_t r2 = fdiv(r, f.div1);
+            j[1] = (int)(r - r2 * (uint32_t)f.n[1]);
+            j[2] = (int)r2;
+        }
+    }
+    Nbrs<D> s;
+    int st = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int na = f.n[a];
+        s.up[a] = (j[a] + 1 == na) ? id - (na - 1) * st : id + st;
+        s.dn[a] = (j[a] == 0) ? id + (na - 1) * st : id - st;
+        st *= na;
+    }
+    return s;
+}
+
+// (-lap_h u)[id] on the periodic grid, the axes in order.
+template <int D>
+__device__ __forceinline__ float neg_lap_d(const float *__restrict__ u, int id, const Nbrs<D> &s,
+                                           const float *idx2)
+{
+    const float c = u[id];
+    float acc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc += (2.0f * c - u[s.up[a]] - u[s.dn[a]]) * idx2[a];
+    return acc;
+}
+
 // (-lap_h u)[id] on the periodic grid.
 __device__ __forceinline__ float neg_lap(const float *__restrict__ u, int64_t id, const int *j,
                                          const FieldBufs &f, const float *idx2)
@@ -209,7 +256,7 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
 // writes, ordered by the __syncthreads before it, are released) and polls
 // with acquire loads, with a bound.  Returns false in every thread of the block if
 // the bound ran out.
-__device__ bool grid_barrier(unsigned *count, unsigned &gen)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned &gen)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -236,7 +283,7 @@ __device__ bool grid_barrier(unsigned *count, unsigned &gen)
 // all K); the totals replace v[] in every thread.  Two calls with the same K must
 // have a block barrier between them (in k_cg_coop, a grid barrier always does).
 template <int K>
-__device__ void cg_block_sums(double (&v)[K])
+__device__ __forceinline__ void cg_block_sums(double (&v)[K])
 {
     __shared__ double red[K][CG_T / 32];
     __shared__ double tot[K];
@@ -259,7 +306,7 @@ __device__ void cg_block_sums(double (&v)[K])
 // Totals of K arrays of per-block partials (L2 loads: written by other blocks of
 // this launch), the same fixed order in every block.
 template <int K>
-__device__ void cg_reduce(double *const (&part)[K], double (&out)[K])
+__device__ __forceinline__ void cg_reduce(double *const (&part)[K], double (&out)[K])
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = 0.0;
@@ -280,12 +327,14 @@ struct CgCoop {
     int latch;           // latch EF_CG when the residual stays above rtol
 };
 
+template <int D>
 __global__ void __launch_bounds__(CG_T)
     k_cg_coop(FieldBufs f, Lap L, CgCoop c, double rtol, unsigned *bar, int *err)
 {
     unsigned gen = 0u;
-    const int64_t stride = (int64_t)gridDim.x * CG_T;
-    const int64_t first = (int64_t)blockIdx.x * CG_T + threadIdx.x;
+    const int stride = (int)gridDim.x * CG_T;
+    const int first = (int)blockIdx.x * CG_T + (int)threadIdx.x;
+    const int cells = (int)f.cells;
     const double N = (double)f.cells;
     auto bail = [&]() {
         if (threadIdx.x == 0) atomicOr(err, EF_TIMEOUT);
@@ -293,11 +342,10 @@ __global__ void __launch_bounds__(CG_T)
     // r = b - A x and its sums
     {
         double v[3] = {0.0, 0.0, 0.0};  // r.r, sum r, b.b
-        for (int64_t id = first; id < f.cells; id += stride) {
-            int j[3];
-            node_coords(id, f, j);
+        for (int id = first; id < cells; id += stride) {
+            const Nbrs<D> nb = neighbours<D>(id, f);
             const float bi = c.b[id];
-            const float ri = bi - neg_lap(c.x, id, j, f, L.idx2);
+            const float ri = bi - neg_lap_d<D>(c.x, id, nb, L.idx2);
             f.r[id] = ri;
             v[0] += (double)ri * ri;
             v[1] += ri;
@@ -327,29 +375,25 @@ __global__ void __launch_bounds__(CG_T)
     double beta = 0.0;
     int it = 0;
     while (!done) {
-        const float *po = c.pp[(it + 1) & 1];
-        float *pn = c.pp[it & 1];
+        // the previous direction and this iteration's (ping-pong, selected rather than
+        // indexed so that the parameter array stays out of local memory)
+        const float *po = (it & 1) ? c.pp[0] : c.pp[1];
+        float *pn = (it & 1) ? c.pp[1] : c.pp[0];
         const float mf = (float)m, bf = (float)beta;
         // p = (r - m) / diag + beta p_old at each node and its neighbours; q = A p
-        auto dir = [&](int64_t k) {
+        auto dir = [&](int k) {
             float v = (f.r[k] - mf) * L.inv_diag;
             if (it > 0) v += bf * po[k];
             return v;
         };
         double pq[1] = {0.0};
-        for (int64_t id = first; id < f.cells; id += stride) {
-            int j[3];
-            node_coords(id, f, j);
+        for (int id = first; id < cells; id += stride) {
+            const Nbrs<D> nb = neighbours<D>(id, f);
             const float pc = dir(id);
             float acc = 0.0f;
-            int64_t st = 1;
-            for (int a = 0; a < f.ndim; ++a) {
-                const int na = f.n[a];
-                const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * st : id + st;
-                const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * st : id - st;
-                acc += (2.0f * pc - dir(up) - dir(dn)) * L.idx2[a];
-                st *= na;
-            }
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                acc += (2.0f * pc - dir(nb.up[a]) - dir(nb.dn[a])) * L.idx2[a];
             pn[id] = pc;
             f.q[id] = acc;
             pq[0] += (double)pc * acc;
@@ -366,7 +410,7 @@ __global__ void __launch_bounds__(CG_T)
         if (!(pqs[0] > 0.0) || !isfinite(a64)) break;  // breakdown: keep x as it is
         const float alpha = (float)a64;
         double v[2] = {0.0, 0.0};  // r.r, sum r
-        for (int64_t id = first; id < f.cells; id += stride) {
+        for (int id = first; id < cells; id += stride) {
             c.x[id] += alpha * pn[id];
             const float ri = (f.r[id] - mf) - alpha * f.q[id];
             f.r[id] = ri;
@@ -405,7 +449,7 @@ int cg_coop_blocks(int64_t cells)
     static std::atomic<int> per_sm{0};
     int c = per_sm.load(std::memory_order_relaxed);
     if (!c) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cg_coop, CG_T, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_cg_coop<3>, CG_T, 0) != cudaSuccess ||
             c < 1) {
             cudaGetLastError();
             c = 1;
@@ -445,7 +489,10 @@ cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol,
     unsigned *bar = f.gbar;
     void *args[] = {&f, &L, &c, &rtol, &bar, &err};
     const int nb = cg_coop_blocks(f.cells);
-    e = cudaLaunchCooperativeKernel((const void *)k_cg_coop, dim3(nb), dim3(CG_T), args, 0, st);
+    const void *fn = f.ndim == 1   ? (const void *)k_cg_coop<1>
+                     : f.ndim == 2 ? (const void *)k_cg_coop<2>
+                                   : (const void *)k_cg_coop<3>;
+    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(CG_T), args, 0, st);
     note_launch();
     return e;
 }
@@ -458,35 +505,30 @@ cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol,
 // rounded to FP32 as the right-hand side of a correction solve A x = r (FP32 CG,
 // FP64 dots), and phi += x, until the FP64 residual meets the tolerance.
 
-__device__ __forceinline__ double neg_lap64(const float *__restrict__ u, int64_t id, const int *j,
-                                            const FieldBufs &f, const double *idx2)
+template <int D>
+__device__ __forceinline__ double neg_lap64(const float *__restrict__ u, int id, const Nbrs<D> &s,
+                                            const double *idx2)
 {
     const double c = u[id];
     double acc = 0.0;
-    int64_t stride = 1;
-    for (int a = 0; a < f.ndim; ++a) {
-        const int na = f.n[a];
-        const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
-        const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
-        acc += (2.0 * c - (double)u[up] - (double)u[dn]) * idx2[a];
-        stride *= na;
-    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc += (2.0 * c - (double)u[s.up[a]] - (double)u[s.dn[a]]) * idx2[a];
     return acc;
 }
 
+template <int D>
 __global__ void __launch_bounds__(FT)
     k_residual64(FieldBufs f, double i0, double i1, double i2, double scale, double bg,
                  double mean_total)
 {
     const double idx2[3] = {i0, i1, i2};
     double rr = 0.0, bb = 0.0;
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        int j[3];
-        node_coords(id, f, j);
+    const int cells = (int)f.cells;
+    for (int id = (int)blockIdx.x * FT + (int)threadIdx.x; id < cells; id += (int)gridDim.x * FT) {
+        const Nbrs<D> nb = neighbours<D>(id, f);
         const double rho = scale * (double)(long long)f.acc[id] + bg;
         const double bj = rho - mean_total;
-        const double rj = bj - neg_lap64(f.phi, id, j, f, idx2);
+        const double rj = bj - neg_lap64<D>(f.phi, id, nb, idx2);
         f.b[id] = (float)rj;
         rr += rj * rj;
         bb += bj * bj;
@@ -526,7 +568,12 @@ cudaError_t launch_residual64(FieldBufs &f, double scale, double bg, double mean
 {
     double i2[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < f.ndim; ++a) i2[a] = 1.0 / (f.dx[a] * f.dx[a]);
-    k_residual64<<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], scale, bg, mean_total);
+    if (f.ndim == 1)
+        k_residual64<1><<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], scale, bg, mean_total);
+    else if (f.ndim == 2)
+        k_residual64<2><<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], scale, bg, mean_total);
+    else
+        k_residual64<3><<<f.nblocks, FT, 0, st>>>(f, i2[0], i2[1], i2[2], scale, bg, mean_total);
     note_launch();
     return cudaGetLastError();
 }
@@ -547,34 +594,28 @@ cudaError_t launch_add_correction(FieldBufs &f, cudaStream_t st)
 
 // ---- E = -grad phi ---------------------------------------------------------------------------
 
+template <int D>
 __global__ void __launch_bounds__(FT) k_efield(FieldBufs f, float h0, float h1, float h2)
 {
     const float h[3] = {h0, h1, h2};  // 1 / (2 dx_a)
     double fe = 0.0;
-    for (int64_t id = (int64_t)blockIdx.x * FT + threadIdx.x; id < f.cells;
-         id += (int64_t)gridDim.x * FT) {
-        int j[3];
-        node_coords(id, f, j);
+    const int cells = (int)f.cells;
+    for (int id = (int)blockIdx.x * FT + (int)threadIdx.x; id < cells; id += (int)gridDim.x * FT) {
+        const Nbrs<D> nb = neighbours<D>(id, f);
         float e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        int64_t stride = 1;
-        for (int a = 0; a < f.ndim; ++a) {
-            const int na = f.n[a];
-            const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
-            const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
-            e[a] = -(f.phi[up] - f.phi[dn]) * h[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            e[a] = -(f.phi[nb.up[a]] - f.phi[nb.dn[a]]) * h[a];
             fe += (double)e[a] * e[a];
-            stride *= na;
         }
         // 1D and 2D: pairs (node x holds its own field and that of x + 1), so a node's
         // field goes to its own first half and to its lower x-neighbour's second half
-        if (f.ndim == 1) {
-            const int64_t left = j[0] == 0 ? id + f.n[0] - 1 : id - 1;
+        if (D == 1) {
             f.E[2 * id] = e[0];
-            f.E[2 * left + 1] = e[0];
-        } else if (f.ndim == 2) {
-            const int64_t left = j[0] == 0 ? id + f.n[0] - 1 : id - 1;
+            f.E[2 * nb.dn[0] + 1] = e[0];
+        } else if (D == 2) {
             reinterpret_cast<float2 *>(f.E)[2 * id] = make_float2(e[0], e[1]);
-            reinterpret_cast<float2 *>(f.E)[2 * left + 1] = make_float2(e[0], e[1]);
+            reinterpret_cast<float2 *>(f.E)[2 * nb.dn[0] + 1] = make_float2(e[0], e[1]);
         } else {
             reinterpret_cast<float4 *>(f.E)[id] = make_float4(e[0], e[1], e[2], 0.0f);
         }
@@ -587,7 +628,9 @@ cudaError_t launch_efield(FieldBufs &f, cudaStream_t st)
 {
     float h[3] = {0.0f, 0.0f, 0.0f};
     for (int a = 0; a < f.ndim; ++a) h[a] = (float)(0.5 / f.dx[a]);
-    k_efield<<<f.nblocks, FT, 0, st>>>(f, h[0], h[1], h[2]);
+    if (f.ndim == 1) k_efield<1><<<f.nblocks, FT, 0, st>>>(f, h[0], h[1], h[2]);
+    else if (f.ndim == 2) k_efield<2><<<f.nblocks, FT, 0, st>>>(f, h[0], h[1], h[2]);
+    else k_efield<3><<<f.nblocks, FT, 0, st>>>(f, h[0], h[1], h[2]);
     note_launch();
     return cudaGetLastError();
 }
