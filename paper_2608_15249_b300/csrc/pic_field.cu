@@ -335,6 +335,11 @@ __global__ void __launch_bounds__(CG_T)
     const int stride = (int)gridDim.x * CG_T;
     const int first = (int)blockIdx.x * CG_T + (int)threadIdx.x;
     const int cells = (int)f.cells;
+    // the vectors, unaliased (lets the loads of several nodes be in flight together)
+    const float *__restrict__ bv = c.b;
+    float *__restrict__ xv = c.x;
+    float *__restrict__ rv = f.r;
+    float *__restrict__ qv = f.q;
     const double N = (double)f.cells;
     auto bail = [&]() {
         if (threadIdx.x == 0) atomicOr(err, EF_TIMEOUT);
@@ -342,11 +347,12 @@ __global__ void __launch_bounds__(CG_T)
     // r = b - A x and its sums
     {
         double v[3] = {0.0, 0.0, 0.0};  // r.r, sum r, b.b
+#pragma unroll 4
         for (int id = first; id < cells; id += stride) {
             const Nbrs<D> nb = neighbours<D>(id, f);
-            const float bi = c.b[id];
-            const float ri = bi - neg_lap_d<D>(c.x, id, nb, L.idx2);
-            f.r[id] = ri;
+            const float bi = bv[id];
+            const float ri = bi - neg_lap_d<D>(xv, id, nb, L.idx2);
+            rv[id] = ri;
             v[0] += (double)ri * ri;
             v[1] += ri;
             v[2] += (double)bi * bi;
@@ -377,16 +383,17 @@ __global__ void __launch_bounds__(CG_T)
     while (!done) {
         // the previous direction and this iteration's (ping-pong, selected rather than
         // indexed so that the parameter array stays out of local memory)
-        const float *po = (it & 1) ? c.pp[0] : c.pp[1];
-        float *pn = (it & 1) ? c.pp[1] : c.pp[0];
+        const float *__restrict__ po = (it & 1) ? c.pp[0] : c.pp[1];
+        float *__restrict__ pn = (it & 1) ? c.pp[1] : c.pp[0];
         const float mf = (float)m, bf = (float)beta;
         // p = (r - m) / diag + beta p_old at each node and its neighbours; q = A p
         auto dir = [&](int k) {
-            float v = (f.r[k] - mf) * L.inv_diag;
+            float v = (rv[k] - mf) * L.inv_diag;
             if (it > 0) v += bf * po[k];
             return v;
         };
         double pq[1] = {0.0};
+#pragma unroll 4
         for (int id = first; id < cells; id += stride) {
             const Nbrs<D> nb = neighbours<D>(id, f);
             const float pc = dir(id);
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(CG_T)
             for (int a = 0; a < D; ++a)
                 acc += (2.0f * pc - dir(nb.up[a]) - dir(nb.dn[a])) * L.idx2[a];
             pn[id] = pc;
-            f.q[id] = acc;
+            qv[id] = acc;
             pq[0] += (double)pc * acc;
         }
         cg_block_sums<1>(pq);
@@ -410,10 +417,11 @@ __global__ void __launch_bounds__(CG_T)
         if (!(pqs[0] > 0.0) || !isfinite(a64)) break;  // breakdown: keep x as it is
         const float alpha = (float)a64;
         double v[2] = {0.0, 0.0};  // r.r, sum r
+#pragma unroll 4
         for (int id = first; id < cells; id += stride) {
-            c.x[id] += alpha * pn[id];
-            const float ri = (f.r[id] - mf) - alpha * f.q[id];
-            f.r[id] = ri;
+            xv[id] += alpha * pn[id];
+            const float ri = (rv[id] - mf) - alpha * qv[id];
+            rv[id] = ri;
             v[0] += (double)ri * ri;
             v[1] += ri;
         }
