@@ -98,9 +98,13 @@ def _spectral_bytes_per_node(ndim):
     first reads the FP32 right-hand side, 4 + 8 B; the last writes the FP32
     potential, 8 + 4 B; the others 8 + 8 B; in 1D one real-to-real pass, 4 + 4 B),
     the refinement's last pass also reading the potential it adds to (4 B), the FP64
-    residual (8 B rho + 4 B phi + 4 B out) and E = -grad phi (4 B + 4 B per axis)."""
+    residual (8 B charge accumulator + 4 B phi + 4 B out) and E = -grad phi (4 B + 4 B per
+    axis)."""
     solve = 8 if ndim == 1 else 12 + 16 * (2 * ndim - 3) + 12
     return 2 * solve + 4 + 16 + 4 + 4 * ndim
+
+
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth, for the fraction beside the measured one
 
 
 def _roofline(alg_bytes, ms, kernel, peak, peak_kind, traffic=None, **extra):
@@ -108,7 +112,8 @@ def _roofline(alg_bytes, ms, kernel, peak, peak_kind, traffic=None, **extra):
     out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": ms,
-           "peak_kind": peak_kind}
+           "peak_kind": peak_kind,
+           "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     out.update(extra)
     return out
 
@@ -393,7 +398,8 @@ def bench_ours(args):
                          "kernel": ("k_plain_pass" if f64 else "k_particle_pass")
                          + " (gather+Boris+move+deposit)",
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
-                         "peak_kind": peak_kind},
+                         "peak_kind": peak_kind,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
             "stage_ms_per_call": breakdown,
             "field_solve_ms": field_ms,
             "spectral_solve": spectral,
@@ -983,7 +989,8 @@ def run_batch(args, pk, torch, stream, embedded=False):
                      "kernel": "batch push_deposit (k_particle_pass per dimension class "
                                "+ memset + k_b_convert)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": pd_ms,
-                     "peak_kind": peak_kind},
+                     "peak_kind": peak_kind,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "field_solve_ms": solve_ms,
         "full_step_ms": full_ms,
         "full_step_particle_steps_per_s": total / (full_ms * 1e-3),
