@@ -89,26 +89,10 @@ __device__ double reduce_partials(const double *__restrict__ part, int n)
     return block_sum(s);
 }
 
-// Node coordinates from a flat index (axis 0 fastest); cells < 2^30, so 32-bit
-// multiply-high division (a runtime division would issue float conversions on
-// this GPU's slow FP64 pipe).
-__device__ __forceinline__ void node_coords(int64_t id, const FieldBufs &f, int *j)
-{
-    const uint32_t u = (uint32_t)id;
-    const uint32_t r = fdiv(u, f.div0);
-    j[0] = (int)(u - r * (uint32_t)f.n[0]);
-    if (f.ndim >= 2) {
-        const uint32_t r2 = fdiv(r, f.div1);
-        j[1] = (int)(r - r2 * (uint32_t)f.n[1]);
-        j[2] = (int)r2;
-    } else {
-        j[1] = 0;
-        j[2] = 0;
-    }
-}
-
 // The periodic neighbours of node id along each of the D axes, as 32-bit node
 // indices (cells < 2^31), for stencils whose axis loop is unrolled at compile time.
+// The coordinates come from the multiply-high division (a runtime integer division
+// would issue float conversions on this GPU's slow FP64 pipe).
 template <int D>
 struct Nbrs {
     int up[D], dn[D];
@@ -151,23 +135,6 @@ __device__ __forceinline__ float neg_lap_d(const float *__restrict__ u, int id, 
     float acc = 0.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) acc += (2.0f * c - u[s.up[a]] - u[s.dn[a]]) * idx2[a];
-    return acc;
-}
-
-// (-lap_h u)[id] on the periodic grid.
-__device__ __forceinline__ float neg_lap(const float *__restrict__ u, int64_t id, const int *j,
-                                         const FieldBufs &f, const float *idx2)
-{
-    const float c = u[id];
-    float acc = 0.0f;
-    int64_t stride = 1;
-    for (int a = 0; a < f.ndim; ++a) {
-        const int na = f.n[a];
-        const int64_t up = (j[a] + 1 == na) ? id - (int64_t)(na - 1) * stride : id + stride;
-        const int64_t dn = (j[a] == 0) ? id + (int64_t)(na - 1) * stride : id - stride;
-        acc += (2.0f * c - u[up] - u[dn]) * idx2[a];
-        stride *= na;
-    }
     return acc;
 }
 
