@@ -58,3 +58,40 @@ def test_cpml_absorbs_an_outgoing_pulse(orc):
     _, f = _pulse_run(orc, 72, 12, steps=900)
     _, fpec = _pulse_run(orc, 72, 0, steps=900)
     assert f.energy() < 1e-6 * fpec.energy()
+
+
+def test_cpml_profile_values(orc):
+    """The layer's coefficients along one axis (n = 40 nodes, 10-cell layers, c = 1.5,
+    dx = 0.75, step h = 0.4, cubic grading): outside the layers b = 1, c = 0, 1/kappa = 1
+    (the plain FDTD update); at the outer node (depth 1) sigma is the matched value
+    0.8 (m + 1) c / dx, so b = exp(-sigma_max h) and, with kappa = 1 and alpha = 0,
+    c = b - 1; one cell in (depth 0.9) sigma = sigma_max 0.9^3; the profile is mirror
+    symmetric and the damping grows towards the wall.  With kappa_max and alpha_max set,
+    c = sigma (b - 1) / (sigma kappa + kappa^2 alpha) at a hand-evaluated point."""
+    n, npml, dx, h, cl, m = 40, 10, 0.75, 0.4, 1.5, 3
+    prof = orc.cpml_axis(n, npml, dx, h, cl, m=m)
+    b, cc, ik = prof["int"]
+    smax = 0.8 * (m + 1) * cl / dx
+    inner = slice(npml, n - npml)
+    np.testing.assert_array_equal(b[inner], 1.0)
+    np.testing.assert_array_equal(cc[inner], 0.0)
+    np.testing.assert_array_equal(ik, 1.0)
+    assert b[0] == pytest.approx(math.exp(-smax * h), rel=1e-15)
+    assert cc[0] == pytest.approx(b[0] - 1.0, rel=1e-14)
+    assert b[1] == pytest.approx(math.exp(-smax * 0.9 ** 3 * h), rel=1e-15)
+    np.testing.assert_allclose(b, b[::-1], rtol=0, atol=0)
+    assert np.all(np.diff(b[: npml + 1]) > 0)
+    bh, ch, _ = prof["half"]
+    # half positions: node i + 1/2 mirrors node n - 2 - i + 1/2
+    np.testing.assert_allclose(bh[: n - 1], bh[: n - 1][::-1], rtol=1e-15)
+    assert bh[0] == pytest.approx(math.exp(-smax * 0.95 ** 3 * h), rel=1e-15)
+    # kappa and alpha grading
+    kmax, amax = 4.0, 0.2
+    prof = orc.cpml_axis(n, npml, dx, h, cl, m=m, kappa_max=kmax, alpha_max=amax)
+    b, cc, ik = prof["int"]
+    d = 0.9
+    sig, kap, alp = smax * d ** m, 1.0 + (kmax - 1.0) * d ** m, amax * (1.0 - d)
+    bb = math.exp(-(sig / kap + alp) * h)
+    assert b[1] == pytest.approx(bb, rel=1e-15)
+    assert cc[1] == pytest.approx(sig * (bb - 1.0) / (sig * kap + kap * kap * alp), rel=1e-14)
+    assert ik[1] == pytest.approx(1.0 / kap, rel=1e-15)

@@ -163,6 +163,19 @@ def test_hc_without_B_is_leapfrog_in_momentum(orc):
     np.testing.assert_allclose(u, want, rtol=0, atol=1e-14)
 
 
+def test_lorentz_gamma_values(orc):
+    """gamma = sqrt(1 + |u|^2 / c^2): |u| = c sqrt(3) gives 2 in any direction, |u| = c
+    gives sqrt(2), u = 0 gives 1, and c = infinity gives 1 for any u."""
+    c = 2.5
+    rng = np.random.default_rng(11)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    np.testing.assert_allclose(orc.lorentz_gamma(dirs * c * math.sqrt(3.0), c), 2.0, rtol=1e-15)
+    np.testing.assert_allclose(orc.lorentz_gamma(dirs * c, c), math.sqrt(2.0), rtol=1e-15)
+    assert orc.lorentz_gamma(np.zeros((1, 3)), c)[0] == 1.0
+    np.testing.assert_array_equal(orc.lorentz_gamma(dirs * 1e3, None), 1.0)
+
+
 def test_relativistic_kinetic_energy(orc):
     u, _ = _rand_fields(34)
     c, mw = 1.7, 2.5
