@@ -444,6 +444,58 @@ __host__ __device__ constexpr int pass_tile()
     return Src::FIXED_TILE ? Src::FIXED_TILE : tile_of_dim<D>();
 }
 
+// The fixed charge window: FW2_X x FW2_Y nodes in 2D (FW3_X x FW3_Y x FW3_Z in 3D),
+// x fastest, placed by a reference cell: the cells up to W / 2 - 1 away from it on
+// each axis are inside.  The extents are compile-time constants, so the window
+// index and its decode in the flush are a few multiply-adds, and no box of the
+// tile's cells (nor the barrier that box needs) is computed.  Particles drift away
+// from their sorted tiles over a sort cycle; those outside the window take global
+// atomics.  Measured on 512^2 x 64 ppc and 128^3 x 64 ppc over 20-step sort cycles,
+// these extents and groups of three tiles in 2D (single tiles in 3D) were the
+// fastest tried: larger windows cost more in the flush, smaller ones in spills.
+constexpr int TILE_GROUP = 3, TILE_GROUP_3D = 1;
+constexpr int FW2_X = 40, FW2_Y = 20;
+constexpr int FW3_X = 16, FW3_Y = 16, FW3_Z = 8;
+template <int D>
+__host__ __device__ constexpr bool fixed_window() { return D >= 2; }
+template <int D>
+__host__ __device__ constexpr int fw_ext(int a)
+{
+    return D == 2 ? (a == 0 ? FW2_X : FW2_Y) : (a == 0 ? FW3_X : (a == 1 ? FW3_Y : FW3_Z));
+}
+// window stride of axis a
+template <int D>
+__host__ __device__ constexpr int fw_stride(int a)
+{
+    return a == 0 ? 1 : (a == 1 ? fw_ext<D>(0) : fw_ext<D>(0) * fw_ext<D>(1));
+}
+template <int D>
+__host__ __device__ constexpr int fw_total() { return fw_stride<D>(D - 1) * fw_ext<D>(D - 1); }
+// window offset of corner k (bit a of k: the upper node on axis a)
+template <int D>
+__host__ __device__ constexpr int fw_corner(int k)
+{
+    return (k & 1) + (D > 1 ? ((k >> 1) & 1) * fw_stride<D>(1) : 0) +
+           (D > 2 ? ((k >> 2) & 1) * fw_stride<D>(2) : 0);
+}
+
+// Words of the charge window: the fixed window, else the largest dynamic box.
+template <int D>
+__host__ __device__ constexpr int win_cap() { return fixed_window<D>() ? fw_total<D>() : WIN_CAP; }
+
+// Tile groups (2D single instances): a CTA takes TILE_GROUP consecutive tiles of the
+// sorted order, each depositing into a window of its own, and flushes the windows
+// together after the last of them (one global atomic per node for the group, whose
+// tiles share most of their nodes).  Separate 32-bit windows keep the per-tile bound
+// of the window words; the flush sums them in 64 bits.
+template <int D, class Src>
+__host__ __device__ constexpr int tile_group()
+{
+    return Src::PER_TILE_DIAG ? 1 : (D == 2 ? TILE_GROUP : (D == 3 ? TILE_GROUP_3D : 1));
+}
+template <int D, class Src>
+__host__ __device__ constexpr int win_words() { return win_cap<D>() * tile_group<D, Src>(); }
+
 // Particle (index within the tile) of slot r of thread `tid`, for tiles of
 // R * 32 NW particles (NW warps) seen as NW R rows of 32: lane i of warp w takes
 // column i of row (w R + r + i) mod NW R.  For each column the pairs (w, r) cover
@@ -485,13 +537,15 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
     constexpr bool NEED_V = PUSH || MOVE;
     constexpr int NA = 1 + D + (NEED_V ? NV : 0);
     constexpr bool WRITE = PUSH || MOVE;  // the record changes and goes back to global
+    constexpr bool FIXED_WIN = fixed_window<D>();
+    constexpr int G = tile_group<D, Src>();
     float *stage_base = reinterpret_cast<float *>(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * NA_MAX * TILE * 4);
     // per-tile charge window (int32 fixed point, kept zero between tiles) and the
     // tile's box of new cells (min, max of the unwrapped offset from the tile's
     // reference cell, per axis)
     unsigned *s_win = reinterpret_cast<unsigned *>(bars + STAGES);
-    int *s_box = reinterpret_cast<int *>(s_win + WIN_CAP);
+    int *s_box = reinterpret_cast<int *>(s_win + win_words<D, Src>());
     // the current and the next tile's parameters (copied by one thread for a batch,
     // one tile ahead), the tile's reference cell, and per-warp diagnostic partials
     // of a batch tile
@@ -499,14 +553,26 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
     __shared__ int s_ref_cell;
     __shared__ float s_diag[NT / 32][4];
 
+    // groups of G consecutive tiles: group blockIdx.x + j gridDim.x for this CTA (the
+    // last group of the grid short when G does not divide ntiles).  Interleaving the
+    // groups across CTAs measured faster than a contiguous range of tiles per CTA,
+    // which would balance the tail better.
     const int64_t ntiles = src.ntiles();
-    const int my_tiles =
-        blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const int64_t ngroups = (ntiles + G - 1) / G;
+    int my_tiles = blockIdx.x < ngroups ? (int)((ngroups - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    if (G > 1) {
+        my_tiles *= G;
+        if (my_tiles > 0 && (ngroups - 1) % gridDim.x == blockIdx.x)
+            my_tiles -= (int)(G * ngroups - ntiles);
+    }
     const int tid = threadIdx.x, lane = tid & 31;
 
     // stage s, array a (0: cell, 1..D: offsets, D+1..: velocities)
     auto stage_arr = [&](int st, int a) { return stage_base + ((size_t)st * NA_MAX + a) * TILE; };
-    auto tile_of = [&](int k) { return (int64_t)blockIdx.x + (int64_t)k * gridDim.x; };
+    auto tile_of = [&](int k) {
+        return G > 1 ? G * ((int64_t)blockIdx.x + (int64_t)(k / G) * gridDim.x) + k % G
+                     : (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+    };
     auto tile_bytes = [&](int64_t t) { return (uint32_t)(((src.count(t) + 3) / 4) * 16); };
     auto issue_load = [&](int k, int st) {
         const int64_t t = tile_of(k);
@@ -549,7 +615,7 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
         if (my_tiles > 0) src.load_params(tile_of(0), &s_tp[0]);
     }
     if (DEPOSIT) {
-        for (int i = tid; i < WIN_CAP; i += NT) s_win[i] = 0u;
+        for (int i = tid; i < win_words<D, Src>(); i += NT) s_win[i] = 0u;
         if (tid < 3) {
             s_box[tid] = 0x7fffffff;
             s_box[3 + tid] = -0x7fffffff;
@@ -572,9 +638,17 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
         // finished at that tile's closing barrier); this tile's came one tile ago
         if (tid == 0 && k + 1 < my_tiles) src.load_params(tile_of(k + 1), &s_tp[(k + 1) & 1]);
         const bool ok_wait = mbar_wait_bounded(smem_addr(&bars[st]), parity);
-        // the tile's reference cell (its first particle's cell before the move), kept
-        // before the barrier so that no thread overwrites it first
-        if (tid == 0 && ok_wait) s_ref_cell = reinterpret_cast<const int32_t *>(stage_arr(st, 0))[0];
+        // the tile's reference cell (before the move: the cell of its first particle
+        // for the box, of its middle one for the fixed window, of the last one of the
+        // first tile of a group of several), kept before the barrier so that no
+        // thread overwrites it first
+        const int kg = k % G;  // the tile's place in its group
+        if (tid == 0 && ok_wait && kg == 0) {
+            const int cnt0 = src.count(t);
+            const bool several = G > 1 && k + 1 < my_tiles;
+            s_ref_cell = reinterpret_cast<const int32_t *>(stage_arr(st, 0))[
+                several ? cnt0 - 1 : (FIXED_WIN ? (cnt0 - 1) / 2 : 0)];
+        }
         if (__syncthreads_or(!ok_wait)) {
             // a copy did not land within the cap: report, drain what is in flight, stop
             if (tid == 0) {
@@ -685,7 +759,76 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
         // box of cells (they were sorted); when its nodes fit the shared-memory
         // window, every corner is added there and each touched node goes to the
         // global accumulator once; otherwise the corners go to global memory.
-        if (DEPOSIT) {
+        if (DEPOSIT && FIXED_WIN) {
+            // the fixed window: its origin (the node of window index 0) sits half the
+            // window below the reference cell, wrapped into the grid; an axis shorter
+            // than the window takes origin 0, so that every cell is inside and the
+            // upper node of the last cell has a slot of its own (flushed to node 0)
+            int org[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int W = fw_ext<D>(a);
+                int o = ref[a] - (W / 2 - 1);
+                o += o < 0 ? g.n[a] : 0;
+                org[a] = g.n[a] >= W ? o : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!valid[r]) continue;
+                int q[1 << D];
+                cic_quanta<D>(f[r], scale, one, q);
+                unsigned base = 0u;
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    int d = c[r][a] - org[a];
+                    d += d < 0 ? g.n[a] : 0;
+                    in = in && d < fw_ext<D>(a) - 1;
+                    base += (unsigned)d * (unsigned)fw_stride<D>(a);
+                }
+                if (in) {
+                    unsigned *w = s_win + kg * fw_total<D>();
+#pragma unroll
+                    for (int kc = 0; kc < (1 << D); ++kc)
+                        atomicAdd(&w[base + fw_corner<D>(kc)], (unsigned)q[kc]);
+                } else {
+                    int node[1 << D];
+                    corner_nodes<D>(c[r], g.n, node);
+#pragma unroll
+                    for (int kc = 0; kc < (1 << D); ++kc)
+                        atomicAdd(acc + node[kc], (unsigned long long)(long long)q[kc]);
+                }
+            }
+            // flush as below, over the whole fixed window (with tile groups, after the
+            // last tile of the group, or the CTA's last tile)
+            const bool flush = kg == G - 1 || k + 1 == my_tiles;
+            if (flush) __syncthreads();
+            for (int i = tid; flush && i < fw_total<D>(); i += NT) {
+                unsigned u[G];
+                unsigned any = 0u;
+#pragma unroll
+                for (int h = 0; h < G; ++h) {
+                    u[h] = s_win[h * fw_total<D>() + i];
+                    any |= u[h];
+                }
+                if (any == 0u) continue;
+                long long val = 0;
+#pragma unroll
+                for (int h = 0; h < G; ++h) {
+                    s_win[h * fw_total<D>() + i] = 0u;
+                    val += u[h] >= WIN_NEG ? (long long)u[h] - (1ll << 32) : (long long)u[h];
+                }
+                int node = 0, stride = 1;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    int x = org[a] + (int)(((unsigned)i / fw_stride<D>(a)) % fw_ext<D>(a));
+                    x -= x >= g.n[a] ? g.n[a] : 0;
+                    node += x * stride;
+                    stride *= g.n[a];
+                }
+                atomicAdd(acc + node, (unsigned long long)val);
+            }
+        } else if (DEPOSIT) {
             int q[R][1 << D], dd[R][3];
             int lo[3], hi[3];
 #pragma unroll
@@ -729,7 +872,8 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
                 bits[a] = 32 - __clz(w - 1);              // ceil(log2 w)
                 tot_bits += bits[a];
             }
-            const bool use_win = tot_bits <= WIN_BITS && s_box[3] >= s_box[0];
+            const bool use_win =
+                tot_bits <= WIN_BITS && (1 << tot_bits) <= win_cap<D>() && s_box[3] >= s_box[0];
             if (use_win) {
                 // shared-memory atomics into the window: corner k of a particle sits at
                 // its cell's window index plus a per-tile offset
@@ -850,7 +994,8 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
 template <int D, int NV, class Src>
 constexpr size_t pass_smem_bytes()
 {
-    return (size_t)STAGES * (1 + D + NV) * pass_tile<D, Src>() * 4 + STAGES * 8 + WIN_CAP * 4 +
+    return (size_t)STAGES * (1 + D + NV) * pass_tile<D, Src>() * 4 + STAGES * 8 +
+           win_words<D, Src>() * 4 +
            8 * 4;
 }
 

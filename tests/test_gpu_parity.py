@@ -42,6 +42,9 @@ def small_cases():
         # shared-memory window, so the warp-scan + global-atomic path runs
         "2d_sparse": plasma.sparse_box(2, (160, 128), 1500, seed=39),
         "3d_sparse": plasma.sparse_box(3, (40, 32, 24), 1300, seed=40),
+        # both axes shorter than the fixed charge window (every cell inside it, the
+        # upper node of the last cell in a slot of its own)
+        "2d_small": plasma.maxwellian_box(2, (24, 12), ppc=20, nv=2, dt=0.1, seed=41),
     }
 
 
@@ -144,7 +147,55 @@ def test_one_step_from_identical_state(pk, name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["1d", "2d_two_stream", "3d_mag", "2d_sparse", "3d_sparse"])
+# The fused pass's fixed charge window, restated on the host: tiles of 768 (2D) or 512
+# (3D) consecutive particles, in groups of 3 (2D) or 1 (3D) consecutive tiles (the
+# last group shorter when the tiles run out).  The reference cell is that of the
+# last particle of a group's first tile when the group has several tiles, else of
+# the tile's middle particle; origin = reference minus (W / 2 - 1), wrapped, or 0 on
+# an axis shorter than the window; a particle's corners go to the window when its
+# cell lies within W - 2 cells above the origin (wrapped) on every axis, else to the
+# global accumulator.
+FW = {2: (np.array([40, 20]), 768, 3), 3: (np.array([16, 16, 8]), 512, 1)}
+
+
+def fixed_window_split(cell, ndim, n):
+    W, tile, group = FW[ndim]
+    n = np.asarray(n[:ndim])
+    c = np.stack([(cell // int(np.prod(n[:a]))) % n[a] for a in range(ndim)], 1)
+    inside = np.zeros(len(c), bool)
+    span = tile * group
+    for first in range(0, len(c), span):
+        blk = c[first:first + span]
+        ref = blk[tile - 1] if len(blk) > tile else blk[(len(blk) - 1) // 2]
+        org = np.where(n >= W, (ref - (W // 2 - 1)) % n, 0)
+        d = (blk - org) % n
+        inside[first:first + span] = (d < W - 1).all(1)
+    return inside
+
+
+@pytest.mark.parametrize("name,paths", [("2d_sparse", "both"), ("3d_sparse", "both"),
+                                        ("2d_small", "window"), ("3d_mag", "both")])
+def test_fixed_window_paths(pk, name, paths):
+    """The deposit at load runs on the sorted particles: the host restatement of the
+    window rule on the GPU's sorted cells shows which corners took the shared-memory
+    window and which the global atomics; rho is then within 1e-5 of the oracle's."""
+    w = small_cases()[name]
+    g = _gpu(pk, w).load(w.x, w.v, half_push=False)
+    cell, _, _, _ = g.get_particles(positions=False)
+    inside = fixed_window_split(np.asarray(cell, np.int64), w.ndim, w.n)
+    if paths == "both":
+        assert 0 < inside.sum() < len(inside), inside.sum()
+    else:
+        assert inside.all()
+    sim = _oracle_sim(w).load(w.x, w.v, half_push=False)
+    assert rel_inf(g.get_rho(), sim.rho, np.abs(sim.rho_e).max()) <= TOL
+    d = g.get_diag()
+    assert d["charge_fx_sum"] == w.np_ * (1 << d["fx_bits"])
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["1d", "2d_two_stream", "3d_mag", "2d_sparse", "3d_sparse",
+                                  "2d_small"])
 def test_ten_steps_with_sorts(pk, name):
     """Ten cycles with a sort every 3 steps: per-particle state, rho and E stay within
     1e-5 of the oracle; particle identity is tracked through the sort permutations."""
