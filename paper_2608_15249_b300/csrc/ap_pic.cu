@@ -92,10 +92,11 @@ struct ap_pic {
     // own non-blocking stream fenced to the caller's
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
-    cudaGraphExec_t graphs[8] = {};
-    int64_t graph_launches[8] = {};
-    int graph_slot[8] = {};
+    cudaGraphExec_t graphs[16] = {};
+    int64_t graph_launches[16] = {};
+    int graph_slot[16] = {};
     int parity = 0;  // flips with every sort (the ping-pong particle buffers)
+    int acc_parity = 0;  // flips with every FP32 push_deposit (the two accumulators)
 
     // electromagnetic step (cfg.em)
     bool em = false;
@@ -599,6 +600,7 @@ static ap_pic_status create_grid(ap_pic *h)
     f.nblocks = field_blocks(h->cells);
     const size_t c = (size_t)h->cells;
     TRY(alloc_n(h, &f.acc, c));
+    TRY(alloc_n(h, &f.acc_spare, c));
     TRY(alloc_n(h, &f.b, c));
     TRY(alloc_n(h, &f.phi, c));
     TRY(alloc_n(h, &f.r, c));
@@ -621,6 +623,7 @@ static ap_pic_status create_grid(ap_pic *h)
     TRY(alloc_n(h, &h->d_accsum, 1));
     TRY(alloc_n(h, &h->d_err, 1));
     CU(h, cudaMemsetAsync(f.acc, 0, c * 8, h->stream));
+    CU(h, cudaMemsetAsync(f.acc_spare, 0, c * 8, h->stream));
     CU(h, cudaMemsetAsync(f.phi, 0, c * 4, h->stream));
     CU(h, cudaMemsetAsync(f.E, 0, c * f.Estride * 4, h->stream));
     CU(h, cudaMemsetAsync(f.isum_part, 0, (size_t)f.nblocks * 8, h->stream));
@@ -730,6 +733,8 @@ extern "C" ap_pic_status ap_pic_get_config(const ap_pic *h, ap_pic_config *out)
     return AP_PIC_OK;
 }
 
+static void drop_graphs(ap_pic *h);
+
 extern "C" ap_pic_status ap_pic_destroy(ap_pic *h)
 {
     if (!h) return AP_PIC_OK;
@@ -741,8 +746,7 @@ extern "C" ap_pic_status ap_pic_destroy(ap_pic *h)
     if (h->h_accsum) cudaFreeHost(h->h_accsum);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_iters) cudaFreeHost(h->h_iters);
-    for (auto &gx : h->graphs)
-        if (gx) cudaGraphExecDestroy(gx);
+    drop_graphs(h);
     if (h->gev_in) cudaEventDestroy(h->gev_in);
     if (h->gev_out) cudaEventDestroy(h->gev_out);
     if (h->gstream) cudaStreamDestroy(h->gstream);
@@ -752,8 +756,25 @@ extern "C" ap_pic_status ap_pic_destroy(ap_pic *h)
 
 // ---- particle storage ------------------------------------------------------------------------
 
+// Captured step graphs hold the particle buffers, the particle count and the
+// fixed-point scale of the load they were captured under: a new load drops them
+// (after any replay still in flight).
+static void drop_graphs(ap_pic *h)
+{
+    bool any = false;
+    for (auto &gx : h->graphs) any = any || gx != nullptr;
+    if (!any) return;
+    if (h->gstream) cudaStreamSynchronize(h->gstream);
+    for (auto &gx : h->graphs)
+        if (gx) {
+            cudaGraphExecDestroy(gx);
+            gx = nullptr;
+        }
+}
+
 static ap_pic_status alloc_particles(ap_pic *h, int64_t np)
 {
+    drop_graphs(h);
     free_particles(h);
     h->np = np;
     const size_t n = (size_t)(np > 0 ? np : 1);
@@ -823,7 +844,7 @@ static double rho_scale(const ap_pic *h)
 
 // rho from the accumulator: rho_e = q w / dV * acc / 2^S;  b = rho_e - mean(rho_e)
 // (mean exact: every particle deposits 2^S, so mean(rho_e) = q w np / V).
-static ap_pic_status convert_rho(ap_pic *h)
+static ap_pic_status convert_rho(ap_pic *h, unsigned long long *clear = nullptr)
 {
     const double scale = rho_scale(h);
     const double mean_e = h->cfg.q * h->cfg.weight * (double)h->np / h->V;
@@ -836,7 +857,7 @@ static ap_pic_status convert_rho(ap_pic *h)
         const unsigned long long C = (unsigned long long)h->cells;
         const unsigned long long q = M / C;
         CU(h, launch_rho_convert(h->f, (long long)q, (float)((double)(M - q * C) / (double)C),
-                                 (float)scale, h->stream));
+                                 (float)scale, clear, h->stream));
     }
     stage_end(h, mk);
     return AP_PIC_OK;
@@ -1176,6 +1197,15 @@ extern "C" ap_pic_status ap_pic_deposit(ap_pic *h)
     return deposit_only(h);
 }
 
+// The two FP32-form accumulators trade places (see push_deposit).
+static void swap_acc(ap_pic *h)
+{
+    unsigned long long *t = h->f.acc;
+    h->f.acc = h->f.acc_spare;
+    h->f.acc_spare = t;
+    h->acc_parity ^= 1;
+}
+
 static ap_pic_status push_deposit(ap_pic *h, bool diag)
 {
     if (h->plain) {
@@ -1187,13 +1217,15 @@ static ap_pic_status push_deposit(ap_pic *h, bool diag)
         stage_end(h, mk);
         return convert_rho(h);
     }
-    CU(h, cudaMemsetAsync(h->f.acc, 0, (size_t)h->cells * 8, h->stream));
+    // deposit into the spare accumulator (zero), make it the current one, and convert
+    // it while clearing the previous one: no memset per step
     const GridParams g = grid_params(h, h->cfg.dt);
     const int mk = stage_begin(h, AP_PIC_STAGE_PUSH_DEPOSIT);
-    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc, true, true, true,
+    CU(h, launch_particle_pass(g, h->p, h->f.E, h->f.acc_spare, true, true, true,
                                diag ? h->dpart : DiagPartials{}, h->d_err, h->stream));
     stage_end(h, mk);
-    return convert_rho(h);
+    swap_acc(h);
+    return convert_rho(h, h->f.acc_spare);
 }
 
 extern "C" ap_pic_status ap_pic_push_deposit(ap_pic *h)
@@ -1301,7 +1333,7 @@ static ap_pic_status graph_step(ap_pic *h, bool diag, bool sort)
         CU(h, cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
         CU(h, cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
     }
-    const int key = h->parity * 4 + (diag ? 2 : 0) + (sort ? 1 : 0);
+    const int key = h->acc_parity * 8 + h->parity * 4 + (diag ? 2 : 0) + (sort ? 1 : 0);
     // fence: the graph stream after the caller's work
     CU(h, cudaEventRecord(h->gev_in, h->stream));
     CU(h, cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
@@ -1329,17 +1361,20 @@ static ap_pic_status graph_step(ap_pic *h, bool diag, bool sort)
         cudaGraphDestroy(graph);
         CU(h, ie);
         // the capture recorded the launches without running them; the host state
-        // (a sort's buffer swap) is already that of after the step
+        // (the accumulators' and a sort's buffer swaps) is already that of after the step
         h->graph_launches[key] = ap_pic_kernel_launches() - before;
         note_launch(-(int)h->graph_launches[key]);
         h->graph_slot[key] = h->perm_slot;
-    } else if (sort) {
-        // replay of a step with a sort: the host side of the swap
-        h->parity ^= 1;
-        ParticlesF32 t = h->p;
-        h->p = h->p_alt;
-        h->p_alt = t;
-        h->perm_slot = h->graph_slot[key];
+    } else {
+        // replay: the host side of the swaps
+        swap_acc(h);
+        if (sort) {
+            h->parity ^= 1;
+            ParticlesF32 t = h->p;
+            h->p = h->p_alt;
+            h->p_alt = t;
+            h->perm_slot = h->graph_slot[key];
+        }
     }
     CU(h, cudaGraphLaunch(h->graphs[key], h->gstream));
     note_launch((int)h->graph_launches[key]);

@@ -140,13 +140,17 @@ __device__ __forceinline__ float neg_lap_d(const float *__restrict__ u, int id, 
 
 // ---- charge conversion ----------------------------------------------------------------------
 
+// b from the accumulator, its integer sum, and (clear non-null) the other
+// accumulator zeroed for the next deposit.
 __global__ void __launch_bounds__(FT)
-    k_rho_convert(FieldBufs f, long long mean_q, float mean_r, float scale)
+    k_rho_convert(FieldBufs f, long long mean_q, float mean_r, float scale,
+                  unsigned long long *__restrict__ clear)
 {
     long long isum = 0;
     for (int64_t j = (int64_t)blockIdx.x * FT + threadIdx.x; j < f.cells;
          j += (int64_t)gridDim.x * FT) {
         const long long a = (long long)f.acc[j];
+        if (clear) clear[j] = 0ull;
         isum += a;
         // acc - mean: the integer difference is exact, its float rounds once, then the
         // fraction of the mean and the scale (no cancellation of large terms)
@@ -157,9 +161,9 @@ __global__ void __launch_bounds__(FT)
 }
 
 cudaError_t launch_rho_convert(FieldBufs &f, long long mean_q, float mean_r, float scale,
-                               cudaStream_t st)
+                               unsigned long long *clear, cudaStream_t st)
 {
-    k_rho_convert<<<f.nblocks, FT, 0, st>>>(f, mean_q, mean_r, scale);
+    k_rho_convert<<<f.nblocks, FT, 0, st>>>(f, mean_q, mean_r, scale, clear);
     note_launch();
     return cudaGetLastError();
 }

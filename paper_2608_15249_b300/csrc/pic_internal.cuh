@@ -253,7 +253,10 @@ struct FieldBufs {
     FastDiv div0, div1;        // division by n[0], n[1] (node coordinates)
     int64_t cells;
     double dx[3];
-    unsigned long long *acc;   // int64 fixed point
+    unsigned long long *acc;   // int64 fixed point: the latest deposit
+    unsigned long long *acc_spare;  // the other accumulator, zero between steps (the
+                               // step deposits into it, converts it while clearing the
+                               // previous one, and the two trade places)
     float *b;                  // rho - mean(rho), FP32 (rho itself, in FP64, is formed
                                // from acc where it is read)
     float *phi, *r, *p, *q;    // CG vectors
@@ -282,7 +285,7 @@ int field_blocks(int64_t cells);
 // scale acc + bg in FP64, is formed where it is read (the refinement's residual, the
 // read-back).
 cudaError_t launch_rho_convert(FieldBufs &f, long long mean_q, float mean_r, float scale,
-                               cudaStream_t st);
+                               unsigned long long *clear, cudaStream_t st);
 // The whole Jacobi-PCG solve of A x = b (warm start x) as one cooperative launch,
 // convergence tested on the device: iterations to *iters, final relative residual
 // to scal[relres_slot]; the cap is maxit - *it_used when it_used is given; latch:

@@ -129,6 +129,31 @@ def test_step_graph_replay_equals_direct_launches(pk):
     assert a[4]["step"] == b[4]["step"] == 9 and a[4]["kinetic"] == b[4]["kinetic"]
 
 
+def test_step_graphs_dropped_on_reload(pk):
+    """A second load on a handle drops the step graphs captured under the first (they
+    hold its particle buffers and count): stepping after the reload gives, bit for
+    bit, what a fresh handle with the second load gives without graphs."""
+    w = cases()["2d_mixed"]
+    w2 = plasma.two_stream_2d(n=(64, 48), ppc=11, mode=(1, 1), seed=60)
+    # one configuration for both handles (the particle weight goes with w2's ppc)
+    g = pk.from_workload(w2, solver=pk.AP_PIC_SOLVER_FFT, sort_every=2, diag_every=3)
+    g.load(w.x, w.v)
+    g.step(5)
+    g.load(w2.x, w2.v)
+    g.step(5)
+    f = pk.from_workload(w2, solver=pk.AP_PIC_SOLVER_FFT, sort_every=2, diag_every=3)
+    f.load(w2.x, w2.v)
+    f.set_timing(True)
+    f.step(5)
+    np.testing.assert_array_equal(g.get_rho_fx(), f.get_rho_fx())
+    np.testing.assert_array_equal(g.get_E(), f.get_E())
+    for x, y in zip(g.get_particles(), f.get_particles()):
+        np.testing.assert_array_equal(x, y)
+    assert g.get_diag()["kinetic"] == f.get_diag()["kinetic"]
+    g.close()
+    f.close()
+
+
 @pytest.mark.parametrize("n", [4096, 4095])
 def test_fft_longest_axes(pk, n):
     """The longest axes: 4096 (the largest power-of-two line: four radix-8 passes and a
