@@ -606,10 +606,15 @@ static ap_pic_status create_grid(ap_pic *h)
     TRY(alloc_n(h, &f.r, c));
     TRY(alloc_n(h, &f.p, c));
     TRY(alloc_n(h, &f.p2, c));
+    TRY(alloc_n(h, &f.r2, c));
+    TRY(alloc_n(h, &f.w2, c));
+    TRY(alloc_n(h, &f.s2, c));
     TRY(alloc_n(h, &f.q, c));
     TRY(alloc_n(h, &f.x, c));
     TRY(alloc_n(h, &f.E, c * f.Estride));
     for (int k = 0; k < 3; ++k) TRY(alloc_n(h, &f.part[k], (size_t)f.nblocks));
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 5; ++k) TRY(alloc_n(h, &f.cgpart[j][k], (size_t)f.nblocks));
     TRY(alloc_n(h, &f.ticket, 1));
     CU(h, cudaMemsetAsync(f.ticket, 0, 4, h->stream));
     TRY(alloc_n(h, &f.scal, 8));

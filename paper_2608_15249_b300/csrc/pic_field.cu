@@ -196,17 +196,34 @@ static Lap make_lap(const FieldBufs &f)
 
 // ---- the whole CG solve in one cooperative launch ----------------------------------------------
 //
-// A CG loop of separate launches (direction, matvec, update: three per
-// iteration) needs the host to read a done flag between blocks of launches.
-// k_cg_coop runs Jacobi-PCG (FP32 vectors, FP64 dots, zero-mean projection of r,
-// breakdown guard) as one cooperative launch of one block per SM: blocks meet at
-// a grid barrier, every block re-reduces the block partials in the same fixed
-// order (so all see bit-identical scalars and take the same decisions), and the
-// convergence test never leaves the device.  The direction update is fused into the matvec: each
-// node recomputes p = (r - mean r) / diag + beta p_old at itself and its
-// neighbours from r and the previous direction (p ping-pongs between two
-// buffers), so an iteration takes two grid barriers.
-constexpr int CG_T = 512;                 // threads per block of the cooperative solve
+// A CG loop of separate launches needs the host to read a done flag between blocks
+// of launches.  k_cg_coop runs the Jacobi-PCG (FP32 vectors, FP64 dots, zero-mean
+// projection of r, breakdown guard) as one cooperative launch of one block per SM:
+// blocks meet at a grid barrier, every block re-reduces the block partials in the
+// same fixed order (so all see bit-identical scalars and take the same decisions),
+// and the convergence test never leaves the device.
+//
+// The iteration is the single-reduction (Chronopoulos-Gear) arrangement of the same
+// PCG, so that it takes one grid barrier instead of two.  With z = M^-1 r, w = A z
+// and s = A p carried by recurrences, both dots of an iteration, (r, z) and (w, z),
+// come from one reduction:
+//   p = z + beta p_old;  s = w + beta s_old;  x += alpha p;  r -= alpha s;
+//   z = M^-1 r;  w = A z;  gamma' = (r, z);  delta = (w, z);
+//   beta' = gamma' / gamma;  alpha' = gamma' / (delta - beta' gamma' / alpha),
+// (first step: beta = 0, alpha = gamma / delta); in exact arithmetic it takes the
+// same steps as the two-reduction form.  On this grid the Jacobi preconditioner is
+// the scalar c = 1 / diag, and A annihilates constants, so with r projected onto zero
+// mean (rb = r - mean r): z = c rb, w = c A r, gamma = c ((r, r) - N m^2) and
+// delta = c^2 ((A r, r) - m sum A r) need only the sums (r, r), sum r, (A r, r) and
+// sum A r of the unprojected r.  A node gets the new r at its neighbours, for its
+// w, from their previous r, w and s (kept in ping-pong buffers), so the iteration
+// has no second barrier.
+// Threads per block of the cooperative solve.  Its iteration is bound by the
+// latency of the block and grid reductions, which grow with the block: one block
+// of 256 per SM measured 12.9 ms per 512^2 solve (786 iterations) against 15.0 ms
+// with 128, 17.2 ms with 512 and 29.9 ms with 1024 (two or four blocks per SM were
+// slower still).
+constexpr int CG_T = 256;
 constexpr int GRID_WAIT_LIMIT = 1 << 22;  // polls of a grid barrier before giving up
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
@@ -290,7 +307,6 @@ __device__ __forceinline__ void cg_reduce(double *const (&part)[K], double (&out
 struct CgCoop {
     const float *b;      // right-hand side
     float *x;            // solution, warm start on entry
-    float *pp[2];        // the direction's two buffers
     int maxit;           // iteration cap
     const int *it_used;  // iterations already spent (budget = maxit - *it_used), or null
     int *iters;          // iterations taken (out)
@@ -299,7 +315,7 @@ struct CgCoop {
 };
 
 template <int D>
-__global__ void __launch_bounds__(CG_T)
+__global__ void __launch_bounds__(CG_T, 1)
     k_cg_coop(FieldBufs f, Lap L, CgCoop c, double rtol, unsigned *bar, int *err)
 {
     unsigned gen = 0u;
@@ -309,111 +325,128 @@ __global__ void __launch_bounds__(CG_T)
     // the vectors, unaliased (lets the loads of several nodes be in flight together)
     const float *__restrict__ bv = c.b;
     float *__restrict__ xv = c.x;
-    float *__restrict__ rv = f.r;
-    float *__restrict__ qv = f.q;
+    float *__restrict__ pv = f.p;
+    float *const R[2] = {f.r, f.r2}, *const W[2] = {f.q, f.w2}, *const S[2] = {f.p2, f.s2};
     const double N = (double)f.cells;
+    const float cd = L.inv_diag;  // the Jacobi preconditioner (a scalar here)
     auto bail = [&]() {
         if (threadIdx.x == 0) atomicOr(err, EF_TIMEOUT);
     };
-    // r = b - A x and its sums
+    // r = b - A x, and b.b
+    double bb = 0.0;
     {
-        double v[3] = {0.0, 0.0, 0.0};  // r.r, sum r, b.b
+        float *__restrict__ r0 = R[0];
 #pragma unroll 4
         for (int id = first; id < cells; id += stride) {
             const Nbrs<D> nb = neighbours<D>(id, f);
             const float bi = bv[id];
-            const float ri = bi - neg_lap_d<D>(xv, id, nb, L.idx2);
-            rv[id] = ri;
-            v[0] += (double)ri * ri;
-            v[1] += ri;
-            v[2] += (double)bi * bi;
-        }
-        cg_block_sums<3>(v);
-        if (threadIdx.x == 0) {
-            f.part[0][blockIdx.x] = v[0];
-            f.part[1][blockIdx.x] = v[1];
-            f.part[2][blockIdx.x] = v[2];
+            r0[id] = bi - neg_lap_d<D>(xv, id, nb, L.idx2);
+            bb += (double)bi * bi;
         }
     }
     if (!grid_barrier(bar, gen)) return bail();
-    double m, rr, bn;
+    // w = c A r and the sums (r, r), sum r, (A r, r), sum A r, (b, b)
     {
-        double *const parts[3] = {f.part[0], f.part[1], f.part[2]};
-        double t[3];
-        cg_reduce<3>(parts, t);
-        m = t[1] / N;
-        rr = fmax(t[0] - N * m * m, 0.0);
-        bn = sqrt(t[2]);
-    }
-    double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
-    double rz = rr * (double)L.inv_diag;
-    const int maxit = c.it_used ? max(c.maxit - *c.it_used, 1) : c.maxit;
-    bool done = bn == 0.0 || rel <= rtol || maxit <= 0;
-    double beta = 0.0;
-    int it = 0;
-    while (!done) {
-        // the previous direction and this iteration's (ping-pong, selected rather than
-        // indexed so that the parameter array stays out of local memory)
-        const float *__restrict__ po = (it & 1) ? c.pp[0] : c.pp[1];
-        float *__restrict__ pn = (it & 1) ? c.pp[1] : c.pp[0];
-        const float mf = (float)m, bf = (float)beta;
-        // p = (r - m) / diag + beta p_old at each node and its neighbours; q = A p
-        auto dir = [&](int k) {
-            float v = (rv[k] - mf) * L.inv_diag;
-            if (it > 0) v += bf * po[k];
-            return v;
-        };
-        double pq[1] = {0.0};
+        const float *__restrict__ r0 = R[0];
+        float *__restrict__ w0 = W[0];
+        double v[5] = {0.0, 0.0, 0.0, 0.0, bb};
 #pragma unroll 4
         for (int id = first; id < cells; id += stride) {
             const Nbrs<D> nb = neighbours<D>(id, f);
-            const float pc = dir(id);
-            float acc = 0.0f;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                acc += (2.0f * pc - dir(nb.up[a]) - dir(nb.dn[a])) * L.idx2[a];
-            pn[id] = pc;
-            qv[id] = acc;
-            pq[0] += (double)pc * acc;
-        }
-        cg_block_sums<1>(pq);
-        if (threadIdx.x == 0) f.part[0][blockIdx.x] = pq[0];
-        if (!grid_barrier(bar, gen)) return bail();
-        double pqs[1];
-        {
-            double *const parts[1] = {f.part[0]};
-            cg_reduce<1>(parts, pqs);
-        }
-        const double a64 = rz / pqs[0];
-        if (!(pqs[0] > 0.0) || !isfinite(a64)) break;  // breakdown: keep x as it is
-        const float alpha = (float)a64;
-        double v[2] = {0.0, 0.0};  // r.r, sum r
-#pragma unroll 4
-        for (int id = first; id < cells; id += stride) {
-            xv[id] += alpha * pn[id];
-            const float ri = (rv[id] - mf) - alpha * qv[id];
-            rv[id] = ri;
+            const float ri = r0[id];
+            const float ar = neg_lap_d<D>(r0, id, nb, L.idx2);
+            w0[id] = cd * ar;
             v[0] += (double)ri * ri;
             v[1] += ri;
+            v[2] += (double)ri * ar;
+            v[3] += ar;
         }
-        cg_block_sums<2>(v);
-        if (threadIdx.x == 0) {
-            f.part[1][blockIdx.x] = v[0];
-            f.part[2][blockIdx.x] = v[1];
+        cg_block_sums<5>(v);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) f.cgpart[0][k][blockIdx.x] = v[k];
+    }
+    if (!grid_barrier(bar, gen)) return bail();
+    double m, rr, bn, gamma, delta;
+    {
+        double *const parts[5] = {f.cgpart[0][0], f.cgpart[0][1], f.cgpart[0][2],
+                                  f.cgpart[0][3], f.cgpart[0][4]};
+        double t[5];
+        cg_reduce<5>(parts, t);
+        m = t[1] / N;
+        rr = fmax(t[0] - N * m * m, 0.0);
+        bn = sqrt(t[4]);
+        gamma = (double)cd * rr;
+        delta = (double)cd * cd * (t[2] - m * t[3]);
+    }
+    double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+    const int maxit = c.it_used ? max(c.maxit - *c.it_used, 1) : c.maxit;
+    bool done = bn == 0.0 || rel <= rtol || maxit <= 0;
+    double gamma_old = 0.0, alpha_old = 0.0;
+    int it = 0;
+    while (!done) {
+        const double beta = it == 0 ? 0.0 : gamma / gamma_old;
+        const double den = it == 0 ? delta : delta - beta * gamma / alpha_old;
+        const double a64 = gamma / den;
+        if (!(den > 0.0) || !isfinite(a64)) break;  // breakdown: keep x as it is
+        // this iteration's buffers and the next (selected rather than indexed, so
+        // that the arrays stay out of local memory)
+        const bool odd = (it & 1) != 0;
+        const float *__restrict__ ri = odd ? R[1] : R[0];
+        const float *__restrict__ wi = odd ? W[1] : W[0];
+        const float *__restrict__ so = odd ? S[1] : S[0];  // s of the previous iteration
+        float *__restrict__ rn = odd ? R[0] : R[1];
+        float *__restrict__ wn = odd ? W[0] : W[1];
+        float *__restrict__ sn = odd ? S[0] : S[1];
+        const float mf = (float)m, bf = (float)beta, af = (float)a64;
+        const bool first_it = it == 0;
+        // s and the new r at node k, from the previous r, w and s there
+        auto s_at = [&](int k) { return first_it ? wi[k] : wi[k] + bf * so[k]; };
+        auto r_at = [&](int k) { return (ri[k] - mf) - af * s_at(k); };
+        double v[4] = {0.0, 0.0, 0.0, 0.0};  // (r, r), sum r, (A r, r), sum A r
+#pragma unroll 4
+        for (int id = first; id < cells; id += stride) {
+            const Nbrs<D> nb = neighbours<D>(id, f);
+            const float sc = s_at(id);
+            const float rc = (ri[id] - mf) - af * sc;
+            float pc = cd * (ri[id] - mf);
+            if (!first_it) pc += bf * pv[id];
+            pv[id] = pc;
+            xv[id] += af * pc;
+            sn[id] = sc;
+            rn[id] = rc;
+            float ar = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) ar += (2.0f * rc - r_at(nb.up[a]) - r_at(nb.dn[a])) * L.idx2[a];
+            wn[id] = cd * ar;
+            v[0] += (double)rc * rc;
+            v[1] += rc;
+            v[2] += (double)rc * ar;
+            v[3] += ar;
         }
+        // partials: set 1 in even iterations, set 0 in odd ones (the initial reduction
+        // used set 0), so that no set is written while its last reduction is read
+        double *const parts[4] = {odd ? f.cgpart[0][0] : f.cgpart[1][0],
+                                  odd ? f.cgpart[0][1] : f.cgpart[1][1],
+                                  odd ? f.cgpart[0][2] : f.cgpart[1][2],
+                                  odd ? f.cgpart[0][3] : f.cgpart[1][3]};
+        cg_block_sums<4>(v);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) parts[k][blockIdx.x] = v[k];
         if (!grid_barrier(bar, gen)) return bail();
         {
-            double *const parts[2] = {f.part[1], f.part[2]};
-            double t[2];
-            cg_reduce<2>(parts, t);
+            double t[4];
+            cg_reduce<4>(parts, t);
             m = t[1] / N;
             rr = fmax(t[0] - N * m * m, 0.0);
+            gamma_old = gamma;
+            alpha_old = a64;
+            gamma = (double)cd * rr;
+            delta = (double)cd * cd * (t[2] - m * t[3]);
         }
         rel = sqrt(rr) / bn;
         ++it;
-        const double rz_new = rr * (double)L.inv_diag;
-        beta = rz_new / rz;
-        rz = rz_new;
         done = rel <= rtol || it >= maxit;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -435,9 +468,9 @@ int cg_coop_blocks(int64_t cells)
         }
         per_sm.store(c, std::memory_order_relaxed);
     }
-    // one block per SM (the barrier's cost grows with the blocks; two per SM measured
-    // slower), never more than the co-resident capacity, the reduction partials
-    // (field_blocks) or the work
+    // one block per SM (the barrier's cost grows with the blocks; two or four per SM
+    // measured slower), never more than the co-resident capacity, the reduction
+    // partials (field_blocks) or the work
     const int64_t need = (cells + CG_T - 1) / CG_T;
     int64_t b = (int64_t)sm_count();
     const int64_t cap = (int64_t)sm_count() * c;
@@ -458,8 +491,6 @@ cudaError_t launch_cg_solve(FieldBufs &f, const float *b, float *x, double rtol,
     CgCoop c;
     c.b = b;
     c.x = x;
-    c.pp[0] = f.p;
-    c.pp[1] = f.p2;
     c.maxit = maxit;
     c.it_used = it_used;
     c.iters = iters;

@@ -260,7 +260,9 @@ struct FieldBufs {
     float *b;                  // rho - mean(rho), FP32 (rho itself, in FP64, is formed
                                // from acc where it is read)
     float *phi, *r, *p, *q;    // CG vectors
-    float *p2;                 // second buffer of the direction (cooperative solve)
+    float *p2;                 // the cooperative CG's second buffers: r2 of r, q and w2
+    float *r2, *w2, *s2;       // of w = c A r, p2 and s2 of s = A p (ping-pong, see
+                               // k_cg_coop)
     unsigned *gbar;            // grid barrier of the cooperative solve (count, generation)
     float *x;                  // correction of the refinement step
     float *E;                  // interleaved, Estride floats per node: 1D and 2D the
@@ -268,6 +270,9 @@ struct FieldBufs {
                                // 3D (Ex, Ey, Ez, 0)
     int Estride;
     double *part[3];           // reduction partials (ping-pong + spare), nblocks each
+    double *cgpart[2][5];      // the cooperative CG's partials: two sets, for alternate
+                               // reductions (a block may write the next reduction's
+                               // partials while another still reads this one's)
     int nblocks;
     double *scal;              // device scalars, see pic_field.cu
     int *done;                 // CG done flag

@@ -541,9 +541,10 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
     constexpr int G = tile_group<D, Src>();
     float *stage_base = reinterpret_cast<float *>(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * NA_MAX * TILE * 4);
-    // per-tile charge window (int32 fixed point, kept zero between tiles) and the
-    // tile's box of new cells (min, max of the unwrapped offset from the tile's
-    // reference cell, per axis)
+    // the charge windows (int32 fixed point, kept zero between flushes: in 2D and 3D
+    // one fixed window per tile of a group, in 1D one window sized by the tile's box)
+    // and, in 1D, the tile's box of new cells (min, max of the unwrapped offset from
+    // the tile's reference cell, per axis)
     unsigned *s_win = reinterpret_cast<unsigned *>(bars + STAGES);
     int *s_box = reinterpret_cast<int *>(s_win + win_words<D, Src>());
     // the current and the next tile's parameters (copied by one thread for a batch,
@@ -755,10 +756,11 @@ __global__ void __launch_bounds__(Src::NT, pass_min_blocks<D, Src>())
             }
             if (!finite) bad = true;
         }
-        // phase C: deposit at the (new) positions.  The tile's particles occupy a small
-        // box of cells (they were sorted); when its nodes fit the shared-memory
-        // window, every corner is added there and each touched node goes to the
-        // global accumulator once; otherwise the corners go to global memory.
+        // phase C: deposit at the (new) positions.  The tile's particles occupy a few
+        // cells around its reference cell (they were sorted): corners inside the
+        // shared-memory window are added there, and each touched node goes to the
+        // global accumulator once per flush; other corners go to global memory.  In
+        // 2D and 3D the window is fixed; in 1D it is the box of the tile's cells.
         if (DEPOSIT && FIXED_WIN) {
             // the fixed window: its origin (the node of window index 0) sits half the
             // window below the reference cell, wrapped into the grid; an axis shorter
