@@ -213,16 +213,17 @@ static Lap make_lap(const FieldBufs &f)
 // (first step: beta = 0, alpha = gamma / delta); in exact arithmetic it takes the
 // same steps as the two-reduction form.  On this grid the Jacobi preconditioner is
 // the scalar c = 1 / diag, and A annihilates constants, so with r projected onto zero
-// mean (rb = r - mean r): z = c rb, w = c A r, gamma = c ((r, r) - N m^2) and
+// mean (m = mean r, rb = r - m): z = c rb, w = c A r, gamma = c ((r, r) - N m^2) and
 // delta = c^2 ((A r, r) - m sum A r) need only the sums (r, r), sum r, (A r, r) and
 // sum A r of the unprojected r.  A node gets the new r at its neighbours, for its
 // w, from their previous r, w and s (kept in ping-pong buffers), so the iteration
 // has no second barrier.
+
 // Threads per block of the cooperative solve.  Its iteration is bound by the
 // latency of the block and grid reductions, which grow with the block: one block
 // of 256 per SM measured 12.9 ms per 512^2 solve (786 iterations) against 15.0 ms
 // with 128, 17.2 ms with 512 and 29.9 ms with 1024 (two or four blocks per SM were
-// slower still).
+// slower than one).
 constexpr int CG_T = 256;
 constexpr int GRID_WAIT_LIMIT = 1 << 22;  // polls of a grid barrier before giving up
 
